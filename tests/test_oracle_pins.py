@@ -1,0 +1,271 @@
+"""Pins for the FP64 CPU oracle (no GPU).
+
+Each test checks the oracle against something other than itself: a direct O(N^2)/O(N^4)
+DFT, numpy/LAPACK routines the oracle does not use, the closed forms of Eq. 1 for a
+point source and for the quadratic Gauss sum, the invariants of Eqs. 4-7 (Parseval,
+C = I^T I, trace, PSD, SVD identity of Eqs. 2-3 and 5), and closed-form spectra.
+Where useful, a test also shows that a plausible mistake (wrong DFT sign, wrong
+retained range) would be caught.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from dh_synth import known_rank_frames, speckle_window
+
+LAM, Z, PITCH = 785e-9, 0.35, 20e-6  # the workload's Fresnel parameters
+
+
+def direct_dft1(x, sign):
+    n = len(x)
+    k = np.arange(n)
+    return np.exp(sign * 2j * np.pi * np.outer(k, k) / n) @ x
+
+
+def direct_dft2(x, sign):
+    ny, nx = x.shape
+    ky, kx = np.arange(ny), np.arange(nx)
+    Ey = np.exp(sign * 2j * np.pi * np.outer(ky, ky) / ny)
+    Ex = np.exp(sign * 2j * np.pi * np.outer(kx, kx) / nx)
+    # X[y, x] = sum_{l, k} x[l, k] Ey[y, l] Ex[x, k]  (written as an explicit 4-index sum)
+    return np.einsum("yl,xk,lk->yx", Ey, Ex, x)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+# ----------------------------------------------------------------------------- FFT
+@pytest.mark.parametrize("n", [2, 4, 8, 16, 32])
+@pytest.mark.parametrize("sign", [+1, -1])
+def test_fft1d_matches_direct_dft(n, sign):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    assert rel(oracle.fft1d(x, sign), direct_dft1(x, sign)) < 1e-13
+
+
+@pytest.mark.parametrize("shape", [(16, 16), (4, 8), (8, 4), (2, 16)])
+def test_fft2d_matches_direct_dft(shape):
+    rng = np.random.default_rng(7)
+    xc = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    xr = rng.integers(0, 4096, size=shape).astype(np.float64)
+    for x in (xc, xr):
+        assert rel(oracle.fft2d(x, +1), direct_dft2(x, +1)) < 1e-13
+
+
+def test_fft2d_matches_numpy_ifft2():
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((64, 128)) + 1j * rng.standard_normal((64, 128))
+    # numpy's ifft2 is (1/N) sum x exp(+2 pi i ...): the same kernel as Eq. 1's DFT.
+    assert rel(oracle.fft2d(x, +1), np.fft.ifft2(x) * x.size) < 1e-13
+
+
+def test_fft_sign_mistake_is_caught():
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((16, 16)) + 1j * rng.standard_normal((16, 16))
+    assert rel(oracle.fft2d(x, -1), direct_dft2(x, +1)) > 0.5
+
+
+# --------------------------------------------------------------------- Fresnel, Eq. 1
+def fresnel_convolution_point(nx, ny, k0, l0, lam, z, pitch):
+    """Eq. 1 as written (a convolution) for I = delta at pixel (k0, l0), sampled on the
+    one-FFT output grid X = x lam z / (nx pitch), Y = y lam z / (ny pitch), without the
+    constant prefactor."""
+    x = np.arange(nx)[None, :] * lam * z / (nx * pitch)
+    y = np.arange(ny)[:, None] * lam * z / (ny * pitch)
+    xs = (k0 - nx // 2) * pitch  # centred source coordinates
+    ys = (l0 - ny // 2) * pitch
+    return np.exp(-1j * np.pi / (lam * z) * ((x - xs) ** 2 + (y - ys) ** 2))
+
+
+@pytest.mark.parametrize("nx,ny", [(32, 16), (64, 64)])
+def test_point_sources_match_fresnel_convolution(nx, ny):
+    """Two point sources: the per-pixel ratio of their holograms is independent of the
+    dropped output chirp, so it must equal the ratio of Eq. 1's convolution integrals."""
+    sources = [(3, 5, 1000), (nx - 7, ny // 2 + 1, 250)]
+    frames = np.zeros((2, ny, nx), dtype=np.uint16)
+    for t, (k, l, A) in enumerate(sources):
+        frames[t, l, k] = A
+    H = oracle.render(frames, LAM, Z, PITCH)
+    s = 1.0 / np.sqrt(nx * ny)
+    for t, (k, l, A) in enumerate(sources):
+        assert np.allclose(np.abs(H[t]), s * A, rtol=1e-12, atol=0)
+    ratio = H[0] / H[1]
+    (k0, l0, A0), (k1, l1, A1) = sources
+    expect = (A0 / A1) * fresnel_convolution_point(nx, ny, k0, l0, LAM, Z, PITCH) / \
+        fresnel_convolution_point(nx, ny, k1, l1, LAM, Z, PITCH)
+    assert rel(ratio, expect) < 1e-10
+
+
+def test_uniform_frame_quadratic_gauss_sum():
+    """a = pitch^2/(lambda z) = 1/N makes each 1-D sum a quadratic Gauss sum of modulus
+    sqrt(N): a uniform frame of value A gives |H| = s A N = A at every pixel."""
+    N, A = 64, 1234
+    z = PITCH ** 2 * N / LAM
+    frames = np.full((1, N, N), A, dtype=np.uint16)
+    H = oracle.render(frames, LAM, z, PITCH)
+    assert np.allclose(np.abs(H[0]), A, rtol=1e-11)
+    # a slightly different z breaks it (the pin sees the chirp coefficient)
+    H2 = oracle.render(frames, LAM, z * 1.01, PITCH)
+    assert np.max(np.abs(np.abs(H2[0]) - A)) > 1.0
+
+
+def test_parseval_per_frame():
+    f = speckle_window(32, 16, 4, seed=11).numpy()
+    H = oracle.render(f, LAM, Z, PITCH)
+    for t in range(4):
+        e_raw = np.sum(f[t].astype(np.float64) ** 2)
+        assert abs(np.sum(np.abs(H[t]) ** 2) - e_raw) <= 1e-12 * e_raw
+
+
+# ------------------------------------------------------------------ covariance, Eq. 4
+def test_covariance_equals_integer_gram_of_raw_frames():
+    """Unitary chirp + unitary DFT preserve inner products per frame, so C = I^T I
+    exactly; I^T I is computed here in int64 from the raw uint16 frames."""
+    f = speckle_window(64, 32, 16, seed=2).numpy()
+    H = oracle.render(f, LAM, Z, PITCH)
+    C = oracle.covariance(H)
+    I = f.reshape(16, -1).astype(np.int64)
+    G = (I @ I.T).astype(np.float64)
+    assert rel(C.real, G) < 1e-13
+    assert np.max(np.abs(C.imag)) < 1e-13 * np.max(np.abs(G))
+
+
+def test_covariance_hermitian_psd_trace():
+    rng = np.random.default_rng(1)
+    H = rng.standard_normal((8, 300)) + 1j * rng.standard_normal((8, 300))
+    C = oracle.covariance(H)
+    assert rel(C, C.conj().T) < 1e-15
+    assert np.min(np.linalg.eigvalsh(C)) > -1e-12 * np.trace(C).real
+    assert abs(np.trace(C).real - np.sum(np.abs(H) ** 2)) < 1e-12 * np.sum(np.abs(H) ** 2)
+    # against numpy's matmul (BLAS), which the oracle does not use
+    assert rel(C, H.conj() @ H.T) < 1e-13
+
+
+# ----------------------------------------------------------------- eigen, Eq. 5
+@pytest.mark.parametrize("T", [4, 16, 32, 64])
+def test_eig_residual_orthonormal_and_lapack(T):
+    rng = np.random.default_rng(T)
+    X = rng.standard_normal((T, 3 * T)) + 1j * rng.standard_normal((T, 3 * T))
+    C = X @ X.conj().T
+    lam, V, sweeps = oracle.eig(C)
+    nC = np.linalg.norm(C, 2)
+    assert np.all(np.diff(lam) <= 0)
+    assert np.linalg.norm(C @ V - V * lam[None, :]) <= 1e-12 * nC
+    assert np.linalg.norm(V.conj().T @ V - np.eye(T)) <= 1e-13 * T
+    assert abs(np.sum(lam) - np.trace(C).real) <= 1e-12 * nC * T
+    ref = np.linalg.eigvalsh(C)[::-1]  # LAPACK heevd-type solver
+    assert np.max(np.abs(lam - ref)) <= 1e-12 * nC
+    assert sweeps <= 20
+
+
+def test_eigenvalues_are_squared_singular_values():
+    """Eq. 5 with Eq. 2: Lambda = Delta^2 for C = H^{t*} H."""
+    f = speckle_window(32, 32, 8, seed=4).numpy()
+    H = oracle.render(f, LAM, Z, PITCH).reshape(8, -1).T  # (n_x n_y, n_t)
+    lam, _, _ = oracle.eig(oracle.covariance(H.T))
+    sv = np.linalg.svd(H, compute_uv=False)
+    assert np.max(np.abs(lam - sv ** 2)) <= 1e-12 * lam[0]
+
+
+@pytest.mark.parametrize("T", [16, 32, 64])
+def test_known_rank_spectrum(T):
+    comps = [(1, 40, 300), (3, 25, 700), (T - 1, 10, 1500), (T // 2, 60, 90)]
+    f, lam_exact = known_rank_frames(64, 64, T, 2000, comps, support_seed=T)
+    H = oracle.render(f, LAM, Z, PITCH)
+    lam, V, _ = oracle.eig(oracle.covariance(H))
+    assert np.max(np.abs(lam - lam_exact)) <= 1e-11 * lam_exact[0]
+
+
+def test_degenerate_and_diagonal_inputs():
+    C = np.diag([5.0, 5.0, 1.0, 0.0]).astype(np.complex128)
+    lam, V, sweeps = oracle.eig(C)
+    assert np.allclose(lam, [5, 5, 1, 0]) and sweeps == 0
+    assert np.allclose(np.abs(V), np.eye(4))
+
+
+# -------------------------------------------------------------- projection, Eqs. 6-7
+def _window(nx=32, ny=32, T=16, seed=9):
+    f = speckle_window(nx, ny, T, seed=seed).numpy()
+    return f, oracle.render(f, LAM, Z, PITCH)
+
+
+def test_projection_parseval_full_range():
+    f, H = _window()
+    lam, V, _ = oracle.eig(oracle.covariance(H))
+    M = oracle.project_power(H, V, 0, H.shape[0] - 1)
+    assert rel(M, np.sum(np.abs(H) ** 2, axis=0)) < 1e-12
+
+
+@pytest.mark.parametrize("k0,k1", [(2, 15), (0, 0), (5, 9), (15, 15)])
+def test_projection_matches_svd_filter(k0, k1):
+    """Eq. 3: H_f = U Delta I_f V^{t*}; sum_t |H_f|^2 equals M of Eqs. 6-7."""
+    f, H = _window()
+    T = H.shape[0]
+    lam, V, _ = oracle.eig(oracle.covariance(H))
+    M = oracle.project_power(H, V, k0, k1)
+    Hs = H.reshape(T, -1).T
+    U, sv, Vh = np.linalg.svd(Hs, full_matrices=False)  # decreasing singular values
+    Hf = (U[:, k0:k1 + 1] * sv[k0:k1 + 1]) @ Vh[k0:k1 + 1, :]
+    Mf = np.sum(np.abs(Hf) ** 2, axis=1).reshape(M.shape)
+    assert rel(M, Mf) < 1e-10
+    # an off-by-one retained range is a different image
+    if k1 + 1 < T:
+        assert rel(oracle.project_power(H, V, k0, k1 + 1), Mf) > 1e-3
+
+
+def test_projection_diagonal_covariance():
+    """Frames on disjoint pixel supports have a diagonal C: the components are the
+    frames themselves (ordered by energy), so M is a sum of per-frame powers."""
+    T, n = 8, 32
+    f = np.zeros((T, n, n), dtype=np.uint16)
+    rng = np.random.default_rng(0)
+    perm = rng.permutation(n * n)
+    energy = []
+    for t in range(T):
+        pix = perm[t * 40:(t + 1) * 40]
+        vals = rng.integers(100, 4000, size=40) * (t + 1) // T + 1
+        f[t].flat[pix] = vals
+        energy.append(np.sum(vals.astype(np.float64) ** 2))
+    H = oracle.render(f, LAM, Z, PITCH)
+    lam, V, _ = oracle.eig(oracle.covariance(H))
+    order = np.argsort(-np.array(energy), kind="stable")
+    assert np.allclose(lam, np.array(energy)[order], rtol=1e-12)
+    k0, k1 = 2, 6
+    expect = np.sum(np.abs(H[order[k0:k1 + 1]]) ** 2, axis=0)
+    assert rel(oracle.project_power(H, V, k0, k1), expect) < 1e-10
+
+
+# ------------------------------------------------------------ whole window, numpy pipeline
+def numpy_pipeline(frames, lam_m, z_m, pitch_m, k0, k1):
+    """The same equations computed with numpy's FFT and LAPACK eigensolver."""
+    T, ny, nx = frames.shape
+    a = pitch_m ** 2 / (lam_m * z_m)
+    kx, ky = np.arange(nx) - nx // 2, np.arange(ny) - ny // 2
+    chirp2 = np.exp(-1j * np.pi * a * (ky[:, None] ** 2 + kx[None, :] ** 2))
+    H = np.fft.ifft2(frames * chirp2, norm="ortho")
+    Hs = H.reshape(T, -1).T
+    C = Hs.conj().T @ Hs
+    w, V = np.linalg.eigh(C)
+    order = np.argsort(-w, kind="stable")
+    w, V = w[order], V[:, order]
+    P = Hs @ V[:, k0:k1 + 1]
+    return np.sum(np.abs(P) ** 2, axis=1).reshape(ny, nx), w, C
+
+
+@pytest.mark.parametrize("nx,ny,T", [(32, 16, 8), (64, 64, 16), (16, 16, 4)])
+def test_pca_window_matches_numpy_pipeline(nx, ny, T):
+    f = speckle_window(nx, ny, T, seed=nx + T).numpy()
+    k0, k1 = 2, T - 1
+    M, lam, C, _ = oracle.pca_window(f, LAM, Z, PITCH, k0, k1)
+    Mn, wn, Cn = numpy_pipeline(f.astype(np.float64), LAM, Z, PITCH, k0, k1)
+    assert rel(C, Cn) < 1e-12
+    assert np.max(np.abs(lam - wn)) < 1e-12 * wn[0]
+    assert rel(M, Mn) < 1e-9
+
+
+def test_pca_window_rejects_bad_range():
+    f = speckle_window(16, 16, 4, seed=1).numpy()
+    with pytest.raises(RuntimeError):
+        oracle.pca_window(f, LAM, Z, PITCH, 3, 4)
