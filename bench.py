@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Benchmark of the retinal-holography PCA path (Puyo et al., arXiv 2004.00923).
+
+One step = the whole hot path (Fresnel rendering, covariance, eigendecomposition,
+projection + power image) over one batch: 2048 synthetic 1024x1024 uint16 frames cut into
+64 non-overlapping 32-frame windows, holograms stored FP16, k0..k1 = 2..31.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line on rank 0. Under torchrun each rank processes its own 64 windows
+(weak scaling, no collective on the data path); the step time is the max over ranks.
+`--impl reference` times the FP64 CPU oracle (the reference arm of this workload) on the
+host cores, one window per step.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCA windows/s @1024²×32 vs plain FP32, ≤1e-3 rel err; %HBM roofline; p99 ms"
+UNIT = "windows/s"
+NX = NY = 1024
+T = 32
+NWIN = 64
+K0, K1 = 2, 31
+LAM, Z, PITCH = 785e-9, 0.35, 20e-6
+PAPER_WINDOWS_PER_S = 20.0  # the paper's PCA rate at 1024^2 x 32 (Titan RTX)
+WORKLOAD = "1024x1024 uint16 frames, 64 non-overlapping 32-frame windows per step, FP16 holograms"
+
+
+# --------------------------------------------------------------------------- helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(ws):
+    if ws > 1 and not torch.distributed.is_initialized():
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        torch.distributed.init_process_group(backend=backend)
+
+
+def barrier(ws):
+    if ws > 1:
+        torch.distributed.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    """Largest value of x over all ranks (the slowest rank sets the step time)."""
+    if ws == 1:
+        return x
+    dev = "cuda" if torch.cuda.is_available() and torch.distributed.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, ws: int, ms_per_step_max: float) -> float:
+    """Units all ranks processed per second, over the slowest rank's step time."""
+    return units_per_rank * ws / (ms_per_step_max / 1e3)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="dh_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    return 6400.0, 1800.0, "fallback"
+
+
+def traffic_record(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the
+    summary is absent or the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["sha256"]:
+        return None
+    return float(rec["bytes_per_launch"])
+
+
+# Algorithmic DRAM bytes of one step, per kernel (minimum traffic of the store-H schedule:
+# the row-pass intermediate stays in L2 by construction and is not counted).
+def algorithmic_bytes(npix, frames, windows, T, hbytes):
+    return {
+        "render_rows": frames * npix * 2,                    # uint16 frames in
+        "render_cols": frames * npix * 2 * hbytes,           # Re/Im planes out
+        "gram_tc": windows * T * npix * 2 * hbytes,          # H read once per window
+        "gram_simt": windows * T * npix * 2 * hbytes,
+        "project_tc": windows * (T * npix * 2 * hbytes + npix * 4),  # H read + image out
+        "project_simt": windows * (T * npix * 2 * hbytes + npix * 4),
+    }
+
+
+# --------------------------------------------------------------------------- arms
+def run_reference(args, ws, rank):
+    """The FP64 CPU oracle, as it stands, on the host cores: one 1024^2 x 32 window/step."""
+    if rank != 0:
+        return 0
+    import oracle
+    from dh_synth import SpeckleParams, SpeckleStream
+    frames = SpeckleStream(SpeckleParams(NX, NY), seed=1000, device="cpu").next(T).numpy()
+    for _ in range(args.warmup):
+        oracle.pca_window(frames, LAM, Z, PITCH, K0, K1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.pca_window(frames, LAM, Z, PITCH, K0, K1)
+        times.append(time.perf_counter() - t0)
+    sec = sum(times) / len(times)
+    value = 1.0 / sec
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_WINDOWS_PER_S,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " (one window of it per step)", "nx": NX, "ny": NY,
+                   "T": T, "k0": K0, "k1": K1},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "1 window of 1024x1024x32 per step (FP64 C oracle, OpenMP)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, ws, rank, local):
+    import paper_2004_00923_b300 as dh
+    from dh_synth import SpeckleParams, SpeckleStream
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    nframes = NWIN * T
+    # config-1 stream: seed 1000 * config + rank, 2048 frames resident in HBM (4 GiB > L2)
+    frames = SpeckleStream(SpeckleParams(NX, NY), seed=1000 + rank, device=dev).next(nframes)
+    npix = NX * NY
+
+    plan = dh.Plan(NX, NY, LAM, Z, PITCH, T=T, precision=args.precision, max_frames=nframes,
+                   max_windows=NWIN)
+    images = torch.empty((NWIN, NY, NX), dtype=torch.float32, device=dev)
+    eig = torch.empty((NWIN, T), dtype=torch.float64, device=dev)
+
+    def step(p):
+        p.pca_batch(frames, NWIN, T, K0, K1, images, eig)
+
+    for _ in range(max(args.warmup, 0)):
+        step(plan)
+    torch.cuda.synchronize()
+
+    # ---------------------------------------------------------------- timed region
+    clocks = ClockSampler(local)
+    plan.profile(True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for k in range(args.steps):
+        step(plan)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clock_info = clocks.stop()
+    prof = plan.profile_read()
+    plan.profile(False)
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    ms = ev[0].elapsed_time(ev[-1]) / args.steps
+    ms_max = max_over_ranks(ms, ws)
+    value = whole_job_rate(NWIN, ws, ms_max)
+    flags = plan.status()
+
+    # ---------------------------------------------------------------- roofline
+    hbm, bf16_peak, peak_kind = measured_peaks()
+    hbytes = 2 if args.precision in ("fp16", "bf16") else 4
+    alg = algorithmic_bytes(npix, nframes, NWIN, T, hbytes)
+    per_kernel = {}
+    launches_total = 0
+    for name, (n, tot) in prof.items():
+        if n:
+            launches_total += n
+            per_kernel[name] = {"launches": n, "ms_total": tot, "share": 0.0}
+    tot_ms = sum(v["ms_total"] for v in per_kernel.values()) or 1.0
+    for v in per_kernel.values():
+        v["share"] = v["ms_total"] / tot_ms
+    dom = max((k for k in per_kernel if k in alg), key=lambda k: per_kernel[k]["ms_total"])
+    d = per_kernel[dom]
+    steps = args.steps
+    bytes_per_launch = alg[dom] * steps / d["launches"]
+    avg_launch_s = d["ms_total"] / d["launches"] / 1e3
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    traffic = traffic_record(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic,
+                "peak_kind": f"{peak_kind} copy bandwidth",
+                "step_hbm_frac": sum(alg[k] for k in per_kernel if k in alg) / (ms / 1e3) / 1e9 / hbm,
+                "kernels": per_kernel}
+
+    # ---------------------------------------------------------------- end to end (host buffers)
+    e2e = None
+    if not args.no_e2e:
+        host_frames = torch.empty(frames.shape, dtype=torch.uint16, pin_memory=True)
+        host_frames.copy_(frames)
+        host_images = torch.empty(images.shape, dtype=torch.float32, pin_memory=True)
+        host_eig = torch.empty(eig.shape, dtype=torch.float64, pin_memory=True)
+        dev_frames = torch.empty_like(frames)
+
+        def e2e_step():
+            dev_frames.copy_(host_frames, non_blocking=True)
+            plan.pca_batch(dev_frames, NWIN, T, K0, K1, images, eig)
+            host_images.copy_(images, non_blocking=True)
+            host_eig.copy_(eig, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        n_e2e = max(2, min(args.steps, 5))
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / n_e2e, ws)
+        e2e = {"value": whole_job_rate(NWIN, ws, e_ms), "unit": UNIT,
+               "h2d_bytes_per_step": int(host_frames.numel() * 2),
+               "d2h_bytes_per_step": int(host_images.numel() * 4 + host_eig.numel() * 8),
+               "ms_per_step": e_ms}
+        del host_frames, dev_frames
+
+    # ---------------------------------------------------------------- plain FP32 GPU path
+    plain = None
+    if not args.no_plain and args.precision != "fp32":
+        p32 = dh.Plan(NX, NY, LAM, Z, PITCH, T=T, precision="fp32", max_frames=nframes,
+                      max_windows=NWIN)
+        step(p32)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n32 = max(2, min(args.steps, 5))
+        a.record(stream)
+        for _ in range(n32):
+            step(p32)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms32 = max_over_ranks(a.elapsed_time(b) / n32, ws)
+        plain = {"value": whole_job_rate(NWIN, ws, ms32), "unit": UNIT, "ms_per_step": ms32}
+        p32.close()
+        step(plan)  # the headline plan's images again for the parity sample below
+        torch.cuda.synchronize()
+
+    # ---------------------------------------------------------------- oracle sample (rank 0)
+    cpu_baseline, parity = None, None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        f0 = frames[:T].cpu().numpy()
+        t0 = time.perf_counter()
+        M, lam_ref, _, _ = oracle.pca_window(f0, LAM, Z, PITCH, K0, K1)
+        sec = time.perf_counter() - t0
+        cpu_baseline = {"value": 1.0 / sec, "unit": UNIT, "cores": oracle.num_threads(),
+                        "kind": "oracle",
+                        "sample": "window 0 of the step (1024x1024x32), FP64 C oracle, OpenMP"}
+        img0 = images[0].double().cpu().numpy()
+        lam0 = eig[0].cpu().numpy()
+        parity = {"window": 0,
+                  "image_rel_l2": float(np.linalg.norm(img0 - M) / np.linalg.norm(M)),
+                  "eig_normwise": float(np.max(np.abs(lam0 - lam_ref)) / lam_ref[0]),
+                  "tolerance_image": 1e-3 if args.precision != "fp32" else 1e-4,
+                  "tolerance_eig": 1e-5}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": value / PAPER_WINDOWS_PER_S,
+            "dtype": "mixed: f32 FFT, f16 tensor-core products (f32 accumulate), f64 eig",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "T": T,
+                       "windows_per_step": NWIN, "frames_per_step": nframes, "k0": K0, "k1": K1,
+                       "precision": args.precision,
+                       "l2": "no flush: 4 GiB of input frames per step exceed the 126 MB L2",
+                       "parallelism": f"replicas x{ws}"},
+            "frames_per_s": value * T,
+            "step_ms": {"p50": statistics.median(step_ms), "max": max(step_ms)},
+            "roofline": roofline,
+            "cpu_baseline": cpu_baseline,
+            "e2e": e2e,
+            "plain_fp32": plain,
+            "speedup_vs_plain_fp32": (value / plain["value"]) if plain else None,
+            "parity": parity,
+            "gpu_launches": launches_total,
+            "device_flags": flags,
+            "clocks": clock_info,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp16", "bf16", "fp32"], default="fp16")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    dist_init(ws)
+    try:
+        return run_ours(args, ws, rank, local)
+    finally:
+        if ws > 1 and torch.distributed.is_initialized():
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

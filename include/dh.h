@@ -1,0 +1,167 @@
+/*
+ * dh.h -- C ABI of libdh: real-time digital holography of the retina by principal
+ * component analysis (Puyo et al., arXiv 2004.00923) on one NVIDIA B300 (sm_103a).
+ *
+ * The library computes, for windows of n_t consecutive 16-bit interferograms
+ * I(x, y, t) of n_x x n_y pixels:
+ *   1. Fresnel holograms H(x, y, t) of every frame (Eq. 1, one 2-D FFT per frame),
+ *   2. the covariance C = H^{t*} H of each window (Eq. 4),
+ *   3. its eigendecomposition C = V Lambda V^{t*} (Eq. 5),
+ *   4. the power image M(x, y) = sum_{k=k0..k1} |(H V)(x, y, k)|^2 (Eqs. 6-7).
+ *
+ * Conventions shared by every entry point:
+ *  - Discrete form of Eq. 1 used here: with a = pitch^2 / (lambda z) and centred input
+ *    coordinates, H[t,y,x] = s sum_{k,l} I[t,l,k] c(k) c(l) exp(+2 pi i (xk/n_x + yl/n_y)),
+ *    c(k) = exp(-i pi a (k - n/2)^2), s = 1/sqrt(n_x n_y). The output chirp and the
+ *    constant prefactor of Eq. 1 have unit modulus per pixel; they cancel in C and in
+ *    |H V|^2 and are not applied. Output pixels are in natural FFT order.
+ *  - Eigenvalues are ordered DEcreasing and components are numbered from 0; (k0, k1)
+ *    is the inclusive retained range in that order (the paper orders increasingly
+ *    from 1: its index j is component k = n_t - j here).
+ *  - Device pointers are CUDA device addresses owned by the caller; the library never
+ *    frees them. Host pointers are plain host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Every call is asynchronous on that stream unless its comment says otherwise.
+ *  - Errors are returned as dh_status; nothing is thrown across the ABI. After
+ *    DH_ERR_CUDA, dh_last_error() gives the CUDA error text.
+ *  - A plan is not re-entrant: calls on one plan from two host threads at once return
+ *    DH_ERR_STATE.
+ */
+#ifndef DH_H_
+#define DH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dh_plan *dh_plan_t; /* opaque, library-owned */
+
+typedef enum {
+  DH_OK = 0,
+  DH_ERR_INVALID_ARG = 1,
+  DH_ERR_UNSUPPORTED_SIZE = 2,
+  DH_ERR_OOM = 3,
+  DH_ERR_CUDA = 4,
+  DH_ERR_TIMEOUT = 5,
+  DH_ERR_FRAME_GAP = 6,
+  DH_ERR_STATE = 7
+} dh_status;
+
+/* Storage type of the holograms H (paper: single-precision cuComplex, "plain" here).
+ * DH_PREC_FP32: H stored FP32; covariance and projection on FP32 CUDA cores.
+ * DH_PREC_FP16 / DH_PREC_BF16: H stored as 16-bit real/imaginary planes; covariance and
+ * projection run on the tensor cores (tcgen05, FP32 accumulation), with the eigenvector
+ * operand split into hi + lo 16-bit parts. */
+typedef enum { DH_PREC_FP32 = 0, DH_PREC_FP16 = 1, DH_PREC_BF16 = 2 } dh_precision;
+
+/* Device status bits returned by dh_plan_status(). */
+#define DH_FLAG_STORE_OVERFLOW 0x1u  /* a hologram value was not finite after 16-bit storage */
+#define DH_FLAG_NONFINITE_C 0x2u     /* the covariance held a NaN/Inf */
+#define DH_FLAG_EIG_NOT_CONVERGED 0x4u
+#define DH_FLAG_WAIT_TIMEOUT 0x8u    /* a bounded device-side wait gave up (kernel skipped work) */
+
+/* Create a plan for n_x x n_y frames (powers of two in [16, 4096]) and windows of
+ * T frames (T in {16, 32, 64}); lambda_m, z_m, pitch_m > 0 are the wavelength, the
+ * sensor-to-object distance and the pixel pitch of Eq. 1, in metres. Builds the chirp
+ * and twiddle tables in FP64 on the host and allocates the device buffers for one
+ * window of FP32 holograms on the current CUDA device. Synchronous.
+ * Errors: DH_ERR_INVALID_ARG (NULL out, non-positive/non-finite optics),
+ * DH_ERR_UNSUPPORTED_SIZE (n_x, n_y or T), DH_ERR_OOM, DH_ERR_CUDA. */
+dh_status dh_plan_create(dh_plan_t *out, int nx, int ny, double lambda_m, double z_m,
+                         double pitch_m, int T);
+
+/* Release every device buffer of the plan. NULL-safe. Synchronises the device. */
+void dh_destroy(dh_plan_t plan);
+
+/* Select the hologram storage type (default DH_PREC_FP32). Reallocates the hologram
+ * store; previously rendered holograms are discarded. Synchronous. */
+dh_status dh_plan_set_precision(dh_plan_t plan, dh_precision prec);
+
+/* Reserve device storage for up to max_frames rendered frames (hologram "slots") and
+ * up to max_windows windows per dh_pca_windows call. Default: T slots, 1 window.
+ * Synchronous; previously rendered holograms are discarded when the store grows. */
+dh_status dh_plan_reserve(dh_plan_t plan, int max_frames, int max_windows);
+
+/* Bytes of device memory the plan holds now (all buffers). */
+size_t dh_plan_device_bytes(dh_plan_t plan);
+
+/* Eq. 1 for n_frames frames: frame i (uint16, row-major n_y x n_x, caller-owned device
+ * memory at frames_dev + i * frame_stride_elems) is rendered into hologram slot
+ * first_slot + i. Requires frame_stride_elems >= n_x n_y and the slots within the
+ * reservation. Asynchronous. */
+dh_status dh_render_frames(dh_plan_t plan, const uint16_t *frames_dev,
+                           int64_t frame_stride_elems, int n_frames, int first_slot,
+                           void *stream);
+
+/* Eqs. 4-7 for n_windows windows; window w covers slots
+ * [first_slot + w * slot_stride, ... + T). Writes image w (FP32, n_y x n_x row-major) to
+ * images_dev + w * n_x n_y, and, if eigvals_dev is not NULL, the T eigenvalues of window
+ * w (FP64, decreasing) to eigvals_dev + w * T. 0 <= k0 <= k1 < T. Overlapping windows
+ * (slot_stride < T) share the rendered holograms. Asynchronous. */
+dh_status dh_pca_windows(dh_plan_t plan, int first_slot, int slot_stride, int n_windows,
+                         int k0, int k1, float *images_dev, double *eigvals_dev,
+                         void *stream);
+
+/* The single-window calls of the paper's statement of the problem: render T frames
+ * (frames_dev + t * frame_stride_elems, t < T) into slots [0, T). Asynchronous. */
+dh_status dh_render_stack(dh_plan_t plan, const uint16_t *frames_dev,
+                          int64_t frame_stride_elems, void *stream);
+
+/* PCA of the window held in slots [0, T): image to image_dev (n_y x n_x FP32). If
+ * eigvals_host is not NULL the call synchronises `stream` and copies the T eigenvalues
+ * (FP64, decreasing) to it. */
+dh_status dh_pca_window(dh_plan_t plan, int k0, int k1, float *image_dev,
+                        double *eigvals_host, void *stream);
+
+/* Render then demodulate n_windows windows whose first frames are
+ * window_stride_frames apart: frames are rendered once into slots
+ * [0, (n_windows - 1) * window_stride_frames + T) and window w uses slots
+ * [w * window_stride_frames, + T). Asynchronous. */
+dh_status dh_pca_batch(dh_plan_t plan, const uint16_t *frames_dev,
+                       int64_t frame_stride_elems, int n_windows,
+                       int window_stride_frames, int k0, int k1, float *images_dev,
+                       double *eigvals_dev, void *stream);
+
+/* Inspection (tests): copy hologram slot `slot` as interleaved FP32 (re, im) pairs,
+ * n_x n_y of them, to out_dev. Asynchronous. */
+dh_status dh_debug_hologram(dh_plan_t plan, int slot, float *out_dev, void *stream);
+
+/* Inspection (tests): after dh_pca_windows, copy window w's covariance C (Eq. 4) as
+ * T x T interleaved FP64 (re, im), row-major, to out_dev. Asynchronous. */
+dh_status dh_debug_covariance(dh_plan_t plan, int w, double *out_dev, void *stream);
+
+/* Inspection (tests): after dh_pca_windows, copy window w's eigenvectors V (Eq. 5,
+ * columns in decreasing-eigenvalue order) as T x T interleaved FP64 (re, im), V[t][k]
+ * row-major, to out_dev. Asynchronous. */
+dh_status dh_debug_eigvecs(dh_plan_t plan, int w, double *out_dev, void *stream);
+
+/* Synchronise the device, return the plan's accumulated DH_FLAG_* bits in *flags and
+ * clear them. */
+dh_status dh_plan_status(dh_plan_t plan, uint32_t *flags);
+
+/* Tracing: with on != 0, every kernel the plan launches from now on is bracketed by two
+ * CUDA events on its stream (a few microseconds of overhead per launch); on == 0 stops
+ * and discards the records. The paper has no tracing facility; this one exists to
+ * attribute device time to the stages of Eqs. 1, 4, 5, 6-7. */
+dh_status dh_profile_enable(dh_plan_t plan, int on);
+
+/* Synchronise on the recorded events and report, for each of the library's kernels
+ * (index k < n), its name (static string), the number of launches and the summed device
+ * milliseconds since the last read; the records are then cleared. Any output array may be
+ * NULL. Returns the number of kernel kinds the library has (write at most n entries). */
+int dh_profile_read(dh_plan_t plan, int n, const char **names, int *launches, double *total_ms);
+
+/* Text of a status code, and of the last CUDA error recorded by the library. */
+const char *dh_status_string(dh_status s);
+const char *dh_last_error(void);
+
+/* Library version string. */
+const char *dh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DH_H_ */

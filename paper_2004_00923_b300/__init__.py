@@ -1,0 +1,177 @@
+"""Real-time digital holography of the retina by PCA on one B300 (sm_103a).
+
+Python binding of libdh (include/dh.h): every method marshals tensors and the current
+CUDA stream into one C-ABI call; all computation runs in the library's CUDA kernels.
+
+    plan = Plan(1024, 1024, 785e-9, 0.35, 20e-6, T=32, precision="fp16",
+                max_frames=2048, max_windows=64)
+    images, lam = plan.pca_batch(frames, n_windows=64, window_stride=32, k0=2, k1=31)
+
+Paper: Puyo et al., "Real-time digital holography of the retina by principal component
+analysis", arXiv 2004.00923 (Eqs. 1, 4, 5, 6, 7).
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import DHError, PREC  # noqa: F401
+
+__all__ = ["Plan", "DHError", "PREC", "version"]
+
+
+def version() -> str:
+    return _lib.load().dh_version().decode()
+
+
+def _stream_ptr(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return int(t.data_ptr())
+
+
+class Plan:
+    """A device-resident plan: chirp/twiddle tables, hologram store and workspaces."""
+
+    def __init__(self, nx: int, ny: int, lambda_m: float, z_m: float, pitch_m: float, T: int,
+                 precision: str = "fp32", max_frames: int | None = None, max_windows: int = 1):
+        self._lib = _lib.load()
+        self.nx, self.ny, self.T = int(nx), int(ny), int(T)
+        self.precision = precision
+        h = ctypes.c_void_p()
+        _lib.check("dh_plan_create", self._lib.dh_plan_create(
+            ctypes.byref(h), self.nx, self.ny, float(lambda_m), float(z_m), float(pitch_m), self.T))
+        self._h = h
+        if precision != "fp32":
+            _lib.check("dh_plan_set_precision", self._lib.dh_plan_set_precision(h, PREC[precision]))
+        self.max_frames = max(int(max_frames or T), self.T)
+        self.max_windows = int(max_windows)
+        if self.max_frames != self.T or self.max_windows != 1:
+            _lib.check("dh_plan_reserve",
+                       self._lib.dh_plan_reserve(h, self.max_frames, self.max_windows))
+
+    # -- lifetime -------------------------------------------------------------
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.dh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def device_bytes(self) -> int:
+        return int(self._lib.dh_plan_device_bytes(self._h))
+
+    # -- checks ---------------------------------------------------------------
+    def _frames(self, frames: torch.Tensor) -> torch.Tensor:
+        if frames.dtype != torch.uint16 or not frames.is_cuda:
+            raise TypeError("frames must be a CUDA uint16 tensor [F, ny, nx]")
+        if frames.dim() != 3 or frames.shape[1:] != (self.ny, self.nx) or not frames.is_contiguous():
+            raise ValueError(f"frames must be contiguous [F, {self.ny}, {self.nx}]")
+        return frames
+
+    # -- the C ABI ------------------------------------------------------------
+    def render_frames(self, frames: torch.Tensor, first_slot: int = 0, stream=None) -> None:
+        """Eq. 1 for every frame of `frames` into slots first_slot, first_slot+1, ..."""
+        f = self._frames(frames)
+        _lib.check("dh_render_frames", self._lib.dh_render_frames(
+            self._h, _ptr(f), self.nx * self.ny, f.shape[0], int(first_slot), _stream_ptr(stream)))
+
+    def pca_windows(self, first_slot: int, slot_stride: int, n_windows: int, k0: int, k1: int,
+                    images: torch.Tensor | None = None, eigvals: torch.Tensor | None = None,
+                    want_eigvals: bool = True, stream=None):
+        """Eqs. 4-7 for windows [first_slot + w*slot_stride, +T). Returns (images, eigvals)."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if images is None:
+            images = torch.empty((n_windows, self.ny, self.nx), dtype=torch.float32, device=dev)
+        if eigvals is None and want_eigvals:
+            eigvals = torch.empty((n_windows, self.T), dtype=torch.float64, device=dev)
+        _lib.check("dh_pca_windows", self._lib.dh_pca_windows(
+            self._h, int(first_slot), int(slot_stride), int(n_windows), int(k0), int(k1),
+            _ptr(images), _ptr(eigvals) if eigvals is not None else None, _stream_ptr(stream)))
+        return images, eigvals
+
+    def render_stack(self, frames: torch.Tensor, stream=None) -> None:
+        f = self._frames(frames)
+        if f.shape[0] < self.T:
+            raise ValueError("render_stack needs T frames")
+        _lib.check("dh_render_stack", self._lib.dh_render_stack(
+            self._h, _ptr(f), self.nx * self.ny, _stream_ptr(stream)))
+
+    def pca_window(self, k0: int, k1: int, image: torch.Tensor | None = None, stream=None):
+        """Eqs. 4-7 on slots [0, T); returns (image, eigenvalues as a host float64 tensor)."""
+        if image is None:
+            image = torch.empty((self.ny, self.nx), dtype=torch.float32,
+                                device=torch.device("cuda", torch.cuda.current_device()))
+        lam = torch.empty(self.T, dtype=torch.float64)
+        _lib.check("dh_pca_window", self._lib.dh_pca_window(
+            self._h, int(k0), int(k1), _ptr(image), _ptr(lam), _stream_ptr(stream)))
+        return image, lam
+
+    def pca_batch(self, frames: torch.Tensor, n_windows: int, window_stride: int, k0: int, k1: int,
+                  images: torch.Tensor | None = None, eigvals: torch.Tensor | None = None,
+                  want_eigvals: bool = True, stream=None):
+        f = self._frames(frames)
+        dev = f.device
+        if images is None:
+            images = torch.empty((n_windows, self.ny, self.nx), dtype=torch.float32, device=dev)
+        if eigvals is None and want_eigvals:
+            eigvals = torch.empty((n_windows, self.T), dtype=torch.float64, device=dev)
+        _lib.check("dh_pca_batch", self._lib.dh_pca_batch(
+            self._h, _ptr(f), self.nx * self.ny, int(n_windows), int(window_stride), int(k0),
+            int(k1), _ptr(images), _ptr(eigvals) if eigvals is not None else None,
+            _stream_ptr(stream)))
+        return images, eigvals
+
+    # -- inspection -----------------------------------------------------------
+    def debug_hologram(self, slot: int, stream=None) -> torch.Tensor:
+        out = torch.empty((self.ny, self.nx, 2), dtype=torch.float32, device="cuda")
+        _lib.check("dh_debug_hologram", self._lib.dh_debug_hologram(
+            self._h, int(slot), _ptr(out), _stream_ptr(stream)))
+        return torch.view_as_complex(out)
+
+    def debug_covariance(self, w: int = 0, stream=None) -> torch.Tensor:
+        out = torch.empty((self.T, self.T, 2), dtype=torch.float64, device="cuda")
+        _lib.check("dh_debug_covariance", self._lib.dh_debug_covariance(
+            self._h, int(w), _ptr(out), _stream_ptr(stream)))
+        return torch.view_as_complex(out)
+
+    def debug_eigvecs(self, w: int = 0, stream=None) -> torch.Tensor:
+        out = torch.empty((self.T, self.T, 2), dtype=torch.float64, device="cuda")
+        _lib.check("dh_debug_eigvecs", self._lib.dh_debug_eigvecs(
+            self._h, int(w), _ptr(out), _stream_ptr(stream)))
+        return torch.view_as_complex(out)
+
+    def profile(self, on: bool = True) -> None:
+        """Enable/disable per-kernel CUDA-event timing inside the library."""
+        _lib.check("dh_profile_enable", self._lib.dh_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self) -> dict:
+        """{kernel name: (launches, total device ms)} since the last read (synchronises)."""
+        n = 16
+        names = (ctypes.c_char_p * n)()
+        launches = (ctypes.c_int * n)()
+        ms = (ctypes.c_double * n)()
+        k = self._lib.dh_profile_read(self._h, n, names, launches, ms)
+        return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(min(k, n))}
+
+    def status(self) -> int:
+        flags = ctypes.c_uint32(0)
+        _lib.check("dh_plan_status", self._lib.dh_plan_status(self._h, ctypes.byref(flags)))
+        return int(flags.value)

@@ -1,0 +1,78 @@
+"""ctypes declarations of libdh (include/dh.h). Argument marshalling only."""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch  # noqa: F401  (loads the CUDA runtime that libdh shares)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdh.so")
+
+DH_OK = 0
+STATUS_NAMES = {0: "DH_OK", 1: "DH_ERR_INVALID_ARG", 2: "DH_ERR_UNSUPPORTED_SIZE",
+                3: "DH_ERR_OOM", 4: "DH_ERR_CUDA", 5: "DH_ERR_TIMEOUT",
+                6: "DH_ERR_FRAME_GAP", 7: "DH_ERR_STATE"}
+PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
+FLAG_STORE_OVERFLOW, FLAG_NONFINITE_C, FLAG_EIG_NOT_CONVERGED, FLAG_WAIT_TIMEOUT = 1, 2, 4, 8
+
+# (name, restype, argtypes) for every entry point of include/dh.h
+_vp, _i, _i64, _d, _u32p = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, \
+    ctypes.POINTER(ctypes.c_uint32)
+SIGNATURES = [
+    ("dh_plan_create", _i, [ctypes.POINTER(_vp), _i, _i, _d, _d, _d, _i]),
+    ("dh_destroy", None, [_vp]),
+    ("dh_plan_set_precision", _i, [_vp, _i]),
+    ("dh_plan_reserve", _i, [_vp, _i, _i]),
+    ("dh_plan_device_bytes", ctypes.c_size_t, [_vp]),
+    ("dh_render_frames", _i, [_vp, _vp, _i64, _i, _i, _vp]),
+    ("dh_pca_windows", _i, [_vp, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
+    ("dh_render_stack", _i, [_vp, _vp, _i64, _vp]),
+    ("dh_pca_window", _i, [_vp, _i, _i, _vp, _vp, _vp]),
+    ("dh_pca_batch", _i, [_vp, _vp, _i64, _i, _i, _i, _i, _vp, _vp, _vp]),
+    ("dh_debug_hologram", _i, [_vp, _i, _vp, _vp]),
+    ("dh_debug_covariance", _i, [_vp, _i, _vp, _vp]),
+    ("dh_debug_eigvecs", _i, [_vp, _i, _vp, _vp]),
+    ("dh_plan_status", _i, [_vp, _u32p]),
+    ("dh_profile_enable", _i, [_vp, _i]),
+    ("dh_profile_read", _i, [_vp, _i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_i),
+                             ctypes.POINTER(_d)]),
+    ("dh_status_string", ctypes.c_char_p, [_i]),
+    ("dh_last_error", ctypes.c_char_p, []),
+    ("dh_version", ctypes.c_char_p, []),
+]
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libdh.so; raise (never fall back) if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"libdh.so not found at {LIB_PATH}: build it with "
+                "`python -m paper_2004_00923_b300.build` (nvcc, sm_103a)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class DHError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        lib = load()
+        msg = f"{fn} -> {STATUS_NAMES.get(code, code)} ({lib.dh_status_string(code).decode()})"
+        if code == 4:
+            msg += f": {lib.dh_last_error().decode()}"
+        super().__init__(msg)
+        self.code = code
+
+
+def check(fn: str, code: int) -> None:
+    if code != DH_OK:
+        raise DHError(fn, code)

@@ -1,0 +1,328 @@
+// The C ABI of libdh (declared in include/dh.h): plan lifetime, argument checks, device
+// buffers and the order of the stages. Every step of the computation runs in the
+// library's own CUDA kernels; this file only validates, allocates and launches.
+#include "dh_internal.cuh"
+
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+struct dh_plan {
+  dh::Plan p;
+  std::atomic<int> busy{0};
+};
+
+namespace dh {
+
+static thread_local std::string g_last_error = "no error";
+
+const char *set_cuda_error(cudaError_t e) {
+  g_last_error = std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e);
+  return g_last_error.c_str();
+}
+
+dh_status fail_cuda(cudaError_t e) {
+  set_cuda_error(e);
+  (void)cudaGetLastError();  // clear a non-sticky error
+  return e == cudaErrorMemoryAllocation ? DH_ERR_OOM : DH_ERR_CUDA;
+}
+
+
+namespace {
+
+bool pow2_in_range(int n) { return n >= kMinDim && n <= kMaxDim && (n & (n - 1)) == 0; }
+
+template <typename Ptr>
+dh_status dalloc(Plan &p, Ptr **ptr, size_t bytes) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+  if (e != cudaSuccess) return fail_cuda(e);
+  *ptr = static_cast<Ptr *>(q);
+  p.bytes += bytes;
+  return DH_OK;
+}
+
+template <typename Ptr>
+void dfree(Ptr *&ptr) {
+  if (ptr) cudaFree((void *)ptr);
+  ptr = nullptr;
+}
+
+void free_store(Plan &p) {
+  dfree(p.d_H); dfree(p.d_part); dfree(p.d_C); dfree(p.d_lam); dfree(p.d_V); dfree(p.d_B);
+  dfree(p.d_mid);
+  p.tmaps_ok = false;
+}
+
+size_t table_bytes(const Plan &p) {
+  return sizeof(float2) * (p.nx + p.ny + twiddle_len(p.lognx) + twiddle_len(p.logny)) + 16;
+}
+
+// (Re)allocate everything whose size depends on the reservation or the precision.
+dh_status alloc_store(Plan &p) {
+  free_store(p);
+  p.bytes = table_bytes(p);
+  const int M = 2 * p.T;
+  p.H_elem_bytes = p.prec == DH_PREC_FP32 ? 4 : 2;
+  dh_status st;
+  if ((st = dalloc(p, &p.d_H, (size_t)p.max_frames * 2 * p.npix * p.H_elem_bytes)) != DH_OK) return st;
+  p.parts_total = p.max_windows * parts_per_window(p);
+  if ((st = dalloc(p, &p.d_part, (size_t)p.parts_total * M * M * sizeof(double))) != DH_OK) return st;
+  if ((st = dalloc(p, &p.d_C, (size_t)p.max_windows * p.T * p.T * 2 * sizeof(double))) != DH_OK) return st;
+  if ((st = dalloc(p, &p.d_lam, (size_t)p.max_windows * p.T * sizeof(double))) != DH_OK) return st;
+  if ((st = dalloc(p, &p.d_V, (size_t)p.max_windows * p.T * p.T * 2 * sizeof(double))) != DH_OK) return st;
+  // operand of Eq. 6 per window: FP32 [2T][2T], or 16-bit hi and lo [2][2T][2T]
+  size_t bw = p.prec == DH_PREC_FP32 ? (size_t)M * M * 4 : (size_t)2 * M * M * 2;
+  p.B_window_bytes = (bw + 1023) / 1024 * 1024;
+  if ((st = dalloc(p, &p.d_B, p.B_window_bytes * p.max_windows)) != DH_OK) return st;
+  // row-pass intermediate: a chunk of frames sized to stay in L2 (~48 MiB)
+  long long mf = (48ll << 20) / (p.npix * (long long)sizeof(float2));
+  if (mf < 1) mf = 1;
+  if (mf > 64) mf = 64;
+  p.mid_frames = (int)mf;
+  if ((st = dalloc(p, &p.d_mid, (size_t)p.mid_frames * p.npix * sizeof(float2))) != DH_OK) return st;
+  DH_CUDA_TRY(cudaMemset(p.d_B, 0, p.B_window_bytes * p.max_windows));
+  if (p.prec != DH_PREC_FP32) {
+    if ((st = make_tensor_maps(p)) != DH_OK) return st;
+  }
+  return DH_OK;
+}
+
+std::vector<float2> chirp_table(int n, double a) {
+  // c(k) = exp(-i pi a (k - n/2)^2) / sqrt(n); the phase a d^2 is reduced mod 2 in FP64
+  std::vector<float2> c(n);
+  const double inv = 1.0 / std::sqrt((double)n);
+  const double pi = 3.141592653589793238462643383279502884;
+  for (int k = 0; k < n; ++k) {
+    const double d = (double)(k - n / 2);
+    const double ph = std::fmod(a * (d * d), 2.0);
+    c[k] = make_float2((float)(std::cos(pi * ph) * inv), (float)(-std::sin(pi * ph) * inv));
+  }
+  return c;
+}
+
+struct Busy {
+  std::atomic<int> &b;
+  bool ok;
+  explicit Busy(std::atomic<int> &x) : b(x) { int z = 0; ok = b.compare_exchange_strong(z, 1); }
+  ~Busy() { if (ok) b.store(0); }
+};
+
+}  // namespace
+}  // namespace dh
+
+using namespace dh;
+
+extern "C" {
+
+const char *dh_version(void) { return "libdh 0.1 (sm_103a)"; }
+
+const char *dh_last_error(void) { return g_last_error.c_str(); }
+
+const char *dh_status_string(dh_status s) {
+  switch (s) {
+    case DH_OK: return "ok";
+    case DH_ERR_INVALID_ARG: return "invalid argument";
+    case DH_ERR_UNSUPPORTED_SIZE: return "unsupported size";
+    case DH_ERR_OOM: return "out of device memory";
+    case DH_ERR_CUDA: return "CUDA error";
+    case DH_ERR_TIMEOUT: return "device-side wait timed out";
+    case DH_ERR_FRAME_GAP: return "frame sequence gap";
+    case DH_ERR_STATE: return "plan busy or in the wrong state";
+  }
+  return "unknown status";
+}
+
+dh_status dh_plan_create(dh_plan_t *out, int nx, int ny, double lambda_m, double z_m,
+                         double pitch_m, int T) {
+  if (!out) return DH_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!(std::isfinite(lambda_m) && lambda_m > 0) || !(std::isfinite(z_m) && z_m > 0) ||
+      !(std::isfinite(pitch_m) && pitch_m > 0))
+    return DH_ERR_INVALID_ARG;
+  if (!pow2_in_range(nx) || !pow2_in_range(ny) || !(T == 16 || T == 32 || T == 64))
+    return DH_ERR_UNSUPPORTED_SIZE;
+  dh_plan *h = new (std::nothrow) dh_plan();
+  if (!h) return DH_ERR_OOM;
+  Plan &p = h->p;
+  p.nx = nx; p.ny = ny; p.T = T;
+  p.lognx = ilog2(nx); p.logny = ilog2(ny);
+  p.npix = (long long)nx * ny;
+  p.lambda = lambda_m; p.z = z_m; p.pitch = pitch_m;
+  p.a = pitch_m * pitch_m / (lambda_m * z_m);
+  p.max_frames = T;
+  p.max_windows = 1;
+  cudaError_t e = cudaGetDevice(&p.device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device);
+  dh_status st = e == cudaSuccess ? DH_OK : fail_cuda(e);
+  if (st == DH_OK) {
+    std::vector<float2> cx = chirp_table(nx, p.a), cy = chirp_table(ny, p.a);
+    std::vector<float2> twx(twiddle_len(p.lognx)), twy(twiddle_len(p.logny));
+    build_twiddles(p.lognx, twx.data());
+    build_twiddles(p.logny, twy.data());
+    if ((st = dalloc(p, &p.d_cx, cx.size() * sizeof(float2))) == DH_OK &&
+        (st = dalloc(p, &p.d_cy, cy.size() * sizeof(float2))) == DH_OK &&
+        (st = dalloc(p, &p.d_twx, twx.size() * sizeof(float2))) == DH_OK &&
+        (st = dalloc(p, &p.d_twy, twy.size() * sizeof(float2))) == DH_OK &&
+        (st = dalloc(p, &p.d_status, sizeof(uint32_t))) == DH_OK) {
+      cudaError_t c = cudaMemcpy(p.d_cx, cx.data(), cx.size() * sizeof(float2), cudaMemcpyHostToDevice);
+      if (c == cudaSuccess) c = cudaMemcpy(p.d_cy, cy.data(), cy.size() * sizeof(float2), cudaMemcpyHostToDevice);
+      if (c == cudaSuccess) c = cudaMemcpy(p.d_twx, twx.data(), twx.size() * sizeof(float2), cudaMemcpyHostToDevice);
+      if (c == cudaSuccess) c = cudaMemcpy(p.d_twy, twy.data(), twy.size() * sizeof(float2), cudaMemcpyHostToDevice);
+      if (c == cudaSuccess) c = cudaMemset(p.d_status, 0, sizeof(uint32_t));
+      st = c == cudaSuccess ? alloc_store(p) : fail_cuda(c);
+    }
+  }
+  if (st != DH_OK) {
+    dh_destroy(h);
+    return st;
+  }
+  *out = h;
+  return DH_OK;
+}
+
+void dh_destroy(dh_plan_t h) {
+  if (!h) return;
+  Plan &p = h->p;
+  cudaDeviceSynchronize();
+  free_store(p);
+  profile_free(p);
+  dfree(p.d_cx); dfree(p.d_cy); dfree(p.d_twx); dfree(p.d_twy); dfree(p.d_status);
+  delete h;
+}
+
+dh_status dh_plan_set_precision(dh_plan_t h, dh_precision prec) {
+  if (!h) return DH_ERR_INVALID_ARG;
+  if (prec != DH_PREC_FP32 && prec != DH_PREC_FP16 && prec != DH_PREC_BF16) return DH_ERR_INVALID_ARG;
+  Busy g(h->busy);
+  if (!g.ok) return DH_ERR_STATE;
+  DH_CUDA_TRY(cudaDeviceSynchronize());
+  h->p.prec = prec;
+  return alloc_store(h->p);
+}
+
+dh_status dh_plan_reserve(dh_plan_t h, int max_frames, int max_windows) {
+  if (!h || max_frames < h->p.T || max_windows < 1) return DH_ERR_INVALID_ARG;
+  Busy g(h->busy);
+  if (!g.ok) return DH_ERR_STATE;
+  DH_CUDA_TRY(cudaDeviceSynchronize());
+  h->p.max_frames = max_frames;
+  h->p.max_windows = max_windows;
+  return alloc_store(h->p);
+}
+
+size_t dh_plan_device_bytes(dh_plan_t h) { return h ? h->p.bytes : 0; }
+
+dh_status dh_render_frames(dh_plan_t h, const uint16_t *frames_dev, int64_t frame_stride_elems,
+                           int n_frames, int first_slot, void *stream) {
+  if (!h || !frames_dev || n_frames < 1 || first_slot < 0) return DH_ERR_INVALID_ARG;
+  Plan &p = h->p;
+  if (frame_stride_elems < p.npix || (long long)first_slot + n_frames > p.max_frames)
+    return DH_ERR_INVALID_ARG;
+  Busy g(h->busy);
+  if (!g.ok) return DH_ERR_STATE;
+  return launch_render(p, frames_dev, frame_stride_elems, n_frames, first_slot,
+                       static_cast<cudaStream_t>(stream));
+}
+
+dh_status dh_pca_windows(dh_plan_t h, int first_slot, int slot_stride, int n_windows, int k0,
+                         int k1, float *images_dev, double *eigvals_dev, void *stream) {
+  if (!h || !images_dev || n_windows < 1 || first_slot < 0 || slot_stride < 1) return DH_ERR_INVALID_ARG;
+  Plan &p = h->p;
+  if (k0 < 0 || k1 < k0 || k1 >= p.T) return DH_ERR_INVALID_ARG;
+  if (n_windows > p.max_windows) return DH_ERR_INVALID_ARG;
+  if ((long long)first_slot + (long long)(n_windows - 1) * slot_stride + p.T > p.max_frames)
+    return DH_ERR_INVALID_ARG;
+  Busy g(h->busy);
+  if (!g.ok) return DH_ERR_STATE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nS = k1 - k0 + 1;
+  int parts = 0;
+  dh_status st;
+  if (p.prec == DH_PREC_FP32) {
+    const int nrows = 2 * nS;
+    if ((st = launch_gram_simt(p, first_slot, slot_stride, n_windows, &parts, s)) != DH_OK) return st;
+    if ((st = launch_eig(p, n_windows, parts, k0, k1, nrows, eigvals_dev, s)) != DH_OK) return st;
+    return launch_project_simt(p, first_slot, slot_stride, n_windows, nrows, images_dev, s);
+  }
+  const int Npad = (2 * nS + 15) / 16 * 16;
+  if ((st = launch_gram_tc(p, first_slot, slot_stride, n_windows, &parts, s)) != DH_OK) return st;
+  if ((st = launch_eig(p, n_windows, parts, k0, k1, Npad, eigvals_dev, s)) != DH_OK) return st;
+  return launch_project_tc(p, first_slot, slot_stride, n_windows, Npad, images_dev, s);
+}
+
+dh_status dh_render_stack(dh_plan_t h, const uint16_t *frames_dev, int64_t frame_stride_elems,
+                          void *stream) {
+  if (!h) return DH_ERR_INVALID_ARG;
+  return dh_render_frames(h, frames_dev, frame_stride_elems, h->p.T, 0, stream);
+}
+
+dh_status dh_pca_window(dh_plan_t h, int k0, int k1, float *image_dev, double *eigvals_host,
+                        void *stream) {
+  if (!h) return DH_ERR_INVALID_ARG;
+  dh_status st = dh_pca_windows(h, 0, h->p.T, 1, k0, k1, image_dev, nullptr, stream);
+  if (st != DH_OK || !eigvals_host) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DH_CUDA_TRY(cudaMemcpyAsync(eigvals_host, h->p.d_lam, sizeof(double) * h->p.T,
+                              cudaMemcpyDeviceToHost, s));
+  DH_CUDA_TRY(cudaStreamSynchronize(s));
+  return DH_OK;
+}
+
+dh_status dh_pca_batch(dh_plan_t h, const uint16_t *frames_dev, int64_t frame_stride_elems,
+                       int n_windows, int window_stride_frames, int k0, int k1, float *images_dev,
+                       double *eigvals_dev, void *stream) {
+  if (!h || n_windows < 1 || window_stride_frames < 1) return DH_ERR_INVALID_ARG;
+  const long long nf = (long long)(n_windows - 1) * window_stride_frames + h->p.T;
+  if (nf > h->p.max_frames || n_windows > h->p.max_windows) return DH_ERR_INVALID_ARG;
+  dh_status st = dh_render_frames(h, frames_dev, frame_stride_elems, (int)nf, 0, stream);
+  if (st != DH_OK) return st;
+  return dh_pca_windows(h, 0, window_stride_frames, n_windows, k0, k1, images_dev, eigvals_dev,
+                        stream);
+}
+
+dh_status dh_debug_hologram(dh_plan_t h, int slot, float *out_dev, void *stream) {
+  if (!h || !out_dev || slot < 0 || slot >= h->p.max_frames) return DH_ERR_INVALID_ARG;
+  return launch_hologram_to_f32(h->p, slot, out_dev, static_cast<cudaStream_t>(stream));
+}
+
+dh_status dh_debug_covariance(dh_plan_t h, int w, double *out_dev, void *stream) {
+  if (!h || !out_dev || w < 0 || w >= h->p.max_windows) return DH_ERR_INVALID_ARG;
+  const size_t n = (size_t)h->p.T * h->p.T * 2;
+  DH_CUDA_TRY(cudaMemcpyAsync(out_dev, h->p.d_C + n * w, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                              static_cast<cudaStream_t>(stream)));
+  return DH_OK;
+}
+
+dh_status dh_debug_eigvecs(dh_plan_t h, int w, double *out_dev, void *stream) {
+  if (!h || !out_dev || w < 0 || w >= h->p.max_windows) return DH_ERR_INVALID_ARG;
+  const size_t n = (size_t)h->p.T * h->p.T * 2;
+  DH_CUDA_TRY(cudaMemcpyAsync(out_dev, h->p.d_V + n * w, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                              static_cast<cudaStream_t>(stream)));
+  return DH_OK;
+}
+
+dh_status dh_profile_enable(dh_plan_t h, int on) {
+  if (!h) return DH_ERR_INVALID_ARG;
+  Busy g(h->busy);
+  if (!g.ok) return DH_ERR_STATE;
+  return profile_enable(h->p, on);
+}
+
+int dh_profile_read(dh_plan_t h, int n, const char **names, int *launches, double *total_ms) {
+  if (!h) return 0;
+  return profile_read(h->p, n, names, launches, total_ms);
+}
+
+dh_status dh_plan_status(dh_plan_t h, uint32_t *flags) {
+  if (!h || !flags) return DH_ERR_INVALID_ARG;
+  DH_CUDA_TRY(cudaDeviceSynchronize());
+  DH_CUDA_TRY(cudaMemcpy(flags, h->p.d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  DH_CUDA_TRY(cudaMemset(h->p.d_status, 0, sizeof(uint32_t)));
+  return DH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+// Internal declarations shared by the translation units of libdh.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dh.h"
+
+namespace dh {
+
+constexpr int kMaxDim = 4096;
+constexpr int kMinDim = 16;
+
+// One device-resident plan (see dh.h). Host-side bookkeeping plus device buffers.
+struct Plan {
+  int nx = 0, ny = 0, T = 0, lognx = 0, logny = 0;
+  long long npix = 0;
+  double lambda = 0, z = 0, pitch = 0, a = 0;
+  dh_precision prec = DH_PREC_FP32;
+  int device = 0;
+  int num_sms = 148;
+
+  int max_frames = 0;   // hologram slots
+  int max_windows = 0;  // windows per dh_pca_windows call
+
+  // tables
+  float2 *d_cx = nullptr, *d_cy = nullptr;   // chirp * 1/sqrt(n) per axis
+  float2 *d_twx = nullptr, *d_twy = nullptr; // Stockham twiddles per axis
+  // render intermediate (row-pass output), chunk of frames kept L2-sized
+  float2 *d_mid = nullptr;
+  int mid_frames = 0;
+  // hologram store: [max_frames][2][npix] of the storage type
+  void *d_H = nullptr;
+  size_t H_elem_bytes = 4;
+  // covariance partials: [max_windows][parts_per_window][2T][2T] FP64
+  double *d_part = nullptr;
+  int parts_total = 0;  // partial Gram matrices the buffer holds (all windows)
+  double *d_C = nullptr;    // [max_windows][T][T][2]
+  double *d_lam = nullptr;  // [max_windows][T]
+  double *d_V = nullptr;    // [max_windows][T][T][2]
+  void *d_B = nullptr;      // projection operand per window
+  size_t B_window_bytes = 0;
+  uint32_t *d_status = nullptr;
+
+  // tensor maps for the tensor-core kernels (16-bit storage only)
+  CUtensorMap tmap_H;
+  CUtensorMap tmap_B;
+  bool tmaps_ok = false;
+
+  size_t bytes = 0;
+  int busy = 0;
+  void *prof = nullptr;  // per-kernel event timing state (profile.cu), null when disabled
+};
+
+// ---------------------------------------------------------------- tracing
+enum KernelId {
+  K_RENDER_ROWS = 0, K_RENDER_COLS, K_GRAM_SIMT, K_GRAM_TC, K_REDUCE_COV, K_JACOBI,
+  K_PROJECT_SIMT, K_PROJECT_TC, K_COUNT
+};
+const char *kernel_name(int kid);
+dh_status profile_enable(Plan &p, int on);
+int profile_read(Plan &p, int n, const char **names, int *launches, double *total_ms);
+void profile_free(Plan &p);
+// Brackets one kernel launch with CUDA events on its stream when the plan's profiler is on.
+struct ProfScope {
+  Plan &p;
+  int kid;
+  cudaStream_t s;
+  int slot;
+  ProfScope(Plan &plan, int k, cudaStream_t st);
+  ~ProfScope();
+};
+
+// ---------------------------------------------------------------- host helpers
+const char *set_cuda_error(cudaError_t e);
+dh_status fail_cuda(cudaError_t e);
+
+#define DH_CUDA_TRY(expr)                         \
+  do {                                            \
+    cudaError_t e__ = (expr);                     \
+    if (e__ != cudaSuccess) return fail_cuda(e__); \
+  } while (0)
+
+// ---------------------------------------------------------------- stage launchers
+// Eq. 1: render n_frames frames into hologram slots [slot0, slot0 + n_frames).
+dh_status launch_render(Plan &p, const uint16_t *frames, long long frame_stride, int n_frames,
+                        int slot0, cudaStream_t s);
+void build_twiddles(int logn, float2 *host_out);  // host, FP64 -> FP32
+int twiddle_len(int logn);
+
+// Partial Gram matrices per window (split-K over pixels), fixed per frame size.
+int gram_units(long long npix);
+int gram_tc_parts(const Plan &p);
+inline int parts_per_window(const Plan &p) {
+  return p.prec == DH_PREC_FP32 ? gram_units(p.npix) : gram_tc_parts(p);
+}
+// Eq. 4, FP32 CUDA cores: partial real Gram matrices of X = [Re H_t ; Im H_t] rows.
+dh_status launch_gram_simt(Plan &p, int first_slot, int slot_stride, int n_windows,
+                           int *parts_per_window, cudaStream_t s);
+// Eq. 4, tensor cores (16-bit storage).
+dh_status launch_gram_tc(Plan &p, int first_slot, int slot_stride, int n_windows,
+                         int *parts_per_window, cudaStream_t s);
+// Eq. 5 + ordering + operand build for Eq. 6.
+dh_status launch_eig(Plan &p, int n_windows, int parts_per_window, int k0, int k1, int Npad,
+                     double *eigvals_out, cudaStream_t s);
+// Eqs. 6-7.
+dh_status launch_project_simt(Plan &p, int first_slot, int slot_stride, int n_windows, int Npad,
+                              float *images, cudaStream_t s);
+dh_status launch_project_tc(Plan &p, int first_slot, int slot_stride, int n_windows, int Npad,
+                            float *images, cudaStream_t s);
+dh_status make_tensor_maps(Plan &p);
+
+// conversions for inspection
+dh_status launch_hologram_to_f32(Plan &p, int slot, float *out, cudaStream_t s);
+
+inline int ilog2(long long v) {
+  int l = 0;
+  while ((1ll << l) < v) ++l;
+  return l;
+}
+
+}  // namespace dh

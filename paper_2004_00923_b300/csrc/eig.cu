@@ -1,0 +1,244 @@
+// Eq. 4 (final FP64 reduction) and Eq. 5 on the GPU.
+//
+// k_reduce_cov: C[t][u] = sum over partial Gram matrices of
+//     (G[2t][2u] + G[2t+1][2u+1]) + i (G[2t][2u+1] - G[2t+1][2u])   in FP64.
+// k_jacobi: one CTA per window. Hermitian eigendecomposition C = V Lambda V^{t*} by the
+//   two-sided complex Jacobi method in FP64 (Forsythe & Henrici 1960; Golub & Van Loan
+//   Sec. 8.5) with the parallel round-robin ordering: each of the T-1 steps of a sweep
+//   rotates T/2 disjoint pairs at once (Brent & Luk 1985). For a pair with
+//   C_pq = g e^{i alpha}, the real 2x2 Schur rotation (c, s) of [[C_pp, g], [g, C_qq]] is
+//   combined with the phase: J_pp = J_qq = c, J_pq = s e^{i alpha}, J_qp = -s e^{-i alpha},
+//   C <- J^{t*} C J, V <- V J. Eigenvalues are then ordered decreasing (ties by index)
+//   and the retained columns k0..k1 are packed into the operand of Eq. 6.
+#include "dh_internal.cuh"
+
+namespace dh {
+namespace {
+
+template <int T>
+__global__ void __launch_bounds__(256)
+k_reduce_cov(const double *__restrict__ part, int parts, int n_windows, double *__restrict__ C,
+             uint32_t *__restrict__ status) {
+  constexpr int M = 2 * T;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_windows * T * T) return;
+  const int w = idx / (T * T), e = idx % (T * T), t = e / T, u = e % T;
+  const double *P = part + (long long)w * parts * M * M;
+  double re = 0.0, im = 0.0;
+  for (int q = 0; q < parts; ++q) {
+    const double *G = P + (long long)q * M * M;
+    re += G[(2 * t) * M + 2 * u] + G[(2 * t + 1) * M + 2 * u + 1];
+    im += G[(2 * t) * M + 2 * u + 1] - G[(2 * t + 1) * M + 2 * u];
+  }
+  C[2 * ((long long)w * T * T + e)] = re;
+  C[2 * ((long long)w * T * T + e) + 1] = im;
+  if (!isfinite(re) || !isfinite(im)) atomicOr(status, DH_FLAG_NONFINITE_C);
+}
+
+__device__ __forceinline__ double block_sum(double v, double *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  return s;
+}
+
+template <typename T16> __device__ __forceinline__ T16 from_f32(float x);
+template <> __device__ __forceinline__ __half from_f32<__half>(float x) { return __float2half_rn(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float x) {
+  return __float2bfloat16_rn(x);
+}
+template <typename T16> __device__ __forceinline__ float to_f32(T16 x);
+template <> __device__ __forceinline__ float to_f32<__half>(__half x) { return __half2float(x); }
+template <> __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 x) {
+  return __bfloat162float(x);
+}
+
+// Pack value v of operand entry (j, r) for the projection of Eq. 6 (see launch_eig).
+template <typename T16>
+__device__ __forceinline__ void put_split(T16 *hi, T16 *lo, long long i, double v) {
+  const T16 h = from_f32<T16>((float)v);
+  hi[i] = h;
+  lo[i] = from_f32<T16>((float)(v - (double)to_f32<T16>(h)));
+}
+
+template <int T>
+__global__ void __launch_bounds__(256)
+k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restrict__ Vout,
+         double *__restrict__ eig_user, int prec, void *__restrict__ Bop, long long B_stride,
+         int k0, int k1, int Npad, double tol, int max_sweeps, uint32_t *__restrict__ status) {
+  constexpr int NP = T / 2;
+  constexpr int LD = T + 1;
+  constexpr int M = 2 * T;
+  extern __shared__ double sm[];
+  double *ar = sm, *ai = ar + T * LD, *vr = ai + T * LD, *vi = vr + T * LD;
+  __shared__ double rc[NP], rwr[NP], rwi[NP], red[8], dsort[T];
+  __shared__ int rp[NP], rq[NP], perm[T];
+  const int w = blockIdx.x, tid = threadIdx.x;
+  const double *Cw = C + 2ll * w * T * T;
+
+  double fro2 = 0.0;
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    const int i = e / T, j = e % T;
+    const double re = 0.5 * (Cw[2 * (i * T + j)] + Cw[2 * (j * T + i)]);
+    const double im = i == j ? 0.0 : 0.5 * (Cw[2 * (i * T + j) + 1] - Cw[2 * (j * T + i) + 1]);
+    ar[i * LD + j] = re;
+    ai[i * LD + j] = im;
+    vr[i * LD + j] = i == j ? 1.0 : 0.0;
+    vi[i * LD + j] = 0.0;
+    fro2 += re * re + im * im;
+  }
+  const double fro = sqrt(block_sum(fro2, red));
+
+  bool converged = false;
+  for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
+    double off2 = 0.0;
+    for (int e = tid; e < T * T; e += blockDim.x) {
+      const int i = e / T, j = e % T;
+      if (i != j) off2 += ar[i * LD + j] * ar[i * LD + j] + ai[i * LD + j] * ai[i * LD + j];
+    }
+    off2 = block_sum(off2, red);
+    if (sqrt(off2) <= tol * fro) { converged = true; break; }
+    if (sweep == max_sweeps) break;
+    for (int step = 0; step < T - 1; ++step) {
+      if (tid < NP) {
+        int a, b;
+        if (tid == 0) { a = step; b = T - 1; }
+        else { a = (step + tid) % (T - 1); b = (step - tid + T - 1) % (T - 1); }
+        const int p = a < b ? a : b, q = a < b ? b : a;
+        const double gr = ar[p * LD + q], gi = ai[p * LD + q];
+        const double g = sqrt(gr * gr + gi * gi);
+        double c = 1.0, wr = 0.0, wi = 0.0;
+        if (g > 1e-300) {
+          const double tau = (ar[q * LD + q] - ar[p * LD + p]) / (2.0 * g);
+          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + t * t);
+          const double s = t * c;
+          wr = s * gr / g;
+          wi = s * gi / g;
+        }
+        rp[tid] = p; rq[tid] = q; rc[tid] = c; rwr[tid] = wr; rwi[tid] = wi;
+      }
+      __syncthreads();
+      // columns of A and V: X_ip' = c X_ip - conj(w) X_iq ;  X_iq' = w X_ip + c X_iq
+      for (int it = tid; it < NP * T; it += blockDim.x) {
+        const int k = it / T, i = it % T;
+        const int p = rp[k], q = rq[k];
+        const double c = rc[k], wr = rwr[k], wi = rwi[k];
+        double xpr = ar[i * LD + p], xpi = ai[i * LD + p], xqr = ar[i * LD + q], xqi = ai[i * LD + q];
+        ar[i * LD + p] = c * xpr - (wr * xqr + wi * xqi);
+        ai[i * LD + p] = c * xpi - (wr * xqi - wi * xqr);
+        ar[i * LD + q] = (wr * xpr - wi * xpi) + c * xqr;
+        ai[i * LD + q] = (wr * xpi + wi * xpr) + c * xqi;
+        xpr = vr[i * LD + p]; xpi = vi[i * LD + p]; xqr = vr[i * LD + q]; xqi = vi[i * LD + q];
+        vr[i * LD + p] = c * xpr - (wr * xqr + wi * xqi);
+        vi[i * LD + p] = c * xpi - (wr * xqi - wi * xqr);
+        vr[i * LD + q] = (wr * xpr - wi * xpi) + c * xqr;
+        vi[i * LD + q] = (wr * xpi + wi * xpr) + c * xqi;
+      }
+      __syncthreads();
+      // rows of A: A_pj' = c A_pj - w A_qj ;  A_qj' = conj(w) A_pj + c A_qj
+      for (int it = tid; it < NP * T; it += blockDim.x) {
+        const int k = it / T, j = it % T;
+        const int p = rp[k], q = rq[k];
+        const double c = rc[k], wr = rwr[k], wi = rwi[k];
+        const double xpr = ar[p * LD + j], xpi = ai[p * LD + j], xqr = ar[q * LD + j], xqi = ai[q * LD + j];
+        ar[p * LD + j] = c * xpr - (wr * xqr - wi * xqi);
+        ai[p * LD + j] = c * xpi - (wr * xqi + wi * xqr);
+        ar[q * LD + j] = (wr * xpr + wi * xpi) + c * xqr;
+        ai[q * LD + j] = (wr * xpi - wi * xpr) + c * xqi;
+      }
+      __syncthreads();
+      if (tid < NP) {
+        const int p = rp[tid], q = rq[tid];
+        ar[p * LD + q] = ai[p * LD + q] = ar[q * LD + p] = ai[q * LD + p] = 0.0;
+        ai[p * LD + p] = ai[q * LD + q] = 0.0;
+      }
+      __syncthreads();
+    }
+  }
+  if (!converged && tid == 0) atomicOr(status, DH_FLAG_EIG_NOT_CONVERGED);
+
+  // decreasing order, ties by original index
+  if (tid < T) dsort[tid] = ar[tid * LD + tid];
+  __syncthreads();
+  if (tid < T) {
+    const double d = dsort[tid];
+    int rank = 0;
+    for (int j = 0; j < T; ++j) rank += (dsort[j] > d) || (dsort[j] == d && j < tid);
+    perm[rank] = tid;
+  }
+  __syncthreads();
+  if (tid < T) {
+    lam[(long long)w * T + tid] = dsort[perm[tid]];
+    if (eig_user) eig_user[(long long)w * T + tid] = dsort[perm[tid]];
+  }
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    const int t = e / T, k = e % T;
+    Vout[2 * ((long long)w * T * T + e)] = vr[t * LD + perm[k]];
+    Vout[2 * ((long long)w * T * T + e) + 1] = vi[t * LD + perm[k]];
+  }
+  // Operand of Eq. 6 in the real embedding [P_re P_im] = [Re H, Im H] * B^T, rows r = 2t + c:
+  //   j < nS       (P_re of component k = k0 + j):  B[j][2t] = Re V_tk, B[j][2t+1] = -Im V_tk
+  //   nS <= j < 2nS (P_im of k = k0 + j - nS):      B[j][2t] = Im V_tk, B[j][2t+1] =  Re V_tk
+  const int nS = k1 - k0 + 1;
+  for (int e = tid; e < Npad * M; e += blockDim.x) {
+    const int j = e / M, r = e % M, t = r >> 1, c = r & 1;
+    double v = 0.0;
+    if (j < 2 * nS) {
+      const int k = k0 + (j < nS ? j : j - nS);
+      const double re = vr[t * LD + perm[k]], im = vi[t * LD + perm[k]];
+      v = j < nS ? (c == 0 ? re : -im) : (c == 0 ? im : re);
+    }
+    if (prec == DH_PREC_FP32) {
+      static_cast<float *>(Bop)[w * B_stride + e] = (float)v;
+    } else if (prec == DH_PREC_FP16) {
+      __half *hi = static_cast<__half *>(Bop) + w * B_stride;
+      put_split<__half>(hi, hi + (long long)Npad * M, e, v);
+    } else {
+      __nv_bfloat16 *hi = static_cast<__nv_bfloat16 *>(Bop) + w * B_stride;
+      put_split<__nv_bfloat16>(hi, hi + (long long)Npad * M, e, v);
+    }
+  }
+}
+
+template <int T>
+dh_status launch_eig_t(Plan &p, int n_windows, int parts, int k0, int k1, int Npad,
+                       double *eig_user, cudaStream_t s) {
+  const int total = n_windows * T * T;
+  {
+    ProfScope ps(p, K_REDUCE_COV, s);
+    k_reduce_cov<T><<<(total + 255) / 256, 256, 0, s>>>(p.d_part, parts, n_windows, p.d_C, p.d_status);
+  }
+  DH_CUDA_TRY(cudaGetLastError());
+  const size_t smem = 4ull * T * (T + 1) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    DH_CUDA_TRY(cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  const long long B_stride = (long long)(p.B_window_bytes / (p.prec == DH_PREC_FP32 ? 4 : 2));
+  ProfScope ps(p, K_JACOBI, s);
+  k_jacobi<T><<<n_windows, 256, smem, s>>>(p.d_C, p.d_lam, p.d_V, eig_user, (int)p.prec, p.d_B,
+                                           B_stride, k0, k1, Npad, 1e-14, 30, p.d_status);
+  DH_CUDA_TRY(cudaGetLastError());
+  return DH_OK;
+}
+
+}  // namespace
+
+dh_status launch_eig(Plan &p, int n_windows, int parts, int k0, int k1, int Npad,
+                     double *eig_user, cudaStream_t s) {
+  switch (p.T) {
+    case 16: return launch_eig_t<16>(p, n_windows, parts, k0, k1, Npad, eig_user, s);
+    case 32: return launch_eig_t<32>(p, n_windows, parts, k0, k1, Npad, eig_user, s);
+    case 64: return launch_eig_t<64>(p, n_windows, parts, k0, k1, Npad, eig_user, s);
+  }
+  return DH_ERR_UNSUPPORTED_SIZE;
+}
+
+}  // namespace dh

@@ -1,0 +1,102 @@
+// Eq. 4 on FP32 CUDA cores (the plain path): partial real Gram matrices
+//   G = X X^T,  X = the 2T rows [Re H_0; Im H_0; Re H_1; Im H_1; ...] over a pixel range.
+// Each CTA owns one (window, pixel range) unit and accumulates products in FP32 over
+// 256-pixel runs, then in FP64; units are summed in FP64 by the reduction kernel.
+// C[t][u] = (G[2t][2u] + G[2t+1][2u+1]) + i (G[2t][2u+1] - G[2t+1][2u]).
+#include "dh_internal.cuh"
+
+namespace dh {
+namespace {
+
+template <int T>
+__global__ void __launch_bounds__(256)
+k_gram_simt(const float *__restrict__ H, long long npix, int first_slot, int slot_stride,
+            int units, long long pix_per_unit, double *__restrict__ part) {
+  constexpr int M = 2 * T;
+  constexpr int TM = M / 16;
+  constexpr int KC = 32;
+  constexpr int LD = KC + 2;  // row stride: 8-byte aligned pairs, conflict-free columns
+  __shared__ __align__(16) float xs[M * LD];
+  const int w = blockIdx.x / units, u = blockIdx.x % units;
+  const float *X = H + (long long)(first_slot + w * slot_stride) * 2 * npix + u * pix_per_unit;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float acc[TM][TM];
+  double acc64[TM][TM];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int k = 0; k < TM; ++k) acc[i][k] = 0.f, acc64[i][k] = 0.0;
+  int chunk = 0;
+  for (long long pc = 0; pc < pix_per_unit; pc += KC, ++chunk) {
+    for (int e = threadIdx.x; e < M * KC; e += 256) {
+      const int r = e / KC, k = e % KC;
+      xs[r * LD + k] = X[(long long)r * npix + pc + k];
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < KC; k += 2) {
+      float2 a[TM], b[TM];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+        a[i] = *reinterpret_cast<const float2 *>(&xs[(ty + 16 * i) * LD + k]);
+        b[i] = *reinterpret_cast<const float2 *>(&xs[(tx + 16 * i) * LD + k]);
+      }
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int q = 0; q < TM; ++q) {
+          acc[i][q] = fmaf(a[i].x, b[q].x, acc[i][q]);
+          acc[i][q] = fmaf(a[i].y, b[q].y, acc[i][q]);
+        }
+    }
+    __syncthreads();
+    if ((chunk & 7) == 7) {
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int q = 0; q < TM; ++q) acc64[i][q] += (double)acc[i][q], acc[i][q] = 0.f;
+    }
+  }
+  double *dst = part + (long long)(w * units + u) * M * M;
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int q = 0; q < TM; ++q)
+      dst[(ty + 16 * i) * M + tx + 16 * q] = acc64[i][q] + (double)acc[i][q];
+}
+
+template <int T>
+dh_status launch_t(Plan &p, int first_slot, int slot_stride, int n_windows, int units,
+                   cudaStream_t s) {
+  const long long ppu = p.npix / units;
+  ProfScope ps(p, K_GRAM_SIMT, s);
+  k_gram_simt<T><<<n_windows * units, 256, 0, s>>>(static_cast<const float *>(p.d_H), p.npix,
+                                                  first_slot, slot_stride, units, ppu, p.d_part);
+  DH_CUDA_TRY(cudaGetLastError());
+  return DH_OK;
+}
+
+}  // namespace
+
+// Split-K units per window: a function of the frame size only (never of the batch), so a
+// window's covariance is bitwise the same alone and inside any batch.
+int gram_units(long long npix) {
+  long long u = npix / 4096;
+  if (u < 1) u = 1;
+  if (u > 64) u = 64;
+  return (int)u;
+}
+
+dh_status launch_gram_simt(Plan &p, int first_slot, int slot_stride, int n_windows,
+                           int *parts_per_window, cudaStream_t s) {
+  const int units = gram_units(p.npix);
+  *parts_per_window = units;
+  switch (p.T) {
+    case 16: return launch_t<16>(p, first_slot, slot_stride, n_windows, units, s);
+    case 32: return launch_t<32>(p, first_slot, slot_stride, n_windows, units, s);
+    case 64: return launch_t<64>(p, first_slot, slot_stride, n_windows, units, s);
+  }
+  return DH_ERR_UNSUPPORTED_SIZE;
+}
+
+}  // namespace dh

@@ -1,0 +1,469 @@
+// Eq. 1 on the GPU: Fresnel rendering of 16-bit interferograms into holograms.
+//
+//   H[t,y,x] = s * sum_{k,l} I[t,l,k] c(k) c(l) exp(+2 pi i (x k / n_x + y l / n_y)),
+//   c(k) = exp(-i pi a (k - n/2)^2),  a = pitch^2 / (lambda z),  s = 1/sqrt(n_x n_y).
+//
+// Two passes over each frame, both on FP32 CUDA cores:
+//   rows:    uint16 load -> x chirp (scale folded in) -> n_x-point FFT -> y chirp -> mid
+//   columns: mid (L2-resident chunk of frames) -> n_y-point FFT -> 16/32-bit planes of H
+// The FFT is a Stockham auto-sort transform (Govindaraju et al., SC'08 formulation):
+// each thread keeps R points in registers, runs an in-register radix-R DIF transform with
+// compile-time twiddles, and exchanges through padded shared memory between passes.
+// Inter-pass twiddles come from FP64-built tables. Frames are processed in chunks whose
+// intermediate fits in L2, so HBM sees only the uint16 input and the hologram output.
+#include "dh_internal.cuh"
+
+#include <math.h>
+#include <vector>
+
+namespace dh {
+namespace {
+
+// cos / sin (2 pi m / 64), m = 0..63 (mathematical constants, rounded to float)
+constexpr float kCos64[64] = {
+    1.000000000e+00f, 9.951847267e-01f, 9.807852804e-01f, 9.569403357e-01f,
+    9.238795325e-01f, 8.819212643e-01f, 8.314696123e-01f, 7.730104534e-01f,
+    7.071067812e-01f, 6.343932842e-01f, 5.555702330e-01f, 4.713967368e-01f,
+    3.826834324e-01f, 2.902846773e-01f, 1.950903220e-01f, 9.801714033e-02f,
+    6.123233996e-17f, -9.801714033e-02f, -1.950903220e-01f, -2.902846773e-01f,
+    -3.826834324e-01f, -4.713967368e-01f, -5.555702330e-01f, -6.343932842e-01f,
+    -7.071067812e-01f, -7.730104534e-01f, -8.314696123e-01f, -8.819212643e-01f,
+    -9.238795325e-01f, -9.569403357e-01f, -9.807852804e-01f, -9.951847267e-01f,
+    -1.000000000e+00f, -9.951847267e-01f, -9.807852804e-01f, -9.569403357e-01f,
+    -9.238795325e-01f, -8.819212643e-01f, -8.314696123e-01f, -7.730104534e-01f,
+    -7.071067812e-01f, -6.343932842e-01f, -5.555702330e-01f, -4.713967368e-01f,
+    -3.826834324e-01f, -2.902846773e-01f, -1.950903220e-01f, -9.801714033e-02f,
+    -1.836970199e-16f, 9.801714033e-02f, 1.950903220e-01f, 2.902846773e-01f,
+    3.826834324e-01f, 4.713967368e-01f, 5.555702330e-01f, 6.343932842e-01f,
+    7.071067812e-01f, 7.730104534e-01f, 8.314696123e-01f, 8.819212643e-01f,
+    9.238795325e-01f, 9.569403357e-01f, 9.807852804e-01f, 9.951847267e-01f,
+};
+constexpr float kSin64[64] = {
+    0.000000000e+00f, 9.801714033e-02f, 1.950903220e-01f, 2.902846773e-01f,
+    3.826834324e-01f, 4.713967368e-01f, 5.555702330e-01f, 6.343932842e-01f,
+    7.071067812e-01f, 7.730104534e-01f, 8.314696123e-01f, 8.819212643e-01f,
+    9.238795325e-01f, 9.569403357e-01f, 9.807852804e-01f, 9.951847267e-01f,
+    1.000000000e+00f, 9.951847267e-01f, 9.807852804e-01f, 9.569403357e-01f,
+    9.238795325e-01f, 8.819212643e-01f, 8.314696123e-01f, 7.730104534e-01f,
+    7.071067812e-01f, 6.343932842e-01f, 5.555702330e-01f, 4.713967368e-01f,
+    3.826834324e-01f, 2.902846773e-01f, 1.950903220e-01f, 9.801714033e-02f,
+    1.224646799e-16f, -9.801714033e-02f, -1.950903220e-01f, -2.902846773e-01f,
+    -3.826834324e-01f, -4.713967368e-01f, -5.555702330e-01f, -6.343932842e-01f,
+    -7.071067812e-01f, -7.730104534e-01f, -8.314696123e-01f, -8.819212643e-01f,
+    -9.238795325e-01f, -9.569403357e-01f, -9.807852804e-01f, -9.951847267e-01f,
+    -1.000000000e+00f, -9.951847267e-01f, -9.807852804e-01f, -9.569403357e-01f,
+    -9.238795325e-01f, -8.819212643e-01f, -8.314696123e-01f, -7.730104534e-01f,
+    -7.071067812e-01f, -6.343932842e-01f, -5.555702330e-01f, -4.713967368e-01f,
+    -3.826834324e-01f, -2.902846773e-01f, -1.950903220e-01f, -9.801714033e-02f,
+};
+constexpr float kRsqrt2 = 0.7071067811865475244f;
+
+__host__ __device__ constexpr int log_radix(int logn) {
+  return logn == 6 ? 3 : (logn == 5 || logn == 9 || logn == 10) ? 5 : 4;
+}
+
+__host__ __device__ constexpr int bitrev(int k, int bits) {
+  int r = 0;
+  for (int i = 0; i < bits; ++i) r = (r << 1) | ((k >> i) & 1);
+  return r;
+}
+
+// Factorisation of one FFT length: L passes of radix R, then (if R2 > 1) one pass of
+// radix R2 in which each thread runs B = R / R2 butterflies. P threads per transform.
+template <int LOGN>
+struct Shape {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int LOGR = log_radix(LOGN);
+  static constexpr int R = 1 << LOGR;
+  static constexpr int P = N / R;
+  static constexpr int L = LOGN / LOGR;
+  static constexpr int LOGR2 = LOGN - L * LOGR;
+  static constexpr int R2 = 1 << LOGR2;
+  static constexpr int B = R / R2;
+  static constexpr int NPASS = L + (R2 > 1 ? 1 : 0);
+  static constexpr int PADN = N + (N >> LOGR);  // padded shared-memory length
+};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// x * w_N^I with w_N = exp(+2 pi i / N), N <= 64, I < N/2: compile-time constants.
+template <int N, int I>
+__device__ __forceinline__ float2 tw_mul(float2 x) {
+  constexpr int M = (I * (64 / N)) & 63;
+  if constexpr (M == 0) {
+    return x;
+  } else if constexpr (M == 16) {
+    return make_float2(-x.y, x.x);
+  } else if constexpr (M == 8) {
+    return make_float2((x.x - x.y) * kRsqrt2, (x.x + x.y) * kRsqrt2);
+  } else if constexpr (M == 24) {
+    return make_float2(-(x.x + x.y) * kRsqrt2, (x.x - x.y) * kRsqrt2);
+  } else {
+    constexpr float c = kCos64[M], s = kSin64[M];
+    return make_float2(fmaf(x.x, c, -x.y * s), fmaf(x.x, s, x.y * c));
+  }
+}
+
+// Radix-2 decimation in frequency over v[O], v[O+S], ..., v[O+(N-1)S]; the result is
+// left in bit-reversed order: v[O + S*bitrev(k)] = X[k].
+template <int N, int S, int O, int I, int RR>
+__device__ __forceinline__ void dif_level(float2 (&v)[RR]) {
+  if constexpr (I < N / 2) {
+    const float2 a = v[O + I * S], b = v[O + (I + N / 2) * S];
+    v[O + I * S] = make_float2(a.x + b.x, a.y + b.y);
+    v[O + (I + N / 2) * S] = tw_mul<N, I>(make_float2(a.x - b.x, a.y - b.y));
+    dif_level<N, S, O, I + 1, RR>(v);
+  }
+}
+template <int N, int S, int O, int RR>
+__device__ __forceinline__ void dif(float2 (&v)[RR]) {
+  if constexpr (N > 1) {
+    dif_level<N, S, O, 0, RR>(v);
+    dif<N / 2, S, O, RR>(v);
+    dif<N / 2, S, O + (N / 2) * S, RR>(v);
+  }
+}
+template <int N, int S, int Q, int RR>
+__device__ __forceinline__ void dif_each(float2 (&v)[RR]) {
+  if constexpr (Q < S) {
+    dif<N, S, Q, RR>(v);
+    dif_each<N, S, Q + 1, RR>(v);
+  }
+}
+
+// One length-N transform spread over P threads (index j). On entry v[r] = x[j + r P];
+// on exit element j + i P of the transform is v[out_reg(i)].
+template <int LOGN, bool CTA_SYNC>
+struct Engine {
+  using S = Shape<LOGN>;
+  static __device__ __forceinline__ void sync() {
+    if constexpr (CTA_SYNC) __syncthreads(); else __syncwarp();
+  }
+  static __device__ __forceinline__ int pad(int i) { return i + (i >> S::LOGR); }
+  static __host__ __device__ constexpr int out_reg(int i) {
+    return S::R2 == 1 ? bitrev(i, S::LOGR)
+                      : (i % S::B) + S::B * bitrev(i / S::B, S::LOGR2);
+  }
+
+  static __device__ __forceinline__ void run(float2 (&v)[S::R], float2 *sm, int j,
+                                             const float2 *__restrict__ tw) {
+    dif<S::R, 1, 0, S::R>(v);  // pass 0 (span 1): no inter-pass twiddles
+    if constexpr (S::NPASS > 1) {
+      sync();  // earlier readers of sm are done
+#pragma unroll
+      for (int r = 0; r < S::R; ++r) sm[pad(j * S::R + r)] = v[bitrev(r, S::LOGR)];
+      sync();
+      int tw_off = 0;
+#pragma unroll
+      for (int p = 1; p < S::L; ++p) {
+        const int Ns = 1 << (p * S::LOGR);
+#pragma unroll
+        for (int r = 0; r < S::R; ++r) v[r] = sm[pad(j + r * S::P)];
+        const int m = j & (Ns - 1);
+#pragma unroll
+        for (int r = 1; r < S::R; ++r) v[r] = cmul(v[r], __ldg(&tw[tw_off + (r - 1) * Ns + m]));
+        tw_off += (S::R - 1) * Ns;
+        dif<S::R, 1, 0, S::R>(v);
+        if (p == S::L - 1 && S::R2 == 1) return;
+        sync();
+        const int base = (j >> (p * S::LOGR)) * Ns * S::R + m;
+#pragma unroll
+        for (int r = 0; r < S::R; ++r) sm[pad(base + r * Ns)] = v[bitrev(r, S::LOGR)];
+        sync();
+      }
+      if constexpr (S::R2 > 1) {
+        constexpr int NsE = 1 << (S::L * S::LOGR);
+#pragma unroll
+        for (int i = 0; i < S::R; ++i) v[i] = sm[pad(j + i * S::P)];
+#pragma unroll
+        for (int q = 0; q < S::B; ++q) {
+          const int b = j + q * S::P;
+#pragma unroll
+          for (int r2 = 1; r2 < S::R2; ++r2)
+            v[q + S::B * r2] = cmul(v[q + S::B * r2], __ldg(&tw[tw_off + (r2 - 1) * NsE + b]));
+        }
+        dif_each<S::R2, S::B, 0, S::R>(v);
+      }
+    }
+  }
+};
+
+template <int LOGN>
+__host__ __device__ constexpr int row_fpc() { return Shape<LOGN>::P >= 256 ? 1 : (256 / Shape<LOGN>::P < 16 ? 256 / Shape<LOGN>::P : 16); }
+template <int LOGN>
+__host__ __device__ constexpr int col_fpc() {
+  // columns per CTA: wide enough for >= 32-byte segments where registers allow
+  return Shape<LOGN>::P <= 16 ? 16 : Shape<LOGN>::P == 32 ? 8 : Shape<LOGN>::P == 128 ? 4 : 2;
+}
+template <int LOGN>
+__host__ __device__ constexpr int row_stride() { return Shape<LOGN>::PADN; }
+template <int LOGN>
+__host__ __device__ constexpr int col_stride() {
+  constexpr int t = 16 / col_fpc<LOGN>();
+  constexpr int pn = Shape<LOGN>::PADN;
+  return pn + (((t - pn % 16) % 16) + 16) % 16;
+}
+
+// Row pass: frames (uint16) -> mid (FP32 complex), chirped, transformed along x.
+template <int LOGN>
+__global__ void __launch_bounds__(row_fpc<LOGN>() * Shape<LOGN>::P)
+k_render_rows(const uint16_t *__restrict__ frames, long long frame_stride, int ny,
+              const float2 *__restrict__ cx, const float2 *__restrict__ cy,
+              const float2 *__restrict__ tw, float2 *__restrict__ mid, int n_items) {
+  using S = Shape<LOGN>;
+  constexpr int FPC = row_fpc<LOGN>();
+  using E = Engine<LOGN, (S::P > 32)>;
+  extern __shared__ float2 smem[];
+  const int fft = threadIdx.x / S::P, j = threadIdx.x % S::P;
+  float2 *sm = smem + fft * row_stride<LOGN>();
+  const int groups = ny / FPC;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int f = item / groups;
+    const int y = (item % groups) * FPC + fft;
+    const uint16_t *src = frames + (long long)f * frame_stride + (long long)y * S::N;
+    float2 v[S::R];
+#pragma unroll
+    for (int r = 0; r < S::R; ++r) {
+      const int x = j + r * S::P;
+      const float a = (float)__ldg(src + x);
+      const float2 c = __ldg(cx + x);
+      v[r] = make_float2(a * c.x, a * c.y);
+    }
+    E::run(v, sm, j, tw);
+    const float2 cyy = __ldg(cy + y);
+    float2 *dst = mid + ((long long)f * ny + y) * S::N;
+#pragma unroll
+    for (int i = 0; i < S::R; ++i) dst[j + i * S::P] = cmul(v[E::out_reg(i)], cyy);
+  }
+}
+
+template <typename T> __device__ __forceinline__ T to_store(float x);
+template <> __device__ __forceinline__ float to_store<float>(float x) { return x; }
+template <> __device__ __forceinline__ __half to_store<__half>(float x) { return __float2half_rn(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(float x) {
+  return __float2bfloat16_rn(x);
+}
+template <typename T> __device__ __forceinline__ bool stored_finite(T h);
+template <> __device__ __forceinline__ bool stored_finite<float>(float h) { return isfinite(h); }
+template <> __device__ __forceinline__ bool stored_finite<__half>(__half h) {
+  return isfinite(__half2float(h));
+}
+template <> __device__ __forceinline__ bool stored_finite<__nv_bfloat16>(__nv_bfloat16 h) {
+  return isfinite(__bfloat162float(h));
+}
+
+// Column pass: mid -> hologram planes (re plane, im plane) of slot slot0 + f.
+template <int LOGN, typename OutT>
+__global__ void __launch_bounds__(col_fpc<LOGN>() * Shape<LOGN>::P)
+k_render_cols(const float2 *__restrict__ mid, int nx, const float2 *__restrict__ tw,
+              OutT *__restrict__ H, long long npix, int slot0, int n_items,
+              uint32_t *__restrict__ status) {
+  using S = Shape<LOGN>;
+  constexpr int FPC = col_fpc<LOGN>();
+  using E = Engine<LOGN, true>;
+  extern __shared__ float2 smem[];
+  const int fft = threadIdx.x % FPC, j = threadIdx.x / FPC;
+  float2 *sm = smem + fft * col_stride<LOGN>();
+  const int groups = nx / FPC;
+  bool finite = true;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int f = item / groups;
+    const int x = (item % groups) * FPC + fft;
+    // offsets inside one frame fit in 32 bits (n_x n_y <= 2^24)
+    const float2 *src = mid + (long long)f * npix + x;
+    const unsigned row_step = (unsigned)(S::P * nx);
+    unsigned off = (unsigned)(j * nx);
+    float2 v[S::R];
+#pragma unroll
+    for (int r = 0; r < S::R; ++r, off += row_step) v[r] = src[off];
+    E::run(v, sm, j, tw);
+    OutT *re = H + (long long)(slot0 + f) * 2 * npix + x;
+    OutT *im = re + npix;
+    off = (unsigned)(j * nx);
+#pragma unroll
+    for (int i = 0; i < S::R; ++i, off += row_step) {
+      const float2 o = v[E::out_reg(i)];
+      const OutT a = to_store<OutT>(o.x), b = to_store<OutT>(o.y);
+      finite &= stored_finite<OutT>(a) & stored_finite<OutT>(b);
+      re[off] = a;
+      im[off] = b;
+    }
+  }
+  if (!finite) atomicOr(status, DH_FLAG_STORE_OVERFLOW);
+}
+
+template <typename T>
+__global__ void k_hologram_to_f32(const T *__restrict__ H, long long npix, float *__restrict__ out) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
+       p += (long long)gridDim.x * blockDim.x) {
+    float r, i;
+    if constexpr (sizeof(T) == 4) { r = H[p]; i = H[p + npix]; }
+    else if constexpr (std::is_same<T, __half>::value) { r = __half2float(H[p]); i = __half2float(H[p + npix]); }
+    else { r = __bfloat162float(H[p]); i = __bfloat162float(H[p + npix]); }
+    out[2 * p] = r;
+    out[2 * p + 1] = i;
+  }
+}
+
+// ----------------------------------------------------------------- host side
+struct RowLaunch {
+  int threads, fpc;
+  size_t smem;
+};
+
+template <int LOGN>
+dh_status launch_rows_t(const uint16_t *frames, long long fstride, int ny, const Plan &p,
+                        float2 *mid, int nf, cudaStream_t s) {
+  using S = Shape<LOGN>;
+  constexpr int FPC = row_fpc<LOGN>();
+  const int threads = FPC * S::P;
+  const size_t smem = S::NPASS > 1 ? (size_t)FPC * row_stride<LOGN>() * sizeof(float2) : 0;
+  auto kern = k_render_rows<LOGN>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    DH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set = true;
+  }
+  int per_sm = 0;
+  DH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+  const int items = nf * (ny / FPC);
+  int grid = per_sm * p.num_sms;
+  if (grid < 1) grid = 1;
+  if (grid > items) grid = items;
+  ProfScope ps(const_cast<Plan &>(p), K_RENDER_ROWS, s);
+  kern<<<grid, threads, smem, s>>>(frames, fstride, ny, p.d_cx, p.d_cy, p.d_twx, mid, items);
+  DH_CUDA_TRY(cudaGetLastError());
+  return DH_OK;
+}
+
+template <int LOGN, typename OutT>
+dh_status launch_cols_t(const Plan &p, const float2 *mid, int nf, int slot0, cudaStream_t s) {
+  using S = Shape<LOGN>;
+  constexpr int FPC = col_fpc<LOGN>();
+  const int threads = FPC * S::P;
+  const size_t smem = S::NPASS > 1 ? (size_t)FPC * col_stride<LOGN>() * sizeof(float2) : 0;
+  auto kern = k_render_cols<LOGN, OutT>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    DH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set = true;
+  }
+  int per_sm = 0;
+  DH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+  const int items = nf * (p.nx / FPC);
+  int grid = per_sm * p.num_sms;
+  if (grid < 1) grid = 1;
+  if (grid > items) grid = items;
+  ProfScope ps(const_cast<Plan &>(p), K_RENDER_COLS, s);
+  kern<<<grid, threads, smem, s>>>(mid, p.nx, p.d_twy, static_cast<OutT *>(p.d_H), p.npix,
+                                    slot0, items, p.d_status);
+  DH_CUDA_TRY(cudaGetLastError());
+  return DH_OK;
+}
+
+dh_status launch_rows(const Plan &p, const uint16_t *frames, long long fstride, float2 *mid,
+                      int nf, cudaStream_t s) {
+  switch (p.lognx) {
+    case 4: return launch_rows_t<4>(frames, fstride, p.ny, p, mid, nf, s);
+    case 5: return launch_rows_t<5>(frames, fstride, p.ny, p, mid, nf, s);
+    case 6: return launch_rows_t<6>(frames, fstride, p.ny, p, mid, nf, s);
+    case 7: return launch_rows_t<7>(frames, fstride, p.ny, p, mid, nf, s);
+    case 8: return launch_rows_t<8>(frames, fstride, p.ny, p, mid, nf, s);
+    case 9: return launch_rows_t<9>(frames, fstride, p.ny, p, mid, nf, s);
+    case 10: return launch_rows_t<10>(frames, fstride, p.ny, p, mid, nf, s);
+    case 11: return launch_rows_t<11>(frames, fstride, p.ny, p, mid, nf, s);
+    case 12: return launch_rows_t<12>(frames, fstride, p.ny, p, mid, nf, s);
+  }
+  return DH_ERR_UNSUPPORTED_SIZE;
+}
+
+template <typename OutT>
+dh_status launch_cols_typed(const Plan &p, const float2 *mid, int nf, int slot0, cudaStream_t s) {
+  switch (p.logny) {
+    case 4: return launch_cols_t<4, OutT>(p, mid, nf, slot0, s);
+    case 5: return launch_cols_t<5, OutT>(p, mid, nf, slot0, s);
+    case 6: return launch_cols_t<6, OutT>(p, mid, nf, slot0, s);
+    case 7: return launch_cols_t<7, OutT>(p, mid, nf, slot0, s);
+    case 8: return launch_cols_t<8, OutT>(p, mid, nf, slot0, s);
+    case 9: return launch_cols_t<9, OutT>(p, mid, nf, slot0, s);
+    case 10: return launch_cols_t<10, OutT>(p, mid, nf, slot0, s);
+    case 11: return launch_cols_t<11, OutT>(p, mid, nf, slot0, s);
+    case 12: return launch_cols_t<12, OutT>(p, mid, nf, slot0, s);
+  }
+  return DH_ERR_UNSUPPORTED_SIZE;
+}
+
+}  // namespace
+
+int twiddle_len(int logn) {
+  const int logr = log_radix(logn), R = 1 << logr, L = logn / logr;
+  const int logr2 = logn - L * logr, R2 = 1 << logr2;
+  int len = 0;
+  for (int p = 1; p < L; ++p) len += (R - 1) * (1 << (p * logr));
+  if (R2 > 1) len += (R2 - 1) * (1 << (L * logr));
+  return len > 0 ? len : 1;
+}
+
+// Inter-pass twiddles w_M^e = exp(+2 pi i e / M), the exponent reduced exactly in integers
+// before the angle is formed in FP64.
+void build_twiddles(int logn, float2 *out) {
+  const int logr = log_radix(logn), R = 1 << logr, L = logn / logr;
+  const int logr2 = logn - L * logr, R2 = 1 << logr2, N = 1 << logn;
+  const double two_pi = 6.283185307179586476925286766559;
+  auto w = [&](long long e, long long M) {
+    const double ang = two_pi * (double)(e % M) / (double)M;
+    return make_float2((float)cos(ang), (float)sin(ang));
+  };
+  int off = 0;
+  for (int p = 1; p < L; ++p) {
+    const int Ns = 1 << (p * logr);
+    for (int r = 1; r < R; ++r)
+      for (int m = 0; m < Ns; ++m) out[off + (r - 1) * Ns + m] = w((long long)m * r, (long long)Ns * R);
+    off += (R - 1) * Ns;
+  }
+  if (R2 > 1) {
+    const int Ns = 1 << (L * logr);
+    for (int r = 1; r < R2; ++r)
+      for (int m = 0; m < Ns; ++m) out[off + (r - 1) * Ns + m] = w((long long)m * r, N);
+  }
+  if (off == 0 && R2 == 1) out[0] = make_float2(1.f, 0.f);
+}
+
+dh_status launch_render(Plan &p, const uint16_t *frames, long long frame_stride, int n_frames,
+                        int slot0, cudaStream_t s) {
+  for (int f0 = 0; f0 < n_frames; f0 += p.mid_frames) {
+    const int nf = (n_frames - f0) < p.mid_frames ? (n_frames - f0) : p.mid_frames;
+    dh_status st = launch_rows(p, frames + (long long)f0 * frame_stride, frame_stride, p.d_mid, nf, s);
+    if (st != DH_OK) return st;
+    switch (p.prec) {
+      case DH_PREC_FP32: st = launch_cols_typed<float>(p, p.d_mid, nf, slot0 + f0, s); break;
+      case DH_PREC_FP16: st = launch_cols_typed<__half>(p, p.d_mid, nf, slot0 + f0, s); break;
+      case DH_PREC_BF16: st = launch_cols_typed<__nv_bfloat16>(p, p.d_mid, nf, slot0 + f0, s); break;
+    }
+    if (st != DH_OK) return st;
+  }
+  return DH_OK;
+}
+
+dh_status launch_hologram_to_f32(Plan &p, int slot, float *out, cudaStream_t s) {
+  const int grid = p.num_sms * 4;
+  const long long off = (long long)slot * 2 * p.npix;
+  switch (p.prec) {
+    case DH_PREC_FP32:
+      k_hologram_to_f32<float><<<grid, 256, 0, s>>>(static_cast<float *>(p.d_H) + off, p.npix, out);
+      break;
+    case DH_PREC_FP16:
+      k_hologram_to_f32<__half><<<grid, 256, 0, s>>>(static_cast<__half *>(p.d_H) + off, p.npix, out);
+      break;
+    case DH_PREC_BF16:
+      k_hologram_to_f32<__nv_bfloat16>
+          <<<grid, 256, 0, s>>>(static_cast<__nv_bfloat16 *>(p.d_H) + off, p.npix, out);
+      break;
+  }
+  DH_CUDA_TRY(cudaGetLastError());
+  return DH_OK;
+}
+
+}  // namespace dh
