@@ -199,18 +199,19 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    nframes = NWIN * T
+    nwin = args.windows
+    nframes = nwin * T
     # config-1 stream: seed 1000 * config + rank, 2048 frames resident in HBM (4 GiB > L2)
     frames = SpeckleStream(SpeckleParams(NX, NY), seed=1000 + rank, device=dev).next(nframes)
     npix = NX * NY
 
     plan = dh.Plan(NX, NY, LAM, Z, PITCH, T=T, precision=args.precision, max_frames=nframes,
-                   max_windows=NWIN)
-    images = torch.empty((NWIN, NY, NX), dtype=torch.float32, device=dev)
-    eig = torch.empty((NWIN, T), dtype=torch.float64, device=dev)
+                   max_windows=nwin)
+    images = torch.empty((nwin, NY, NX), dtype=torch.float32, device=dev)
+    eig = torch.empty((nwin, T), dtype=torch.float64, device=dev)
 
     def step(p):
-        p.pca_batch(frames, NWIN, T, K0, K1, images, eig)
+        p.pca_batch(frames, nwin, T, K0, K1, images, eig)
 
     for _ in range(max(args.warmup, 0)):
         step(plan)
@@ -236,13 +237,13 @@ def run_ours(args, ws, rank, local):
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     ms = ev[0].elapsed_time(ev[-1]) / args.steps
     ms_max = max_over_ranks(ms, ws)
-    value = whole_job_rate(NWIN, ws, ms_max)
+    value = whole_job_rate(nwin, ws, ms_max)
     flags = plan.status()
 
     # ---------------------------------------------------------------- roofline
     hbm, bf16_peak, peak_kind = measured_peaks()
     hbytes = 2 if args.precision in ("fp16", "bf16") else 4
-    alg = algorithmic_bytes(npix, nframes, NWIN, T, hbytes)
+    alg = algorithmic_bytes(npix, nframes, nwin, T, hbytes)
     per_kernel = {}
     launches_total = 0
     for name, (n, tot) in prof.items():
@@ -276,7 +277,7 @@ def run_ours(args, ws, rank, local):
 
         def e2e_step():
             dev_frames.copy_(host_frames, non_blocking=True)
-            plan.pca_batch(dev_frames, NWIN, T, K0, K1, images, eig)
+            plan.pca_batch(dev_frames, nwin, T, K0, K1, images, eig)
             host_images.copy_(images, non_blocking=True)
             host_eig.copy_(eig, non_blocking=True)
 
@@ -289,7 +290,7 @@ def run_ours(args, ws, rank, local):
             e2e_step()
         torch.cuda.synchronize()
         e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / n_e2e, ws)
-        e2e = {"value": whole_job_rate(NWIN, ws, e_ms), "unit": UNIT,
+        e2e = {"value": whole_job_rate(nwin, ws, e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(host_frames.numel() * 2),
                "d2h_bytes_per_step": int(host_images.numel() * 4 + host_eig.numel() * 8),
                "ms_per_step": e_ms}
@@ -299,7 +300,7 @@ def run_ours(args, ws, rank, local):
     plain = None
     if not args.no_plain and args.precision != "fp32":
         p32 = dh.Plan(NX, NY, LAM, Z, PITCH, T=T, precision="fp32", max_frames=nframes,
-                      max_windows=NWIN)
+                      max_windows=nwin)
         step(p32)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -310,7 +311,7 @@ def run_ours(args, ws, rank, local):
         b.record(stream)
         torch.cuda.synchronize()
         ms32 = max_over_ranks(a.elapsed_time(b) / n32, ws)
-        plain = {"value": whole_job_rate(NWIN, ws, ms32), "unit": UNIT, "ms_per_step": ms32}
+        plain = {"value": whole_job_rate(nwin, ws, ms32), "unit": UNIT, "ms_per_step": ms32}
         p32.close()
         step(plan)  # the headline plan's images again for the parity sample below
         torch.cuda.synchronize()
@@ -342,7 +343,7 @@ def run_ours(args, ws, rank, local):
             "dtype": "mixed: f32 FFT, f16 tensor-core products (f32 accumulate), f64 eig",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "T": T,
-                       "windows_per_step": NWIN, "frames_per_step": nframes, "k0": K0, "k1": K1,
+                       "windows_per_step": nwin, "frames_per_step": nframes, "k0": K0, "k1": K1,
                        "precision": args.precision,
                        "l2": "no flush: 4 GiB of input frames per step exceed the 126 MB L2",
                        "parallelism": f"replicas x{ws}"},
@@ -370,6 +371,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp16", "bf16", "fp32"], default="fp16")
+    ap.add_argument("--windows", type=int, default=NWIN,
+                    help="windows per step (default 64; smaller only for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

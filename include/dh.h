@@ -90,8 +90,9 @@ size_t dh_plan_device_bytes(dh_plan_t plan);
 
 /* Eq. 1 for n_frames frames: frame i (uint16, row-major n_y x n_x, caller-owned device
  * memory at frames_dev + i * frame_stride_elems) is rendered into hologram slot
- * first_slot + i. Requires frame_stride_elems >= n_x n_y and the slots within the
- * reservation. Asynchronous. */
+ * first_slot + i. Requires frame_stride_elems >= n_x n_y and a multiple of 8,
+ * frames_dev 16-byte aligned (frames are read with 16-byte loads), and the slots within
+ * the reservation; otherwise DH_ERR_INVALID_ARG. Asynchronous. */
 dh_status dh_render_frames(dh_plan_t plan, const uint16_t *frames_dev,
                            int64_t frame_stride_elems, int n_frames, int first_slot,
                            void *stream);

@@ -222,6 +222,9 @@ dh_status dh_render_frames(dh_plan_t h, const uint16_t *frames_dev, int64_t fram
   Plan &p = h->p;
   if (frame_stride_elems < p.npix || (long long)first_slot + n_frames > p.max_frames)
     return DH_ERR_INVALID_ARG;
+  // frames are read with 16-byte vector loads
+  if ((reinterpret_cast<uintptr_t>(frames_dev) & 15u) != 0 || (frame_stride_elems & 7) != 0)
+    return DH_ERR_INVALID_ARG;
   Busy g(h->busy);
   if (!g.ok) return DH_ERR_STATE;
   return launch_render(p, frames_dev, frame_stride_elems, n_frames, first_slot,

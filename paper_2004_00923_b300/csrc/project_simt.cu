@@ -12,7 +12,7 @@ template <int T>
 __global__ void __launch_bounds__(256)
 k_project_simt(const float *__restrict__ H, long long npix, int first_slot, int slot_stride,
                const float *__restrict__ Bop, long long B_stride, int nrows, int blocks_per_window,
-               float *__restrict__ images) {
+               int nx, int ny, float *__restrict__ images) {
   constexpr int M = 2 * T;
   extern __shared__ float4 bs4[];
   const int w = blockIdx.x / blocks_per_window, b = blockIdx.x % blocks_per_window;
@@ -41,7 +41,7 @@ k_project_simt(const float *__restrict__ H, long long npix, int first_slot, int 
       }
       m = fmaf(acc, acc, m);
     }
-    img[p] = m;
+    img[(p % ny) * nx + p / ny] = m;  // holograms are column-major: p = kx n_y + ky
   }
 }
 
@@ -62,7 +62,7 @@ dh_status launch_t(Plan &p, int first_slot, int slot_stride, int n_windows, int 
   ProfScope ps(p, K_PROJECT_SIMT, s);
   k_project_simt<T><<<(int)(n_windows * bpw), 256, smem, s>>>(
       static_cast<const float *>(p.d_H), p.npix, first_slot, slot_stride,
-      static_cast<const float *>(p.d_B), B_stride, nrows, (int)bpw, images);
+      static_cast<const float *>(p.d_B), B_stride, nrows, (int)bpw, p.nx, p.ny, images);
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
 }

@@ -4,8 +4,12 @@
 //   c(k) = exp(-i pi a (k - n/2)^2),  a = pitch^2 / (lambda z),  s = 1/sqrt(n_x n_y).
 //
 // Two passes over each frame, both on FP32 CUDA cores:
-//   rows:    uint16 load -> x chirp (scale folded in) -> n_x-point FFT -> y chirp -> mid
-//   columns: mid (L2-resident chunk of frames) -> n_y-point FFT -> 16/32-bit planes of H
+//   rows:    uint16 load -> x chirp (scale folded in) -> n_x-point FFT -> y chirp ->
+//            mid, written transposed (mid[f][kx][y]) through a shared staging tile
+//   columns: mid (L2-resident chunk of frames, read contiguously) -> n_y-point FFT ->
+//            16/32-bit planes of H in column-major pixel order p = kx n_y + ky
+// Every transform is done by P threads of one warp (or of one CTA for n >= 2048), with
+// coalesced global loads and stores on both passes.
 // The FFT is a Stockham auto-sort transform (Govindaraju et al., SC'08 formulation):
 // each thread keeps R points in registers, runs an in-register radix-R DIF transform with
 // compile-time twiddles, and exchanges through padded shared memory between passes.
@@ -82,6 +86,7 @@ struct Shape {
   static constexpr int B = R / R2;
   static constexpr int NPASS = L + (R2 > 1 ? 1 : 0);
   static constexpr int PADN = N + (N >> LOGR);  // padded shared-memory length
+  static constexpr int RSTRIDE = (PADN + 1) & ~1;  // per-transform region, 16-byte multiple
 };
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -190,53 +195,10 @@ struct Engine {
   }
 };
 
+// FFTs per CTA (256 threads, or one FFT when it needs more threads than that).
 template <int LOGN>
-__host__ __device__ constexpr int row_fpc() { return Shape<LOGN>::P >= 256 ? 1 : (256 / Shape<LOGN>::P < 16 ? 256 / Shape<LOGN>::P : 16); }
-template <int LOGN>
-__host__ __device__ constexpr int col_fpc() {
-  // columns per CTA: wide enough for >= 32-byte segments where registers allow
-  return Shape<LOGN>::P <= 16 ? 16 : Shape<LOGN>::P == 32 ? 8 : Shape<LOGN>::P == 128 ? 4 : 2;
-}
-template <int LOGN>
-__host__ __device__ constexpr int row_stride() { return Shape<LOGN>::PADN; }
-template <int LOGN>
-__host__ __device__ constexpr int col_stride() {
-  constexpr int t = 16 / col_fpc<LOGN>();
-  constexpr int pn = Shape<LOGN>::PADN;
-  return pn + (((t - pn % 16) % 16) + 16) % 16;
-}
-
-// Row pass: frames (uint16) -> mid (FP32 complex), chirped, transformed along x.
-template <int LOGN>
-__global__ void __launch_bounds__(row_fpc<LOGN>() * Shape<LOGN>::P)
-k_render_rows(const uint16_t *__restrict__ frames, long long frame_stride, int ny,
-              const float2 *__restrict__ cx, const float2 *__restrict__ cy,
-              const float2 *__restrict__ tw, float2 *__restrict__ mid, int n_items) {
-  using S = Shape<LOGN>;
-  constexpr int FPC = row_fpc<LOGN>();
-  using E = Engine<LOGN, (S::P > 32)>;
-  extern __shared__ float2 smem[];
-  const int fft = threadIdx.x / S::P, j = threadIdx.x % S::P;
-  float2 *sm = smem + fft * row_stride<LOGN>();
-  const int groups = ny / FPC;
-  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    const int f = item / groups;
-    const int y = (item % groups) * FPC + fft;
-    const uint16_t *src = frames + (long long)f * frame_stride + (long long)y * S::N;
-    float2 v[S::R];
-#pragma unroll
-    for (int r = 0; r < S::R; ++r) {
-      const int x = j + r * S::P;
-      const float a = (float)__ldg(src + x);
-      const float2 c = __ldg(cx + x);
-      v[r] = make_float2(a * c.x, a * c.y);
-    }
-    E::run(v, sm, j, tw);
-    const float2 cyy = __ldg(cy + y);
-    float2 *dst = mid + ((long long)f * ny + y) * S::N;
-#pragma unroll
-    for (int i = 0; i < S::R; ++i) dst[j + i * S::P] = cmul(v[E::out_reg(i)], cyy);
-  }
+__host__ __device__ constexpr int fpc() {
+  return Shape<LOGN>::P >= 256 ? 1 : (256 / Shape<LOGN>::P < 16 ? 256 / Shape<LOGN>::P : 16);
 }
 
 template <typename T> __device__ __forceinline__ T to_store(float x);
@@ -254,72 +216,146 @@ template <> __device__ __forceinline__ bool stored_finite<__nv_bfloat16>(__nv_bf
   return isfinite(__bfloat162float(h));
 }
 
-// Column pass: mid -> hologram planes (re plane, im plane) of slot slot0 + f.
+// Row pass: FPC consecutive rows of one frame per item. The next item's uint16 rows are
+// prefetched into registers with 16-byte loads while the current rows are transformed.
+// Each transform's input row is parked at the head of its own exchange region. Outputs
+// (times the y chirp) are written TRANSPOSED, mid[f][kx][y], through a swizzled shared
+// staging tile so that every store is a run of FPC consecutive y (64 bytes for FPC = 8).
+template <int LOGN>
+__global__ void __launch_bounds__(fpc<LOGN>() * Shape<LOGN>::P, (fpc<LOGN>() * Shape<LOGN>::P <= 256 ? 2 : 1))
+k_render_rows(const uint16_t *__restrict__ frames, long long frame_stride, int ny,
+              const float2 *__restrict__ cx, const float2 *__restrict__ cy,
+              const float2 *__restrict__ tw, float2 *__restrict__ mid, int n_items) {
+  using S = Shape<LOGN>;
+  constexpr int FPC = fpc<LOGN>();
+  constexpr int NT = FPC * S::P;                // threads
+  constexpr int CHUNKS = FPC * S::N / 8;        // 16-byte chunks of the uint16 rows
+  constexpr int CPT = CHUNKS / NT;              // chunks per thread (= R / 8)
+  constexpr int CPR = S::N / 8;                 // chunks per row
+  using E = Engine<LOGN, (S::P > 32)>;
+  extern __shared__ float2 smem[];
+  const int fft = threadIdx.x / S::P, j = threadIdx.x % S::P;
+  float2 *sm = smem + fft * S::RSTRIDE;
+  const int groups = ny / FPC;
+  const long long npix = (long long)S::N * ny;
+
+  uint4 pf[CPT];
+  auto prefetch = [&](int item) {
+    const int f = item / groups, y0 = (item % groups) * FPC;
+    const uint4 *src = reinterpret_cast<const uint4 *>(frames + (long long)f * frame_stride + (long long)y0 * S::N);
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) pf[k] = __ldg(src + threadIdx.x + k * NT);
+  };
+  if (blockIdx.x < n_items) prefetch(blockIdx.x);
+
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int f = item / groups, y0 = (item % groups) * FPC;
+    __syncthreads();  // previous item's staging tile fully read
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {  // park each row at the head of its transform's region
+      const int c = threadIdx.x + k * NT, row = c / CPR, cr = c % CPR;
+      reinterpret_cast<uint4 *>(smem + row * S::RSTRIDE)[cr] = pf[k];
+    }
+    if (item + (int)gridDim.x < n_items) prefetch(item + gridDim.x);
+    __syncthreads();
+    const uint16_t *row16 = reinterpret_cast<const uint16_t *>(sm);
+    float2 v[S::R];
+#pragma unroll
+    for (int r = 0; r < S::R; ++r) {
+      const int x = j + r * S::P;
+      const float a = (float)row16[x];
+      const float2 c = __ldg(cx + x);
+      v[r] = make_float2(a * c.x, a * c.y);
+    }
+    E::run(v, sm, j, tw);  // its first exchange store is ordered after the reads above
+    const float2 cyy = __ldg(cy + y0 + fft);
+    __syncthreads();  // every transform is done with its exchange region
+    // staging tile [kx][y], y swizzled by kx so that both phases are conflict-free
+#pragma unroll
+    for (int i = 0; i < S::R; ++i) {
+      const int kx = j + i * S::P;
+      smem[kx * FPC + (fft ^ (kx & (FPC - 1)))] = cmul(v[E::out_reg(i)], cyy);
+    }
+    __syncthreads();
+    float2 *dst = mid + (long long)f * npix + y0;
+    if constexpr (FPC >= 2) {
+      constexpr int QPK = FPC / 2;  // 16-byte chunks per kx run
+      for (int c = threadIdx.x; c < S::N * QPK; c += NT) {
+        const int kx = c / QPK, q = c % QPK, m = kx & (FPC - 1);
+        float4 t = *reinterpret_cast<const float4 *>(&smem[kx * FPC + ((2 * q) ^ (m & ~1))]);
+        if (m & 1) t = make_float4(t.z, t.w, t.x, t.y);
+        *reinterpret_cast<float4 *>(&dst[(long long)kx * ny + 2 * q]) = t;
+      }
+    } else {
+      for (int kx = threadIdx.x; kx < S::N; kx += NT) dst[(long long)kx * ny] = smem[kx];
+    }
+  }
+}
+
+// Column pass: FPC columns of one frame per item, one transform per P threads, reading the
+// transposed intermediate mid[f][kx][y] contiguously and writing the hologram planes in
+// column-major pixel order p = kx n_y + ky (re plane, then im plane, of slot slot0 + f).
 template <int LOGN, typename OutT>
-__global__ void __launch_bounds__(col_fpc<LOGN>() * Shape<LOGN>::P)
+__global__ void __launch_bounds__(fpc<LOGN>() * Shape<LOGN>::P, (fpc<LOGN>() * Shape<LOGN>::P <= 256 ? 3 : 1))
 k_render_cols(const float2 *__restrict__ mid, int nx, const float2 *__restrict__ tw,
               OutT *__restrict__ H, long long npix, int slot0, int n_items,
               uint32_t *__restrict__ status) {
   using S = Shape<LOGN>;
-  constexpr int FPC = col_fpc<LOGN>();
-  using E = Engine<LOGN, true>;
+  constexpr int FPC = fpc<LOGN>();
+  using E = Engine<LOGN, (S::P > 32)>;
   extern __shared__ float2 smem[];
-  const int fft = threadIdx.x % FPC, j = threadIdx.x / FPC;
-  float2 *sm = smem + fft * col_stride<LOGN>();
+  const int fft = threadIdx.x / S::P, j = threadIdx.x % S::P;
+  float2 *sm = smem + fft * S::RSTRIDE;
   const int groups = nx / FPC;
   bool finite = true;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     const int f = item / groups;
-    const int x = (item % groups) * FPC + fft;
-    // offsets inside one frame fit in 32 bits (n_x n_y <= 2^24)
-    const float2 *src = mid + (long long)f * npix + x;
-    const unsigned row_step = (unsigned)(S::P * nx);
-    unsigned off = (unsigned)(j * nx);
+    const int kx = (item % groups) * FPC + fft;
+    const float2 *src = mid + (long long)f * npix + (long long)kx * S::N;
     float2 v[S::R];
 #pragma unroll
-    for (int r = 0; r < S::R; ++r, off += row_step) v[r] = src[off];
+    for (int r = 0; r < S::R; ++r) v[r] = src[j + r * S::P];
     E::run(v, sm, j, tw);
-    OutT *re = H + (long long)(slot0 + f) * 2 * npix + x;
+    OutT *re = H + (long long)(slot0 + f) * 2 * npix + (long long)kx * S::N;
     OutT *im = re + npix;
-    off = (unsigned)(j * nx);
 #pragma unroll
-    for (int i = 0; i < S::R; ++i, off += row_step) {
+    for (int i = 0; i < S::R; ++i) {
       const float2 o = v[E::out_reg(i)];
       const OutT a = to_store<OutT>(o.x), b = to_store<OutT>(o.y);
       finite &= stored_finite<OutT>(a) & stored_finite<OutT>(b);
-      re[off] = a;
-      im[off] = b;
+      re[j + i * S::P] = a;
+      im[j + i * S::P] = b;
     }
   }
   if (!finite) atomicOr(status, DH_FLAG_STORE_OVERFLOW);
 }
 
+// Inspection: slot planes (column-major pixels p = kx n_y + ky) to interleaved FP32 in
+// row-major order.
 template <typename T>
-__global__ void k_hologram_to_f32(const T *__restrict__ H, long long npix, float *__restrict__ out) {
+__global__ void k_hologram_to_f32(const T *__restrict__ H, int nx, int ny, float *__restrict__ out) {
+  const long long npix = (long long)nx * ny;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
        p += (long long)gridDim.x * blockDim.x) {
     float r, i;
     if constexpr (sizeof(T) == 4) { r = H[p]; i = H[p + npix]; }
     else if constexpr (std::is_same<T, __half>::value) { r = __half2float(H[p]); i = __half2float(H[p + npix]); }
     else { r = __bfloat162float(H[p]); i = __bfloat162float(H[p + npix]); }
-    out[2 * p] = r;
-    out[2 * p + 1] = i;
+    const long long kx = p / ny, ky = p % ny;
+    out[2 * (ky * nx + kx)] = r;
+    out[2 * (ky * nx + kx) + 1] = i;
   }
 }
 
 // ----------------------------------------------------------------- host side
-struct RowLaunch {
-  int threads, fpc;
-  size_t smem;
-};
-
 template <int LOGN>
 dh_status launch_rows_t(const uint16_t *frames, long long fstride, int ny, const Plan &p,
                         float2 *mid, int nf, cudaStream_t s) {
   using S = Shape<LOGN>;
-  constexpr int FPC = row_fpc<LOGN>();
+  constexpr int FPC = fpc<LOGN>();
   const int threads = FPC * S::P;
-  const size_t smem = S::NPASS > 1 ? (size_t)FPC * row_stride<LOGN>() * sizeof(float2) : 0;
+  // exchange regions (also the uint16 rows and the staging tile)
+  const size_t smem = (size_t)FPC * S::RSTRIDE * sizeof(float2);
   auto kern = k_render_rows<LOGN>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -341,9 +377,9 @@ dh_status launch_rows_t(const uint16_t *frames, long long fstride, int ny, const
 template <int LOGN, typename OutT>
 dh_status launch_cols_t(const Plan &p, const float2 *mid, int nf, int slot0, cudaStream_t s) {
   using S = Shape<LOGN>;
-  constexpr int FPC = col_fpc<LOGN>();
+  constexpr int FPC = fpc<LOGN>();
   const int threads = FPC * S::P;
-  const size_t smem = S::NPASS > 1 ? (size_t)FPC * col_stride<LOGN>() * sizeof(float2) : 0;
+  const size_t smem = S::NPASS > 1 ? (size_t)FPC * S::RSTRIDE * sizeof(float2) : 0;
   auto kern = k_render_cols<LOGN, OutT>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -452,14 +488,14 @@ dh_status launch_hologram_to_f32(Plan &p, int slot, float *out, cudaStream_t s) 
   const long long off = (long long)slot * 2 * p.npix;
   switch (p.prec) {
     case DH_PREC_FP32:
-      k_hologram_to_f32<float><<<grid, 256, 0, s>>>(static_cast<float *>(p.d_H) + off, p.npix, out);
+      k_hologram_to_f32<float><<<grid, 256, 0, s>>>(static_cast<float *>(p.d_H) + off, p.nx, p.ny, out);
       break;
     case DH_PREC_FP16:
-      k_hologram_to_f32<__half><<<grid, 256, 0, s>>>(static_cast<__half *>(p.d_H) + off, p.npix, out);
+      k_hologram_to_f32<__half><<<grid, 256, 0, s>>>(static_cast<__half *>(p.d_H) + off, p.nx, p.ny, out);
       break;
     case DH_PREC_BF16:
       k_hologram_to_f32<__nv_bfloat16>
-          <<<grid, 256, 0, s>>>(static_cast<__nv_bfloat16 *>(p.d_H) + off, p.npix, out);
+          <<<grid, 256, 0, s>>>(static_cast<__nv_bfloat16 *>(p.d_H) + off, p.nx, p.ny, out);
       break;
   }
   DH_CUDA_TRY(cudaGetLastError());

@@ -9,7 +9,7 @@
 //     stacked into one 128-row operand used as both A and B of a 128x128 MMA; the
 //     diagonal 2T x 2T blocks are the chunk Gram matrices (the off-diagonal blocks are
 //     discarded). Products of stored 16-bit values are exact in FP32; TMEM accumulators
-//     are flushed every few stages into per-thread compensated (Kahan) FP32 sums, and
+//     are flushed every stage into per-thread compensated (Kahan) FP32 sums, and
 //     the per-unit partials are reduced in FP64 by the covariance reduction kernel.
 //   * projection (Eqs. 6-7): P = X^T B^T per 128-pixel tile (A = X, MN-major), with B the
 //     real embedding of the retained eigenvectors split into hi + lo 16-bit parts (two
@@ -49,7 +49,10 @@ struct GramCfg {
   static constexpr int PIX = 64 * R;               // pixels per stage
   static constexpr int STAGE_BYTES = 128 * 128;    // 128 rows x 64 pixels x 2 bytes
   static constexpr int STAGES = 6;
-  static constexpr int GROUP = 8;                  // stages per TMEM flush
+  // Stages per TMEM flush. The tensor cores' FP32 accumulation rounds toward zero (measured:
+  // about -7e-8 relative per MMA instruction), so accumulators are drained into compensated
+  // sums after every stage of 4 MMAs, bounding that bias near 3e-7.
+  static constexpr int GROUP = 1;
   static constexpr int NCOL = M2 < 64 ? M2 : 64;   // columns each epilogue thread keeps
   static constexpr int EPI_WARPS = 4 * (M2 / NCOL);
   static constexpr int THREADS = 64 + 32 * EPI_WARPS;
@@ -213,8 +216,15 @@ template <int T, bool BF16>
 __global__ void __launch_bounds__(ProjCfg<T>::THREADS, 1)
 k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmB,
              int first_slot, int slot_stride, int n_windows, int tiles_pw, int Npad, int B_rows_pw,
-             float *__restrict__ images, long long npix, uint32_t *__restrict__ status) {
+             float *__restrict__ images, int nx, int ny, uint32_t *__restrict__ status) {
   using C = ProjCfg<T>;
+  const long long npix = (long long)nx * ny;
+  // Holograms are stored with column-major pixels p = kx n_y + ky. Tile t of a window starts
+  // at pixel tile_p(t); when a column holds whole tiles, consecutive tiles are adjacent
+  // columns, so the transposed image stores of consecutive tiles fill the same sectors.
+  auto tile_p = [&](int t) -> int {
+    return ny >= 128 ? (t % nx) * ny + (t / nx) * 128 : t * 128;
+  };
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = align1024(smem_raw);
   uint8_t *stages = smem;
@@ -260,7 +270,7 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
       bool b_pending = false;
       for (long long t = t_begin; t < t_end && !*abort_flag; ++t) {
         const int w = (int)(t / tiles_pw);
-        const int p = (int)(t % tiles_pw) * 128;
+        const int p = tile_p((int)(t % tiles_pw));
         if (w != cur_w) {  // eigenvector operand of this window
           if (!mbar_wait(bempty, bph ^ 1)) { fail(); break; }
           mbar_arrive_expect_tx(bfull, 2 * b_half_bytes);
@@ -337,7 +347,8 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
     int it = 0;
     for (long long t = t_begin; t < t_end && !__any_sync(0xffffffffu, *abort_flag); ++t, ++it) {
       const int w = (int)(t / tiles_pw);
-      const long long p = (t % tiles_pw) * 128 + 32 * q + lane;
+      const int p = tile_p((int)(t % tiles_pw)) + 32 * q + lane;
+      const int kx = p / ny, ky = p % ny;
       const int buf = it & 1;
       if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (it >> 1) & 1))) { fail(); break; }
       fence_after_sync();
@@ -350,7 +361,7 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
       }
       fence_before_sync();
       mbar_arrive(&acc_empty[buf]);
-      images[(long long)w * npix + p] = m;
+      images[(long long)w * npix + (long long)ky * nx + kx] = m;
     }
   }
   fence_before_sync();
@@ -439,7 +450,7 @@ dh_status project_t(Plan &p, int first_slot, int slot_stride, int n_windows, int
   if (grid > total) grid = (int)total;
   ProfScope ps(p, K_PROJECT_TC, s);
   kern<<<grid, C::THREADS, C::SMEM, s>>>(p.tmap_H, tmB, first_slot, slot_stride, n_windows, tiles_pw, Npad,
-                                          (int)B_rows_pw, images, p.npix, p.d_status);
+                                          (int)B_rows_pw, images, p.nx, p.ny, p.d_status);
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
 }

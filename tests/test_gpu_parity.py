@@ -249,7 +249,7 @@ def test_tc_kernels_exact_on_stored_values(dh, T, prec):
             C_gpu = plan.debug_covariance(w).cpu().numpy()
             V = plan.debug_eigvecs(w).cpu().numpy()
             C_exact = Hs.conj() @ Hs.T
-            assert rel(C_gpu, C_exact) < 2e-6
+            assert rel(C_gpu, C_exact) < 1e-6
             P = Hs.T @ V[:, 2:T]
             M_exact = np.sum(np.abs(P) ** 2, axis=1).reshape(ny, nx)
             # V's hi+lo split keeps ~22 (fp16) / ~16 (bf16) significant bits
