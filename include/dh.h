@@ -155,6 +155,23 @@ dh_status dh_profile_enable(dh_plan_t plan, int on);
  * NULL. Returns the number of kernel kinds the library has (write at most n entries). */
 int dh_profile_read(dh_plan_t plan, int n, const char **names, int *launches, double *total_ms);
 
+/* The covariance of one window (the C = H^{t*} H of Eq. 4) without any device
+ * allocation, for callers that cannot call cudaMalloc while running (for example a
+ * frame-grabber callback in a real-time acquisition loop, where an allocation can
+ * synchronise the device, or code whose device memory belongs to another allocator). The
+ * paper has no counterpart: it is a deployment variant of the covariance stage.
+ *   planes_dev: caller-owned device FP32 array [2T][npix]: row 2t = Re H_t, row 2t+1 = Im H_t
+ *               (pixels in any fixed order); npix a positive multiple of 32, <= 2^28.
+ *   T:          16, 32 or 64 (else DH_ERR_UNSUPPORTED_SIZE).
+ *   C_dev:      caller-owned device FP64 output, T x T interleaved (re, im), row-major.
+ * Products are FP32 with FP64 accumulation (as the plain path). The split-K scratch is a
+ * fixed 2 MiB device array inside the library (16 partial matrices at T = 64, 64 at
+ * T <= 32), held by every GPU that loads the library until exit. The first call on a device
+ * looks up that array's address (make it before any stream capture); all calls share the
+ * array, so calls that overlap on the GPU race. Asynchronous on `stream`. */
+dh_status dh_covariance_noalloc(const float *planes_dev, int64_t npix, int T, double *C_dev,
+                                void *stream);
+
 /* Text of a status code, and of the last CUDA error recorded by the library. */
 const char *dh_status_string(dh_status s);
 const char *dh_last_error(void);

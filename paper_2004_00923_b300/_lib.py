@@ -38,6 +38,7 @@ SIGNATURES = [
     ("dh_profile_enable", _i, [_vp, _i]),
     ("dh_profile_read", _i, [_vp, _i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_i),
                              ctypes.POINTER(_d)]),
+    ("dh_covariance_noalloc", _i, [_vp, _i64, _i, _vp, _vp]),
     ("dh_status_string", ctypes.c_char_p, [_i]),
     ("dh_last_error", ctypes.c_char_p, []),
     ("dh_version", ctypes.c_char_p, []),

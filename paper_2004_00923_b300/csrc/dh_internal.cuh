@@ -113,6 +113,12 @@ dh_status launch_project_tc(Plan &p, int first_slot, int slot_stride, int n_wind
                             float *images, cudaStream_t s);
 dh_status make_tensor_maps(Plan &p);
 
+// single-window helpers used by the allocation-free covariance entry point
+dh_status launch_gram_simt_rows(const float *X, long long npix, int T, int units, double *part,
+                                cudaStream_t s);
+dh_status launch_reduce_cov_window(const double *part, int parts, int T, double *C, uint32_t *status,
+                                   cudaStream_t s);
+
 // conversions for inspection
 dh_status launch_hologram_to_f32(Plan &p, int slot, float *out, cudaStream_t s);
 

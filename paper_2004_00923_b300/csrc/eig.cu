@@ -231,6 +231,20 @@ dh_status launch_eig_t(Plan &p, int n_windows, int parts, int k0, int k1, int Np
 
 }  // namespace
 
+// FP64 sum of `parts` partial Gram matrices of one window into C (T x T, interleaved re/im).
+dh_status launch_reduce_cov_window(const double *part, int parts, int T, double *C, uint32_t *status,
+                                   cudaStream_t s) {
+  const int blocks = (T * T + 255) / 256;
+  switch (T) {
+    case 16: k_reduce_cov<16><<<blocks, 256, 0, s>>>(part, parts, 1, C, status); break;
+    case 32: k_reduce_cov<32><<<blocks, 256, 0, s>>>(part, parts, 1, C, status); break;
+    case 64: k_reduce_cov<64><<<blocks, 256, 0, s>>>(part, parts, 1, C, status); break;
+    default: return DH_ERR_UNSUPPORTED_SIZE;
+  }
+  DH_CUDA_TRY(cudaGetLastError());
+  return DH_OK;
+}
+
 dh_status launch_eig(Plan &p, int n_windows, int parts, int k0, int k1, int Npad,
                      double *eig_user, cudaStream_t s) {
   switch (p.T) {

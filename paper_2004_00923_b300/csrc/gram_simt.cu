@@ -78,6 +78,21 @@ dh_status launch_t(Plan &p, int first_slot, int slot_stride, int n_windows, int 
 
 }  // namespace
 
+// Partial Gram matrices of one window's rows X (2T rows of npix FP32, row r at
+// X + r * npix) into part[u][2T][2T], u < units; npix / units must be a multiple of 32.
+dh_status launch_gram_simt_rows(const float *X, long long npix, int T, int units, double *part,
+                                cudaStream_t s) {
+  const long long ppu = npix / units;
+  switch (T) {
+    case 16: k_gram_simt<16><<<units, 256, 0, s>>>(X, npix, 0, 0, units, ppu, part); break;
+    case 32: k_gram_simt<32><<<units, 256, 0, s>>>(X, npix, 0, 0, units, ppu, part); break;
+    case 64: k_gram_simt<64><<<units, 256, 0, s>>>(X, npix, 0, 0, units, ppu, part); break;
+    default: return DH_ERR_UNSUPPORTED_SIZE;
+  }
+  DH_CUDA_TRY(cudaGetLastError());
+  return DH_OK;
+}
+
 // Split-K units per window: a function of the frame size only (never of the batch), so a
 // window's covariance is bitwise the same alone and inside any batch.
 int gram_units(long long npix) {
