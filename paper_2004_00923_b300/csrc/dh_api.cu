@@ -78,8 +78,8 @@ dh_status alloc_store(Plan &p) {
   size_t bw = p.prec == DH_PREC_FP32 ? (size_t)M * M * 4 : (size_t)2 * M * M * 2;
   p.B_window_bytes = (bw + 1023) / 1024 * 1024;
   if ((st = dalloc(p, &p.d_B, p.B_window_bytes * p.max_windows)) != DH_OK) return st;
-  // row-pass intermediate: a chunk of frames sized to stay in L2 (~48 MiB)
-  long long mf = (48ll << 20) / (p.npix * (long long)sizeof(float2));
+  // row-pass intermediate: a chunk of frames sized to stay in L2 (~96 MiB of the 126 MB)
+  long long mf = (96ll << 20) / (p.npix * (long long)sizeof(float2));
   if (mf < 1) mf = 1;
   if (mf > 64) mf = 64;
   p.mid_frames = (int)mf;
@@ -157,6 +157,13 @@ dh_status dh_plan_create(dh_plan_t *out, int nx, int ny, double lambda_m, double
   p.max_windows = 1;
   cudaError_t e = cudaGetDevice(&p.device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p.aux, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaEventCreateWithFlags(&p.ev_rows[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.ev_cols[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.ev_join, cudaEventDisableTiming);
   dh_status st = e == cudaSuccess ? DH_OK : fail_cuda(e);
   if (st == DH_OK) {
     std::vector<float2> cx = chirp_table(nx, p.a), cy = chirp_table(ny, p.a);
@@ -190,6 +197,13 @@ void dh_destroy(dh_plan_t h) {
   cudaDeviceSynchronize();
   free_store(p);
   profile_free(p);
+  for (int k = 0; k < 2; ++k) {
+    if (p.ev_rows[k]) cudaEventDestroy(p.ev_rows[k]);
+    if (p.ev_cols[k]) cudaEventDestroy(p.ev_cols[k]);
+  }
+  if (p.ev_fork) cudaEventDestroy(p.ev_fork);
+  if (p.ev_join) cudaEventDestroy(p.ev_join);
+  if (p.aux) cudaStreamDestroy(p.aux);
   dfree(p.d_cx); dfree(p.d_cy); dfree(p.d_twx); dfree(p.d_twy); dfree(p.d_status);
   delete h;
 }

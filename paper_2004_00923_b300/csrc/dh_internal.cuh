@@ -29,9 +29,12 @@ struct Plan {
   // tables
   float2 *d_cx = nullptr, *d_cy = nullptr;   // chirp * 1/sqrt(n) per axis
   float2 *d_twx = nullptr, *d_twy = nullptr; // Stockham twiddles per axis
-  // render intermediate (row-pass output), chunk of frames kept L2-sized
+  // render intermediate (row-pass output): a chunk of frames sized to stay in L2
   float2 *d_mid = nullptr;
   int mid_frames = 0;
+  cudaStream_t aux = nullptr;  // second stream: eigensolver overlap within a batch
+  cudaEvent_t ev_rows[2] = {nullptr, nullptr}, ev_cols[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // hologram store: [max_frames][2][npix] of the storage type
   void *d_H = nullptr;
   size_t H_elem_bytes = 4;

@@ -16,6 +16,7 @@
 // Inter-pass twiddles come from FP64-built tables. Frames are processed in chunks whose
 // intermediate fits in L2, so HBM sees only the uint16 input and the hologram output.
 #include "dh_internal.cuh"
+#include "tc_sm100.cuh"
 
 #include <math.h>
 #include <vector>
@@ -216,14 +217,27 @@ template <> __device__ __forceinline__ bool stored_finite<__nv_bfloat16>(__nv_bf
   return isfinite(__bfloat162float(h));
 }
 
+// The row-pass output `mid` of a frame is stored in tiles of CW = fpc(log2 n_y) columns:
+// tile t holds columns [t CW, t CW + CW) for every y, row-major [y][CW], and inside a row of
+// the tile the column index is XOR-swizzled by sw(y) = (y >> log2(16/CW)) & (CW - 1). A row
+// transform then writes each output as part of a CW-element run of one tile row (64 bytes
+// for CW = 8), and the column pass reads a whole tile with one bulk copy and walks its
+// columns in shared memory without bank conflicts.
+__device__ __forceinline__ int mid_swz(int y, int cw_log) {
+  return (y >> (4 - cw_log)) & ((1 << cw_log) - 1);
+}
+// element offset inside one frame's intermediate (< n_x n_y <= 2^24)
+__device__ __forceinline__ int mid_index(int kx, int y, int ny, int cw_log) {
+  const int t = kx >> cw_log, c = kx & ((1 << cw_log) - 1);
+  return ((t * ny + y) << cw_log) + (c ^ mid_swz(y, cw_log));
+}
+
 // Row pass: FPC consecutive rows of one frame per item. The next item's uint16 rows are
-// prefetched into registers with 16-byte loads while the current rows are transformed.
-// Each transform's input row is parked at the head of its own exchange region. Outputs
-// (times the y chirp) are written TRANSPOSED, mid[f][kx][y], through a swizzled shared
-// staging tile so that every store is a run of FPC consecutive y (64 bytes for FPC = 8).
+// prefetched into registers with 16-byte loads while the current rows are transformed;
+// each transform's input row is parked at the head of its own exchange region.
 template <int LOGN>
 __global__ void __launch_bounds__(fpc<LOGN>() * Shape<LOGN>::P, (fpc<LOGN>() * Shape<LOGN>::P <= 256 ? 2 : 1))
-k_render_rows(const uint16_t *__restrict__ frames, long long frame_stride, int ny,
+k_render_rows(const uint16_t *__restrict__ frames, long long frame_stride, int ny, int cw_log,
               const float2 *__restrict__ cx, const float2 *__restrict__ cy,
               const float2 *__restrict__ tw, float2 *__restrict__ mid, int n_items) {
   using S = Shape<LOGN>;
@@ -249,8 +263,8 @@ k_render_rows(const uint16_t *__restrict__ frames, long long frame_stride, int n
   if (blockIdx.x < n_items) prefetch(blockIdx.x);
 
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    const int f = item / groups, y0 = (item % groups) * FPC;
-    __syncthreads();  // previous item's staging tile fully read
+    const int f = item / groups, y = (item % groups) * FPC + fft;
+    __syncthreads();  // every transform is done with its region (previous item)
 #pragma unroll
     for (int k = 0; k < CPT; ++k) {  // park each row at the head of its transform's region
       const int c = threadIdx.x + k * NT, row = c / CPR, cr = c % CPR;
@@ -268,33 +282,29 @@ k_render_rows(const uint16_t *__restrict__ frames, long long frame_stride, int n
       v[r] = make_float2(a * c.x, a * c.y);
     }
     E::run(v, sm, j, tw);  // its first exchange store is ordered after the reads above
-    const float2 cyy = __ldg(cy + y0 + fft);
-    __syncthreads();  // every transform is done with its exchange region
-    // staging tile [kx][y], y swizzled by kx so that both phases are conflict-free
+    const float2 cyy = __ldg(cy + y);
+    float2 *dst = mid + (long long)f * npix;
+    if ((S::P & ((1 << cw_log) - 1)) == 0) {
+      // kx = j + i P: the tile column and the swizzle are fixed per thread, and successive
+      // outputs are P n_y elements apart
+      float2 *d = dst + mid_index(j, y, ny, cw_log);
+      const int step = S::P * ny;
 #pragma unroll
-    for (int i = 0; i < S::R; ++i) {
-      const int kx = j + i * S::P;
-      smem[kx * FPC + (fft ^ (kx & (FPC - 1)))] = cmul(v[E::out_reg(i)], cyy);
-    }
-    __syncthreads();
-    float2 *dst = mid + (long long)f * npix + y0;
-    if constexpr (FPC >= 2) {
-      constexpr int QPK = FPC / 2;  // 16-byte chunks per kx run
-      for (int c = threadIdx.x; c < S::N * QPK; c += NT) {
-        const int kx = c / QPK, q = c % QPK, m = kx & (FPC - 1);
-        float4 t = *reinterpret_cast<const float4 *>(&smem[kx * FPC + ((2 * q) ^ (m & ~1))]);
-        if (m & 1) t = make_float4(t.z, t.w, t.x, t.y);
-        *reinterpret_cast<float4 *>(&dst[(long long)kx * ny + 2 * q]) = t;
-      }
+      for (int i = 0; i < S::R; ++i) d[i * step] = cmul(v[E::out_reg(i)], cyy);
     } else {
-      for (int kx = threadIdx.x; kx < S::N; kx += NT) dst[(long long)kx * ny] = smem[kx];
+#pragma unroll
+      for (int i = 0; i < S::R; ++i)
+        dst[mid_index(j + i * S::P, y, ny, cw_log)] = cmul(v[E::out_reg(i)], cyy);
     }
   }
 }
 
-// Column pass: FPC columns of one frame per item, one transform per P threads, reading the
-// transposed intermediate mid[f][kx][y] contiguously and writing the hologram planes in
-// column-major pixel order p = kx n_y + ky (re plane, then im plane, of slot slot0 + f).
+// Column pass: one tile of FPC (= CW) columns of one frame per item. The tile (contiguous,
+// CW n_y FP32 complex values) arrives by bulk asynchronous copy into shared memory; each
+// transform (P threads) reads its column, runs in place in the same buffer, and writes the
+// hologram planes in column-major pixel order p = kx n_y + ky (re plane, then im plane, of
+// slot slot0 + f). A bulk copy that does not complete within the wait budget raises
+// DH_FLAG_WAIT_TIMEOUT and the CTA stops.
 template <int LOGN, typename OutT>
 __global__ void __launch_bounds__(fpc<LOGN>() * Shape<LOGN>::P, (fpc<LOGN>() * Shape<LOGN>::P <= 256 ? 3 : 1))
 k_render_cols(const float2 *__restrict__ mid, int nx, const float2 *__restrict__ tw,
@@ -302,20 +312,51 @@ k_render_cols(const float2 *__restrict__ mid, int nx, const float2 *__restrict__
               uint32_t *__restrict__ status) {
   using S = Shape<LOGN>;
   constexpr int FPC = fpc<LOGN>();
+  constexpr int CW_LOG = FPC == 16 ? 4 : FPC == 8 ? 3 : FPC == 4 ? 2 : FPC == 2 ? 1 : 0;
+  constexpr int TILE_BYTES = FPC * S::N * (int)sizeof(float2);
+  constexpr int CHUNK = TILE_BYTES < 16384 ? TILE_BYTES : 16384;
   using E = Engine<LOGN, (S::P > 32)>;
   extern __shared__ float2 smem[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
   const int fft = threadIdx.x / S::P, j = threadIdx.x % S::P;
   float2 *sm = smem + fft * S::RSTRIDE;
   const int groups = nx / FPC;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_barrier_init();
+    abort_flag = 0;
+  }
+  __syncthreads();
+  uint32_t phase = 0;
   bool finite = true;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    const int f = item / groups;
-    const int kx = (item % groups) * FPC + fft;
-    const float2 *src = mid + (long long)f * npix + (long long)kx * S::N;
-    float2 v[S::R];
+    const int f = item / groups, t = item % groups;
+    if (threadIdx.x == 0) {
+      const char *src = reinterpret_cast<const char *>(mid + (long long)f * npix + (long long)t * FPC * S::N);
+      tc::mbar_arrive_expect_tx(&bar, TILE_BYTES);
 #pragma unroll
-    for (int r = 0; r < S::R; ++r) v[r] = src[j + r * S::P];
+      for (int off = 0; off < TILE_BYTES; off += CHUNK) tc::bulk_load(reinterpret_cast<char *>(smem) + off, src + off, CHUNK, &bar);
+    }
+    if (!tc::mbar_wait(&bar, phase)) abort_flag = 1;
+    phase ^= 1;
+    __syncthreads();
+    if (abort_flag) break;
+    float2 v[S::R];
+    if constexpr (S::P % 16 == 0) {  // y = j + r P keeps the swizzle of j
+      const float2 *col = smem + j * FPC + (fft ^ mid_swz(j, CW_LOG));
+#pragma unroll
+      for (int r = 0; r < S::R; ++r) v[r] = col[r * S::P * FPC];
+    } else {
+#pragma unroll
+      for (int r = 0; r < S::R; ++r) {
+        const int y = j + r * S::P;
+        v[r] = smem[y * FPC + (fft ^ mid_swz(y, CW_LOG))];
+      }
+    }
+    __syncthreads();  // the tile is consumed; its buffer becomes the exchange regions
     E::run(v, sm, j, tw);
+    const int kx = t * FPC + fft;
     OutT *re = H + (long long)(slot0 + f) * 2 * npix + (long long)kx * S::N;
     OutT *im = re + npix;
 #pragma unroll
@@ -326,6 +367,11 @@ k_render_cols(const float2 *__restrict__ mid, int nx, const float2 *__restrict__
       re[j + i * S::P] = a;
       im[j + i * S::P] = b;
     }
+    __syncthreads();  // all transforms are done with the buffer before the next copy lands
+  }
+  if (abort_flag && threadIdx.x == 0) {
+    atomicOr(status, DH_FLAG_WAIT_TIMEOUT);
+    tc::mbar_wait(&bar, phase ^ 1);  // let a late copy land before the CTA exits
   }
   if (!finite) atomicOr(status, DH_FLAG_STORE_OVERFLOW);
 }
@@ -348,9 +394,23 @@ __global__ void k_hologram_to_f32(const T *__restrict__ H, int nx, int ny, float
 }
 
 // ----------------------------------------------------------------- host side
+// log2 of the column-tile width of the intermediate (the column pass's FFTs per CTA)
+int col_tile_log(int logny) {
+  int f = 0;
+  switch (logny) {
+    case 4: f = fpc<4>(); break; case 5: f = fpc<5>(); break; case 6: f = fpc<6>(); break;
+    case 7: f = fpc<7>(); break; case 8: f = fpc<8>(); break; case 9: f = fpc<9>(); break;
+    case 10: f = fpc<10>(); break; case 11: f = fpc<11>(); break; case 12: f = fpc<12>(); break;
+  }
+  int l = 0;
+  while ((1 << l) < f) ++l;
+  return l;
+}
+
 template <int LOGN>
 dh_status launch_rows_t(const uint16_t *frames, long long fstride, int ny, const Plan &p,
                         float2 *mid, int nf, cudaStream_t s) {
+  const int cw_log = col_tile_log(p.logny);
   using S = Shape<LOGN>;
   constexpr int FPC = fpc<LOGN>();
   const int threads = FPC * S::P;
@@ -369,7 +429,7 @@ dh_status launch_rows_t(const uint16_t *frames, long long fstride, int ny, const
   if (grid < 1) grid = 1;
   if (grid > items) grid = items;
   ProfScope ps(const_cast<Plan &>(p), K_RENDER_ROWS, s);
-  kern<<<grid, threads, smem, s>>>(frames, fstride, ny, p.d_cx, p.d_cy, p.d_twx, mid, items);
+  kern<<<grid, threads, smem, s>>>(frames, fstride, ny, cw_log, p.d_cx, p.d_cy, p.d_twx, mid, items);
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
 }
@@ -379,7 +439,10 @@ dh_status launch_cols_t(const Plan &p, const float2 *mid, int nf, int slot0, cud
   using S = Shape<LOGN>;
   constexpr int FPC = fpc<LOGN>();
   const int threads = FPC * S::P;
-  const size_t smem = S::NPASS > 1 ? (size_t)FPC * S::RSTRIDE * sizeof(float2) : 0;
+  // one tile of FPC columns; its buffer is reused in place as the exchange regions
+  const size_t tile = (size_t)FPC * S::N * sizeof(float2);
+  const size_t xchg = (size_t)FPC * S::RSTRIDE * sizeof(float2);
+  const size_t smem = tile > xchg ? tile : xchg;
   auto kern = k_render_cols<LOGN, OutT>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -469,6 +532,10 @@ void build_twiddles(int logn, float2 *out) {
 
 dh_status launch_render(Plan &p, const uint16_t *frames, long long frame_stride, int n_frames,
                         int slot0, cudaStream_t s) {
+  // Chunks of mid_frames frames: the row pass fills the L2-sized intermediate, the column
+  // pass drains it, back to back on the caller's stream. (Running the column pass of one
+  // chunk beside the row pass of the next was measured slower: both passes are issue-bound
+  // and the doubled intermediate no longer stays in L2.)
   for (int f0 = 0; f0 < n_frames; f0 += p.mid_frames) {
     const int nf = (n_frames - f0) < p.mid_frames ? (n_frames - f0) : p.mid_frames;
     dh_status st = launch_rows(p, frames + (long long)f0 * frame_stride, frame_stride, p.d_mid, nf, s);

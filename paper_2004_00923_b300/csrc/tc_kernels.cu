@@ -203,7 +203,7 @@ struct ProjCfg {
   static constexpr int M2 = 2 * T;                         // K of the MMA
   static constexpr int A_BYTES = 128 * M2 * 2;             // 128 pixels x 2T rows
   static constexpr int BOX_BYTES = 64 * M2 * 2;            // one 64-pixel TMA box
-  static constexpr int STAGES = T == 64 ? 4 : (T == 32 ? 6 : 8);
+  static constexpr int STAGES = T == 64 ? 3 : (T == 32 ? 5 : 8);  // two CTAs per SM
   static constexpr int KB = M2 < 64 ? M2 : 64;             // B row width per swizzle atom
   static constexpr int B_ROW = KB * 2;                     // bytes
   static constexpr int B_MAX = 2 * M2 * M2 * 2;            // hi + lo, Npad <= 2T
@@ -219,12 +219,10 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
              float *__restrict__ images, int nx, int ny, uint32_t *__restrict__ status) {
   using C = ProjCfg<T>;
   const long long npix = (long long)nx * ny;
-  // Holograms are stored with column-major pixels p = kx n_y + ky. Tile t of a window starts
-  // at pixel tile_p(t); when a column holds whole tiles, consecutive tiles are adjacent
-  // columns, so the transposed image stores of consecutive tiles fill the same sectors.
-  auto tile_p = [&](int t) -> int {
-    return ny >= 128 ? (t % nx) * ny + (t / nx) * 128 : t * 128;
-  };
+  // Holograms are stored with column-major pixels p = kx n_y + ky; tiles walk p
+  // contiguously (long sequential reads per plane row), and each pixel's power goes to its
+  // row-major image position; the scattered 4-byte stores of neighbouring columns meet in L2.
+  auto tile_p = [&](int t) -> int { return t * 128; };
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = align1024(smem_raw);
   uint8_t *stages = smem;
@@ -408,6 +406,8 @@ dh_status gram_t(Plan &p, int first_slot, int slot_stride, int n_windows, cudaSt
   static bool attr = false;
   if (!attr) {
     DH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+    DH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared));
     attr = true;
   }
   const int units_pw = gram_tc_units(p.npix);
@@ -434,6 +434,8 @@ dh_status project_t(Plan &p, int first_slot, int slot_stride, int n_windows, int
   static bool attr = false;
   if (!attr) {
     DH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+    DH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared));
     attr = true;
   }
   // eigenvector operand map: rows of 2T elements, box = KB x Npad
@@ -446,7 +448,11 @@ dh_status project_t(Plan &p, int first_slot, int slot_stride, int n_windows, int
   if (st != DH_OK) return st;
   const int tiles_pw = (int)(p.npix / 128);
   const long long total = (long long)n_windows * tiles_pw;
-  int grid = p.num_sms;
+  int per_sm = 0;
+  DH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::THREADS, C::SMEM));
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 2) per_sm = 2;  // tensor memory: at most 2 x 256 columns per SM
+  int grid = p.num_sms * per_sm;
   if (grid > total) grid = (int)total;
   ProfScope ps(p, K_PROJECT_TC, s);
   kern<<<grid, C::THREADS, C::SMEM, s>>>(p.tmap_H, tmB, first_slot, slot_stride, n_windows, tiles_pw, Npad,
