@@ -308,7 +308,7 @@ k_render_rows(const uint16_t *__restrict__ frames, long long frame_stride, int n
 template <int LOGN, typename OutT>
 __global__ void __launch_bounds__(fpc<LOGN>() * Shape<LOGN>::P, (fpc<LOGN>() * Shape<LOGN>::P <= 256 ? 3 : 1))
 k_render_cols(const float2 *__restrict__ mid, int nx, const float2 *__restrict__ tw,
-              OutT *__restrict__ H, long long npix, int slot0, int n_items,
+              OutT *__restrict__ H, long long npix, long long rows_total, int slot0, int n_items,
               uint32_t *__restrict__ status) {
   using S = Shape<LOGN>;
   constexpr int FPC = fpc<LOGN>();
@@ -357,15 +357,36 @@ k_render_cols(const float2 *__restrict__ mid, int nx, const float2 *__restrict__
     __syncthreads();  // the tile is consumed; its buffer becomes the exchange regions
     E::run(v, sm, j, tw);
     const int kx = t * FPC + fft;
-    OutT *re = H + (long long)(slot0 + f) * 2 * npix + (long long)kx * S::N;
-    OutT *im = re + npix;
+    if constexpr (sizeof(OutT) == 4) {  // FP32 planes: [slot][re|im][p]
+      OutT *re = H + (long long)(slot0 + f) * 2 * npix + (long long)kx * S::N;
+      OutT *im = re + npix;
 #pragma unroll
-    for (int i = 0; i < S::R; ++i) {
-      const float2 o = v[E::out_reg(i)];
-      const OutT a = to_store<OutT>(o.x), b = to_store<OutT>(o.y);
-      finite &= stored_finite<OutT>(a) & stored_finite<OutT>(b);
-      re[j + i * S::P] = a;
-      im[j + i * S::P] = b;
+      for (int i = 0; i < S::R; ++i) {
+        const float2 o = v[E::out_reg(i)];
+        finite &= isfinite(o.x) & isfinite(o.y);
+        re[j + i * S::P] = o.x;
+        im[j + i * S::P] = o.y;
+      }
+    } else {  // 16-bit planes in 64-pixel blocks: [p / 64][row = 2 slot + c][p % 64]
+      const long long pix0 = (long long)kx * S::N;  // a multiple of 64 when n_y >= 64
+      OutT *base = H + (2ll * (slot0 + f) << 6);
+      const long long bstride = rows_total << 6;
+#pragma unroll
+      for (int i = 0; i < S::R; ++i) {
+        const float2 o = v[E::out_reg(i)];
+        const OutT a = to_store<OutT>(o.x), b = to_store<OutT>(o.y);
+        finite &= stored_finite<OutT>(a) & stored_finite<OutT>(b);
+        OutT *q;
+        if constexpr (S::N >= 64) {
+          const int e = j + i * S::P;  // < n_y
+          q = base + ((pix0 >> 6) + (e >> 6)) * bstride + (e & 63);
+        } else {
+          const long long pix = pix0 + j + i * S::P;
+          q = base + (pix >> 6) * bstride + (pix & 63);
+        }
+        q[0] = a;
+        q[64] = b;
+      }
     }
     __syncthreads();  // all transforms are done with the buffer before the next copy lands
   }
@@ -376,17 +397,28 @@ k_render_cols(const float2 *__restrict__ mid, int nx, const float2 *__restrict__
   if (!finite) atomicOr(status, DH_FLAG_STORE_OVERFLOW);
 }
 
-// Inspection: slot planes (column-major pixels p = kx n_y + ky) to interleaved FP32 in
-// row-major order.
+// Inspection: one slot's hologram (column-major pixels p = kx n_y + ky; FP32 as planes,
+// 16-bit in 64-pixel blocks) to interleaved FP32 in row-major order.
 template <typename T>
-__global__ void k_hologram_to_f32(const T *__restrict__ H, int nx, int ny, float *__restrict__ out) {
+__global__ void k_hologram_to_f32(const T *__restrict__ H, int nx, int ny, long long rows_total, int slot,
+                                  float *__restrict__ out) {
   const long long npix = (long long)nx * ny;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
        p += (long long)gridDim.x * blockDim.x) {
     float r, i;
-    if constexpr (sizeof(T) == 4) { r = H[p]; i = H[p + npix]; }
-    else if constexpr (std::is_same<T, __half>::value) { r = __half2float(H[p]); i = __half2float(H[p + npix]); }
-    else { r = __bfloat162float(H[p]); i = __bfloat162float(H[p + npix]); }
+    if constexpr (sizeof(T) == 4) {
+      const T *re = H + 2ll * slot * npix;
+      r = re[p];
+      i = re[p + npix];
+    } else {
+      const T *blk = H + (p >> 6) * (rows_total << 6) + (p & 63);
+      const long long row = 2ll * slot;
+      if constexpr (std::is_same<T, __half>::value) {
+        r = __half2float(blk[row << 6]); i = __half2float(blk[(row + 1) << 6]);
+      } else {
+        r = __bfloat162float(blk[row << 6]); i = __bfloat162float(blk[(row + 1) << 6]);
+      }
+    }
     const long long kx = p / ny, ky = p % ny;
     out[2 * (ky * nx + kx)] = r;
     out[2 * (ky * nx + kx) + 1] = i;
@@ -457,7 +489,7 @@ dh_status launch_cols_t(const Plan &p, const float2 *mid, int nf, int slot0, cud
   if (grid > items) grid = items;
   ProfScope ps(const_cast<Plan &>(p), K_RENDER_COLS, s);
   kern<<<grid, threads, smem, s>>>(mid, p.nx, p.d_twy, static_cast<OutT *>(p.d_H), p.npix,
-                                    slot0, items, p.d_status);
+                                    2ll * p.max_frames, slot0, items, p.d_status);
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
 }
@@ -552,17 +584,17 @@ dh_status launch_render(Plan &p, const uint16_t *frames, long long frame_stride,
 
 dh_status launch_hologram_to_f32(Plan &p, int slot, float *out, cudaStream_t s) {
   const int grid = p.num_sms * 4;
-  const long long off = (long long)slot * 2 * p.npix;
+  const long long rows = 2ll * p.max_frames;
   switch (p.prec) {
     case DH_PREC_FP32:
-      k_hologram_to_f32<float><<<grid, 256, 0, s>>>(static_cast<float *>(p.d_H) + off, p.nx, p.ny, out);
+      k_hologram_to_f32<float><<<grid, 256, 0, s>>>(static_cast<float *>(p.d_H), p.nx, p.ny, rows, slot, out);
       break;
     case DH_PREC_FP16:
-      k_hologram_to_f32<__half><<<grid, 256, 0, s>>>(static_cast<__half *>(p.d_H) + off, p.nx, p.ny, out);
+      k_hologram_to_f32<__half><<<grid, 256, 0, s>>>(static_cast<__half *>(p.d_H), p.nx, p.ny, rows, slot, out);
       break;
     case DH_PREC_BF16:
       k_hologram_to_f32<__nv_bfloat16>
-          <<<grid, 256, 0, s>>>(static_cast<__nv_bfloat16 *>(p.d_H) + off, p.nx, p.ny, out);
+          <<<grid, 256, 0, s>>>(static_cast<__nv_bfloat16 *>(p.d_H), p.nx, p.ny, rows, slot, out);
       break;
   }
   DH_CUDA_TRY(cudaGetLastError());

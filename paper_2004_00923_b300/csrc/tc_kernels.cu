@@ -1,15 +1,17 @@
 // Eq. 4 and Eqs. 6-7 on the 5th-generation tensor cores (tcgen05, kind::f16, FP32
 // accumulation in tensor memory), for holograms stored as 16-bit planes.
 //
-// Layout: the hologram store is one 2-D array of 2*frames rows by n_x n_y pixels; row
-// 2f is Re H_f and row 2f+1 is Im H_f, so a window's X = [Re H_0; Im H_0; ...] is 2T
-// consecutive rows. One TMA tensor map with 64-pixel x 2T-row boxes (128-byte swizzle)
-// feeds both contractions:
+// Layout: the 16-bit hologram store holds, for each block of 64 consecutive pixels, all
+// 2*frames rows of it (row 2f = Re H_f, row 2f+1 = Im H_f) as [block][row][64]; a window's
+// X = [Re H_0; Im H_0; ...] for one pixel block is 2T consecutive rows, i.e. one contiguous
+// 128 x 2T-byte run. One 3-D TMA tensor map with 64-pixel x 2T-row x 1-block boxes
+// (128-byte swizzle) feeds both contractions:
 //   * covariance (Eq. 4): G = X X^T over pixels, X K-major. 128/(2T) pixel chunks are
 //     stacked into one 128-row operand used as both A and B of a 128x128 MMA; the
 //     diagonal 2T x 2T blocks are the chunk Gram matrices (the off-diagonal blocks are
 //     discarded). Products of stored 16-bit values are exact in FP32; TMEM accumulators
-//     are flushed every stage into per-thread compensated (Kahan) FP32 sums, and
+//     are drained every stage into per-thread FP32 block sums that are merged into
+//     compensated (Kahan) sums every 8 stages, and
 //     the per-unit partials are reduced in FP64 by the covariance reduction kernel.
 //   * projection (Eqs. 6-7): P = X^T B^T per 128-pixel tile (A = X, MN-major), with B the
 //     real embedding of the retained eigenvectors split into hi + lo 16-bit parts (two
@@ -48,15 +50,20 @@ struct GramCfg {
   static constexpr int R = 128 / M2;               // pixel chunks stacked per stage
   static constexpr int PIX = 64 * R;               // pixels per stage
   static constexpr int STAGE_BYTES = 128 * 128;    // 128 rows x 64 pixels x 2 bytes
-  static constexpr int STAGES = 6;
-  // Stages per TMEM flush. The tensor cores' FP32 accumulation rounds toward zero (measured:
-  // about -7e-8 relative per MMA instruction), so accumulators are drained into compensated
-  // sums after every stage of 4 MMAs, bounding that bias near 3e-7.
+  // One TMEM drain per stage of 4 MMAs: the tensor cores' FP32 accumulation rounds toward
+  // zero (measured: about -7e-8 relative per MMA instruction), so short accumulations bound
+  // that bias near 3e-7.
   static constexpr int GROUP = 1;
-  static constexpr int NCOL = M2 < 64 ? M2 : 64;   // columns each epilogue thread keeps
+  // Epilogue: each thread owns NCOL columns of one accumulator row; T = 16 runs two CTAs per
+  // SM, T = 32 / 64 one CTA per SM (8 stages, 4 TMEM accumulators of 128 columns).
+  static constexpr int NCOL = T == 64 ? 64 : 32;
   static constexpr int EPI_WARPS = 4 * (M2 / NCOL);
   static constexpr int THREADS = 64 + 32 * EPI_WARPS;
-  static constexpr int TMEM_COLS = 256;            // two 128-column accumulators
+  static constexpr bool KAHAN = T <= 32;
+  static constexpr int CTAS_PER_SM = T == 16 ? 2 : 1;
+  static constexpr int STAGES = CTAS_PER_SM == 2 ? 6 : 8;
+  static constexpr int NB = CTAS_PER_SM == 2 ? 2 : 4;   // accumulator buffers
+  static constexpr int TMEM_COLS = 128 * NB;
   static constexpr size_t SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 };
 
@@ -71,14 +78,14 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmH, int first_slot, int slot_stri
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::STAGES * C::STAGE_BYTES);
   uint64_t *empty = full + C::STAGES;
   uint64_t *acc_full = empty + C::STAGES;
-  uint64_t *acc_empty = acc_full + 2;
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(acc_empty + 2);
+  uint64_t *acc_empty = acc_full + C::NB;
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(acc_empty + C::NB);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 32 * C::EPI_WARPS); }
+    for (int b = 0; b < C::NB; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 32 * C::EPI_WARPS); }
     *abort_flag = 0;
     fence_barrier_init();
     prefetch_tmap(&tmH);
@@ -105,7 +112,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmH, int first_slot, int slot_stri
           uint8_t *dst = stages + slot * C::STAGE_BYTES;
 #pragma unroll
           for (int c = 0; c < C::R; ++c)
-            tma_load_2d(dst + c * C::M2 * 128, &tmH, &full[slot], p0 + st * C::PIX + c * 64, row);
+            tma_load_3d(dst + c * C::M2 * 128, &tmH, &full[slot], 0, row, (p0 + st * C::PIX + c * 64) >> 6);
           ++issued;
           if (++slot == C::STAGES) { slot = 0; ph ^= 1; }
         }
@@ -124,8 +131,8 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmH, int first_slot, int slot_stri
       for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x) {
         for (int g0 = 0; g0 < stages_per_unit && !*abort_flag; g0 += C::GROUP, ++grp) {
           const int n = stages_per_unit - g0 < C::GROUP ? stages_per_unit - g0 : C::GROUP;
-          const int buf = grp & 1;
-          if (!mbar_wait(&acc_empty[buf], ((grp >> 1) & 1) ^ 1)) { fail(); break; }
+          const int buf = grp % C::NB;
+          if (!mbar_wait(&acc_empty[buf], ((grp / C::NB) & 1) ^ 1)) { fail(); break; }
           fence_after_sync();
           const uint32_t d = tmem + buf * 128;
           for (int i = 0; i < n; ++i) {
@@ -147,7 +154,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmH, int first_slot, int slot_stri
   } else {  // ------------------------------ epilogue warps
     const int e = warp - 2;
     const int q = warp & 3;                 // TMEM lane quarter this warp may access
-    const int ch = e >> 2;                  // column half (T = 64 only)
+    const int ch = e >> 2;                  // which NCOL-column part of the chunk
     const int L = 32 * q + lane;            // accumulator row = TMEM lane
     const int c = L / C::M2, r = L % C::M2; // stacked chunk, row within the chunk
     const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
@@ -155,37 +162,59 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmH, int first_slot, int slot_stri
     // loop exits and waits are decided warp-uniformly (tcgen05.ld is .sync.aligned)
     for (int u = blockIdx.x; u < total_units && !__any_sync(0xffffffffu, *abort_flag); u += gridDim.x) {
       const int w = u / units_pw, uu = u % units_pw;
-      float s[C::NCOL], comp[C::NCOL];
+      // Per-stage values are added plainly into a block sum; every kBlock drains the block is
+      // merged into the unit sum -- compensated (Kahan) where registers allow (T <= 32), plain
+      // for T = 64. (Kahan on every drain was measured to halve the kernel's bandwidth.)
+      constexpr int kBlock = 8;
+      constexpr bool kKahan = C::KAHAN;
+      float s[C::NCOL], blk[C::NCOL], comp[kKahan ? C::NCOL : 1];
 #pragma unroll
-      for (int j = 0; j < C::NCOL; ++j) s[j] = 0.f, comp[j] = 0.f;
+      for (int j = 0; j < C::NCOL; ++j) s[j] = 0.f, blk[j] = 0.f;
+#pragma unroll
+      for (int j = 0; j < (kKahan ? C::NCOL : 1); ++j) comp[j] = 0.f;
+      auto merge = [&]() {
+#pragma unroll
+        for (int i = 0; i < C::NCOL; ++i) {
+          if constexpr (kKahan) {
+            const float y = blk[i] - comp[i];
+            const float t = s[i] + y;
+            comp[i] = (t - s[i]) - y;
+            s[i] = t;
+          } else {
+            s[i] += blk[i];
+          }
+          blk[i] = 0.f;
+        }
+      };
+      int nd = 0;
       bool ok = true;
       for (int g0 = 0; g0 < stages_per_unit; g0 += C::GROUP, ++grp) {
-        const int buf = grp & 1;
-        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (grp >> 1) & 1))) {
+        const int buf = grp % C::NB;
+        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (grp / C::NB) & 1))) {
           fail(); ok = false; break;
         }
         fence_after_sync();
-        const uint32_t ta = tmem + lane_addr + buf * 128 + c * C::M2 + ch * 64;
+        const uint32_t ta = tmem + lane_addr + buf * 128 + c * C::M2 + ch * C::NCOL;
 #pragma unroll
-        for (int j16 = 0; j16 < C::NCOL / 16; ++j16) {
-          float v[16];
-          tmem_ld16(ta + 16 * j16, v);
+        for (int h = 0; h < C::NCOL / 32; ++h) {
+          float v[32];
+          tmem_ld32(ta + 32 * h, v);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {  // compensated summation
-            const float y = v[i] - comp[16 * j16 + i];
-            const float t = s[16 * j16 + i] + y;
-            comp[16 * j16 + i] = (t - s[16 * j16 + i]) - y;
-            s[16 * j16 + i] = t;
-          }
+          for (int i = 0; i < 32; ++i) blk[32 * h + i] += v[i];
         }
         fence_before_sync();
         mbar_arrive(&acc_empty[buf]);
+        if (++nd == kBlock) { nd = 0; merge(); }
       }
       if (!ok) break;
+      merge();
       double *dst = part + ((long long)(w * units_pw + uu) * C::R + c) * C::M2 * C::M2 +
-                    (long long)r * C::M2 + ch * 64;
+                    (long long)r * C::M2 + ch * C::NCOL;
 #pragma unroll
-      for (int j = 0; j < C::NCOL; ++j) dst[j] = (double)s[j] - (double)comp[j];
+      for (int j = 0; j < C::NCOL; ++j) {
+        if constexpr (kKahan) dst[j] = (double)s[j] - (double)comp[j];
+        else dst[j] = (double)s[j];
+      }
     }
   }
   fence_before_sync();
@@ -219,10 +248,16 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
              float *__restrict__ images, int nx, int ny, uint32_t *__restrict__ status) {
   using C = ProjCfg<T>;
   const long long npix = (long long)nx * ny;
-  // Holograms are stored with column-major pixels p = kx n_y + ky; tiles walk p
-  // contiguously (long sequential reads per plane row), and each pixel's power goes to its
-  // row-major image position; the scattered 4-byte stores of neighbouring columns meet in L2.
-  auto tile_p = [&](int t) -> int { return t * 128; };
+  // Holograms are stored with column-major pixels p = kx n_y + ky, so a 128-pixel tile is
+  // (part of) one image column. When n_y >= 128, tiles come in groups of 8 adjacent
+  // columns over the same 128 rows: the epilogue stages the group's powers in shared
+  // memory and writes 32 contiguous bytes per image row instead of 4 scattered bytes.
+  const bool grouped = ny >= 128 && (nx % 8) == 0;
+  auto tile_p = [&](int t) -> int {
+    if (!grouped) return t * 128;
+    const int g = t >> 3, k = t & 7, gx = nx >> 3;
+    return ((g % gx) * 8 + k) * ny + (g / gx) * 128;
+  };
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = align1024(smem_raw);
   uint8_t *stages = smem;
@@ -238,9 +273,13 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long total = (long long)n_windows * tiles_pw;
-  const long long per = total / gridDim.x, rem = total % gridDim.x;
-  const long long t_begin = blockIdx.x * per + (blockIdx.x < rem ? blockIdx.x : rem);
-  const long long t_end = t_begin + per + (blockIdx.x < rem ? 1 : 0);
+  // CTAs take contiguous ranges of whole units: 8-tile groups when grouped (tiles_pw is
+  // then a multiple of 8), single tiles otherwise
+  const int unit = grouped ? 8 : 1;
+  const long long units = total / unit;
+  const long long uper = units / gridDim.x, urem = units % gridDim.x;
+  const long long t_begin = unit * (blockIdx.x * uper + (blockIdx.x < urem ? blockIdx.x : urem));
+  const long long t_end = t_begin + unit * (uper + (blockIdx.x < urem ? 1 : 0));
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -284,8 +323,8 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
         mbar_arrive_expect_tx(&full[slot], C::A_BYTES);
         const int row = 2 * (first_slot + w * slot_stride);
         uint8_t *dst = stages + slot * C::A_BYTES;
-        tma_load_2d(dst, &tmH, &full[slot], p, row);
-        tma_load_2d(dst + C::BOX_BYTES, &tmH, &full[slot], p + 64, row);
+        tma_load_3d(dst, &tmH, &full[slot], 0, row, p >> 6);
+        tma_load_3d(dst + C::BOX_BYTES, &tmH, &full[slot], 0, row, (p >> 6) + 1);
         ++issued;
         if (++slot == C::STAGES) { slot = 0; ph ^= 1; }
       }
@@ -342,6 +381,7 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
   } else {  // ------------------------------ epilogue: 4 warps, one pixel per TMEM lane
     const int q = warp & 3;
     const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
+    float g8[8];
     int it = 0;
     for (long long t = t_begin; t < t_end && !__any_sync(0xffffffffu, *abort_flag); ++t, ++it) {
       const int w = (int)(t / tiles_pw);
@@ -351,15 +391,33 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
       if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (it >> 1) & 1))) { fail(); break; }
       fence_after_sync();
       float m = 0.f;
-      for (int j16 = 0; j16 < Npad / 16; ++j16) {
+      const uint32_t ta = tmem + lane_addr + buf * C::M2;
+      int col = 0;
+      for (; col + 64 <= Npad; col += 64) {
+        float v[64];
+        tmem_ld64(ta + col, v);
+#pragma unroll
+        for (int i = 0; i < 64; ++i) m = fmaf(v[i], v[i], m);
+      }
+      for (; col < Npad; col += 16) {
         float v[16];
-        tmem_ld16(tmem + lane_addr + buf * C::M2 + 16 * j16, v);
+        tmem_ld16(ta + col, v);
 #pragma unroll
         for (int i = 0; i < 16; ++i) m = fmaf(v[i], v[i], m);
       }
       fence_before_sync();
       mbar_arrive(&acc_empty[buf]);
-      images[(long long)w * npix + (long long)ky * nx + kx] = m;
+      if (!grouped) {
+        images[(long long)w * npix + (long long)ky * nx + kx] = m;
+      } else {  // shift this pixel's power into the row of 8 adjacent columns
+        g8[7] = g8[6]; g8[6] = g8[5]; g8[5] = g8[4]; g8[4] = g8[3];
+        g8[3] = g8[2]; g8[2] = g8[1]; g8[1] = g8[0]; g8[0] = m;
+        if ((t & 7) == 7) {  // columns kx-7 .. kx of image row ky
+          float4 *dst = reinterpret_cast<float4 *>(images + (long long)w * npix + (long long)ky * nx + (kx - 7));
+          dst[0] = make_float4(g8[7], g8[6], g8[5], g8[4]);
+          dst[1] = make_float4(g8[3], g8[2], g8[1], g8[0]);
+        }
+      }
     }
   }
   fence_before_sync();
@@ -399,6 +457,39 @@ dh_status encode_2d(CUtensorMap *map, void *base, bool bf16, uint64_t inner, uin
   return r == CUDA_SUCCESS ? DH_OK : DH_ERR_CUDA;
 }
 
+dh_status encode_3d(CUtensorMap *map, void *base, bool bf16, const uint64_t dims[3],
+                    const uint64_t strides_bytes[2], const uint32_t box[3]) {
+  auto fn = encode_fn();
+  if (!fn) return DH_ERR_CUDA;
+  const cuuint64_t d[3] = {dims[0], dims[1], dims[2]};
+  const cuuint64_t st[2] = {strides_bytes[0], strides_bytes[1]};
+  const cuuint32_t b[3] = {box[0], box[1], box[2]};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, d,
+                  st, b, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? DH_OK : DH_ERR_CUDA;
+}
+
+// CTAs of `kern` that fit on one SM by shared memory (with the maximum carveout, which these
+// kernels request) and by registers. The runtime's occupancy query assumes the default
+// carveout and under-reports these kernels.
+template <typename K>
+dh_status resident_ctas(K kern, int threads, size_t smem, int *out) {
+  int dev = 0, smem_sm = 0, reserved = 0, regs_sm = 0;
+  DH_CUDA_TRY(cudaGetDevice(&dev));
+  DH_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  DH_CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+  DH_CUDA_TRY(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+  cudaFuncAttributes fa;
+  DH_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+  const int by_smem = smem_sm / (int)(smem + reserved);
+  const int regs_cta = ((fa.numRegs + 7) / 8 * 8) * ((threads + 31) / 32 * 32);
+  const int by_regs = regs_cta > 0 ? regs_sm / regs_cta : 1;
+  *out = by_smem < by_regs ? by_smem : by_regs;
+  return DH_OK;
+}
+
 template <int T, bool BF16>
 dh_status gram_t(Plan &p, int first_slot, int slot_stride, int n_windows, cudaStream_t s) {
   using C = GramCfg<T>;
@@ -414,8 +505,9 @@ dh_status gram_t(Plan &p, int first_slot, int slot_stride, int n_windows, cudaSt
   const int stages_per_unit = (int)(p.npix / units_pw / C::PIX);
   const int total = n_windows * units_pw;
   int per_sm = 0;
-  DH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::THREADS, C::SMEM));
-  if (per_sm > 2) per_sm = 2;  // tensor memory: two CTAs of 256 columns per SM
+  dh_status rs = resident_ctas(kern, C::THREADS, C::SMEM, &per_sm);
+  if (rs != DH_OK) return rs;
+  if (per_sm > C::CTAS_PER_SM) per_sm = C::CTAS_PER_SM;  // tensor memory: 512 columns per SM
   if (per_sm < 1) per_sm = 1;
   int grid = p.num_sms * per_sm;
   if (grid > total) grid = total;
@@ -449,9 +541,10 @@ dh_status project_t(Plan &p, int first_slot, int slot_stride, int n_windows, int
   const int tiles_pw = (int)(p.npix / 128);
   const long long total = (long long)n_windows * tiles_pw;
   int per_sm = 0;
-  DH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::THREADS, C::SMEM));
+  dh_status rs = resident_ctas(kern, C::THREADS, C::SMEM, &per_sm);
+  if (rs != DH_OK) return rs;
   if (per_sm < 1) per_sm = 1;
-  if (per_sm > 2) per_sm = 2;  // tensor memory: at most 2 x 256 columns per SM
+  if (per_sm * C::TMEM_COLS > 512) per_sm = 512 / C::TMEM_COLS;  // tensor memory per SM
   int grid = p.num_sms * per_sm;
   if (grid > total) grid = (int)total;
   ProfScope ps(p, K_PROJECT_TC, s);
@@ -469,8 +562,11 @@ dh_status make_tensor_maps(Plan &p) {
   p.tmaps_ok = false;
   if (p.prec == DH_PREC_FP32) return DH_OK;
   const bool bf16 = p.prec == DH_PREC_BF16;
-  dh_status st = encode_2d(&p.tmap_H, p.d_H, bf16, (uint64_t)p.npix, (uint64_t)2 * p.max_frames,
-                           (uint64_t)p.npix * 2, 64u, (uint32_t)(2 * p.T), CU_TENSOR_MAP_SWIZZLE_128B);
+  const uint64_t rows = 2ull * p.max_frames;
+  const uint64_t dims[3] = {64, rows, (uint64_t)p.npix / 64};
+  const uint64_t strides[2] = {64 * 2, rows * 64 * 2};
+  const uint32_t box[3] = {64, (uint32_t)(2 * p.T), 1};
+  dh_status st = encode_3d(&p.tmap_H, p.d_H, bf16, dims, strides, box);
   if (st != DH_OK) return st;
   p.tmaps_ok = true;
   return DH_OK;
