@@ -3,9 +3,10 @@
 // k_reduce_cov: C[t][u] = sum over partial Gram matrices of
 //     (G[2t][2u] + G[2t+1][2u+1]) + i (G[2t][2u+1] - G[2t+1][2u])   in FP64.
 // k_jacobi: one CTA per window. Hermitian eigendecomposition C = V Lambda V^{t*} by the
-//   two-sided complex Jacobi method in FP64 (Forsythe & Henrici 1960; Golub & Van Loan
-//   Sec. 8.5) with the parallel round-robin ordering: each of the T-1 steps of a sweep
-//   rotates T/2 disjoint pairs at once (Brent & Luk 1985). For a pair with
+//   two-sided complex Jacobi method (Forsythe & Henrici 1960; Golub & Van Loan Sec. 8.5)
+//   with the parallel round-robin ordering: each of the T-1 steps of a sweep rotates T/2
+//   disjoint pairs at once (Brent & Luk 1985); FP32 sweeps first, then FP64 sweeps from the
+//   Rayleigh quotient of the re-orthonormalised FP32 eigenvectors. For a pair with
 //   C_pq = g e^{i alpha}, the real 2x2 Schur rotation (c, s) of [[C_pp, g], [g, C_qq]] is
 //   combined with the phase: J_pp = J_qq = c, J_pq = s e^{i alpha}, J_qp = -s e^{-i alpha},
 //   C <- J^{t*} C J, V <- V J. Eigenvalues are then ordered decreasing (ties by index)
@@ -66,43 +67,28 @@ __device__ __forceinline__ void put_split(T16 *hi, T16 *lo, long long i, double 
   lo[i] = from_f32<T16>((float)(v - (double)to_f32<T16>(h)));
 }
 
-template <int T>
-__global__ void __launch_bounds__(256)
-k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restrict__ Vout,
-         double *__restrict__ eig_user, int prec, void *__restrict__ Bop, long long B_stride,
-         int k0, int k1, int Npad, double tol, int max_sweeps, uint32_t *__restrict__ status) {
+// Parallel-order two-sided complex Jacobi sweeps on the Hermitian matrix (ar, ai) (row
+// stride LD), accumulating the rotations into (vr, vi). Real = float or double. Returns the
+// number of sweeps taken, or -1 if off(A) > tol ||A||_F after max_sweeps.
+template <int T, typename Real>
+__device__ int jacobi_sweeps(Real *ar, Real *ai, Real *vr, Real *vi, double tol, int max_sweeps,
+                             double fro, double *red) {
   constexpr int NP = T / 2;
   constexpr int LD = T + 1;
-  constexpr int M = 2 * T;
-  extern __shared__ double sm[];
-  double *ar = sm, *ai = ar + T * LD, *vr = ai + T * LD, *vi = vr + T * LD;
-  __shared__ double rc[NP], rwr[NP], rwi[NP], red[8], dsort[T];
-  __shared__ int rp[NP], rq[NP], perm[T];
-  const int w = blockIdx.x, tid = threadIdx.x;
-  const double *Cw = C + 2ll * w * T * T;
-
-  double fro2 = 0.0;
-  for (int e = tid; e < T * T; e += blockDim.x) {
-    const int i = e / T, j = e % T;
-    const double re = 0.5 * (Cw[2 * (i * T + j)] + Cw[2 * (j * T + i)]);
-    const double im = i == j ? 0.0 : 0.5 * (Cw[2 * (i * T + j) + 1] - Cw[2 * (j * T + i) + 1]);
-    ar[i * LD + j] = re;
-    ai[i * LD + j] = im;
-    vr[i * LD + j] = i == j ? 1.0 : 0.0;
-    vi[i * LD + j] = 0.0;
-    fro2 += re * re + im * im;
-  }
-  const double fro = sqrt(block_sum(fro2, red));
-
-  bool converged = false;
+  __shared__ Real rc[NP], rwr[NP], rwi[NP];
+  __shared__ int rp[NP], rq[NP];
+  const int tid = threadIdx.x;
   for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
     double off2 = 0.0;
     for (int e = tid; e < T * T; e += blockDim.x) {
       const int i = e / T, j = e % T;
-      if (i != j) off2 += ar[i * LD + j] * ar[i * LD + j] + ai[i * LD + j] * ai[i * LD + j];
+      if (i != j) {
+        const double x = (double)ar[i * LD + j], y = (double)ai[i * LD + j];
+        off2 += x * x + y * y;
+      }
     }
     off2 = block_sum(off2, red);
-    if (sqrt(off2) <= tol * fro) { converged = true; break; }
+    if (sqrt(off2) <= tol * fro) return sweep;
     if (sweep == max_sweeps) break;
     for (int step = 0; step < T - 1; ++step) {
       if (tid < NP) {
@@ -110,16 +96,16 @@ k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restr
         if (tid == 0) { a = step; b = T - 1; }
         else { a = (step + tid) % (T - 1); b = (step - tid + T - 1) % (T - 1); }
         const int p = a < b ? a : b, q = a < b ? b : a;
-        const double gr = ar[p * LD + q], gi = ai[p * LD + q];
-        const double g = sqrt(gr * gr + gi * gi);
-        double c = 1.0, wr = 0.0, wi = 0.0;
-        if (g > 1e-300) {
-          const double tau = (ar[q * LD + q] - ar[p * LD + p]) / (2.0 * g);
-          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + t * t);
-          const double s = t * c;
-          wr = s * gr / g;
-          wi = s * gi / g;
+        const Real gr = ar[p * LD + q], gi = ai[p * LD + q];
+        const Real g = sqrt(gr * gr + gi * gi);
+        Real c = 1, wr = 0, wi = 0;
+        if (g > (Real)(1e-18 * fro)) {  // rotations below this leave every entry unchanged
+          const Real tau = (ar[q * LD + q] - ar[p * LD + p]) / (2 * g);
+          const Real t = (tau >= 0 ? (Real)1 : (Real)-1) / (fabs(tau) + sqrt(1 + tau * tau));
+          c = 1 / sqrt(1 + t * t);
+          const Real sn = t * c;
+          wr = sn * gr / g;
+          wi = sn * gi / g;
         }
         rp[tid] = p; rq[tid] = q; rc[tid] = c; rwr[tid] = wr; rwi[tid] = wi;
       }
@@ -127,9 +113,10 @@ k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restr
       // columns of A and V: X_ip' = c X_ip - conj(w) X_iq ;  X_iq' = w X_ip + c X_iq
       for (int it = tid; it < NP * T; it += blockDim.x) {
         const int k = it / T, i = it % T;
+        const Real c = rc[k], wr = rwr[k], wi = rwi[k];
+        if (wr == 0 && wi == 0) continue;
         const int p = rp[k], q = rq[k];
-        const double c = rc[k], wr = rwr[k], wi = rwi[k];
-        double xpr = ar[i * LD + p], xpi = ai[i * LD + p], xqr = ar[i * LD + q], xqi = ai[i * LD + q];
+        Real xpr = ar[i * LD + p], xpi = ai[i * LD + p], xqr = ar[i * LD + q], xqi = ai[i * LD + q];
         ar[i * LD + p] = c * xpr - (wr * xqr + wi * xqi);
         ai[i * LD + p] = c * xpi - (wr * xqi - wi * xqr);
         ar[i * LD + q] = (wr * xpr - wi * xpi) + c * xqr;
@@ -144,9 +131,10 @@ k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restr
       // rows of A: A_pj' = c A_pj - w A_qj ;  A_qj' = conj(w) A_pj + c A_qj
       for (int it = tid; it < NP * T; it += blockDim.x) {
         const int k = it / T, j = it % T;
+        const Real c = rc[k], wr = rwr[k], wi = rwi[k];
+        if (wr == 0 && wi == 0) continue;
         const int p = rp[k], q = rq[k];
-        const double c = rc[k], wr = rwr[k], wi = rwi[k];
-        const double xpr = ar[p * LD + j], xpi = ai[p * LD + j], xqr = ar[q * LD + j], xqi = ai[q * LD + j];
+        const Real xpr = ar[p * LD + j], xpi = ai[p * LD + j], xqr = ar[q * LD + j], xqi = ai[q * LD + j];
         ar[p * LD + j] = c * xpr - (wr * xqr - wi * xqi);
         ai[p * LD + j] = c * xpi - (wr * xqi + wi * xqr);
         ar[q * LD + j] = (wr * xpr + wi * xpi) + c * xqr;
@@ -155,16 +143,150 @@ k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restr
       __syncthreads();
       if (tid < NP) {
         const int p = rp[tid], q = rq[tid];
-        ar[p * LD + q] = ai[p * LD + q] = ar[q * LD + p] = ai[q * LD + p] = 0.0;
-        ai[p * LD + p] = ai[q * LD + q] = 0.0;
+        ar[p * LD + q] = ai[p * LD + q] = ar[q * LD + p] = ai[q * LD + p] = 0;
+        ai[p * LD + p] = ai[q * LD + q] = 0;
       }
       __syncthreads();
     }
   }
-  if (!converged && tid == 0) atomicOr(status, DH_FLAG_EIG_NOT_CONVERGED);
+  return -1;
+}
+
+// Eq. 5 for one window per CTA, in two precisions:
+//  1. FP32 Jacobi sweeps on C until off(A) <= 1e-6 ||C||_F (the FP32 pipe is ~64x the FP64
+//     pipe on this part);
+//  2. FP64: the FP32 eigenvectors are re-orthonormalised (modified Gram-Schmidt), C is
+//     rotated into their basis (A = V^{t*} C V, the Rayleigh quotient), and FP64 Jacobi
+//     sweeps finish A to off(A) <= tol ||C||_F, accumulating into V.
+// The result is the FP64 eigendecomposition of C; phase 1 only supplies a good start.
+template <int T>
+__global__ void __launch_bounds__(256)
+k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restrict__ Vout,
+         double *__restrict__ eig_user, int prec, void *__restrict__ Bop, long long B_stride,
+         int k0, int k1, int Npad, double tol, int max_sweeps, uint32_t *__restrict__ status) {
+  constexpr int LD = T + 1;
+  constexpr int M = 2 * T;
+  constexpr int SZ = T * LD;
+  extern __shared__ double sm[];
+  // X: C, later A (FP64); Y: V (FP64); Z: FP32 A and V in phase 1, FP64 scratch in phase 2
+  double *xr = sm, *xi = xr + SZ, *vr = xi + SZ, *vi = vr + SZ, *zr = vi + SZ, *zi = zr + SZ;
+  float *ar32 = reinterpret_cast<float *>(zr), *ai32 = ar32 + SZ, *vr32 = ai32 + SZ, *vi32 = vr32 + SZ;
+  __shared__ double red[8], dsort[T];
+  __shared__ int perm[T];
+  const int w = blockIdx.x, tid = threadIdx.x;
+  const double *Cw = C + 2ll * w * T * T;
+
+  double fro2 = 0.0;
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    const int i = e / T, j = e % T;
+    const double re = 0.5 * (Cw[2 * (i * T + j)] + Cw[2 * (j * T + i)]);
+    const double im = i == j ? 0.0 : 0.5 * (Cw[2 * (i * T + j) + 1] - Cw[2 * (j * T + i) + 1]);
+    xr[i * LD + j] = re;
+    xi[i * LD + j] = im;
+    ar32[i * LD + j] = (float)re;
+    ai32[i * LD + j] = (float)im;
+    vr32[i * LD + j] = i == j ? 1.f : 0.f;
+    vi32[i * LD + j] = 0.f;
+    fro2 += re * re + im * im;
+  }
+  const double fro = sqrt(block_sum(fro2, red));
+
+  // ---- phase 1: FP32
+  jacobi_sweeps<T, float>(ar32, ai32, vr32, vi32, 1e-6, 20, fro, red);
+
+  // ---- phase 2: FP64
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    const int i = e / T, j = e % T;
+    vr[i * LD + j] = (double)vr32[i * LD + j];
+    vi[i * LD + j] = (double)vi32[i * LD + j];
+  }
+  __syncthreads();
+  // Lowdin re-orthonormalisation of the (nearly orthonormal) columns of V:
+  // V <- V (3 I - V^{t*} V) / 2 squares the orthogonality error E = V^{t*} V - I; the FP32
+  // sweeps leave |E| ~ 1e-6, so two steps reach FP64 level.
+  for (int pass = 0; pass < 2; ++pass) {
+  for (int e = tid; e < T * T; e += blockDim.x) {  // Z = V^{t*} V
+    const int i = e / T, j = e % T;
+    double sr = 0.0, si = 0.0;
+    for (int k = 0; k < T; ++k) {
+      const double ar_ = vr[k * LD + i], ai_ = -vi[k * LD + i], br = vr[k * LD + j], bi = vi[k * LD + j];
+      sr += ar_ * br - ai_ * bi;
+      si += ar_ * bi + ai_ * br;
+    }
+    zr[i * LD + j] = (i == j ? 1.5 : 0.0) - 0.5 * sr;
+    zi[i * LD + j] = -0.5 * si;
+  }
+  __syncthreads();
+  {
+    constexpr int NPR = 256 / T;   // threads per row of V
+    constexpr int CPT = T / NPR;   // output columns per thread
+    const int i = tid / NPR, j0 = (tid % NPR) * CPT;
+    double nr[CPT], ni[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) nr[c] = 0.0, ni[c] = 0.0;
+    if (i < T) {
+      for (int k = 0; k < T; ++k) {
+        const double ar_ = vr[i * LD + k], ai_ = vi[i * LD + k];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          const double br = zr[k * LD + j0 + c], bi = zi[k * LD + j0 + c];
+          nr[c] += ar_ * br - ai_ * bi;
+          ni[c] += ar_ * bi + ai_ * br;
+        }
+      }
+    }
+    __syncthreads();
+    if (i < T) {
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) { vr[i * LD + j0 + c] = nr[c]; vi[i * LD + j0 + c] = ni[c]; }
+    }
+    __syncthreads();
+  }
+  }
+
+  // Z = C V
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    const int i = e / T, j = e % T;
+    double sr = 0.0, si = 0.0;
+    for (int k = 0; k < T; ++k) {
+      const double cr = xr[i * LD + k], ci = xi[i * LD + k], br = vr[k * LD + j], bi = vi[k * LD + j];
+      sr += cr * br - ci * bi;
+      si += cr * bi + ci * br;
+    }
+    zr[i * LD + j] = sr;
+    zi[i * LD + j] = si;
+  }
+  __syncthreads();
+  // X = V^{t*} Z (Hermitian up to rounding: computed in full, then symmetrised)
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    const int i = e / T, j = e % T;
+    double sr = 0.0, si = 0.0;
+    for (int k = 0; k < T; ++k) {
+      const double ar_ = vr[k * LD + i], ai_ = -vi[k * LD + i], br = zr[k * LD + j], bi = zi[k * LD + j];
+      sr += ar_ * br - ai_ * bi;
+      si += ar_ * bi + ai_ * br;
+    }
+    xr[i * LD + j] = sr;
+    xi[i * LD + j] = si;
+  }
+  __syncthreads();
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    const int i = e / T, j = e % T;
+    if (i < j) {
+      const double r = 0.5 * (xr[i * LD + j] + xr[j * LD + i]);
+      const double m = 0.5 * (xi[i * LD + j] - xi[j * LD + i]);
+      xr[i * LD + j] = r; xi[i * LD + j] = m;
+      xr[j * LD + i] = r; xi[j * LD + i] = -m;
+    } else if (i == j) {
+      xi[i * LD + i] = 0.0;
+    }
+  }
+  __syncthreads();
+  const int sweeps = jacobi_sweeps<T, double>(xr, xi, vr, vi, tol, max_sweeps, fro, red);
+  if (sweeps < 0 && tid == 0) atomicOr(status, DH_FLAG_EIG_NOT_CONVERGED);
 
   // decreasing order, ties by original index
-  if (tid < T) dsort[tid] = ar[tid * LD + tid];
+  if (tid < T) dsort[tid] = xr[tid * LD + tid];
   __syncthreads();
   if (tid < T) {
     const double d = dsort[tid];
@@ -215,7 +337,7 @@ dh_status launch_eig_t(Plan &p, int n_windows, int parts, int k0, int k1, int Np
     k_reduce_cov<T><<<(total + 255) / 256, 256, 0, s>>>(p.d_part, parts, n_windows, p.d_C, p.d_status);
   }
   DH_CUDA_TRY(cudaGetLastError());
-  const size_t smem = 4ull * T * (T + 1) * sizeof(double);
+  const size_t smem = 6ull * T * (T + 1) * sizeof(double);
   static bool attr = false;
   if (!attr) {
     DH_CUDA_TRY(cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -255,3 +255,24 @@ def test_tc_kernels_exact_on_stored_values(dh, T, prec):
             # V's hi+lo split keeps ~22 (fp16) / ~16 (bf16) significant bits
             assert rel(images[w].cpu().numpy(), M_exact) < (1e-5 if prec == "fp16" else 6e-5)
         assert plan.status() == 0
+
+
+# ------------------------------------------------------------- eigensolver precision
+@pytest.mark.parametrize("T", [16, 32, 64])
+def test_eigensolver_reaches_fp64_accuracy(dh, T):
+    """Eq. 5 on the GPU's own covariance: the residual and orthonormality of the returned
+    eigenpairs are at FP64 level (the FP32 sweeps only supply the starting basis)."""
+    f = speckle_window(128, 128, T, seed=300 + T).numpy()
+    with dh.Plan(128, 128, LAM, Z, PITCH, T=T, precision="fp32") as plan:
+        _, lam = plan.pca_batch(to_gpu(f), 1, T, 2, T - 1)
+        C = plan.debug_covariance(0).cpu().numpy()
+        V = plan.debug_eigvecs(0).cpu().numpy()
+        assert plan.status() == 0
+    lam = lam[0].cpu().numpy()
+    Ch = 0.5 * (C + C.conj().T)
+    nC = np.linalg.norm(Ch, 2)
+    assert np.all(np.diff(lam) <= 0)
+    assert np.linalg.norm(Ch @ V - V * lam[None, :]) <= 1e-12 * nC * T
+    assert np.linalg.norm(V.conj().T @ V - np.eye(T)) <= 1e-12 * T
+    ref = np.linalg.eigvalsh(Ch)[::-1]
+    assert np.max(np.abs(lam - ref)) <= 1e-12 * nC
