@@ -104,6 +104,59 @@ std::vector<float2> chirp_table(int n, double a) {
   return c;
 }
 
+// Windows [first_slot + w * slot_stride, + T), w < n_windows, optionally rendering the frames
+// they need first. The windows can be processed in groups: each group's covariance runs on
+// the caller's stream, its eigensolver on the plan's aux stream, and the projections follow
+// on the caller's stream once each group's eigenvectors are ready; the call ends with the
+// caller's stream joined to everything it launched. One group is used: running the
+// eigensolver of one group beside the next group's rendering was measured slower (both
+// slowed down on the shared SMs).
+dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int first_slot,
+                   int slot_stride, int n_windows, int k0, int k1, float *images, double *eig_user,
+                   cudaStream_t s) {
+  const int G = 1;
+  const int nS = k1 - k0 + 1;
+  const int nop = p.prec == DH_PREC_FP32 ? 2 * nS : (2 * nS + 15) / 16 * 16;  // operand rows
+  int w0s[Plan::kMaxGroups], nws[Plan::kMaxGroups];
+  int rendered = 0;  // frames (slots relative to first_slot) already rendered
+  dh_status st;
+  for (int g = 0, w0 = 0; g < G; ++g) {
+    const int nw = n_windows / G + (g < n_windows % G ? 1 : 0);
+    w0s[g] = w0;
+    nws[g] = nw;
+    if (frames) {
+      const int need = (w0 + nw - 1) * slot_stride + p.T;
+      if (need > rendered) {
+        st = launch_render(p, frames + (long long)rendered * frame_stride, frame_stride, need - rendered,
+                           first_slot + rendered, s);
+        if (st != DH_OK) return st;
+        rendered = need;
+      }
+    }
+    const int fs = first_slot + w0 * slot_stride;
+    int parts = 0;
+    st = p.prec == DH_PREC_FP32 ? launch_gram_simt(p, fs, slot_stride, nw, &parts, s)
+                                : launch_gram_tc(p, fs, slot_stride, nw, &parts, s);
+    if (st != DH_OK) return st;
+    if ((st = launch_reduce(p, nw, parts, w0, s)) != DH_OK) return st;
+    DH_CUDA_TRY(cudaEventRecord(p.ev_grp[g], s));
+    DH_CUDA_TRY(cudaStreamWaitEvent(p.aux, p.ev_grp[g], 0));
+    st = launch_jacobi(p, nw, k0, k1, nop, eig_user ? eig_user + (long long)w0 * p.T : nullptr, w0, p.aux);
+    if (st != DH_OK) return st;
+    DH_CUDA_TRY(cudaEventRecord(p.ev_jac[g], p.aux));
+    w0 += nw;
+  }
+  for (int g = 0; g < G; ++g) {
+    DH_CUDA_TRY(cudaStreamWaitEvent(s, p.ev_jac[g], 0));
+    const int fs = first_slot + w0s[g] * slot_stride;
+    float *img = images + (long long)w0s[g] * p.npix;
+    st = p.prec == DH_PREC_FP32 ? launch_project_simt(p, fs, slot_stride, nws[g], nop, img, w0s[g], s)
+                                : launch_project_tc(p, fs, slot_stride, nws[g], nop, img, w0s[g], s);
+    if (st != DH_OK) return st;
+  }
+  return DH_OK;
+}
+
 struct Busy {
   std::atomic<int> &b;
   bool ok;
@@ -158,12 +211,10 @@ dh_status dh_plan_create(dh_plan_t *out, int nx, int ny, double lambda_m, double
   cudaError_t e = cudaGetDevice(&p.device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p.aux, cudaStreamNonBlocking);
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-    e = cudaEventCreateWithFlags(&p.ev_rows[k], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.ev_cols[k], cudaEventDisableTiming);
+  for (int k = 0; k < Plan::kMaxGroups && e == cudaSuccess; ++k) {
+    e = cudaEventCreateWithFlags(&p.ev_grp[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.ev_jac[k], cudaEventDisableTiming);
   }
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.ev_fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.ev_join, cudaEventDisableTiming);
   dh_status st = e == cudaSuccess ? DH_OK : fail_cuda(e);
   if (st == DH_OK) {
     std::vector<float2> cx = chirp_table(nx, p.a), cy = chirp_table(ny, p.a);
@@ -197,12 +248,10 @@ void dh_destroy(dh_plan_t h) {
   cudaDeviceSynchronize();
   free_store(p);
   profile_free(p);
-  for (int k = 0; k < 2; ++k) {
-    if (p.ev_rows[k]) cudaEventDestroy(p.ev_rows[k]);
-    if (p.ev_cols[k]) cudaEventDestroy(p.ev_cols[k]);
+  for (int k = 0; k < Plan::kMaxGroups; ++k) {
+    if (p.ev_grp[k]) cudaEventDestroy(p.ev_grp[k]);
+    if (p.ev_jac[k]) cudaEventDestroy(p.ev_jac[k]);
   }
-  if (p.ev_fork) cudaEventDestroy(p.ev_fork);
-  if (p.ev_join) cudaEventDestroy(p.ev_join);
   if (p.aux) cudaStreamDestroy(p.aux);
   dfree(p.d_cx); dfree(p.d_cy); dfree(p.d_twx); dfree(p.d_twy); dfree(p.d_status);
   delete h;
@@ -255,20 +304,8 @@ dh_status dh_pca_windows(dh_plan_t h, int first_slot, int slot_stride, int n_win
     return DH_ERR_INVALID_ARG;
   Busy g(h->busy);
   if (!g.ok) return DH_ERR_STATE;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int nS = k1 - k0 + 1;
-  int parts = 0;
-  dh_status st;
-  if (p.prec == DH_PREC_FP32) {
-    const int nrows = 2 * nS;
-    if ((st = launch_gram_simt(p, first_slot, slot_stride, n_windows, &parts, s)) != DH_OK) return st;
-    if ((st = launch_eig(p, n_windows, parts, k0, k1, nrows, eigvals_dev, s)) != DH_OK) return st;
-    return launch_project_simt(p, first_slot, slot_stride, n_windows, nrows, images_dev, s);
-  }
-  const int Npad = (2 * nS + 15) / 16 * 16;
-  if ((st = launch_gram_tc(p, first_slot, slot_stride, n_windows, &parts, s)) != DH_OK) return st;
-  if ((st = launch_eig(p, n_windows, parts, k0, k1, Npad, eigvals_dev, s)) != DH_OK) return st;
-  return launch_project_tc(p, first_slot, slot_stride, n_windows, Npad, images_dev, s);
+  return pca_impl(p, nullptr, 0, first_slot, slot_stride, n_windows, k0, k1, images_dev, eigvals_dev,
+                  static_cast<cudaStream_t>(stream));
 }
 
 dh_status dh_render_stack(dh_plan_t h, const uint16_t *frames_dev, int64_t frame_stride_elems,
@@ -292,13 +329,18 @@ dh_status dh_pca_window(dh_plan_t h, int k0, int k1, float *image_dev, double *e
 dh_status dh_pca_batch(dh_plan_t h, const uint16_t *frames_dev, int64_t frame_stride_elems,
                        int n_windows, int window_stride_frames, int k0, int k1, float *images_dev,
                        double *eigvals_dev, void *stream) {
-  if (!h || n_windows < 1 || window_stride_frames < 1) return DH_ERR_INVALID_ARG;
-  const long long nf = (long long)(n_windows - 1) * window_stride_frames + h->p.T;
-  if (nf > h->p.max_frames || n_windows > h->p.max_windows) return DH_ERR_INVALID_ARG;
-  dh_status st = dh_render_frames(h, frames_dev, frame_stride_elems, (int)nf, 0, stream);
-  if (st != DH_OK) return st;
-  return dh_pca_windows(h, 0, window_stride_frames, n_windows, k0, k1, images_dev, eigvals_dev,
-                        stream);
+  if (!h || !frames_dev || !images_dev || n_windows < 1 || window_stride_frames < 1) return DH_ERR_INVALID_ARG;
+  Plan &p = h->p;
+  if (k0 < 0 || k1 < k0 || k1 >= p.T) return DH_ERR_INVALID_ARG;
+  const long long nf = (long long)(n_windows - 1) * window_stride_frames + p.T;
+  if (nf > p.max_frames || n_windows > p.max_windows) return DH_ERR_INVALID_ARG;
+  if (frame_stride_elems < p.npix || (frame_stride_elems & 7) != 0 ||
+      (reinterpret_cast<uintptr_t>(frames_dev) & 15u) != 0)
+    return DH_ERR_INVALID_ARG;
+  Busy g(h->busy);
+  if (!g.ok) return DH_ERR_STATE;
+  return pca_impl(p, frames_dev, frame_stride_elems, 0, window_stride_frames, n_windows, k0, k1,
+                  images_dev, eigvals_dev, static_cast<cudaStream_t>(stream));
 }
 
 dh_status dh_debug_hologram(dh_plan_t h, int slot, float *out_dev, void *stream) {

@@ -32,9 +32,10 @@ struct Plan {
   // render intermediate (row-pass output): a chunk of frames sized to stay in L2
   float2 *d_mid = nullptr;
   int mid_frames = 0;
-  cudaStream_t aux = nullptr;  // second stream: eigensolver overlap within a batch
-  cudaEvent_t ev_rows[2] = {nullptr, nullptr}, ev_cols[2] = {nullptr, nullptr};
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // second stream: the eigensolver of one group of windows overlaps the next group's work
+  cudaStream_t aux = nullptr;
+  static constexpr int kMaxGroups = 4;
+  cudaEvent_t ev_grp[kMaxGroups] = {}, ev_jac[kMaxGroups] = {};
   // hologram store: [max_frames][2][npix] of the storage type
   void *d_H = nullptr;
   size_t H_elem_bytes = 4;
@@ -106,14 +107,17 @@ dh_status launch_gram_simt(Plan &p, int first_slot, int slot_stride, int n_windo
 // Eq. 4, tensor cores (16-bit storage).
 dh_status launch_gram_tc(Plan &p, int first_slot, int slot_stride, int n_windows,
                          int *parts_per_window, cudaStream_t s);
-// Eq. 5 + ordering + operand build for Eq. 6.
-dh_status launch_eig(Plan &p, int n_windows, int parts_per_window, int k0, int k1, int Npad,
-                     double *eigvals_out, cudaStream_t s);
+// Eq. 4 final FP64 reduction, then Eq. 5 + ordering + operand build for Eq. 6, for windows
+// [woff, woff + n_windows) of the plan's per-window buffers.
+dh_status launch_reduce(Plan &p, int n_windows, int parts_per_window, int woff, cudaStream_t s);
+dh_status launch_jacobi(Plan &p, int n_windows, int k0, int k1, int Npad, double *eig_user, int woff,
+                        cudaStream_t s);
 // Eqs. 6-7.
+// images points at window woff's image; woff selects the windows' operands.
 dh_status launch_project_simt(Plan &p, int first_slot, int slot_stride, int n_windows, int Npad,
-                              float *images, cudaStream_t s);
+                              float *images, int woff, cudaStream_t s);
 dh_status launch_project_tc(Plan &p, int first_slot, int slot_stride, int n_windows, int Npad,
-                            float *images, cudaStream_t s);
+                            float *images, int woff, cudaStream_t s);
 dh_status make_tensor_maps(Plan &p);
 
 // single-window helpers used by the allocation-free covariance entry point

@@ -59,7 +59,7 @@ template <> __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16
   return __bfloat162float(x);
 }
 
-// Pack value v of operand entry (j, r) for the projection of Eq. 6 (see launch_eig).
+// Pack value v of operand entry (j, r) for the projection of Eq. 6 (see k_jacobi).
 template <typename T16>
 __device__ __forceinline__ void put_split(T16 *hi, T16 *lo, long long i, double v) {
   const T16 h = from_f32<T16>((float)v);
@@ -99,7 +99,8 @@ __device__ int jacobi_sweeps(Real *ar, Real *ai, Real *vr, Real *vi, double tol,
         const Real gr = ar[p * LD + q], gi = ai[p * LD + q];
         const Real g = sqrt(gr * gr + gi * gi);
         Real c = 1, wr = 0, wi = 0;
-        if (g > (Real)(1e-18 * fro)) {  // rotations below this leave every entry unchanged
+        // rotations this small cannot hold off(A) above tol ||A||_F; they are skipped
+        if (g > (Real)(1e-2 * tol * fro / T)) {
           const Real tau = (ar[q * LD + q] - ar[p * LD + p]) / (2 * g);
           const Real t = (tau >= 0 ? (Real)1 : (Real)-1) / (fabs(tau) + sqrt(1 + tau * tau));
           c = 1 / sqrt(1 + t * t);
@@ -329,14 +330,18 @@ k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restr
 }
 
 template <int T>
-dh_status launch_eig_t(Plan &p, int n_windows, int parts, int k0, int k1, int Npad,
-                       double *eig_user, cudaStream_t s) {
+dh_status launch_reduce_t(Plan &p, int n_windows, int parts, int woff, cudaStream_t s) {
   const int total = n_windows * T * T;
-  {
-    ProfScope ps(p, K_REDUCE_COV, s);
-    k_reduce_cov<T><<<(total + 255) / 256, 256, 0, s>>>(p.d_part, parts, n_windows, p.d_C, p.d_status);
-  }
+  ProfScope ps(p, K_REDUCE_COV, s);
+  k_reduce_cov<T><<<(total + 255) / 256, 256, 0, s>>>(p.d_part, parts, n_windows,
+                                                      p.d_C + 2ll * woff * T * T, p.d_status);
   DH_CUDA_TRY(cudaGetLastError());
+  return DH_OK;
+}
+
+template <int T>
+dh_status launch_jacobi_t(Plan &p, int n_windows, int k0, int k1, int Npad, double *eig_user, int woff,
+                          cudaStream_t s) {
   const size_t smem = 6ull * T * (T + 1) * sizeof(double);
   static bool attr = false;
   if (!attr) {
@@ -344,9 +349,11 @@ dh_status launch_eig_t(Plan &p, int n_windows, int parts, int k0, int k1, int Np
     attr = true;
   }
   const long long B_stride = (long long)(p.B_window_bytes / (p.prec == DH_PREC_FP32 ? 4 : 2));
+  void *B = static_cast<char *>(p.d_B) + (size_t)woff * p.B_window_bytes;
   ProfScope ps(p, K_JACOBI, s);
-  k_jacobi<T><<<n_windows, 256, smem, s>>>(p.d_C, p.d_lam, p.d_V, eig_user, (int)p.prec, p.d_B,
-                                           B_stride, k0, k1, Npad, 1e-14, 30, p.d_status);
+  k_jacobi<T><<<n_windows, 256, smem, s>>>(p.d_C + 2ll * woff * T * T, p.d_lam + (long long)woff * T,
+                                           p.d_V + 2ll * woff * T * T, eig_user, (int)p.prec, B, B_stride,
+                                           k0, k1, Npad, 5e-14, 30, p.d_status);
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
 }
@@ -367,12 +374,24 @@ dh_status launch_reduce_cov_window(const double *part, int parts, int T, double 
   return DH_OK;
 }
 
-dh_status launch_eig(Plan &p, int n_windows, int parts, int k0, int k1, int Npad,
-                     double *eig_user, cudaStream_t s) {
+// FP64 reduction of the covariance partials of windows [woff, woff + n_windows).
+dh_status launch_reduce(Plan &p, int n_windows, int parts, int woff, cudaStream_t s) {
   switch (p.T) {
-    case 16: return launch_eig_t<16>(p, n_windows, parts, k0, k1, Npad, eig_user, s);
-    case 32: return launch_eig_t<32>(p, n_windows, parts, k0, k1, Npad, eig_user, s);
-    case 64: return launch_eig_t<64>(p, n_windows, parts, k0, k1, Npad, eig_user, s);
+    case 16: return launch_reduce_t<16>(p, n_windows, parts, woff, s);
+    case 32: return launch_reduce_t<32>(p, n_windows, parts, woff, s);
+    case 64: return launch_reduce_t<64>(p, n_windows, parts, woff, s);
+  }
+  return DH_ERR_UNSUPPORTED_SIZE;
+}
+
+// Eq. 5 + ordering + operand build for windows [woff, woff + n_windows); eig_user (if not
+// NULL) already points at window woff's eigenvalues.
+dh_status launch_jacobi(Plan &p, int n_windows, int k0, int k1, int Npad, double *eig_user, int woff,
+                        cudaStream_t s) {
+  switch (p.T) {
+    case 16: return launch_jacobi_t<16>(p, n_windows, k0, k1, Npad, eig_user, woff, s);
+    case 32: return launch_jacobi_t<32>(p, n_windows, k0, k1, Npad, eig_user, woff, s);
+    case 64: return launch_jacobi_t<64>(p, n_windows, k0, k1, Npad, eig_user, woff, s);
   }
   return DH_ERR_UNSUPPORTED_SIZE;
 }

@@ -245,7 +245,7 @@ template <int T, bool BF16>
 __global__ void __launch_bounds__(ProjCfg<T>::THREADS, 1)
 k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmB,
              int first_slot, int slot_stride, int n_windows, int tiles_pw, int Npad, int B_rows_pw,
-             float *__restrict__ images, int nx, int ny, uint32_t *__restrict__ status) {
+             int b_row0, float *__restrict__ images, int nx, int ny, uint32_t *__restrict__ status) {
   using C = ProjCfg<T>;
   const long long npix = (long long)nx * ny;
   // Holograms are stored with column-major pixels p = kx n_y + ky, so a 128-pixel tile is
@@ -314,7 +314,7 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
           for (int half = 0; half < 2; ++half)
             for (int kh = 0; kh < C::M2 / C::KB; ++kh)
               tma_load_2d(bsm + half * b_half_bytes + kh * Npad * C::B_ROW, &tmB, bfull, kh * C::KB,
-                          w * B_rows_pw + half * Npad);
+                          b_row0 + w * B_rows_pw + half * Npad);
           b_pending = true;
           bph ^= 1;
           cur_w = w;
@@ -520,7 +520,7 @@ dh_status gram_t(Plan &p, int first_slot, int slot_stride, int n_windows, cudaSt
 
 template <int T, bool BF16>
 dh_status project_t(Plan &p, int first_slot, int slot_stride, int n_windows, int Npad, float *images,
-                    cudaStream_t s) {
+                    int woff, cudaStream_t s) {
   using C = ProjCfg<T>;
   auto kern = k_project_tc<T, BF16>;
   static bool attr = false;
@@ -549,7 +549,8 @@ dh_status project_t(Plan &p, int first_slot, int slot_stride, int n_windows, int
   if (grid > total) grid = (int)total;
   ProfScope ps(p, K_PROJECT_TC, s);
   kern<<<grid, C::THREADS, C::SMEM, s>>>(p.tmap_H, tmB, first_slot, slot_stride, n_windows, tiles_pw, Npad,
-                                          (int)B_rows_pw, images, p.nx, p.ny, p.d_status);
+                                          (int)B_rows_pw, (int)(woff * B_rows_pw), images, p.nx, p.ny,
+                                          p.d_status);
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
 }
@@ -589,16 +590,16 @@ dh_status launch_gram_tc(Plan &p, int first_slot, int slot_stride, int n_windows
 }
 
 dh_status launch_project_tc(Plan &p, int first_slot, int slot_stride, int n_windows, int Npad,
-                            float *images, cudaStream_t s) {
+                            float *images, int woff, cudaStream_t s) {
   if (!p.tmaps_ok) return DH_ERR_STATE;
   const bool bf16 = p.prec == DH_PREC_BF16;
   switch (p.T) {
-    case 16: return bf16 ? project_t<16, true>(p, first_slot, slot_stride, n_windows, Npad, images, s)
-                         : project_t<16, false>(p, first_slot, slot_stride, n_windows, Npad, images, s);
-    case 32: return bf16 ? project_t<32, true>(p, first_slot, slot_stride, n_windows, Npad, images, s)
-                         : project_t<32, false>(p, first_slot, slot_stride, n_windows, Npad, images, s);
-    case 64: return bf16 ? project_t<64, true>(p, first_slot, slot_stride, n_windows, Npad, images, s)
-                         : project_t<64, false>(p, first_slot, slot_stride, n_windows, Npad, images, s);
+    case 16: return bf16 ? project_t<16, true>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s)
+                         : project_t<16, false>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s);
+    case 32: return bf16 ? project_t<32, true>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s)
+                         : project_t<32, false>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s);
+    case 64: return bf16 ? project_t<64, true>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s)
+                         : project_t<64, false>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s);
   }
   return DH_ERR_UNSUPPORTED_SIZE;
 }
