@@ -37,7 +37,8 @@
 extern "C" {
 #endif
 
-typedef struct dh_plan *dh_plan_t; /* opaque, library-owned */
+typedef struct dh_plan *dh_plan_t;   /* opaque, library-owned */
+typedef struct dh_graph *dh_graph_t; /* opaque, library-owned */
 
 typedef enum {
   DH_OK = 0,
@@ -73,8 +74,24 @@ typedef enum { DH_PREC_FP32 = 0, DH_PREC_FP16 = 1, DH_PREC_BF16 = 2 } dh_precisi
 dh_status dh_plan_create(dh_plan_t *out, int nx, int ny, double lambda_m, double z_m,
                          double pitch_m, int T);
 
-/* Release every device buffer of the plan. NULL-safe. Synchronises the device. */
+/* Release every device buffer of the plan. NULL-safe. Synchronises the device. A plan
+ * whose store live views still read keeps that store until its last view is destroyed. */
 void dh_destroy(dh_plan_t plan);
+
+/* A view: a plan for windows of T' frames (T' in {16, 32, 64}, T' <= the base's slots)
+ * over the hologram store of `base`, so that windows of several lengths share one
+ * rendering of each frame (Eq. 1 is per frame; Eqs. 4-7 are per window). The view has
+ * its own covariance, eigenvector and projection buffers (one window until
+ * dh_plan_reserve(view, ., max_windows)), the base's frame size, optics and storage
+ * type, and renders nothing: dh_render_frames / dh_render_stack / dh_pca_batch on a
+ * view return DH_ERR_STATE. While views live, dh_plan_set_precision on the base and a
+ * dh_plan_reserve that changes its slot count return DH_ERR_STATE. Work on the base and
+ * on its views touches the same store: order it (one stream, or events) as for one plan.
+ * A view of a view reads the same store. The paper renders each frame once and runs one
+ * window length; views extend that to several lengths at once. Synchronous.
+ * Errors: DH_ERR_INVALID_ARG (NULL out or base, T' above the base's slots),
+ * DH_ERR_UNSUPPORTED_SIZE (T'), DH_ERR_OOM, DH_ERR_CUDA. */
+dh_status dh_plan_create_view(dh_plan_t *out, dh_plan_t base, int T);
 
 /* Select the hologram storage type (default DH_PREC_FP32). Reallocates the hologram
  * store; previously rendered holograms are discarded. Synchronous. */
@@ -171,6 +188,22 @@ int dh_profile_read(dh_plan_t plan, int n, const char **names, int *launches, do
  * array, so calls that overlap on the GPU race. Asynchronous on `stream`. */
 dh_status dh_covariance_noalloc(const float *planes_dev, int64_t npix, int T, double *C_dev,
                                 void *stream);
+
+/* CUDA graphs of library calls. dh_graph_begin starts capturing `stream` (a created
+ * stream, not NULL: the legacy default stream cannot be captured; capture mode
+ * thread-local). Every library call made on that stream until dh_graph_end is recorded,
+ * not run, including the work the library forks onto a plan's internal stream and joins
+ * back. dh_graph_end ends the capture and instantiates it into *out; dh_graph_launch runs
+ * it on a stream (asynchronous), any number of times, against the same buffers and
+ * arguments as captured. Calls that synchronise (dh_pca_window with eigvals_host,
+ * dh_plan_status, create/reserve/destroy) must not be made during a capture (they fail
+ * with DH_ERR_CUDA and invalidate it). Per-kernel tracing skips captured launches. The
+ * paper launches library calls one by one; graphs remove the host launch cost of the
+ * many short launches of small frames. */
+dh_status dh_graph_begin(void *stream);
+dh_status dh_graph_end(void *stream, dh_graph_t *out);
+dh_status dh_graph_launch(dh_graph_t graph, void *stream);
+void dh_graph_destroy(dh_graph_t graph); /* NULL-safe */
 
 /* Text of a status code, and of the last CUDA error recorded by the library. */
 const char *dh_status_string(dh_status s);

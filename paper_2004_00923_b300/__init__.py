@@ -13,6 +13,7 @@ analysis", arXiv 2004.00923 (Eqs. 1, 4, 5, 6, 7).
 
 from __future__ import annotations
 
+import contextlib
 import ctypes
 
 import torch
@@ -20,7 +21,7 @@ import torch
 from . import _lib
 from ._lib import DHError, PREC  # noqa: F401
 
-__all__ = ["Plan", "DHError", "PREC", "version"]
+__all__ = ["Plan", "Graph", "capture", "DHError", "PREC", "version"]
 
 
 def version() -> str:
@@ -55,6 +56,24 @@ class Plan:
         if self.max_frames != self.T or self.max_windows != 1:
             _lib.check("dh_plan_reserve",
                        self._lib.dh_plan_reserve(h, self.max_frames, self.max_windows))
+
+    def view(self, T: int, max_windows: int = 1) -> "Plan":
+        """A plan for windows of T frames over this plan's hologram store
+        (dh_plan_create_view): windows of several lengths share one rendering."""
+        v = Plan.__new__(Plan)
+        v._lib = self._lib
+        v.nx, v.ny, v.T = self.nx, self.ny, int(T)
+        v.precision = self.precision
+        h = ctypes.c_void_p()
+        _lib.check("dh_plan_create_view",
+                   self._lib.dh_plan_create_view(ctypes.byref(h), self._h, v.T))
+        v._h = h
+        v.max_frames = self.max_frames
+        v.max_windows = int(max_windows)
+        if v.max_windows != 1:
+            _lib.check("dh_plan_reserve",
+                       self._lib.dh_plan_reserve(h, v.max_frames, v.max_windows))
+        return v
 
     # -- lifetime -------------------------------------------------------------
     def close(self) -> None:
@@ -175,3 +194,47 @@ class Plan:
         flags = ctypes.c_uint32(0)
         _lib.check("dh_plan_status", self._lib.dh_plan_status(self._h, ctypes.byref(flags)))
         return int(flags.value)
+
+
+class Graph:
+    """An instantiated CUDA graph of library calls (dh_graph_*)."""
+
+    def __init__(self):
+        self._lib = _lib.load()
+        self._h = None
+
+    def launch(self, stream=None) -> None:
+        _lib.check("dh_graph_launch", self._lib.dh_graph_launch(self._h, _stream_ptr(stream)))
+
+    def close(self) -> None:
+        if self._h is not None and self._h.value:
+            self._lib.dh_graph_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@contextlib.contextmanager
+def capture(stream: torch.cuda.Stream):
+    """Record the library calls made on `stream` (a created stream, made current inside the
+    block) into a Graph instead of running them. Pass preallocated output tensors to calls
+    made inside the block: nothing may allocate device memory during a capture."""
+    lib = _lib.load()
+    g = Graph()
+    ptr = int(stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        _lib.check("dh_graph_begin", lib.dh_graph_begin(ptr))
+        ok = False
+        try:
+            yield g
+            ok = True
+        finally:
+            h = ctypes.c_void_p()
+            code = lib.dh_graph_end(ptr, ctypes.byref(h))
+            g._h = h
+            if ok:
+                _lib.check("dh_graph_end", code)

@@ -23,6 +23,7 @@ _vp, _i, _i64, _d, _u32p = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes
 SIGNATURES = [
     ("dh_plan_create", _i, [ctypes.POINTER(_vp), _i, _i, _d, _d, _d, _i]),
     ("dh_destroy", None, [_vp]),
+    ("dh_plan_create_view", _i, [ctypes.POINTER(_vp), _vp, _i]),
     ("dh_plan_set_precision", _i, [_vp, _i]),
     ("dh_plan_reserve", _i, [_vp, _i, _i]),
     ("dh_plan_device_bytes", ctypes.c_size_t, [_vp]),
@@ -39,6 +40,10 @@ SIGNATURES = [
     ("dh_profile_read", _i, [_vp, _i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_i),
                              ctypes.POINTER(_d)]),
     ("dh_covariance_noalloc", _i, [_vp, _i64, _i, _vp, _vp]),
+    ("dh_graph_begin", _i, [_vp]),
+    ("dh_graph_end", _i, [_vp, ctypes.POINTER(_vp)]),
+    ("dh_graph_launch", _i, [_vp, _vp]),
+    ("dh_graph_destroy", None, [_vp]),
     ("dh_status_string", ctypes.c_char_p, [_i]),
     ("dh_last_error", ctypes.c_char_p, []),
     ("dh_version", ctypes.c_char_p, []),

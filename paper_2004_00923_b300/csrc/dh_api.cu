@@ -13,6 +13,13 @@
 struct dh_plan {
   dh::Plan p;
   std::atomic<int> busy{0};
+  std::atomic<int> refs{1};   // the caller's handle + one per live view of this plan
+  std::atomic<int> views{0};  // live views sharing this plan's hologram store
+  dh_plan *base = nullptr;    // for a view: the plan whose store it reads
+};
+
+struct dh_graph {
+  cudaGraphExec_t exec = nullptr;
 };
 
 namespace dh {
@@ -51,24 +58,34 @@ void dfree(Ptr *&ptr) {
   ptr = nullptr;
 }
 
-void free_store(Plan &p) {
-  dfree(p.d_H); dfree(p.d_part); dfree(p.d_C); dfree(p.d_lam); dfree(p.d_V); dfree(p.d_B);
-  dfree(p.d_mid);
+// Per-window buffers: covariance partials, C, lambda, V and the projection operand.
+void free_windows(Plan &p) {
+  dfree(p.d_part); dfree(p.d_C); dfree(p.d_lam); dfree(p.d_V); dfree(p.d_B);
   p.tmaps_ok = false;
+  p.bytes -= p.window_bytes;
+  p.window_bytes = 0;
+}
+
+void free_store(Plan &p) {
+  free_windows(p);
+  if (p.is_view) {
+    p.d_H = nullptr;  // owned by the base plan
+  } else {
+    dfree(p.d_H);
+    dfree(p.d_mid);
+  }
 }
 
 size_t table_bytes(const Plan &p) {
   return sizeof(float2) * (p.nx + p.ny + twiddle_len(p.lognx) + twiddle_len(p.logny)) + 16;
 }
 
-// (Re)allocate everything whose size depends on the reservation or the precision.
-dh_status alloc_store(Plan &p) {
-  free_store(p);
-  p.bytes = table_bytes(p);
+// (Re)allocate the per-window buffers for max_windows windows of length T over the store.
+dh_status alloc_windows(Plan &p) {
+  free_windows(p);
+  const size_t before = p.bytes;
   const int M = 2 * p.T;
-  p.H_elem_bytes = p.prec == DH_PREC_FP32 ? 4 : 2;
   dh_status st;
-  if ((st = dalloc(p, &p.d_H, (size_t)p.max_frames * 2 * p.npix * p.H_elem_bytes)) != DH_OK) return st;
   p.parts_total = p.max_windows * parts_per_window(p);
   if ((st = dalloc(p, &p.d_part, (size_t)p.parts_total * M * M * sizeof(double))) != DH_OK) return st;
   if ((st = dalloc(p, &p.d_C, (size_t)p.max_windows * p.T * p.T * 2 * sizeof(double))) != DH_OK) return st;
@@ -78,17 +95,33 @@ dh_status alloc_store(Plan &p) {
   size_t bw = p.prec == DH_PREC_FP32 ? (size_t)M * M * 4 : (size_t)2 * M * M * 2;
   p.B_window_bytes = (bw + 1023) / 1024 * 1024;
   if ((st = dalloc(p, &p.d_B, p.B_window_bytes * p.max_windows)) != DH_OK) return st;
-  // row-pass intermediate: a chunk of frames sized to stay in L2 (~96 MiB of the 126 MB)
-  long long mf = (96ll << 20) / (p.npix * (long long)sizeof(float2));
-  if (mf < 1) mf = 1;
-  if (mf > 64) mf = 64;
-  p.mid_frames = (int)mf;
-  if ((st = dalloc(p, &p.d_mid, (size_t)p.mid_frames * p.npix * sizeof(float2))) != DH_OK) return st;
+  p.window_bytes = p.bytes - before;
   DH_CUDA_TRY(cudaMemset(p.d_B, 0, p.B_window_bytes * p.max_windows));
   if (p.prec != DH_PREC_FP32) {
     if ((st = make_tensor_maps(p)) != DH_OK) return st;
   }
   return DH_OK;
+}
+
+// (Re)allocate everything whose size depends on the reservation or the precision. A view
+// takes the store of `base` instead of allocating one.
+dh_status alloc_store(Plan &p, const Plan *base = nullptr) {
+  free_store(p);
+  p.bytes = p.is_view ? 0 : table_bytes(p);
+  p.H_elem_bytes = p.prec == DH_PREC_FP32 ? 4 : 2;
+  dh_status st;
+  if (p.is_view) {
+    p.d_H = base->d_H;
+  } else {
+    if ((st = dalloc(p, &p.d_H, (size_t)p.max_frames * 2 * p.npix * p.H_elem_bytes)) != DH_OK) return st;
+    // row-pass intermediate: a chunk of frames sized to stay in L2 (~96 MiB of the 126 MB)
+    long long mf = (96ll << 20) / (p.npix * (long long)sizeof(float2));
+    if (mf < 1) mf = 1;
+    if (mf > 64) mf = 64;
+    p.mid_frames = (int)mf;
+    if ((st = dalloc(p, &p.d_mid, (size_t)p.mid_frames * p.npix * sizeof(float2))) != DH_OK) return st;
+  }
+  return alloc_windows(p);
 }
 
 std::vector<float2> chirp_table(int n, double a) {
@@ -242,8 +275,10 @@ dh_status dh_plan_create(dh_plan_t *out, int nx, int ny, double lambda_m, double
   return DH_OK;
 }
 
-void dh_destroy(dh_plan_t h) {
-  if (!h) return;
+namespace {
+// Frees a plan once neither the caller's handle nor a view refers to it any more.
+void release(dh_plan_t h) {
+  if (!h || h->refs.fetch_sub(1) != 1) return;
   Plan &p = h->p;
   cudaDeviceSynchronize();
   free_store(p);
@@ -254,12 +289,61 @@ void dh_destroy(dh_plan_t h) {
   }
   if (p.aux) cudaStreamDestroy(p.aux);
   dfree(p.d_cx); dfree(p.d_cy); dfree(p.d_twx); dfree(p.d_twy); dfree(p.d_status);
+  dh_plan *base = h->base;
   delete h;
+  if (base) {
+    base->views.fetch_sub(1);
+    release(base);
+  }
+}
+}  // namespace
+
+void dh_destroy(dh_plan_t h) { release(h); }
+
+dh_status dh_plan_create_view(dh_plan_t *out, dh_plan_t base_h, int T) {
+  if (!out) return DH_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!base_h) return DH_ERR_INVALID_ARG;
+  if (!(T == 16 || T == 32 || T == 64)) return DH_ERR_UNSUPPORTED_SIZE;
+  while (base_h->base) base_h = base_h->base;  // a view of a view reads the same store
+  const Plan &b = base_h->p;
+  if (T > b.max_frames) return DH_ERR_INVALID_ARG;
+  dh_plan *h = new (std::nothrow) dh_plan();
+  if (!h) return DH_ERR_OOM;
+  Plan &p = h->p;
+  p.is_view = true;
+  p.nx = b.nx; p.ny = b.ny; p.T = T; p.lognx = b.lognx; p.logny = b.logny; p.npix = b.npix;
+  p.lambda = b.lambda; p.z = b.z; p.pitch = b.pitch; p.a = b.a;
+  p.prec = b.prec;
+  p.device = b.device; p.num_sms = b.num_sms;
+  p.max_frames = b.max_frames;
+  p.max_windows = 1;
+  base_h->refs.fetch_add(1);
+  base_h->views.fetch_add(1);
+  h->base = base_h;
+  cudaError_t e = cudaStreamCreateWithFlags(&p.aux, cudaStreamNonBlocking);
+  for (int k = 0; k < Plan::kMaxGroups && e == cudaSuccess; ++k) {
+    e = cudaEventCreateWithFlags(&p.ev_grp[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.ev_jac[k], cudaEventDisableTiming);
+  }
+  dh_status st = e == cudaSuccess ? dalloc(p, &p.d_status, sizeof(uint32_t)) : fail_cuda(e);
+  if (st == DH_OK) {
+    cudaError_t c = cudaMemset(p.d_status, 0, sizeof(uint32_t));
+    st = c == cudaSuccess ? alloc_store(p, &b) : fail_cuda(c);
+  }
+  if (st != DH_OK) {
+    release(h);
+    return st;
+  }
+  *out = h;
+  return DH_OK;
 }
 
 dh_status dh_plan_set_precision(dh_plan_t h, dh_precision prec) {
   if (!h) return DH_ERR_INVALID_ARG;
   if (prec != DH_PREC_FP32 && prec != DH_PREC_FP16 && prec != DH_PREC_BF16) return DH_ERR_INVALID_ARG;
+  // a view follows its base's storage; a base cannot change it under live views
+  if (h->base || h->views.load() > 0) return DH_ERR_STATE;
   Busy g(h->busy);
   if (!g.ok) return DH_ERR_STATE;
   DH_CUDA_TRY(cudaDeviceSynchronize());
@@ -269,11 +353,20 @@ dh_status dh_plan_set_precision(dh_plan_t h, dh_precision prec) {
 
 dh_status dh_plan_reserve(dh_plan_t h, int max_frames, int max_windows) {
   if (!h || max_frames < h->p.T || max_windows < 1) return DH_ERR_INVALID_ARG;
+  if (h->base) {
+    // a view reserves windows only; its slots are the base's
+    if (max_frames > h->base->p.max_frames) return DH_ERR_INVALID_ARG;
+  } else if (h->views.load() > 0 && max_frames != h->p.max_frames) {
+    return DH_ERR_STATE;
+  }
   Busy g(h->busy);
   if (!g.ok) return DH_ERR_STATE;
   DH_CUDA_TRY(cudaDeviceSynchronize());
-  h->p.max_frames = max_frames;
   h->p.max_windows = max_windows;
+  // a view's slots are its base's, and a base with live views keeps its store in place
+  // (the views hold its address): only the per-window buffers change
+  if (h->base || h->views.load() > 0) return alloc_windows(h->p);
+  h->p.max_frames = max_frames;
   return alloc_store(h->p);
 }
 
@@ -285,6 +378,7 @@ dh_status dh_render_frames(dh_plan_t h, const uint16_t *frames_dev, int64_t fram
   Plan &p = h->p;
   if (frame_stride_elems < p.npix || (long long)first_slot + n_frames > p.max_frames)
     return DH_ERR_INVALID_ARG;
+  if (p.is_view) return DH_ERR_STATE;  // views render nothing: render through the base plan
   // frames are read with 16-byte vector loads
   if ((reinterpret_cast<uintptr_t>(frames_dev) & 15u) != 0 || (frame_stride_elems & 7) != 0)
     return DH_ERR_INVALID_ARG;
@@ -337,6 +431,7 @@ dh_status dh_pca_batch(dh_plan_t h, const uint16_t *frames_dev, int64_t frame_st
   if (frame_stride_elems < p.npix || (frame_stride_elems & 7) != 0 ||
       (reinterpret_cast<uintptr_t>(frames_dev) & 15u) != 0)
     return DH_ERR_INVALID_ARG;
+  if (p.is_view) return DH_ERR_STATE;
   Busy g(h->busy);
   if (!g.ok) return DH_ERR_STATE;
   return pca_impl(p, frames_dev, frame_stride_elems, 0, window_stride_frames, n_windows, k0, k1,
@@ -382,6 +477,44 @@ dh_status dh_plan_status(dh_plan_t h, uint32_t *flags) {
   DH_CUDA_TRY(cudaMemcpy(flags, h->p.d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
   DH_CUDA_TRY(cudaMemset(h->p.d_status, 0, sizeof(uint32_t)));
   return DH_OK;
+}
+
+// ---------------------------------------------------------------- CUDA graphs
+dh_status dh_graph_begin(void *stream) {
+  if (!stream) return DH_ERR_INVALID_ARG;  // the legacy default stream cannot be captured
+  DH_CUDA_TRY(cudaStreamBeginCapture(static_cast<cudaStream_t>(stream), cudaStreamCaptureModeThreadLocal));
+  return DH_OK;
+}
+
+dh_status dh_graph_end(void *stream, dh_graph_t *out) {
+  if (!stream || !out) return DH_ERR_INVALID_ARG;
+  *out = nullptr;
+  cudaGraph_t graph = nullptr;
+  DH_CUDA_TRY(cudaStreamEndCapture(static_cast<cudaStream_t>(stream), &graph));
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail_cuda(e);
+  dh_graph *g = new (std::nothrow) dh_graph();
+  if (!g) {
+    cudaGraphExecDestroy(exec);
+    return DH_ERR_OOM;
+  }
+  g->exec = exec;
+  *out = g;
+  return DH_OK;
+}
+
+dh_status dh_graph_launch(dh_graph_t g, void *stream) {
+  if (!g || !g->exec) return DH_ERR_INVALID_ARG;
+  DH_CUDA_TRY(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
+  return DH_OK;
+}
+
+void dh_graph_destroy(dh_graph_t g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  delete g;
 }
 
 }  // extern "C"

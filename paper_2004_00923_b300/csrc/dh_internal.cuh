@@ -23,6 +23,9 @@ struct Plan {
   int device = 0;
   int num_sms = 148;
 
+  // a view computes windows of its own length T over another plan's hologram store; it
+  // holds no store, intermediate or tables of its own and renders nothing
+  bool is_view = false;
   int max_frames = 0;   // hologram slots
   int max_windows = 0;  // windows per dh_pca_windows call
 
@@ -54,7 +57,8 @@ struct Plan {
   CUtensorMap tmap_B;
   bool tmaps_ok = false;
 
-  size_t bytes = 0;
+  size_t bytes = 0;         // device bytes the plan itself allocated
+  size_t window_bytes = 0;  // the part of `bytes` in per-window buffers
   int busy = 0;
   void *prof = nullptr;  // per-kernel event timing state (profile.cu), null when disabled
 };

@@ -29,6 +29,10 @@ const char *kernel_name(int kid) { return kid >= 0 && kid < K_COUNT ? kNames[kid
 
 ProfScope::ProfScope(Plan &plan, int k, cudaStream_t st) : p(plan), kid(k), s(st), slot(-1) {
   if (!p.prof) return;
+  // launches being captured into a CUDA graph are not timed (the events would become graph
+  // nodes, not timestamps of a run)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
   ProfState *ps = static_cast<ProfState *>(p.prof);
   ProfState::Rec r{kid, ps->get(), ps->get()};
   cudaEventRecord(r.a, s);

@@ -13,18 +13,9 @@ import torch
 
 import oracle
 from dh_synth import SpeckleParams, SpeckleStream, known_rank_frames, speckle_window
+from parity_helpers import LAM, PITCH, TOL_IMG, TOL_LAM, Z, check_window, lam_tol, rel, to_gpu
 
 pytestmark = pytest.mark.gpu
-
-LAM, Z, PITCH = 785e-9, 0.35, 20e-6
-TOL_IMG = {"fp32": 1e-4, "fp16": 1e-3}
-TOL_LAM = 1e-5
-
-
-def rel(a, b):
-    a, b = np.asarray(a), np.asarray(b)
-    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
-
 
 @pytest.fixture(scope="module")
 def dh():
@@ -32,10 +23,6 @@ def dh():
         pytest.skip("needs a CUDA GPU")
     import paper_2004_00923_b300 as m
     return m
-
-
-def to_gpu(frames_np):
-    return torch.from_numpy(np.ascontiguousarray(frames_np)).cuda()
 
 
 # ------------------------------------------------------------------------ Eq. 1
@@ -87,46 +74,6 @@ def gpu_windows(dh, frames_np, T, prec, k0, k1, n_windows, stride):
         C = [plan.debug_covariance(w).cpu().numpy() for w in range(n_windows)]
         flags = plan.status()
     return images.cpu().numpy(), lam.cpu().numpy(), C, flags
-
-
-# Relative covariance error each storage achieves (||dC|| / ||C||, measured against the
-# oracle); the image of a retained range [k0, k1] moves by about ||dC|| / gap, where gap is
-# the eigenvalue gap at the range boundary (Davis-Kahan), so the image tolerance is the
-# stated one where the boundary is well separated and eps_C * lambda_max / gap beyond.
-EPS_C = {"fp32": 1e-8, "fp16": 1e-5}
-
-
-def boundary_gap(lam, k0, k1):
-    gaps = []
-    if k0 > 0:
-        gaps.append(lam[k0 - 1] - lam[k0])
-    if k1 < len(lam) - 1:
-        gaps.append(lam[k1] - lam[k1 + 1])
-    return min(gaps) / lam[0] if gaps else 1.0
-
-
-# 16-bit storage rounds every hologram value with unit roundoff u; the resulting covariance
-# noise is ~u/sqrt(n) relative per entry and moves eigenvalues by up to ~4 u/sqrt(n) of
-# lambda_max. At the workload sizes (n >= 256^2) that is below the stated 1e-5; tiny frames
-# used for edge cases get the storage bound instead.
-U16 = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8}
-
-
-def lam_tol(prec, npix):
-    return TOL_LAM if prec == "fp32" else max(TOL_LAM, 4 * U16[prec] / np.sqrt(npix))
-
-
-def check_window(img, lam, C, frames_np, k0, k1, prec):
-    M, lam_ref, C_ref, _ = oracle.pca_window(frames_np, LAM, Z, PITCH, k0, k1)
-    e_img = rel(img, M)
-    e_lam = float(np.max(np.abs(lam - lam_ref)) / lam_ref[0])
-    e_C = rel(C, C_ref)
-    gap = boundary_gap(lam_ref, k0, k1)
-    tol_img = max(TOL_IMG[prec], EPS_C[prec] / gap)
-    assert e_lam <= lam_tol(prec, frames_np[0].size), e_lam
-    assert e_img <= tol_img, (e_img, gap)
-    assert e_C <= (5e-6 if prec == "fp32" else 2e-4), e_C
-    return e_img, e_lam, e_C
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])

@@ -1,0 +1,159 @@
+"""Sliding windows of several lengths over one rendering, and CUDA graphs of library calls.
+
+Each frame is rendered once (Eq. 1 is per frame) into a base plan's hologram store; views of
+that store run Eqs. 4-7 for 16-, 32- and 64-frame windows at stride 8. Every window is
+checked against the FP64 oracle run on that window's own frames, a view's windows are
+bitwise those of a stand-alone plan of the same length, and a captured graph replays the
+whole step bitwise.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from dh_synth import SpeckleParams, SpeckleStream
+from parity_helpers import LAM, PITCH, Z, check_window, to_gpu
+
+pytestmark = pytest.mark.gpu
+
+LENGTHS = (16, 32, 64)
+STRIDE = 8
+
+
+@pytest.fixture(scope="module")
+def dh():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2004_00923_b300 as m
+    return m
+
+
+def counts(n_frames):
+    return {T: (n_frames - T) // STRIDE + 1 for T in LENGTHS}
+
+
+class Sliding:
+    """A base plan (T = 16) plus views for 32 and 64 over one store, with output buffers."""
+
+    def __init__(self, dh, nx, ny, n_frames, prec):
+        self.n = counts(n_frames)
+        self.base = dh.Plan(nx, ny, LAM, Z, PITCH, T=16, precision=prec, max_frames=n_frames,
+                            max_windows=self.n[16])
+        self.plans = {16: self.base, 32: self.base.view(32, self.n[32]),
+                      64: self.base.view(64, self.n[64])}
+        self.images = {T: torch.empty((self.n[T], ny, nx), dtype=torch.float32, device="cuda")
+                       for T in LENGTHS}
+        self.lam = {T: torch.empty((self.n[T], T), dtype=torch.float64, device="cuda")
+                    for T in LENGTHS}
+
+    def step(self, frames_dev):
+        self.base.render_frames(frames_dev)
+        for T in LENGTHS:
+            self.plans[T].pca_windows(0, STRIDE, self.n[T], 2, T - 1, self.images[T], self.lam[T])
+
+    def results(self):
+        torch.cuda.synchronize()
+        return {T: (self.images[T].cpu().numpy(), self.lam[T].cpu().numpy()) for T in LENGTHS}
+
+    def close(self):
+        for p in self.plans.values():
+            p.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_sliding_lengths_share_one_rendering(dh, prec):
+    """96 frames of 128x128: 11 + 9 + 5 windows, every one against the oracle."""
+    frames = SpeckleStream(SpeckleParams(128, 128), seed=21).next(96).numpy()
+    sl = Sliding(dh, 128, 128, 96, prec)
+    sl.step(to_gpu(frames))
+    res = sl.results()
+    for T in LENGTHS:
+        C = [sl.plans[T].debug_covariance(w).cpu().numpy() for w in range(sl.n[T])]
+        img, lam = res[T]
+        for w in range(sl.n[T]):
+            check_window(img[w], lam[w], C[w], frames[w * STRIDE:w * STRIDE + T], 2, T - 1, prec)
+    assert sl.base.status() == 0
+    sl.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_view_equals_own_plan_bitwise(dh, prec):
+    """A view's windows are computed exactly as by a plan of that length that renders the
+    same frames itself."""
+    frames = SpeckleStream(SpeckleParams(256, 128), seed=22).next(80).numpy()
+    sl = Sliding(dh, 256, 128, 80, prec)
+    f = to_gpu(frames)
+    sl.step(f)
+    res = sl.results()
+    for T in (32, 64):
+        with dh.Plan(256, 128, LAM, Z, PITCH, T=T, precision=prec, max_frames=80,
+                     max_windows=sl.n[T]) as own:
+            img, lam = own.pca_batch(f, sl.n[T], STRIDE, 2, T - 1)
+            torch.cuda.synchronize()
+            assert np.array_equal(img.cpu().numpy(), res[T][0])
+            assert np.array_equal(lam.cpu().numpy(), res[T][1])
+    sl.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_graph_replay_matches_eager(dh, prec):
+    """The whole step (render + three window lengths, with the eigensolver forked onto each
+    plan's own stream) captured once and replayed: bitwise the eager results, and replays
+    read the frame buffer as it is at launch time."""
+    gen = SpeckleStream(SpeckleParams(128, 128), seed=23)
+    fa, fb = gen.next(72).numpy(), gen.next(72).numpy()
+    eager = {}
+    for key, fr in (("a", fa), ("b", fb)):
+        sl = Sliding(dh, 128, 128, 72, prec)
+        sl.step(to_gpu(fr))
+        eager[key] = sl.results()
+        sl.close()
+
+    sl = Sliding(dh, 128, 128, 72, prec)
+    buf = to_gpu(fa)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with dh.capture(s) as g:
+        sl.step(buf)
+    for key, fr in (("a", fa), ("b", fb), ("a", fa)):
+        buf.copy_(torch.from_numpy(fr))
+        torch.cuda.synchronize()
+        g.launch(s)
+        s.synchronize()
+        got = sl.results()
+        for T in LENGTHS:
+            assert np.array_equal(got[T][0], eager[key][T][0]), (key, T)
+            assert np.array_equal(got[T][1], eager[key][T][1]), (key, T)
+    g.close()
+    sl.close()
+
+
+def test_view_rules(dh):
+    """Views render nothing, pin their base's storage and slot count, and keep the store
+    alive after the base's handle is closed."""
+    from paper_2004_00923_b300 import _lib
+    lib = _lib.load()
+    frames = to_gpu(SpeckleStream(SpeckleParams(64, 64), seed=24).next(48).numpy())
+    base = dh.Plan(64, 64, LAM, Z, PITCH, T=16, precision="fp16", max_frames=48, max_windows=2)
+    v = base.view(32, max_windows=2)
+    with pytest.raises(dh.DHError) as e:
+        v.render_frames(frames)
+    assert e.value.code == 7
+    with pytest.raises(dh.DHError) as e:
+        v.pca_batch(frames, 1, 8, 2, 31)
+    assert e.value.code == 7
+    assert lib.dh_plan_set_precision(base._h, 0) == 7       # storage pinned by the view
+    assert lib.dh_plan_reserve(base._h, 64, 2) == 7         # slot count pinned by the view
+    assert lib.dh_plan_reserve(base._h, 48, 3) == 0         # windows of the base may change
+    assert lib.dh_plan_reserve(v._h, 48, 3) == 0            # and of the view
+    with pytest.raises(dh.DHError) as e:
+        base.view(128)                                     # unsupported window length
+    assert e.value.code == 2
+    base.render_frames(frames)
+    img_before, lam_before = v.pca_windows(0, 16, 2, 2, 31)
+    torch.cuda.synchronize()
+    base.close()                                           # the view still holds the store
+    img_after, lam_after = v.pca_windows(0, 16, 2, 2, 31)
+    torch.cuda.synchronize()
+    assert torch.equal(img_before, img_after) and torch.equal(lam_before, lam_after)
+    v.close()
