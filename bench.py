@@ -529,6 +529,136 @@ def run_sliding(args, ws, rank, local):
     return 0
 
 
+# --------------------------------------------------------------------------- uneven sizes
+UNEVEN_SIZES = ((512, 40), (1024, 16), (2048, 4))
+
+
+def run_uneven(args, ws, rank, local):
+    """512^2 x 40, 1024^2 x 16 and 2048^2 x 4 windows, alternating 32/64 frames, per-size z,
+    per-window Doppler spread: one dh_batch_run (sizes on concurrent branches) per step,
+    captured in one CUDA graph."""
+    import paper_2004_00923_b300 as dh
+    from dh_synth import uneven_batch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    groups = uneven_batch(UNEVEN_SIZES, seed=3000 + rank, device=dev)
+    stride = 96
+    sizes, items, plans_all = [], [], []
+    for g in groups:
+        n = {L: len(g.starts(L)) for L in (32, 64)}
+        base = dh.Plan(g.n, g.n, LAM, g.z, PITCH, T=32, precision=args.precision,
+                       max_frames=g.frames.shape[0], max_windows=n[32])
+        plans = {32: base, 64: base.view(64, n[64])}
+        out = {L: (torch.empty((n[L], g.n, g.n), dtype=torch.float32, device=dev),
+                   torch.empty((n[L], L), dtype=torch.float64, device=dev)) for L in plans}
+        for i, L in enumerate((32, 64)):
+            it = {"plan": plans[L], "n_windows": n[L], "first_slot": g.starts(L)[0],
+                  "slot_stride": stride, "k0": 2, "k1": L - 1, "images": out[L][0],
+                  "eigvals": out[L][1]}
+            if i == 0:
+                it["frames"] = g.frames
+            items.append(it)
+        sizes.append((g, n, plans, out))
+        plans_all += list(plans.values())
+
+    dh.run_batch(items)
+    torch.cuda.synchronize()
+    # traced run with one batch call per item: the branches then run one after the other, so
+    # each kernel's event interval is its own time (concurrent branches would overlap them)
+    for p in plans_all:
+        p.profile(True)
+    for it in items:
+        dh.run_batch([it])
+    per_kernel = merge_tables([kernel_table(p.profile_read())[0] for p in plans_all])
+    for p in plans_all:
+        p.profile(False)
+    launches = sum(v["launches"] for v in per_kernel.values())
+
+    s = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    with dh.capture(s) as gr:
+        dh.run_batch(items)
+    for _ in range(max(args.warmup, 0)):
+        gr.launch(s)
+    ms, step_ms, clock_info = timed_graph(gr, s, args.steps, ws, local)
+    ms_max = max_over_ranks(ms, ws)
+    nwin = sum(sum(n.values()) for _, n, _, _ in sizes)
+    nframes = sum(g.frames.shape[0] for g in groups)
+    value = whole_job_rate(nwin, ws, ms_max)
+    flags = 0
+    for p in plans_all:
+        flags |= p.status()
+
+    hbm, _, peak_kind = measured_peaks()
+    hb = 2 if args.precision in ("fp16", "bf16") else 4
+    alg = {"render_rows": 0, "render_cols": 0, "gram_tc": 0, "gram_simt": 0, "project_tc": 0,
+           "project_simt": 0}
+    for g, n, _, _ in sizes:
+        npix = g.n * g.n
+        F = g.frames.shape[0]
+        alg["render_rows"] += F * npix * 2
+        alg["render_cols"] += F * npix * 2 * hb
+        hread = sum(n[L] * L * npix * 2 * hb for L in n)
+        for k in ("gram_tc", "gram_simt"):
+            alg[k] += hread
+        for k in ("project_tc", "project_simt"):
+            alg[k] += hread + sum(n.values()) * npix * 4
+    roofline = roofline_of(per_kernel, alg, hbm, peak_kind, ms / 1e3)
+
+    parity, cpu = None, None
+    tol = 1e-3 if args.precision != "fp32" else 1e-4
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        parity, secs, nsamp = {}, 0.0, 0
+        for g, n, plans, out in sizes:
+            picks = [(32, 0)] + ([(64, 0)] if g.n == 512 else [])
+            for L, w in picks:
+                s0 = g.starts(L)[w]
+                fr = g.frames[s0:s0 + L].cpu().numpy()
+                t0 = time.perf_counter()
+                M, lam_ref, _, _ = oracle.pca_window(fr, LAM, g.z, PITCH, 2, L - 1)
+                secs += time.perf_counter() - t0
+                nsamp += 1
+                img = out[L][0][w].double().cpu().numpy()
+                lam = out[L][1][w].cpu().numpy()
+                parity[f"{g.n}x{g.n}_T{L}_w{w}"] = {
+                    "image_rel_l2": float(np.linalg.norm(img - M) / np.linalg.norm(M)),
+                    "eig_normwise": float(np.max(np.abs(lam - lam_ref)) / lam_ref[0]),
+                    "tolerance_image": tol, "tolerance_eig": 1e-5}
+        cpu = {"value": nsamp / secs, "unit": "windows/s", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": "window 0 (32 frames) of each size and one 64-frame "
+                                           "window at 512^2, FP64 C oracle"}
+    if rank == 0:
+        line = {
+            "metric": "uneven-size PCA windows/s (512²×40, 1024²×16, 2048²×4; T 32/64)",
+            "value": value, "unit": "windows/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ("mixed: f32 FFT, f16 tensor-core products (f32 accumulate), f64 eig"
+                      if args.precision != "fp32" else "f32 (f64 covariance reduction and eig)"),
+            "data": "synthetic",
+            "config": {"workload": "uneven: 512^2 x 40, 1024^2 x 16, 2048^2 x 4 windows, "
+                                   "alternating 32/64 frames, per-size z ~ U(0.25, 0.45) m, "
+                                   "sigma_D ~ U(0.1, 1.0) per window, one batch per step "
+                                   "(one CUDA graph)",
+                       "precision": args.precision,
+                       "sizes": [{"n": g.n, "z": g.z, "windows": n, "frames": g.frames.shape[0]}
+                                 for g, n, _, _ in sizes],
+                       "l2": "no flush: 4 GiB of frames per step",
+                       "parallelism": f"replicas x{ws}"},
+            "frames_per_s": nframes * ws / (ms_max / 1e3),
+            "step_ms": {"p50": statistics.median(step_ms), "max": max(step_ms)},
+            "roofline": roofline, "cpu_baseline": cpu, "parity": parity,
+            "gpu_launches": launches, "device_flags": flags, "clocks": clock_info,
+        }
+        print(json.dumps(line), flush=True)
+    gr.close()
+    for p in plans_all:
+        p.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -541,9 +671,10 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["paper", "sliding"], default="paper",
+    ap.add_argument("--workload", choices=["paper", "sliding", "uneven"], default="paper",
                     help="paper: the headline 64 x 1024^2 x 32 step (default); sliding: "
-                         "16/32/64-frame windows at stride 8 over 2048 frames")
+                         "16/32/64-frame windows at stride 8 over 2048 frames; uneven: "
+                         "512^2/1024^2/2048^2 windows of 32/64 frames in one batch")
     args = ap.parse_args(argv)
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -552,6 +683,8 @@ def main(argv=None):
     try:
         if args.workload == "sliding":
             return run_sliding(args, ws, rank, local)
+        if args.workload == "uneven":
+            return run_uneven(args, ws, rank, local)
         return run_ours(args, ws, rank, local)
     finally:
         if ws > 1 and torch.distributed.is_initialized():

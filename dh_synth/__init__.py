@@ -13,3 +13,4 @@ from .speckle import (  # noqa: F401
     known_rank_frames,
     hadamard_rows,
 )
+from .uneven import SizeGroup, uneven_batch  # noqa: F401

@@ -189,6 +189,32 @@ int dh_profile_read(dh_plan_t plan, int n, const char **names, int *launches, do
 dh_status dh_covariance_noalloc(const float *planes_dev, int64_t npix, int T, double *C_dev,
                                 void *stream);
 
+/* One item of a batch (dh_batch_run). */
+typedef struct {
+  dh_plan_t plan;                 /* a plan or a view */
+  const uint16_t *frames_dev;     /* NULL, or frames to render first (Eq. 1), through the
+                                     store's base plan, as dh_render_frames: */
+  int64_t frame_stride_elems;     /*   frame i at frames_dev + i * frame_stride_elems */
+  int n_frames;                   /*   into slots [render_slot, render_slot + n_frames) */
+  int render_slot;
+  int first_slot;                 /* then Eqs. 4-7 for n_windows windows, as dh_pca_windows */
+  int slot_stride;                /* (n_windows = 0: render only) */
+  int n_windows;
+  int k0, k1;
+  float *images_dev;
+  double *eigvals_dev;            /* may be NULL */
+} dh_batch_item;
+
+/* Run a batch of items over any mix of frame sizes, window lengths and plans. Items that
+ * touch the same hologram store (a plan and its views) run in the given order on one branch
+ * stream; branches of different stores run concurrently (up to 8 branches; more stores share
+ * them). Branches fork from `stream` and are joined back into it before the call returns,
+ * so the batch is ordered after earlier work on `stream` and later work waits for all of it;
+ * the whole batch can be captured into one graph (dh_graph_begin). Every item is validated
+ * before anything is launched (DH_ERR_INVALID_ARG); a plan in use by another call gives
+ * DH_ERR_STATE. The paper runs one frame size; this batches several. Asynchronous. */
+dh_status dh_batch_run(const dh_batch_item *items, int n_items, void *stream);
+
 /* CUDA graphs of library calls. dh_graph_begin starts capturing `stream` (a created
  * stream, not NULL: the legacy default stream cannot be captured; capture mode
  * thread-local). Every library call made on that stream until dh_graph_end is recorded,

@@ -21,7 +21,7 @@ import torch
 from . import _lib
 from ._lib import DHError, PREC  # noqa: F401
 
-__all__ = ["Plan", "Graph", "capture", "DHError", "PREC", "version"]
+__all__ = ["Plan", "Graph", "capture", "run_batch", "DHError", "PREC", "version"]
 
 
 def version() -> str:
@@ -194,6 +194,30 @@ class Plan:
         flags = ctypes.c_uint32(0)
         _lib.check("dh_plan_status", self._lib.dh_plan_status(self._h, ctypes.byref(flags)))
         return int(flags.value)
+
+
+def run_batch(items, stream=None) -> None:
+    """dh_batch_run: `items` is a list of dicts with keys plan (a Plan or view), and
+    optionally frames (CUDA uint16 [F, ny, nx] rendered first into slots render_slot...),
+    render_slot, first_slot, slot_stride, n_windows, k0, k1, images, eigvals."""
+    lib = _lib.load()
+    arr = (_lib.BatchItem * len(items))()
+    for a, it in zip(arr, items):
+        plan = it["plan"]
+        a.plan = plan._h.value
+        f = it.get("frames")
+        if f is not None:
+            f = plan._frames(f)
+            a.frames_dev, a.frame_stride_elems, a.n_frames = _ptr(f), plan.nx * plan.ny, f.shape[0]
+            a.render_slot = int(it.get("render_slot", 0))
+        a.n_windows = int(it.get("n_windows", 0))
+        if a.n_windows:
+            a.first_slot, a.slot_stride = int(it.get("first_slot", 0)), int(it["slot_stride"])
+            a.k0, a.k1 = int(it["k0"]), int(it["k1"])
+            a.images_dev = _ptr(it["images"])
+            ev = it.get("eigvals")
+            a.eigvals_dev = _ptr(ev) if ev is not None else None
+    _lib.check("dh_batch_run", lib.dh_batch_run(arr, len(items), _stream_ptr(stream)))
 
 
 class Graph:

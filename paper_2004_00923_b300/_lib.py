@@ -17,6 +17,18 @@ STATUS_NAMES = {0: "DH_OK", 1: "DH_ERR_INVALID_ARG", 2: "DH_ERR_UNSUPPORTED_SIZE
 PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
 FLAG_STORE_OVERFLOW, FLAG_NONFINITE_C, FLAG_EIG_NOT_CONVERGED, FLAG_WAIT_TIMEOUT = 1, 2, 4, 8
 
+
+
+class BatchItem(ctypes.Structure):
+    """dh_batch_item of include/dh.h."""
+    _fields_ = [("plan", ctypes.c_void_p), ("frames_dev", ctypes.c_void_p),
+                ("frame_stride_elems", ctypes.c_int64), ("n_frames", ctypes.c_int),
+                ("render_slot", ctypes.c_int), ("first_slot", ctypes.c_int),
+                ("slot_stride", ctypes.c_int), ("n_windows", ctypes.c_int),
+                ("k0", ctypes.c_int), ("k1", ctypes.c_int), ("images_dev", ctypes.c_void_p),
+                ("eigvals_dev", ctypes.c_void_p)]
+
+
 # (name, restype, argtypes) for every entry point of include/dh.h
 _vp, _i, _i64, _d, _u32p = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, \
     ctypes.POINTER(ctypes.c_uint32)
@@ -40,6 +52,7 @@ SIGNATURES = [
     ("dh_profile_read", _i, [_vp, _i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_i),
                              ctypes.POINTER(_d)]),
     ("dh_covariance_noalloc", _i, [_vp, _i64, _i, _vp, _vp]),
+    ("dh_batch_run", _i, [ctypes.POINTER(BatchItem), _i, _vp]),
     ("dh_graph_begin", _i, [_vp]),
     ("dh_graph_end", _i, [_vp, ctypes.POINTER(_vp)]),
     ("dh_graph_launch", _i, [_vp, _vp]),

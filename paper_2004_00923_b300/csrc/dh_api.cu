@@ -6,6 +6,9 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -196,6 +199,37 @@ struct Busy {
   explicit Busy(std::atomic<int> &x) : b(x) { int z = 0; ok = b.compare_exchange_strong(z, 1); }
   ~Busy() { if (ok) b.store(0); }
 };
+
+// Branch streams of the batch executor, one set per device: a batch forks one branch per
+// hologram store from the caller's stream and joins them back before returning.
+struct Executor {
+  static constexpr int kBranches = 8;
+  std::mutex mu;
+  cudaStream_t st[kBranches] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kBranches] = {};
+  bool ready = false;
+
+  cudaError_t init() {
+    if (ready) return cudaSuccess;
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int b = 0; b < kBranches && e == cudaSuccess; ++b) {
+      e = cudaStreamCreateWithFlags(&st[b], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[b], cudaEventDisableTiming);
+    }
+    ready = e == cudaSuccess;
+    return e;
+  }
+};
+
+Executor &executor(int device) {
+  static std::mutex mu;
+  static std::map<int, Executor *> per_device;
+  std::lock_guard<std::mutex> lk(mu);
+  Executor *&x = per_device[device];
+  if (!x) x = new Executor();  // lives for the process: streams outlast every plan
+  return *x;
+}
 
 }  // namespace
 }  // namespace dh
@@ -515,6 +549,77 @@ void dh_graph_destroy(dh_graph_t g) {
   if (!g) return;
   if (g->exec) cudaGraphExecDestroy(g->exec);
   delete g;
+}
+
+// ---------------------------------------------------------------- batches
+dh_status dh_batch_run(const dh_batch_item *items, int n_items, void *stream) {
+  if (!items || n_items < 1) return DH_ERR_INVALID_ARG;
+  // validate everything before launching anything
+  std::vector<dh_plan *> roots, plans;
+  std::vector<int> branch(n_items);
+  for (int i = 0; i < n_items; ++i) {
+    const dh_batch_item &it = items[i];
+    if (!it.plan) return DH_ERR_INVALID_ARG;
+    dh_plan *root = it.plan;
+    while (root->base) root = root->base;
+    const Plan &p = it.plan->p;
+    if (it.frames_dev) {
+      if (it.n_frames < 1 || it.render_slot < 0 || it.frame_stride_elems < p.npix ||
+          (it.frame_stride_elems & 7) != 0 || (reinterpret_cast<uintptr_t>(it.frames_dev) & 15u) != 0 ||
+          (long long)it.render_slot + it.n_frames > root->p.max_frames)
+        return DH_ERR_INVALID_ARG;
+    }
+    if (it.n_windows < 0 || (it.n_windows == 0 && !it.frames_dev)) return DH_ERR_INVALID_ARG;
+    if (it.n_windows > 0) {
+      if (!it.images_dev || it.first_slot < 0 || it.slot_stride < 1 || it.n_windows > p.max_windows ||
+          it.k0 < 0 || it.k1 < it.k0 || it.k1 >= p.T ||
+          (long long)it.first_slot + (long long)(it.n_windows - 1) * it.slot_stride + p.T > p.max_frames)
+        return DH_ERR_INVALID_ARG;
+    }
+    int r = 0;
+    while (r < (int)roots.size() && roots[r] != root) ++r;
+    if (r == (int)roots.size()) roots.push_back(root);
+    branch[i] = r % Executor::kBranches;
+    for (dh_plan *q : {it.plan, root}) {
+      bool seen = false;
+      for (dh_plan *x : plans) seen |= x == q;
+      if (!seen) plans.push_back(q);
+    }
+  }
+  // every plan involved is held for the duration of the enqueue
+  std::vector<std::unique_ptr<Busy>> held;
+  for (dh_plan *q : plans) {
+    held.emplace_back(new Busy(q->busy));
+    if (!held.back()->ok) return DH_ERR_STATE;
+  }
+  int device = 0;
+  DH_CUDA_TRY(cudaGetDevice(&device));
+  Executor &x = executor(device);
+  std::lock_guard<std::mutex> lk(x.mu);
+  DH_CUDA_TRY(x.init());
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nb = std::min((int)roots.size(), Executor::kBranches);
+  DH_CUDA_TRY(cudaEventRecord(x.fork, s));
+  for (int b = 0; b < nb; ++b) DH_CUDA_TRY(cudaStreamWaitEvent(x.st[b], x.fork, 0));
+  dh_status st = DH_OK;
+  for (int i = 0; i < n_items && st == DH_OK; ++i) {
+    const dh_batch_item &it = items[i];
+    dh_plan *root = it.plan;
+    while (root->base) root = root->base;
+    cudaStream_t bs = x.st[branch[i]];
+    if (it.frames_dev)
+      st = launch_render(root->p, it.frames_dev, it.frame_stride_elems, it.n_frames, it.render_slot, bs);
+    if (st == DH_OK && it.n_windows > 0)
+      st = pca_impl(it.plan->p, nullptr, 0, it.first_slot, it.slot_stride, it.n_windows, it.k0, it.k1,
+                    it.images_dev, it.eigvals_dev, bs);
+  }
+  // join every branch, also after an error, so the caller's stream never runs ahead of them
+  for (int b = 0; b < nb; ++b) {
+    cudaError_t e = cudaEventRecord(x.join[b], x.st[b]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, x.join[b], 0);
+    if (e != cudaSuccess && st == DH_OK) st = fail_cuda(e);
+  }
+  return st;
 }
 
 }  // extern "C"

@@ -51,8 +51,8 @@ def lam_tol(prec, npix):
     return TOL_LAM if prec == "fp32" else max(TOL_LAM, 4 * U16[prec] / np.sqrt(npix))
 
 
-def check_window(img, lam, C, frames_np, k0, k1, prec):
-    M, lam_ref, C_ref, _ = oracle.pca_window(frames_np, LAM, Z, PITCH, k0, k1)
+def check_window(img, lam, C, frames_np, k0, k1, prec, z=Z):
+    M, lam_ref, C_ref, _ = oracle.pca_window(frames_np, LAM, z, PITCH, k0, k1)
     e_img = rel(img, M)
     e_lam = float(np.max(np.abs(lam - lam_ref)) / lam_ref[0])
     e_C = rel(C, C_ref)
