@@ -105,6 +105,12 @@ dh_status dh_plan_reserve(dh_plan_t plan, int max_frames, int max_windows);
 /* Bytes of device memory the plan holds now (all buffers). */
 size_t dh_plan_device_bytes(dh_plan_t plan);
 
+/* Bytes of device memory a plan of these sizes holds after dh_plan_set_precision(prec) and
+ * dh_plan_reserve(max_frames, max_windows), computed without creating it (admission
+ * control budgets with it). 0 for arguments dh_plan_create / dh_plan_reserve reject. */
+size_t dh_plan_footprint(int nx, int ny, int T, dh_precision prec, int max_frames,
+                         int max_windows);
+
 /* Eq. 1 for n_frames frames: frame i (uint16, row-major n_y x n_x, caller-owned device
  * memory at frames_dev + i * frame_stride_elems) is rendered into hologram slot
  * first_slot + i. Requires frame_stride_elems >= n_x n_y and a multiple of 8,
@@ -214,6 +220,77 @@ typedef struct {
  * before anything is launched (DH_ERR_INVALID_ARG); a plan in use by another call gives
  * DH_ERR_STATE. The paper runs one frame size; this batches several. Asynchronous. */
 dh_status dh_batch_run(const dh_batch_item *items, int n_items, void *stream);
+
+/* ---------------------------------------------------------------- serving
+ * A server runs several camera streams at once. Each stream has its own plan (frame size,
+ * optics, window length T, storage type, retained range), a device frame ring and hologram
+ * slots for two windows, an output ring of ring_windows images on the device and in pinned
+ * host memory, and its own CUDA stream: windows of different streams run concurrently on
+ * the device as soon as each is complete. Streams are admitted against an HBM budget. The
+ * paper processes one camera; the server is this library's multi-stream runtime around
+ * the same stages (Eqs. 1, 4-7). */
+typedef struct dh_server *dh_server_t;
+
+typedef struct {
+  int stream_id;
+  int64_t window;              /* window w of the stream covers its frames [w T, w T + T) */
+  const float *image_host;     /* n_x n_y FP32 image (Eq. 7) in the server's pinned ring */
+  const double *eigvals_host;  /* T eigenvalues, decreasing */
+  double t_ready_s;            /* server clock when the push completing the window began */
+  double t_done_s;             /* server clock when image and eigenvalues were in host memory */
+} dh_window_result;
+
+/* A server on the current device with `hbm_budget_bytes` of device memory to admit streams
+ * into. Synchronous. */
+dh_status dh_server_create(dh_server_t *out, size_t hbm_budget_bytes);
+
+/* Device bytes one stream of these parameters is charged (plan with 2T slots and one
+ * window, frame ring of 2T frames, ring_windows images and eigenvalue sets); 0 for
+ * unsupported sizes. */
+size_t dh_server_stream_bytes(int nx, int ny, int T, dh_precision prec, int ring_windows);
+
+/* Admit a stream: DH_ERR_OOM (nothing allocated) when its bytes exceed what is left of the
+ * budget; otherwise allocates it and writes its id. Arguments as dh_plan_create, plus the
+ * storage type, the retained range 0 <= k0 <= k1 < T and ring_windows >= 1. Synchronous
+ * (allocations may briefly stall the device). */
+dh_status dh_server_add_stream(dh_server_t server, int nx, int ny, double lambda_m, double z_m,
+                               double pitch_m, int T, dh_precision prec, int k0, int k1,
+                               int ring_windows, int *stream_id);
+
+/* Wait for the stream's work, drop its unpolled results, free it and return its bytes to
+ * the budget. */
+dh_status dh_server_remove_stream(dh_server_t server, int stream_id);
+
+/* Device bytes charged to admitted streams. */
+size_t dh_server_used_bytes(dh_server_t server);
+
+/* Hand n_frames (1..T) consecutive frames of a stream, starting at frame_index, to the
+ * server: host uint16 frames, n_y x n_x row-major, back to back. They are copied to the
+ * device (asynchronously when the memory is pinned: keep it unchanged until the window
+ * holding the last of them has been polled), rendered, and every window they complete is
+ * launched. Returns without waiting for the device.
+ * Errors: DH_ERR_FRAME_GAP when frame_index is not the stream's next frame (nothing is
+ * done; push the missing frames or remove the stream); DH_ERR_STATE when a completed window
+ * needs an output slot whose previous result has not been released (nothing is done:
+ * poll, release and push again); DH_ERR_INVALID_ARG. */
+dh_status dh_server_push(dh_server_t server, int stream_id, const uint16_t *frames_host,
+                         int64_t frame_index, int n_frames);
+
+/* Up to max_results finished windows of any stream, in completion order; non-blocking.
+ * Returns how many were written. A result's host buffers stay valid until it is released. */
+int dh_server_poll(dh_server_t server, dh_window_result *out, int max_results);
+
+/* Give a result's output slot back to its stream. */
+dh_status dh_server_release(dh_server_t server, int stream_id, int64_t window);
+
+/* Seconds since the server was created, the clock of t_ready_s and t_done_s. */
+double dh_server_clock(dh_server_t server);
+
+/* Wait until every pushed window of every stream has finished. */
+dh_status dh_server_drain(dh_server_t server);
+
+/* Free every stream and the server. NULL-safe. */
+void dh_server_destroy(dh_server_t server);
 
 /* CUDA graphs of library calls. dh_graph_begin starts capturing `stream` (a created
  * stream, not NULL: the legacy default stream cannot be captured; capture mode

@@ -21,7 +21,7 @@ import torch
 from . import _lib
 from ._lib import DHError, PREC  # noqa: F401
 
-__all__ = ["Plan", "Graph", "capture", "run_batch", "DHError", "PREC", "version"]
+__all__ = ["Plan", "Graph", "Server", "capture", "run_batch", "DHError", "PREC", "version"]
 
 
 def version() -> str:
@@ -262,3 +262,91 @@ def capture(stream: torch.cuda.Stream):
             g._h = h
             if ok:
                 _lib.check("dh_graph_end", code)
+
+
+class Server:
+    """The serving runtime (dh_server_*): camera streams admitted against an HBM budget,
+    frames pushed from host memory, finished windows polled with their latency."""
+
+    def __init__(self, hbm_budget_bytes: int):
+        self._lib = _lib.load()
+        h = ctypes.c_void_p()
+        _lib.check("dh_server_create", self._lib.dh_server_create(ctypes.byref(h),
+                                                                  int(hbm_budget_bytes)))
+        self._h = h
+        self.streams = {}  # id -> (nx, ny, T)
+
+    @staticmethod
+    def stream_bytes(nx, ny, T, precision="fp16", ring_windows=4) -> int:
+        return int(_lib.load().dh_server_stream_bytes(nx, ny, T, PREC[precision], ring_windows))
+
+    def add_stream(self, nx, ny, lambda_m, z_m, pitch_m, T, precision="fp16", k0=2, k1=None,
+                   ring_windows=4) -> int:
+        """Admit a stream; raises DHError (code 3, DH_ERR_OOM) when the budget is exhausted."""
+        sid = ctypes.c_int(-1)
+        k1 = T - 1 if k1 is None else k1
+        _lib.check("dh_server_add_stream", self._lib.dh_server_add_stream(
+            self._h, int(nx), int(ny), float(lambda_m), float(z_m), float(pitch_m), int(T),
+            PREC[precision], int(k0), int(k1), int(ring_windows), ctypes.byref(sid)))
+        self.streams[sid.value] = (int(nx), int(ny), int(T))
+        return sid.value
+
+    def remove_stream(self, sid: int) -> None:
+        _lib.check("dh_server_remove_stream", self._lib.dh_server_remove_stream(self._h, sid))
+        self.streams.pop(sid, None)
+
+    @property
+    def used_bytes(self) -> int:
+        return int(self._lib.dh_server_used_bytes(self._h))
+
+    def push(self, sid: int, frames_host: torch.Tensor, frame_index: int) -> None:
+        """Frames [n, ny, nx] uint16 in host memory (pinned for asynchronous copies)."""
+        if frames_host.dtype != torch.uint16 or frames_host.is_cuda or not frames_host.is_contiguous():
+            raise TypeError("frames must be a contiguous host uint16 tensor")
+        _lib.check("dh_server_push", self._lib.dh_server_push(
+            self._h, int(sid), _ptr(frames_host), int(frame_index), int(frames_host.shape[0])))
+
+    def poll(self, max_results: int = 64, copy: bool = True):
+        """Finished windows: list of dicts (stream, window, image, eigvals, t_ready, t_done).
+        With copy=True the image and eigenvalues are copied out and the slot released."""
+        arr = (_lib.WindowResult * max_results)()
+        n = self._lib.dh_server_poll(self._h, arr, max_results)
+        out = []
+        for r in arr[:n]:
+            nx, ny, T = self.streams[r.stream_id]
+            d = {"stream": r.stream_id, "window": int(r.window), "t_ready": r.t_ready_s,
+                 "t_done": r.t_done_s}
+            if copy:
+                img = (ctypes.c_float * (nx * ny)).from_address(r.image_host)
+                lam = (ctypes.c_double * T).from_address(r.eigvals_host)
+                d["image"] = torch.frombuffer(img, dtype=torch.float32).reshape(ny, nx).clone()
+                d["eigvals"] = torch.frombuffer(lam, dtype=torch.float64).clone()
+                self.release(r.stream_id, r.window)
+            out.append(d)
+        return out
+
+    def release(self, sid: int, window: int) -> None:
+        _lib.check("dh_server_release", self._lib.dh_server_release(self._h, int(sid), int(window)))
+
+    def clock(self) -> float:
+        return float(self._lib.dh_server_clock(self._h))
+
+    def drain(self) -> None:
+        _lib.check("dh_server_drain", self._lib.dh_server_drain(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.dh_server_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -29,6 +29,13 @@ class BatchItem(ctypes.Structure):
                 ("eigvals_dev", ctypes.c_void_p)]
 
 
+class WindowResult(ctypes.Structure):
+    """dh_window_result of include/dh.h."""
+    _fields_ = [("stream_id", ctypes.c_int), ("window", ctypes.c_int64),
+                ("image_host", ctypes.c_void_p), ("eigvals_host", ctypes.c_void_p),
+                ("t_ready_s", ctypes.c_double), ("t_done_s", ctypes.c_double)]
+
+
 # (name, restype, argtypes) for every entry point of include/dh.h
 _vp, _i, _i64, _d, _u32p = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, \
     ctypes.POINTER(ctypes.c_uint32)
@@ -39,6 +46,7 @@ SIGNATURES = [
     ("dh_plan_set_precision", _i, [_vp, _i]),
     ("dh_plan_reserve", _i, [_vp, _i, _i]),
     ("dh_plan_device_bytes", ctypes.c_size_t, [_vp]),
+    ("dh_plan_footprint", ctypes.c_size_t, [_i, _i, _i, _i, _i, _i]),
     ("dh_render_frames", _i, [_vp, _vp, _i64, _i, _i, _vp]),
     ("dh_pca_windows", _i, [_vp, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
     ("dh_render_stack", _i, [_vp, _vp, _i64, _vp]),
@@ -53,6 +61,18 @@ SIGNATURES = [
                              ctypes.POINTER(_d)]),
     ("dh_covariance_noalloc", _i, [_vp, _i64, _i, _vp, _vp]),
     ("dh_batch_run", _i, [ctypes.POINTER(BatchItem), _i, _vp]),
+    ("dh_server_create", _i, [ctypes.POINTER(_vp), ctypes.c_size_t]),
+    ("dh_server_stream_bytes", ctypes.c_size_t, [_i, _i, _i, _i, _i]),
+    ("dh_server_add_stream", _i, [_vp, _i, _i, _d, _d, _d, _i, _i, _i, _i, _i,
+                                  ctypes.POINTER(_i)]),
+    ("dh_server_remove_stream", _i, [_vp, _i]),
+    ("dh_server_used_bytes", ctypes.c_size_t, [_vp]),
+    ("dh_server_push", _i, [_vp, _i, _vp, _i64, _i]),
+    ("dh_server_poll", _i, [_vp, ctypes.POINTER(WindowResult), _i]),
+    ("dh_server_release", _i, [_vp, _i, _i64]),
+    ("dh_server_clock", _d, [_vp]),
+    ("dh_server_drain", _i, [_vp]),
+    ("dh_server_destroy", None, [_vp]),
     ("dh_graph_begin", _i, [_vp]),
     ("dh_graph_end", _i, [_vp, ctypes.POINTER(_vp)]),
     ("dh_graph_launch", _i, [_vp, _vp]),

@@ -83,23 +83,55 @@ size_t table_bytes(const Plan &p) {
   return sizeof(float2) * (p.nx + p.ny + twiddle_len(p.lognx) + twiddle_len(p.logny)) + 16;
 }
 
+// Device bytes of every buffer a plan allocates, from its sizes, reservation and precision.
+struct StoreSizes {
+  size_t tables, H, mid, part, C, lam, V, B;
+  int mid_frames, parts_total;
+  size_t B_window;
+  size_t windows() const { return part + C + lam + V + B; }
+  size_t total() const { return tables + H + mid + windows(); }
+};
+
+StoreSizes store_sizes(const Plan &p) {
+  StoreSizes z{};
+  const int M = 2 * p.T;
+  const size_t hb = p.prec == DH_PREC_FP32 ? 4 : 2;
+  z.tables = table_bytes(p);
+  z.H = (size_t)p.max_frames * 2 * p.npix * hb;
+  // row-pass intermediate: a chunk of frames sized to stay in L2 (~96 MiB of the 126 MB),
+  // never more frames than the plan has slots
+  long long mf = (96ll << 20) / (p.npix * (long long)sizeof(float2));
+  if (mf > 64) mf = 64;
+  if (mf > p.max_frames) mf = p.max_frames;
+  if (mf < 1) mf = 1;
+  z.mid_frames = (int)mf;
+  z.mid = (size_t)mf * p.npix * sizeof(float2);
+  z.parts_total = p.max_windows * parts_per_window(p);
+  z.part = (size_t)z.parts_total * M * M * sizeof(double);
+  z.C = (size_t)p.max_windows * p.T * p.T * 2 * sizeof(double);
+  z.lam = (size_t)p.max_windows * p.T * sizeof(double);
+  z.V = z.C;
+  // operand of Eq. 6 per window: FP32 [2T][2T], or 16-bit hi and lo [2][2T][2T]
+  const size_t bw = p.prec == DH_PREC_FP32 ? (size_t)M * M * 4 : (size_t)2 * M * M * 2;
+  z.B_window = (bw + 1023) / 1024 * 1024;
+  z.B = z.B_window * p.max_windows;
+  return z;
+}
+
 // (Re)allocate the per-window buffers for max_windows windows of length T over the store.
 dh_status alloc_windows(Plan &p) {
   free_windows(p);
-  const size_t before = p.bytes;
-  const int M = 2 * p.T;
+  const StoreSizes z = store_sizes(p);
   dh_status st;
-  p.parts_total = p.max_windows * parts_per_window(p);
-  if ((st = dalloc(p, &p.d_part, (size_t)p.parts_total * M * M * sizeof(double))) != DH_OK) return st;
-  if ((st = dalloc(p, &p.d_C, (size_t)p.max_windows * p.T * p.T * 2 * sizeof(double))) != DH_OK) return st;
-  if ((st = dalloc(p, &p.d_lam, (size_t)p.max_windows * p.T * sizeof(double))) != DH_OK) return st;
-  if ((st = dalloc(p, &p.d_V, (size_t)p.max_windows * p.T * p.T * 2 * sizeof(double))) != DH_OK) return st;
-  // operand of Eq. 6 per window: FP32 [2T][2T], or 16-bit hi and lo [2][2T][2T]
-  size_t bw = p.prec == DH_PREC_FP32 ? (size_t)M * M * 4 : (size_t)2 * M * M * 2;
-  p.B_window_bytes = (bw + 1023) / 1024 * 1024;
-  if ((st = dalloc(p, &p.d_B, p.B_window_bytes * p.max_windows)) != DH_OK) return st;
-  p.window_bytes = p.bytes - before;
-  DH_CUDA_TRY(cudaMemset(p.d_B, 0, p.B_window_bytes * p.max_windows));
+  p.parts_total = z.parts_total;
+  p.B_window_bytes = z.B_window;
+  if ((st = dalloc(p, &p.d_part, z.part)) != DH_OK) return st;
+  if ((st = dalloc(p, &p.d_C, z.C)) != DH_OK) return st;
+  if ((st = dalloc(p, &p.d_lam, z.lam)) != DH_OK) return st;
+  if ((st = dalloc(p, &p.d_V, z.V)) != DH_OK) return st;
+  if ((st = dalloc(p, &p.d_B, z.B)) != DH_OK) return st;
+  p.window_bytes = z.windows();
+  DH_CUDA_TRY(cudaMemset(p.d_B, 0, z.B));
   if (p.prec != DH_PREC_FP32) {
     if ((st = make_tensor_maps(p)) != DH_OK) return st;
   }
@@ -110,19 +142,16 @@ dh_status alloc_windows(Plan &p) {
 // takes the store of `base` instead of allocating one.
 dh_status alloc_store(Plan &p, const Plan *base = nullptr) {
   free_store(p);
-  p.bytes = p.is_view ? 0 : table_bytes(p);
+  const StoreSizes z = store_sizes(p);
+  p.bytes = p.is_view ? 0 : z.tables;
   p.H_elem_bytes = p.prec == DH_PREC_FP32 ? 4 : 2;
   dh_status st;
   if (p.is_view) {
     p.d_H = base->d_H;
   } else {
-    if ((st = dalloc(p, &p.d_H, (size_t)p.max_frames * 2 * p.npix * p.H_elem_bytes)) != DH_OK) return st;
-    // row-pass intermediate: a chunk of frames sized to stay in L2 (~96 MiB of the 126 MB)
-    long long mf = (96ll << 20) / (p.npix * (long long)sizeof(float2));
-    if (mf < 1) mf = 1;
-    if (mf > 64) mf = 64;
-    p.mid_frames = (int)mf;
-    if ((st = dalloc(p, &p.d_mid, (size_t)p.mid_frames * p.npix * sizeof(float2))) != DH_OK) return st;
+    if ((st = dalloc(p, &p.d_H, z.H)) != DH_OK) return st;
+    p.mid_frames = z.mid_frames;
+    if ((st = dalloc(p, &p.d_mid, z.mid)) != DH_OK) return st;
   }
   return alloc_windows(p);
 }
@@ -232,6 +261,22 @@ Executor &executor(int device) {
 }
 
 }  // namespace
+
+// Entry points of the serving runtime (server.cu) into one plan, under the plan's guard.
+dh_status plan_pca(dh_plan *h, int first_slot, int slot_stride, int n_windows, int k0, int k1,
+                   float *images, double *eigvals, cudaStream_t s) {
+  Busy g(h->busy);
+  if (!g.ok) return DH_ERR_STATE;
+  return pca_impl(h->p, nullptr, 0, first_slot, slot_stride, n_windows, k0, k1, images, eigvals, s);
+}
+
+dh_status plan_render(dh_plan *h, const uint16_t *frames, long long stride, int n, int slot0,
+                      cudaStream_t s) {
+  Busy g(h->busy);
+  if (!g.ok) return DH_ERR_STATE;
+  return launch_render(h->p, frames, stride, n, slot0, s);
+}
+
 }  // namespace dh
 
 using namespace dh;
@@ -405,6 +450,21 @@ dh_status dh_plan_reserve(dh_plan_t h, int max_frames, int max_windows) {
 }
 
 size_t dh_plan_device_bytes(dh_plan_t h) { return h ? h->p.bytes : 0; }
+
+size_t dh_plan_footprint(int nx, int ny, int T, dh_precision prec, int max_frames, int max_windows) {
+  if (!pow2_in_range(nx) || !pow2_in_range(ny) || !(T == 16 || T == 32 || T == 64) ||
+      max_frames < T || max_windows < 1 ||
+      (prec != DH_PREC_FP32 && prec != DH_PREC_FP16 && prec != DH_PREC_BF16))
+    return 0;
+  Plan p;
+  p.nx = nx; p.ny = ny; p.T = T;
+  p.lognx = ilog2(nx); p.logny = ilog2(ny);
+  p.npix = (long long)nx * ny;
+  p.prec = prec;
+  p.max_frames = max_frames;
+  p.max_windows = max_windows;
+  return store_sizes(p).total();
+}
 
 dh_status dh_render_frames(dh_plan_t h, const uint16_t *frames_dev, int64_t frame_stride_elems,
                            int n_frames, int first_slot, void *stream) {
