@@ -10,6 +10,8 @@ Each wrapper names the equation of Puyo et al. (arXiv 2004.00923) it computes:
   eig              Eq. 5 (C = V Lambda V^{t*}), decreasing order
   project_power    Eqs. 6-7 (H_breve = H V I_f, M = sum |H_breve|^2)
   pca_window       Eqs. 1, 4, 5, 6, 7 in the paper's order
+  fourier_power    Eqs. 8-9 (H_tilde = H W I_f with the unitary DFT W, M = sum |H_tilde|^2)
+  fourier_window   Eqs. 1, 8, 9 in the paper's order
   fft1d / fft2d    the DFT used inside Eq. 1 (exposed for pins)
 
 Parity status: every function above is pinned by `tests/test_oracle_pins.py`
@@ -62,6 +64,11 @@ def _load():
         lib.dho_pca_window.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, u16p,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
+        lib.dho_fourier_power.argtypes = [ctypes.c_longlong, ctypes.c_int, _dp, _dp, ctypes.c_int,
+                                          ctypes.c_int, _dp]
+        lib.dho_fourier_window.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, u16p,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_int, ctypes.c_int, _dp]
         lib.dho_num_threads.argtypes = []
         _lib = lib
     return _lib
@@ -167,3 +174,29 @@ def pca_window(frames: np.ndarray, lambda_m: float, z_m: float, pitch_m: float,
     if rc < 0:
         raise RuntimeError(f"pca_window failed ({rc})")
     return M, lam, cr + 1j * ci, rc
+
+
+def fourier_power(H: np.ndarray, k0: int, k1: int) -> np.ndarray:
+    """Eqs. 8-9: M[p] = sum_{k=k0..k1} |sum_t H[t, p] w_{t,k}|^2 with the unitary DFT
+    w_{t,k} = exp(-2 pi i t k / T) / sqrt(T), bins counted from 0 (the paper's n = k + 1)."""
+    T = H.shape[0]
+    Hm = H.reshape(T, -1)
+    hr, hi = _c(Hm.real, np.float64), _c(Hm.imag, np.float64)
+    M = np.empty(Hm.shape[1])
+    rc = _load().dho_fourier_power(Hm.shape[1], T, _ptr(hr), _ptr(hi), int(k0), int(k1), _ptr(M))
+    if rc != 0:
+        raise ValueError(f"fourier_power failed ({rc})")
+    return M.reshape(H.shape[1:])
+
+
+def fourier_window(frames: np.ndarray, lambda_m: float, z_m: float, pitch_m: float,
+                   k0: int, k1: int) -> np.ndarray:
+    """The Fourier-demodulated window (Eq. 1, then Eqs. 8-9): the image M [ny, nx]."""
+    f = _c(frames, np.uint16)
+    T, ny, nx = f.shape
+    M = np.empty((ny, nx))
+    rc = _load().dho_fourier_window(nx, ny, T, f.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16)),
+                                    lambda_m, z_m, pitch_m, int(k0), int(k1), _ptr(M))
+    if rc != 0:
+        raise RuntimeError(f"fourier_window failed ({rc})")
+    return M

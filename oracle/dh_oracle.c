@@ -30,6 +30,10 @@
  *      Ties keep the lower original index first.
  *  R3. "Complex-valued and symmetric" C (text before Eq. 4) is read as Hermitian, and
  *      the factorization of Eq. 5 as a Hermitian eigendecomposition.
+ *  R4. Eq. 8's filter I_f keeps the diagonal entries n_1..n_2 counted, like the entries
+ *      of W, from 1; here the temporal frequency bins are counted from 0, so the kept
+ *      bins are k = n_1 - 1 .. n_2 - 1 (the paper's n_1 = 8, n_2 = 24 at n_t = 32 are
+ *      bins 7..23).
  */
 #include <math.h>
 #include <stdint.h>
@@ -341,5 +345,56 @@ int dho_pca_window(int nx, int ny, int T, const uint16_t *I, double lambda_m, do
     if (Cim_out) memcpy(Cim_out, ci, sizeof(double) * T * T);
   }
   free(hr); free(hi); free(cr); free(ci); free(vr); free(vi);
+  return rc;
+}
+
+/* Eqs. 8-9: temporal demodulation by the unitary DFT matrix W of Eq. 8,
+ *   w_{t,k} = exp(-2 pi i t k / n_t) / sqrt(n_t)   (t, k counted from 0),
+ * then the frequency filter and the power sum over the kept bins (reading R4):
+ *   M[p] = sum_{k=k0..k1} |sum_t H[t][p] w_{t,k}|^2.
+ * Written as the DFT's definition, O(n_t^2) per pixel; the angle is reduced exactly
+ * (t k mod n_t) before the cosine and sine. */
+int dho_fourier_power(long long npix, int T, const double *Hre, const double *Him, int k0,
+                      int k1, double *M) {
+  if (npix < 1 || T < 1 || k0 < 0 || k1 < k0 || k1 >= T) return -1;
+  double *wr = malloc(sizeof(double) * T * T), *wi = malloc(sizeof(double) * T * T);
+  if (!wr || !wi) { free(wr); free(wi); return -2; }
+  const double s = 1.0 / sqrt((double)T);
+  for (int t = 0; t < T; ++t)
+    for (int k = 0; k < T; ++k) {
+      const double ang = -2.0 * DHO_PI * (double)((t * k) % T) / (double)T;
+      wr[t * T + k] = cos(ang) * s;
+      wi[t * T + k] = sin(ang) * s;
+    }
+#pragma omp parallel for schedule(static)
+  for (long long p = 0; p < npix; ++p) {
+    double acc = 0.0;
+    for (int k = k0; k <= k1; ++k) {
+      double pr = 0.0, pi = 0.0;
+      for (int t = 0; t < T; ++t) {
+        double hr = Hre[(size_t)t * npix + p], hi = Him[(size_t)t * npix + p];
+        pr += hr * wr[t * T + k] - hi * wi[t * T + k];
+        pi += hr * wi[t * T + k] + hi * wr[t * T + k];
+      }
+      acc += pr * pr + pi * pi;
+    }
+    M[p] = acc;
+  }
+  free(wr); free(wi);
+  return 0;
+}
+
+/* The Fourier-demodulated window, in the paper's order: Eq. 1 -> Eqs. 8-9. */
+int dho_fourier_window(int nx, int ny, int T, const uint16_t *I, double lambda_m, double z_m,
+                       double pitch_m, int k0, int k1, double *M) {
+  if (k0 < 0 || k1 < k0 || k1 >= T) return -1;
+  size_t n = (size_t)nx * ny;
+  double *hr = malloc(sizeof(double) * n * T), *hi = malloc(sizeof(double) * n * T);
+  int rc = -2;
+  if (hr && hi) {
+    rc = dho_render(nx, ny, T, I, lambda_m, z_m, pitch_m, hr, hi);
+    if (rc == 0) rc = dho_fourier_power((long long)n, T, hr, hi, k0, k1, M);
+  }
+  free(hr); free(hi);
   return rc;
 }

@@ -269,3 +269,60 @@ def test_pca_window_rejects_bad_range():
     f = speckle_window(16, 16, 4, seed=1).numpy()
     with pytest.raises(RuntimeError):
         oracle.pca_window(f, LAM, Z, PITCH, 3, 4)
+
+
+# ----------------------------------------------------------------- Eqs. 8-9 (Fourier)
+def test_fourier_full_band_is_parseval():
+    """W of Eq. 8 is unitary: keeping every bin returns sum_t |H_t|^2 per pixel."""
+    rng = np.random.default_rng(5)
+    H = rng.standard_normal((32, 8, 16)) + 1j * rng.standard_normal((32, 8, 16))
+    M = oracle.fourier_power(H, 0, 31)
+    assert np.allclose(M, (np.abs(H) ** 2).sum(0), rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("T,k0,k1", [(32, 7, 23), (16, 3, 9), (64, 0, 5), (32, 31, 31)])
+def test_fourier_matches_numpy_fft(T, k0, k1):
+    """numpy's forward FFT with norm='ortho' is exactly Eq. 8's W (exp(-2 pi i t k / T) /
+    sqrt(T)); the oracle writes the DFT out itself."""
+    rng = np.random.default_rng(T + k0)
+    H = rng.standard_normal((T, 4, 8)) + 1j * rng.standard_normal((T, 4, 8))
+    F = np.fft.fft(H, axis=0, norm="ortho")
+    ref = (np.abs(F[k0:k1 + 1]) ** 2).sum(0)
+    assert np.allclose(oracle.fourier_power(H, k0, k1), ref, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("f", [3, 8, 29])
+def test_fourier_complex_tone_lands_in_its_bin(f):
+    """H_t = A exp(+2 pi i f t / T) is bin f of W exactly (|X_f|^2 = |A|^2 T, others 0):
+    the sign of Eq. 8's exponent decides which bin, so a flipped sign (bin T - f) fails."""
+    T = 32
+    A = (1.5 - 0.5j) * np.ones((2, 2))
+    t = np.arange(T)[:, None, None]
+    H = A[None] * np.exp(2j * np.pi * f * t / T)
+    assert np.allclose(oracle.fourier_power(H, f, f), np.abs(A) ** 2 * T, rtol=1e-12)
+    others = [(0, f - 1)] if f > 0 else []
+    others += [(f + 1, T - 1)] if f < T - 1 else []
+    for a, b in others:
+        assert np.max(oracle.fourier_power(H, a, b)) < 1e-20
+
+
+def test_fourier_window_tone_closed_form():
+    """Frames I_t = c0 + a cos(pi t / 2) on a pixel set: the Fresnel transform is linear and
+    unitary per frame, so every pixel's temporal sequence is F(S)(p) (c0 + a cos(2 pi (T/4)
+    t / T)), whose unitary DFT is c0 sqrt(T) at bin 0 and a sqrt(T) / 2 at bins T/4 and 3T/4.
+    The paper's filter n_1 = 8, n_2 = 24 (bins 7..23 counted from 0) keeps bin 8 only, so
+    M / sum_t |H_t|^2 = (a^2 T / 4) / (T c0^2 + a^2 T / 2) at every pixel; the bins 8..24
+    (an off-by-one reading) would double it."""
+    T, n, c0, a = 32, 16, 1000, 400
+    rng = np.random.default_rng(9)
+    S = rng.random((n, n)) < 0.3
+    seq = c0 + a * np.round(np.cos(np.pi * np.arange(T) / 2)).astype(np.int64)
+    frames = (seq[:, None, None] * S[None]).astype(np.uint16)
+    M = oracle.fourier_window(frames, LAM, Z, PITCH, 7, 23)
+    H = oracle.render(frames, LAM, Z, PITCH)
+    P = (np.abs(H) ** 2).sum(0)
+    mask = P > 1e-9 * P.max()
+    ratio = (a * a * T / 4) / (T * c0 * c0 + a * a * T / 2)
+    assert np.allclose(M[mask] / P[mask], ratio, rtol=1e-10)
+    M2 = oracle.fourier_window(frames, LAM, Z, PITCH, 8, 24)
+    assert np.allclose(M2[mask] / P[mask], 2 * ratio, rtol=1e-10)
