@@ -129,6 +129,19 @@ dh_status dh_pca_windows(dh_plan_t plan, int first_slot, int slot_stride, int n_
                          int k0, int k1, float *images_dev, double *eigvals_dev,
                          void *stream);
 
+/* Eqs. 8-9, the paper's Fourier alternative to Eqs. 4-7: temporal demodulation of each
+ * window by the unitary DFT W, w_{t,k} = exp(-2 pi i t k / T) / sqrt(T) (t, k counted from
+ * 0), keeping the frequency bins k0..k1 (0 <= k0 <= k1 < T; the paper's filter indices
+ * n_1..n_2 count from 1, so its n_1 = 8, n_2 = 24 at T = 32 are bins 7..23), and summing
+ * their power: image w (FP32, n_y x n_x row-major, at images_dev + w * n_x n_y) is
+ * M[p] = sum_{k=k0..k1} |sum_t H_t[p] w_{t,k}|^2 for window w = slots
+ * [first_slot + w * slot_stride, + T). No covariance or eigendecomposition is computed;
+ * windows of any number and stride (stride 1 = a new window per frame) share the rendered
+ * holograms. Runs on the tensor cores for 16-bit storage (the DFT operand split into hi +
+ * lo 16-bit parts), on FP32 CUDA cores for FP32 storage. Asynchronous. */
+dh_status dh_fourier_windows(dh_plan_t plan, int first_slot, int slot_stride, int n_windows,
+                             int k0, int k1, float *images_dev, void *stream);
+
 /* The single-window calls of the paper's statement of the problem: render T frames
  * (frames_dev + t * frame_stride_elems, t < T) into slots [0, T). Asynchronous. */
 dh_status dh_render_stack(dh_plan_t plan, const uint16_t *frames_dev,

@@ -126,6 +126,18 @@ class Plan:
             _ptr(images), _ptr(eigvals) if eigvals is not None else None, _stream_ptr(stream)))
         return images, eigvals
 
+    def fourier_windows(self, first_slot: int, slot_stride: int, n_windows: int, k0: int,
+                        k1: int, images: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Eqs. 8-9 for windows [first_slot + w*slot_stride, +T): power of the unitary DFT's
+        bins k0..k1 (counted from 0). Returns the images [n_windows, ny, nx]."""
+        if images is None:
+            images = torch.empty((n_windows, self.ny, self.nx), dtype=torch.float32,
+                                 device=torch.device("cuda", torch.cuda.current_device()))
+        _lib.check("dh_fourier_windows", self._lib.dh_fourier_windows(
+            self._h, int(first_slot), int(slot_stride), int(n_windows), int(k0), int(k1),
+            _ptr(images), _stream_ptr(stream)))
+        return images
+
     def render_stack(self, frames: torch.Tensor, stream=None) -> None:
         f = self._frames(frames)
         if f.shape[0] < self.T:

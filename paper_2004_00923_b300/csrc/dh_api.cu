@@ -63,7 +63,7 @@ void dfree(Ptr *&ptr) {
 
 // Per-window buffers: covariance partials, C, lambda, V and the projection operand.
 void free_windows(Plan &p) {
-  dfree(p.d_part); dfree(p.d_C); dfree(p.d_lam); dfree(p.d_V); dfree(p.d_B);
+  dfree(p.d_part); dfree(p.d_C); dfree(p.d_lam); dfree(p.d_V); dfree(p.d_B); dfree(p.d_W);
   p.tmaps_ok = false;
   p.bytes -= p.window_bytes;
   p.window_bytes = 0;
@@ -85,10 +85,10 @@ size_t table_bytes(const Plan &p) {
 
 // Device bytes of every buffer a plan allocates, from its sizes, reservation and precision.
 struct StoreSizes {
-  size_t tables, H, mid, part, C, lam, V, B;
+  size_t tables, H, mid, part, C, lam, V, B, W;
   int mid_frames, parts_total;
   size_t B_window;
-  size_t windows() const { return part + C + lam + V + B; }
+  size_t windows() const { return part + C + lam + V + B + W; }
   size_t total() const { return tables + H + mid + windows(); }
 };
 
@@ -115,6 +115,7 @@ StoreSizes store_sizes(const Plan &p) {
   const size_t bw = p.prec == DH_PREC_FP32 ? (size_t)M * M * 4 : (size_t)2 * M * M * 2;
   z.B_window = (bw + 1023) / 1024 * 1024;
   z.B = z.B_window * p.max_windows;
+  z.W = z.B_window;  // one operand shared by every window (Eq. 8)
   return z;
 }
 
@@ -130,6 +131,7 @@ dh_status alloc_windows(Plan &p) {
   if ((st = dalloc(p, &p.d_lam, z.lam)) != DH_OK) return st;
   if ((st = dalloc(p, &p.d_V, z.V)) != DH_OK) return st;
   if ((st = dalloc(p, &p.d_B, z.B)) != DH_OK) return st;
+  if ((st = dalloc(p, &p.d_W, z.W)) != DH_OK) return st;
   p.window_bytes = z.windows();
   DH_CUDA_TRY(cudaMemset(p.d_B, 0, z.B));
   if (p.prec != DH_PREC_FP32) {
@@ -494,6 +496,19 @@ dh_status dh_pca_windows(dh_plan_t h, int first_slot, int slot_stride, int n_win
   if (!g.ok) return DH_ERR_STATE;
   return pca_impl(p, nullptr, 0, first_slot, slot_stride, n_windows, k0, k1, images_dev, eigvals_dev,
                   static_cast<cudaStream_t>(stream));
+}
+
+dh_status dh_fourier_windows(dh_plan_t h, int first_slot, int slot_stride, int n_windows, int k0,
+                            int k1, float *images_dev, void *stream) {
+  if (!h || !images_dev || n_windows < 1 || first_slot < 0 || slot_stride < 1) return DH_ERR_INVALID_ARG;
+  Plan &p = h->p;
+  if (k0 < 0 || k1 < k0 || k1 >= p.T) return DH_ERR_INVALID_ARG;
+  if ((long long)first_slot + (long long)(n_windows - 1) * slot_stride + p.T > p.max_frames)
+    return DH_ERR_INVALID_ARG;
+  Busy g(h->busy);
+  if (!g.ok) return DH_ERR_STATE;
+  return launch_fourier(p, first_slot, slot_stride, n_windows, k0, k1, images_dev,
+                        static_cast<cudaStream_t>(stream));
 }
 
 dh_status dh_render_stack(dh_plan_t h, const uint16_t *frames_dev, int64_t frame_stride_elems,

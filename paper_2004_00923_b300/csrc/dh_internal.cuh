@@ -50,6 +50,7 @@ struct Plan {
   double *d_V = nullptr;    // [max_windows][T][T][2]
   void *d_B = nullptr;      // projection operand per window
   size_t B_window_bytes = 0;
+  void *d_W = nullptr;      // projection operand shared by all windows (Eq. 8's DFT columns)
   uint32_t *d_status = nullptr;
 
   // tensor maps for the tensor-core kernels (16-bit storage only)
@@ -66,7 +67,7 @@ struct Plan {
 // ---------------------------------------------------------------- tracing
 enum KernelId {
   K_RENDER_ROWS = 0, K_RENDER_COLS, K_GRAM_SIMT, K_GRAM_TC, K_REDUCE_COV, K_JACOBI,
-  K_PROJECT_SIMT, K_PROJECT_TC, K_COUNT
+  K_PROJECT_SIMT, K_PROJECT_TC, K_FOURIER_OP, K_COUNT
 };
 const char *kernel_name(int kid);
 dh_status profile_enable(Plan &p, int on);
@@ -116,12 +117,17 @@ dh_status launch_gram_tc(Plan &p, int first_slot, int slot_stride, int n_windows
 dh_status launch_reduce(Plan &p, int n_windows, int parts_per_window, int woff, cudaStream_t s);
 dh_status launch_jacobi(Plan &p, int n_windows, int k0, int k1, int Npad, double *eig_user, int woff,
                         cudaStream_t s);
-// Eqs. 6-7.
-// images points at window woff's image; woff selects the windows' operands.
+// Eqs. 6-7 (and 8-9).
+// images points at window woff's image; woff selects the windows' operands, unless
+// shared_op is given: then every window projects onto that one operand (one window's
+// layout, as d_W holds it).
 dh_status launch_project_simt(Plan &p, int first_slot, int slot_stride, int n_windows, int Npad,
-                              float *images, int woff, cudaStream_t s);
+                              float *images, int woff, cudaStream_t s, const void *shared_op = nullptr);
 dh_status launch_project_tc(Plan &p, int first_slot, int slot_stride, int n_windows, int Npad,
-                            float *images, int woff, cudaStream_t s);
+                            float *images, int woff, cudaStream_t s, const void *shared_op = nullptr);
+// Eqs. 8-9: power of the DFT bins k0..k1 of every window.
+dh_status launch_fourier(Plan &p, int first_slot, int slot_stride, int n_windows, int k0, int k1,
+                         float *images, cudaStream_t s);
 dh_status make_tensor_maps(Plan &p);
 
 // single-window helpers used by the allocation-free covariance entry point

@@ -47,7 +47,7 @@ k_project_simt(const float *__restrict__ H, long long npix, int first_slot, int 
 
 template <int T>
 dh_status launch_t(Plan &p, int first_slot, int slot_stride, int n_windows, int nrows,
-                   float *images, int woff, cudaStream_t s) {
+                   float *images, int woff, cudaStream_t s, const void *shared_op) {
   // about 4 CTAs per SM in total, at least 256 pixels per CTA
   long long bpw = 1;
   while (bpw * 2 * n_windows <= 8ll * p.num_sms && p.npix / (bpw * 2) >= 256) bpw *= 2;
@@ -59,11 +59,12 @@ dh_status launch_t(Plan &p, int first_slot, int slot_stride, int n_windows, int 
     attr = true;
   }
   const long long B_stride = (long long)(p.B_window_bytes / sizeof(float));
+  const float *op = shared_op ? static_cast<const float *>(shared_op)
+                              : static_cast<const float *>(p.d_B) + (long long)woff * B_stride;
   ProfScope ps(p, K_PROJECT_SIMT, s);
   k_project_simt<T><<<(int)(n_windows * bpw), 256, smem, s>>>(
-      static_cast<const float *>(p.d_H), p.npix, first_slot, slot_stride,
-      static_cast<const float *>(p.d_B) + (long long)woff * B_stride, B_stride, nrows, (int)bpw, p.nx,
-      p.ny, images);
+      static_cast<const float *>(p.d_H), p.npix, first_slot, slot_stride, op,
+      shared_op ? 0 : B_stride, nrows, (int)bpw, p.nx, p.ny, images);
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
 }
@@ -71,11 +72,11 @@ dh_status launch_t(Plan &p, int first_slot, int slot_stride, int n_windows, int 
 }  // namespace
 
 dh_status launch_project_simt(Plan &p, int first_slot, int slot_stride, int n_windows, int Npad,
-                              float *images, int woff, cudaStream_t s) {
+                              float *images, int woff, cudaStream_t s, const void *shared_op) {
   switch (p.T) {
-    case 16: return launch_t<16>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s);
-    case 32: return launch_t<32>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s);
-    case 64: return launch_t<64>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s);
+    case 16: return launch_t<16>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op);
+    case 32: return launch_t<32>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op);
+    case 64: return launch_t<64>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op);
   }
   return DH_ERR_UNSUPPORTED_SIZE;
 }

@@ -520,7 +520,7 @@ dh_status gram_t(Plan &p, int first_slot, int slot_stride, int n_windows, cudaSt
 
 template <int T, bool BF16>
 dh_status project_t(Plan &p, int first_slot, int slot_stride, int n_windows, int Npad, float *images,
-                    int woff, cudaStream_t s) {
+                    int woff, cudaStream_t s, const void *shared_op) {
   using C = ProjCfg<T>;
   auto kern = k_project_tc<T, BF16>;
   static bool attr = false;
@@ -533,8 +533,10 @@ dh_status project_t(Plan &p, int first_slot, int slot_stride, int n_windows, int
   // eigenvector operand map: rows of 2T elements, box = KB x Npad
   const int M2 = 2 * T;
   const long long B_rows_pw = (long long)(p.B_window_bytes / (M2 * 2));
+  // a shared operand is one window's rows, read by every window (row stride 0 per window)
   CUtensorMap tmB;
-  dh_status st = encode_2d(&tmB, p.d_B, BF16, (uint64_t)M2, (uint64_t)(B_rows_pw * p.max_windows),
+  dh_status st = encode_2d(&tmB, shared_op ? const_cast<void *>(shared_op) : p.d_B, BF16, (uint64_t)M2,
+                           (uint64_t)(B_rows_pw * (shared_op ? 1 : p.max_windows)),
                            (uint64_t)M2 * 2, (uint32_t)C::KB, (uint32_t)Npad,
                            T == 16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
   if (st != DH_OK) return st;
@@ -549,7 +551,8 @@ dh_status project_t(Plan &p, int first_slot, int slot_stride, int n_windows, int
   if (grid > total) grid = (int)total;
   ProfScope ps(p, K_PROJECT_TC, s);
   kern<<<grid, C::THREADS, C::SMEM, s>>>(p.tmap_H, tmB, first_slot, slot_stride, n_windows, tiles_pw, Npad,
-                                          (int)B_rows_pw, (int)(woff * B_rows_pw), images, p.nx, p.ny,
+                                          shared_op ? 0 : (int)B_rows_pw,
+                                          shared_op ? 0 : (int)(woff * B_rows_pw), images, p.nx, p.ny,
                                           p.d_status);
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
@@ -590,16 +593,16 @@ dh_status launch_gram_tc(Plan &p, int first_slot, int slot_stride, int n_windows
 }
 
 dh_status launch_project_tc(Plan &p, int first_slot, int slot_stride, int n_windows, int Npad,
-                            float *images, int woff, cudaStream_t s) {
+                            float *images, int woff, cudaStream_t s, const void *shared_op) {
   if (!p.tmaps_ok) return DH_ERR_STATE;
   const bool bf16 = p.prec == DH_PREC_BF16;
   switch (p.T) {
-    case 16: return bf16 ? project_t<16, true>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s)
-                         : project_t<16, false>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s);
-    case 32: return bf16 ? project_t<32, true>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s)
-                         : project_t<32, false>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s);
-    case 64: return bf16 ? project_t<64, true>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s)
-                         : project_t<64, false>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s);
+    case 16: return bf16 ? project_t<16, true>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op)
+                         : project_t<16, false>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op);
+    case 32: return bf16 ? project_t<32, true>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op)
+                         : project_t<32, false>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op);
+    case 64: return bf16 ? project_t<64, true>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op)
+                         : project_t<64, false>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op);
   }
   return DH_ERR_UNSUPPORTED_SIZE;
 }

@@ -1,0 +1,73 @@
+"""Fourier temporal demodulation (Eqs. 8-9) on the GPU against the FP64 oracle.
+
+Every window's image is the power of the unitary DFT's bins k0..k1 (counted from 0; the
+paper's n_1 = 8, n_2 = 24 at n_t = 32 are bins 7..23). Tolerances as for Eqs. 6-7: image
+relative L2 <= 1e-4 (FP32 holograms) and <= 1e-3 (16-bit holograms).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from dh_synth import SpeckleParams, SpeckleStream
+from parity_helpers import LAM, PITCH, TOL_IMG, Z, rel, to_gpu
+
+pytestmark = pytest.mark.gpu
+
+BANDS = {16: (3, 11), 32: (7, 23), 64: (15, 47)}
+
+
+@pytest.fixture(scope="module")
+def dh():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2004_00923_b300 as m
+    return m
+
+
+@pytest.mark.parametrize("T", [16, 32, 64])
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_fourier_windows_match_oracle(dh, T, prec):
+    k0, k1 = BANDS[T]
+    frames = SpeckleStream(SpeckleParams(128, 256), seed=50 + T).next(2 * T).numpy()
+    with dh.Plan(128, 256, LAM, Z, PITCH, T=T, precision=prec, max_frames=2 * T) as plan:
+        plan.render_frames(to_gpu(frames))
+        img = plan.fourier_windows(0, T, 2, k0, k1).cpu().numpy()
+        assert plan.status() == 0
+    for w in range(2):
+        M = oracle.fourier_window(frames[w * T:(w + 1) * T], LAM, Z, PITCH, k0, k1)
+        assert rel(img[w], M) <= TOL_IMG[prec], (w, rel(img[w], M))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_fourier_stride1_sliding_windows(dh, prec):
+    """A new window per frame (the paper's Fourier mode runs at the frame rate)."""
+    T, n = 32, 9
+    frames = SpeckleStream(SpeckleParams(128, 128), seed=60).next(T + n - 1).numpy()
+    with dh.Plan(128, 128, LAM, Z, PITCH, T=T, precision=prec, max_frames=T + n - 1) as plan:
+        plan.render_frames(to_gpu(frames))
+        img = plan.fourier_windows(0, 1, n, 7, 23).cpu().numpy()
+    for w in range(n):
+        M = oracle.fourier_window(frames[w:w + T], LAM, Z, PITCH, 7, 23)
+        assert rel(img[w], M) <= TOL_IMG[prec], (w, rel(img[w], M))
+
+
+def test_fourier_full_band_is_parseval(dh):
+    """All bins kept: the unitary W preserves each pixel's temporal energy."""
+    T = 32
+    frames = SpeckleStream(SpeckleParams(64, 64), seed=61).next(T).numpy()
+    with dh.Plan(64, 64, LAM, Z, PITCH, T=T) as plan:
+        plan.render_frames(to_gpu(frames))
+        img = plan.fourier_windows(0, T, 1, 0, T - 1)[0].double().cpu().numpy()
+        energy = sum((plan.debug_hologram(t).abs() ** 2).double().cpu().numpy() for t in range(T))
+    assert rel(img, energy) <= 1e-6
+
+
+def test_fourier_rejects_bad_bins(dh):
+    with dh.Plan(64, 64, LAM, Z, PITCH, T=16) as plan:
+        with pytest.raises(dh.DHError) as e:
+            plan.fourier_windows(0, 16, 1, 5, 16)
+        assert e.value.code == 1
+        with pytest.raises(dh.DHError):
+            plan.fourier_windows(0, 1, 2, 0, 3)  # window 1 runs past the slots
