@@ -529,6 +529,95 @@ def run_sliding(args, ws, rank, local):
     return 0
 
 
+# --------------------------------------------------------------------------- Fourier mode
+FOURIER_FRAMES, FOURIER_BINS = 2048, (7, 23)  # the paper's n_1 = 8, n_2 = 24, from 0
+PAPER_FFT_GVOXEL_S = 17.0  # Table 1, FFT row: output voxels of 32 x 1024^2 windows per s
+
+
+def run_fourier(args, ws, rank, local):
+    """Eqs. 8-9 with a new 32-frame window per frame (stride 1) over 2048 frames of 1024^2:
+    each frame rendered once (FP16), then the DFT-bin power image of all 2017 windows."""
+    import paper_2004_00923_b300 as dh
+    from dh_synth import SpeckleParams, SpeckleStream
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    F = FOURIER_FRAMES
+    nwin = F - T + 1
+    k0, k1 = FOURIER_BINS
+    frames = SpeckleStream(SpeckleParams(NX, NY), seed=5000 + rank, device=dev).next(F)
+    plan = dh.Plan(NX, NY, LAM, Z, PITCH, T=T, precision=args.precision, max_frames=F)
+    images = torch.empty((nwin, NY, NX), dtype=torch.float32, device=dev)
+
+    def step():
+        plan.render_frames(frames)
+        plan.fourier_windows(0, 1, nwin, k0, k1, images)
+
+    step()
+    torch.cuda.synchronize()
+    plan.profile(True)
+    step()
+    per_kernel, launches = kernel_table(plan.profile_read())
+    plan.profile(False)
+    s = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    with dh.capture(s) as g:
+        step()
+    for _ in range(max(args.warmup, 0)):
+        g.launch(s)
+    ms, step_ms, clock_info = timed_graph(g, s, args.steps, ws, local)
+    ms_max = max_over_ranks(ms, ws)
+    value = whole_job_rate(nwin, ws, ms_max)
+    flags = plan.status()
+    hbm, _, peak_kind = measured_peaks()
+    npix = NX * NY
+    hb = 2 if args.precision in ("fp16", "bf16") else 4
+    hread = nwin * T * npix * 2 * hb
+    alg = {"render_rows": F * npix * 2, "render_cols": F * npix * 2 * hb,
+           "project_tc": hread + nwin * npix * 4, "project_simt": hread + nwin * npix * 4}
+    roofline = roofline_of(per_kernel, alg, hbm, peak_kind, ms / 1e3)
+    parity, cpu = None, None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        parity, secs = {}, 0.0
+        for w in (0, nwin // 2, nwin - 1):
+            fr = frames[w:w + T].cpu().numpy()
+            t0 = time.perf_counter()
+            M = oracle.fourier_window(fr, LAM, Z, PITCH, k0, k1)
+            secs += time.perf_counter() - t0
+            im = images[w].double().cpu().numpy()
+            parity[f"window{w}"] = {"image_rel_l2": float(np.linalg.norm(im - M) / np.linalg.norm(M)),
+                                    "tolerance_image": 1e-3 if hb == 2 else 1e-4}
+        cpu = {"value": 3 / secs, "unit": "windows/s", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": "windows 0, 1008 and 2016 (1024x1024x32), FP64 C oracle"}
+    gvox = value * T * npix / 1e9
+    if rank == 0:
+        line = {
+            "metric": "Fourier-demodulation windows/s (Eqs. 8-9, stride-1 32-frame windows) @1024²",
+            "value": value, "unit": "windows/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": gvox / PAPER_FFT_GVOXEL_S,
+            "dtype": ("mixed: f32 FFT, f16 tensor-core products (f32 accumulate)"
+                      if hb == 2 else "f32"),
+            "data": "synthetic",
+            "config": {"workload": "fourier: 2048 frames of 1024x1024 uint16, a 32-frame window "
+                                   "per frame (2017 windows), DFT bins 7..23, one CUDA graph "
+                                   "per step", "precision": args.precision,
+                       "l2": "no flush: 4 GiB of frames and 8 GiB of holograms per step",
+                       "parallelism": f"replicas x{ws}"},
+            "output_gvoxel_per_s": gvox,
+            "vs_baseline_note": "output voxels/s over the paper's ~17 Gvoxel/s (Table 1, FFT)",
+            "frames_per_s": F * ws / (ms_max / 1e3),
+            "step_ms": {"p50": statistics.median(step_ms), "max": max(step_ms)},
+            "roofline": roofline, "cpu_baseline": cpu, "parity": parity,
+            "gpu_launches": launches, "device_flags": flags, "clocks": clock_info,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    plan.close()
+    return 0
+
+
 # --------------------------------------------------------------------------- uneven sizes
 UNEVEN_SIZES = ((512, 40), (1024, 16), (2048, 4))
 
@@ -865,11 +954,13 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="stream time replayed by --workload serving")
-    ap.add_argument("--workload", choices=["paper", "sliding", "uneven", "serving"], default="paper",
+    ap.add_argument("--workload", choices=["paper", "sliding", "uneven", "serving", "fourier"],
+                    default="paper",
                     help="paper: the headline 64 x 1024^2 x 32 step (default); sliding: "
                          "16/32/64-frame windows at stride 8 over 2048 frames; uneven: "
                          "512^2/1024^2/2048^2 windows of 32/64 frames in one batch; serving: "
-                         "4 x 1024^2 @ 500 fps + 1 x 2048^2 @ 125 fps camera streams")
+                         "4 x 1024^2 @ 500 fps + 1 x 2048^2 @ 125 fps camera streams; fourier: "
+                         "Eqs. 8-9 with stride-1 32-frame windows over 2048 frames")
     args = ap.parse_args(argv)
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -882,6 +973,8 @@ def main(argv=None):
             return run_uneven(args, ws, rank, local)
         if args.workload == "serving":
             return run_serving(args, ws, rank, local)
+        if args.workload == "fourier":
+            return run_fourier(args, ws, rank, local)
         return run_ours(args, ws, rank, local)
     finally:
         if ws > 1 and torch.distributed.is_initialized():
