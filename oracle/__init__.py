@@ -12,6 +12,7 @@ Each wrapper names the equation of Puyo et al. (arXiv 2004.00923) it computes:
   pca_window       Eqs. 1, 4, 5, 6, 7 in the paper's order
   fourier_power    Eqs. 8-9 (H_tilde = H W I_f with the unitary DFT W, M = sum |H_tilde|^2)
   fourier_window   Eqs. 1, 8, 9 in the paper's order
+  svd_fourier_window  Eqs. 1, 4, 5, then the SVD filter of Eqs. 2-3 and Eqs. 8-9
   fft1d / fft2d    the DFT used inside Eq. 1 (exposed for pins)
 
 Parity status: every function above is pinned by `tests/test_oracle_pins.py`
@@ -69,6 +70,10 @@ def _load():
         lib.dho_fourier_window.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, u16p,
                                            ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_int, ctypes.c_int, _dp]
+        lib.dho_svd_fourier_window.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, u16p,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, _dp, _dp]
         lib.dho_num_threads.argtypes = []
         _lib = lib
     return _lib
@@ -200,3 +205,19 @@ def fourier_window(frames: np.ndarray, lambda_m: float, z_m: float, pitch_m: flo
     if rc != 0:
         raise RuntimeError(f"fourier_window failed ({rc})")
     return M
+
+
+def svd_fourier_window(frames: np.ndarray, lambda_m: float, z_m: float, pitch_m: float,
+                       k0: int, k1: int, b0: int, b1: int):
+    """The SVD-filtered, Fourier-demodulated window (Eq. 1; Eqs. 4-5 for V; H_f = H V I_f
+    V^{t*} of Eqs. 2-3 keeping components k0..k1 in decreasing order; Eqs. 8-9 over bins
+    b0..b1). Returns (M [ny, nx], lam [T] decreasing)."""
+    f = _c(frames, np.uint16)
+    T, ny, nx = f.shape
+    M, lam = np.empty((ny, nx)), np.empty(T)
+    rc = _load().dho_svd_fourier_window(nx, ny, T, f.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16)),
+                                        lambda_m, z_m, pitch_m, int(k0), int(k1), int(b0),
+                                        int(b1), _ptr(M), _ptr(lam))
+    if rc < 0:
+        raise RuntimeError(f"svd_fourier_window failed ({rc})")
+    return M, lam

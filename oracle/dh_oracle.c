@@ -398,3 +398,52 @@ int dho_fourier_window(int nx, int ny, int T, const uint16_t *I, double lambda_m
   free(hr); free(hi);
   return rc;
 }
+
+/* Eqs. 2-3 then Eqs. 8-9: singular value filtering of the window followed by temporal
+ * demodulation by the unitary DFT, the paper's earlier (prior-art) pipeline.
+ * Eq. 2 gives H = U Delta V^{t*}, so U Delta = H V with V the eigenvectors of C (Eq. 5),
+ * and Eq. 3's filtered stack is H_f = U Delta I_f V^{t*} = (H V) I_f V^{t*}: for every pixel,
+ *   P_k = sum_t H[t][p] V[t][k] for the kept components k = k0..k1 (reading R2),
+ *   H_f[t][p] = sum_{k=k0..k1} P_k conj(V[t][k]),
+ * then Eq. 8 with the filter of bins b0..b1 (reading R4) and Eq. 9:
+ *   M[p] = sum_{b=b0..b1} |sum_t H_f[t][p] w_{t,b}|^2. */
+int dho_svd_fourier_window(int nx, int ny, int T, const uint16_t *I, double lambda_m, double z_m,
+                           double pitch_m, int k0, int k1, int b0, int b1, double *M,
+                           double *lam) {
+  if (k0 < 0 || k1 < k0 || k1 >= T || b0 < 0 || b1 < b0 || b1 >= T) return -1;
+  size_t n = (size_t)nx * ny;
+  double *hr = malloc(sizeof(double) * n * T), *hi = malloc(sizeof(double) * n * T);
+  double *cr = malloc(sizeof(double) * T * T), *ci = malloc(sizeof(double) * T * T);
+  double *vr = malloc(sizeof(double) * T * T), *vi = malloc(sizeof(double) * T * T);
+  double *fr = malloc(sizeof(double) * n * T), *fi = malloc(sizeof(double) * n * T);
+  int rc = -2;
+  if (hr && hi && cr && ci && vr && vi && fr && fi) {
+    rc = dho_render(nx, ny, T, I, lambda_m, z_m, pitch_m, hr, hi);
+    if (rc == 0) rc = dho_covariance((long long)n, T, hr, hi, cr, ci);
+    if (rc == 0) {
+      rc = dho_eig(T, cr, ci, lam, vr, vi, 1e-15, 60);
+      if (rc >= 0) {
+#pragma omp parallel for schedule(static)
+        for (long long p = 0; p < (long long)n; ++p) {
+          for (int t = 0; t < T; ++t) { fr[(size_t)t * n + p] = 0.0; fi[(size_t)t * n + p] = 0.0; }
+          for (int k = k0; k <= k1; ++k) {
+            double pr = 0.0, pi = 0.0;
+            for (int t = 0; t < T; ++t) {
+              double a = hr[(size_t)t * n + p], b = hi[(size_t)t * n + p];
+              pr += a * vr[t * T + k] - b * vi[t * T + k];
+              pi += a * vi[t * T + k] + b * vr[t * T + k];
+            }
+            for (int t = 0; t < T; ++t) { /* P_k conj(V[t][k]) */
+              fr[(size_t)t * n + p] += pr * vr[t * T + k] + pi * vi[t * T + k];
+              fi[(size_t)t * n + p] += pi * vr[t * T + k] - pr * vi[t * T + k];
+            }
+          }
+        }
+        int frc = dho_fourier_power((long long)n, T, fr, fi, b0, b1, M);
+        if (frc != 0) rc = frc;
+      }
+    }
+  }
+  free(hr); free(hi); free(cr); free(ci); free(vr); free(vi); free(fr); free(fi);
+  return rc;
+}

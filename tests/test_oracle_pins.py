@@ -326,3 +326,39 @@ def test_fourier_window_tone_closed_form():
     assert np.allclose(M[mask] / P[mask], ratio, rtol=1e-10)
     M2 = oracle.fourier_window(frames, LAM, Z, PITCH, 8, 24)
     assert np.allclose(M2[mask] / P[mask], 2 * ratio, rtol=1e-10)
+
+
+# ------------------------------------------------- Eqs. 2-3 then 8-9 (SVD filter + DFT)
+def test_svd_fourier_reduces_to_fourier_with_every_component():
+    """I_f of Eq. 3 keeping every component leaves H_f = H (V unitary)."""
+    f = speckle_window(16, 32, 16, seed=71).numpy()
+    M, _ = oracle.svd_fourier_window(f, LAM, Z, PITCH, 0, 15, 3, 11)
+    ref = oracle.fourier_window(f, LAM, Z, PITCH, 3, 11)
+    assert np.allclose(M, ref, rtol=1e-9, atol=1e-12 * ref.max())
+
+
+def test_svd_fourier_reduces_to_pca_with_every_bin():
+    """Keeping every DFT bin, Eq. 9 is Parseval of H_f = (H V) I_f V^{t*}: the power of the
+    kept principal components, i.e. the image of Eqs. 6-7."""
+    f = speckle_window(32, 16, 32, seed=72).numpy()
+    M, lam = oracle.svd_fourier_window(f, LAM, Z, PITCH, 2, 31, 0, 31)
+    ref, lam_ref, _, _ = oracle.pca_window(f, LAM, Z, PITCH, 2, 31)
+    assert np.allclose(M, ref, rtol=1e-9, atol=1e-12 * ref.max())
+    assert np.allclose(lam, lam_ref, rtol=0, atol=1e-12 * lam_ref[0])
+
+
+@pytest.mark.parametrize("k0,k1,b0,b1", [(2, 15, 3, 11), (5, 12, 0, 7), (0, 9, 8, 15)])
+def test_svd_fourier_matches_numpy_svd_pipeline(k0, k1, b0, b1):
+    """Eqs. 2-3 with numpy's SVD of the (pixels, n_t) matrix (singular values sorted
+    decreasing, so index k of that order is kept for k0 <= k <= k1), then numpy's FFT."""
+    f = speckle_window(16, 16, 16, seed=73 + k0).numpy()
+    H = oracle.render(f, LAM, Z, PITCH).reshape(16, -1).T          # (pixels, n_t)
+    U, d, Vh = np.linalg.svd(H, full_matrices=False)
+    keep = np.zeros(16)
+    keep[k0:k1 + 1] = 1.0
+    Hf = (U * (d * keep)) @ Vh
+    F = np.fft.fft(Hf, axis=1, norm="ortho")
+    ref = (np.abs(F[:, b0:b1 + 1]) ** 2).sum(1).reshape(16, 16)
+    M, lam = oracle.svd_fourier_window(f, LAM, Z, PITCH, k0, k1, b0, b1)
+    assert np.allclose(M, ref, rtol=1e-8, atol=1e-10 * ref.max())
+    assert np.allclose(lam, d ** 2, rtol=0, atol=1e-10 * d[0] ** 2)
