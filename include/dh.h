@@ -142,6 +142,16 @@ dh_status dh_pca_windows(dh_plan_t plan, int first_slot, int slot_stride, int n_
 dh_status dh_fourier_windows(dh_plan_t plan, int first_slot, int slot_stride, int n_windows,
                              int k0, int k1, float *images_dev, void *stream);
 
+/* Eqs. 2-3 then Eqs. 8-9, the paper's earlier pipeline: singular value filtering of each
+ * window, keeping components k0..k1 of the decreasing order (H_f = U Delta I_f V^{t*} =
+ * H V I_f V^{t*}, V from Eqs. 4-5), then temporal demodulation of H_f by the unitary DFT,
+ * keeping bins b0..b1 (counted from 0), and the power sum of Eq. 9. Image w and, if
+ * eigvals_dev is not NULL, window w's T eigenvalues are written as by dh_pca_windows.
+ * 0 <= k0 <= k1 < T, 0 <= b0 <= b1 < T. Asynchronous. */
+dh_status dh_svd_fourier_windows(dh_plan_t plan, int first_slot, int slot_stride, int n_windows,
+                                 int k0, int k1, int b0, int b1, float *images_dev,
+                                 double *eigvals_dev, void *stream);
+
 /* The single-window calls of the paper's statement of the problem: render T frames
  * (frames_dev + t * frame_stride_elems, t < T) into slots [0, T). Asynchronous. */
 dh_status dh_render_stack(dh_plan_t plan, const uint16_t *frames_dev,

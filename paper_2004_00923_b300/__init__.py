@@ -138,6 +138,23 @@ class Plan:
             _ptr(images), _stream_ptr(stream)))
         return images
 
+    def svd_fourier_windows(self, first_slot: int, slot_stride: int, n_windows: int, k0: int,
+                            k1: int, b0: int, b1: int, images: torch.Tensor | None = None,
+                            eigvals: torch.Tensor | None = None, want_eigvals: bool = True,
+                            stream=None):
+        """Eqs. 2-3 then 8-9: SVD filter keeping components k0..k1 (decreasing order), DFT
+        bins b0..b1. Returns (images, eigvals)."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if images is None:
+            images = torch.empty((n_windows, self.ny, self.nx), dtype=torch.float32, device=dev)
+        if eigvals is None and want_eigvals:
+            eigvals = torch.empty((n_windows, self.T), dtype=torch.float64, device=dev)
+        _lib.check("dh_svd_fourier_windows", self._lib.dh_svd_fourier_windows(
+            self._h, int(first_slot), int(slot_stride), int(n_windows), int(k0), int(k1),
+            int(b0), int(b1), _ptr(images), _ptr(eigvals) if eigvals is not None else None,
+            _stream_ptr(stream)))
+        return images, eigvals
+
     def render_stack(self, frames: torch.Tensor, stream=None) -> None:
         f = self._frames(frames)
         if f.shape[0] < self.T:

@@ -178,11 +178,13 @@ std::vector<float2> chirp_table(int n, double a) {
 // caller's stream joined to everything it launched. One group is used: running the
 // eigensolver of one group beside the next group's rendering was measured slower (both
 // slowed down on the shared SMs).
+// With b0 >= 0 the operand of Eq. 6 is replaced, per window, by the SVD-filter + DFT operand
+// of Eqs. 2-3 and 8-9 (components k0..k1 kept, bins b0..b1).
 dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int first_slot,
                    int slot_stride, int n_windows, int k0, int k1, float *images, double *eig_user,
-                   cudaStream_t s) {
+                   cudaStream_t s, int b0 = -1, int b1 = -1) {
   const int G = 1;
-  const int nS = k1 - k0 + 1;
+  const int nS = b0 >= 0 ? b1 - b0 + 1 : k1 - k0 + 1;  // projected columns
   const int nop = p.prec == DH_PREC_FP32 ? 2 * nS : (2 * nS + 15) / 16 * 16;  // operand rows
   int w0s[Plan::kMaxGroups], nws[Plan::kMaxGroups];
   int rendered = 0;  // frames (slots relative to first_slot) already rendered
@@ -210,6 +212,8 @@ dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int 
     DH_CUDA_TRY(cudaStreamWaitEvent(p.aux, p.ev_grp[g], 0));
     st = launch_jacobi(p, nw, k0, k1, nop, eig_user ? eig_user + (long long)w0 * p.T : nullptr, w0, p.aux);
     if (st != DH_OK) return st;
+    if (b0 >= 0 && (st = launch_svd_fourier_operand(p, nw, k0, k1, b0, b1, nop, w0, p.aux)) != DH_OK)
+      return st;
     DH_CUDA_TRY(cudaEventRecord(p.ev_jac[g], p.aux));
     w0 += nw;
   }
@@ -496,6 +500,21 @@ dh_status dh_pca_windows(dh_plan_t h, int first_slot, int slot_stride, int n_win
   if (!g.ok) return DH_ERR_STATE;
   return pca_impl(p, nullptr, 0, first_slot, slot_stride, n_windows, k0, k1, images_dev, eigvals_dev,
                   static_cast<cudaStream_t>(stream));
+}
+
+dh_status dh_svd_fourier_windows(dh_plan_t h, int first_slot, int slot_stride, int n_windows, int k0,
+                                int k1, int b0, int b1, float *images_dev, double *eigvals_dev,
+                                void *stream) {
+  if (!h || !images_dev || n_windows < 1 || first_slot < 0 || slot_stride < 1) return DH_ERR_INVALID_ARG;
+  Plan &p = h->p;
+  if (k0 < 0 || k1 < k0 || k1 >= p.T || b0 < 0 || b1 < b0 || b1 >= p.T) return DH_ERR_INVALID_ARG;
+  if (n_windows > p.max_windows) return DH_ERR_INVALID_ARG;
+  if ((long long)first_slot + (long long)(n_windows - 1) * slot_stride + p.T > p.max_frames)
+    return DH_ERR_INVALID_ARG;
+  Busy g(h->busy);
+  if (!g.ok) return DH_ERR_STATE;
+  return pca_impl(p, nullptr, 0, first_slot, slot_stride, n_windows, k0, k1, images_dev, eigvals_dev,
+                  static_cast<cudaStream_t>(stream), b0, b1);
 }
 
 dh_status dh_fourier_windows(dh_plan_t h, int first_slot, int slot_stride, int n_windows, int k0,

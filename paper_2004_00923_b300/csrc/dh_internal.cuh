@@ -67,7 +67,7 @@ struct Plan {
 // ---------------------------------------------------------------- tracing
 enum KernelId {
   K_RENDER_ROWS = 0, K_RENDER_COLS, K_GRAM_SIMT, K_GRAM_TC, K_REDUCE_COV, K_JACOBI,
-  K_PROJECT_SIMT, K_PROJECT_TC, K_FOURIER_OP, K_COUNT
+  K_PROJECT_SIMT, K_PROJECT_TC, K_FOURIER_OP, K_SVD_FOURIER_OP, K_COUNT
 };
 const char *kernel_name(int kid);
 dh_status profile_enable(Plan &p, int on);
@@ -125,6 +125,10 @@ dh_status launch_project_simt(Plan &p, int first_slot, int slot_stride, int n_wi
                               float *images, int woff, cudaStream_t s, const void *shared_op = nullptr);
 dh_status launch_project_tc(Plan &p, int first_slot, int slot_stride, int n_windows, int Npad,
                             float *images, int woff, cudaStream_t s, const void *shared_op = nullptr);
+// Eqs. 2-3 then 8-9: per window, the operand Q = V_S V_S^{t*} W_band from the sorted
+// eigenvectors of windows [woff, woff + n_windows), replacing the Eq. 6 operand.
+dh_status launch_svd_fourier_operand(Plan &p, int n_windows, int k0, int k1, int b0, int b1, int Npad,
+                                     int woff, cudaStream_t s);
 // Eqs. 8-9: power of the DFT bins k0..k1 of every window.
 dh_status launch_fourier(Plan &p, int first_slot, int slot_stride, int n_windows, int k0, int k1,
                          float *images, cudaStream_t s);

@@ -71,3 +71,26 @@ def test_fourier_rejects_bad_bins(dh):
         assert e.value.code == 1
         with pytest.raises(dh.DHError):
             plan.fourier_windows(0, 1, 2, 0, 3)  # window 1 runs past the slots
+
+
+@pytest.mark.parametrize("T", [16, 32, 64])
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_svd_fourier_windows_match_oracle(dh, T, prec):
+    """Eqs. 2-3 then 8-9: SVD filter keeping components 2..T-1, then DFT bins. The filter is
+    the projector onto the kept eigenvectors, so like the image of Eqs. 6-7 it moves by about
+    ||dC|| / gap at the range boundary (the same gap-aware tolerance)."""
+    from parity_helpers import EPS_C, boundary_gap, lam_tol
+    b0, b1 = BANDS[T]
+    frames = SpeckleStream(SpeckleParams(128, 128), seed=70 + T).next(2 * T).numpy()
+    with dh.Plan(128, 128, LAM, Z, PITCH, T=T, precision=prec, max_frames=2 * T,
+                 max_windows=2) as plan:
+        plan.render_frames(to_gpu(frames))
+        img, lam = plan.svd_fourier_windows(0, T, 2, 2, T - 1, b0, b1)
+        img, lam = img.cpu().numpy(), lam.cpu().numpy()
+        assert plan.status() == 0
+    for w in range(2):
+        M, lam_ref = oracle.svd_fourier_window(frames[w * T:(w + 1) * T], LAM, Z, PITCH, 2, T - 1,
+                                               b0, b1)
+        tol = max(TOL_IMG[prec], EPS_C[prec] / boundary_gap(lam_ref, 2, T - 1))
+        assert rel(img[w], M) <= tol, (w, rel(img[w], M), tol)
+        assert np.max(np.abs(lam[w] - lam_ref)) / lam_ref[0] <= lam_tol(prec, 128 * 128)
