@@ -13,6 +13,7 @@ Each wrapper names the equation of Puyo et al. (arXiv 2004.00923) it computes:
   fourier_power    Eqs. 8-9 (H_tilde = H W I_f with the unitary DFT W, M = sum |H_tilde|^2)
   fourier_window   Eqs. 1, 8, 9 in the paper's order
   svd_fourier_window  Eqs. 1, 4, 5, then the SVD filter of Eqs. 2-3 and Eqs. 8-9
+  normalize / display_u8  display normalisation of an image by its mean (text after Eq. 9)
   fft1d / fft2d    the DFT used inside Eq. 1 (exposed for pins)
 
 Parity status: every function above is pinned by `tests/test_oracle_pins.py`
@@ -221,3 +222,20 @@ def svd_fourier_window(frames: np.ndarray, lambda_m: float, z_m: float, pitch_m:
     if rc < 0:
         raise RuntimeError(f"svd_fourier_window failed ({rc})")
     return M, lam
+
+
+def normalize(M: np.ndarray):
+    """An image divided by its own mean (the paper normalises every displayed image by its
+    average value). Returns (M / mean, mean) in FP64."""
+    M = np.asarray(M, dtype=np.float64)
+    mean = float(M.mean())
+    return M / mean, mean
+
+
+def display_u8(M: np.ndarray, mean: float, gain: float = 128.0) -> np.ndarray:
+    """8-bit display codes of an image with the given mean: clamp(rint(gain * M / mean), 0,
+    255), the product taken in FP32 as float(M) * float(gain / mean) (the precision in which
+    the kernel decides the code); the mean maps to code `gain`."""
+    scale = np.float32(np.float64(gain) / np.float64(mean))
+    v = np.asarray(M, dtype=np.float32) * scale
+    return np.clip(np.rint(v), 0, 255).astype(np.uint8)

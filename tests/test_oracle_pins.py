@@ -362,3 +362,21 @@ def test_svd_fourier_matches_numpy_svd_pipeline(k0, k1, b0, b1):
     M, lam = oracle.svd_fourier_window(f, LAM, Z, PITCH, k0, k1, b0, b1)
     assert np.allclose(M, ref, rtol=1e-8, atol=1e-10 * ref.max())
     assert np.allclose(lam, d ** 2, rtol=0, atol=1e-10 * d[0] ** 2)
+
+
+# ------------------------------------------------------- display normalisation by the mean
+def test_normalized_image_has_unit_mean_and_is_scale_free():
+    rng = np.random.default_rng(80)
+    M = rng.gamma(2.0, 3.0, size=(64, 32))
+    N, mean = oracle.normalize(M)
+    assert abs(N.mean() - 1.0) < 1e-14 and np.isclose(mean, M.sum() / M.size, rtol=1e-14)
+    N2, _ = oracle.normalize(7.5 * M)
+    assert np.allclose(N, N2, rtol=1e-14)
+
+
+def test_display_codes_of_known_images():
+    """A constant image shows the mean's code; 2x the mean and above saturate; 0 is black."""
+    const = np.full((8, 8), 3.25)
+    assert np.all(oracle.display_u8(const, 3.25) == 128)
+    ramp = np.array([0.0, 0.5, 1.0, 1.5, 1.99, 2.0, 10.0])
+    assert list(oracle.display_u8(ramp, 1.0)) == [0, 64, 128, 192, 255, 255, 255]
