@@ -172,6 +172,18 @@ dh_status dh_pca_batch(dh_plan_t plan, const uint16_t *frames_dev,
                        int window_stride_frames, int k0, int k1, float *images_dev,
                        double *eigvals_dev, void *stream);
 
+/* Display normalisation of n_images FP32 images of npix pixels each (back to back at
+ * images_dev, e.g. the output of dh_pca_windows): the paper divides every displayed image by
+ * its own average value. Writes each image's mean (FP64, fixed-order reduction) to
+ * means_dev[i]; if normalized_dev is not NULL, image / mean (FP32, may equal images_dev); if
+ * display_dev is not NULL, 8-bit display codes clamp(rint(gain * M / mean), 0, 255) (FP32
+ * product; the mean maps to code `display_gain`), n_images x npix bytes: the headless
+ * output of a display path (no graphics stack is used). Requires npix a multiple of 4,
+ * 16-byte aligned images and normalized buffers, display_gain > 0. Asynchronous. */
+dh_status dh_normalize_images(const float *images_dev, int n_images, int64_t npix,
+                              float *normalized_dev, uint8_t *display_dev, float display_gain,
+                              double *means_dev, void *stream);
+
 /* Inspection (tests): copy hologram slot `slot` as interleaved FP32 (re, im) pairs,
  * n_x n_y of them, to out_dev. Asynchronous. */
 dh_status dh_debug_hologram(dh_plan_t plan, int slot, float *out_dev, void *stream);

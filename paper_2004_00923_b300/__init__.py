@@ -21,7 +21,8 @@ import torch
 from . import _lib
 from ._lib import DHError, PREC  # noqa: F401
 
-__all__ = ["Plan", "Graph", "Server", "capture", "run_batch", "DHError", "PREC", "version"]
+__all__ = ["Plan", "Graph", "Server", "capture", "run_batch", "normalize_images", "save_pgm",
+           "DHError", "PREC", "version"]
 
 
 def version() -> str:
@@ -223,6 +224,32 @@ class Plan:
         flags = ctypes.c_uint32(0)
         _lib.check("dh_plan_status", self._lib.dh_plan_status(self._h, ctypes.byref(flags)))
         return int(flags.value)
+
+
+def normalize_images(images: torch.Tensor, normalized: bool = True, display: bool = False,
+                     gain: float = 128.0, in_place: bool = False, stream=None):
+    """dh_normalize_images on CUDA FP32 images [n, ny, nx]: returns (normalized or None,
+    display uint8 or None, means float64 [n])."""
+    if images.dtype != torch.float32 or not images.is_cuda or not images.is_contiguous():
+        raise TypeError("images must be a contiguous CUDA float32 tensor [n, ny, nx]")
+    imgs = images if images.dim() == 3 else images.unsqueeze(0)
+    n, npix = imgs.shape[0], imgs.shape[1] * imgs.shape[2]
+    means = torch.empty(n, dtype=torch.float64, device=imgs.device)
+    norm = (imgs if in_place else torch.empty_like(imgs)) if normalized else None
+    disp = torch.empty(imgs.shape, dtype=torch.uint8, device=imgs.device) if display else None
+    _lib.check("dh_normalize_images", _lib.load().dh_normalize_images(
+        _ptr(imgs), n, npix, _ptr(norm) if norm is not None else None,
+        _ptr(disp) if disp is not None else None, float(gain), _ptr(means), _stream_ptr(stream)))
+    return norm, disp, means
+
+
+def save_pgm(path: str, image_u8) -> None:
+    """Write an 8-bit image [ny, nx] (host or device tensor) as a binary PGM file."""
+    a = image_u8.detach().cpu().numpy() if isinstance(image_u8, torch.Tensor) else image_u8
+    ny, nx = a.shape
+    with open(path, "wb") as f:
+        f.write(f"P5\n{nx} {ny}\n255\n".encode())
+        f.write(a.astype("uint8").tobytes())
 
 
 def run_batch(items, stream=None) -> None:
