@@ -152,6 +152,7 @@ def algorithmic_bytes(npix, frames, windows, T, hbytes):
     return {
         "render_rows": frames * npix * 2,                    # uint16 frames in
         "render_cols": frames * npix * 2 * hbytes,           # Re/Im planes out
+        "render_fused": frames * npix * (2 + 2 * hbytes),    # both, one persistent launch
         "gram_tc": windows * T * npix * 2 * hbytes,          # H read once per window
         "gram_simt": windows * T * npix * 2 * hbytes,
         "project_tc": windows * (T * npix * 2 * hbytes + npix * 4),  # H read + image out
@@ -207,6 +208,11 @@ def run_ours(args, ws, rank, local):
 
     plan = dh.Plan(NX, NY, LAM, Z, PITCH, T=T, precision=args.precision, max_frames=nframes,
                    max_windows=nwin)
+    if args.render_schedule == "auto":
+        tuned = plan.autotune(256)  # setup, outside the timed region
+    else:
+        plan.set_render_schedule(args.render_schedule == "persistent", args.render_ring, args.render_lag)
+        tuned = plan.render_schedule()
     images = torch.empty((nwin, NY, NX), dtype=torch.float32, device=dev)
     eig = torch.empty((nwin, T), dtype=torch.float64, device=dev)
 
@@ -346,6 +352,7 @@ def run_ours(args, ws, rank, local):
                        "windows_per_step": nwin, "frames_per_step": nframes, "k0": K0, "k1": K1,
                        "precision": args.precision,
                        "l2": "no flush: 4 GiB of input frames per step exceed the 126 MB L2",
+                       "render_schedule": tuned,
                        "parallelism": f"replicas x{ws}"},
             "frames_per_s": value * T,
             "step_ms": {"p50": statistics.median(step_ms), "max": max(step_ms)},
@@ -487,8 +494,8 @@ def run_sliding(args, ws, rank, local):
     hbm, _, peak_kind = measured_peaks()
     npix = NX * NY
     gram = sum(n[L] * L * npix * 4 for L in SLIDE_LENGTHS)
-    alg = {"render_rows": F * npix * 2, "render_cols": F * npix * 4, "gram_tc": gram,
-           "project_tc": gram + nwin * npix * 4}
+    alg = {"render_rows": F * npix * 2, "render_cols": F * npix * 4, "render_fused": F * npix * 6,
+           "gram_tc": gram, "project_tc": gram + nwin * npix * 4}
     roofline = roofline_of(per_kernel, alg, hbm, peak_kind, ms / 1e3)
 
     parity, cpu = None, None
@@ -574,6 +581,7 @@ def run_fourier(args, ws, rank, local):
     hb = 2 if args.precision in ("fp16", "bf16") else 4
     hread = nwin * T * npix * 2 * hb
     alg = {"render_rows": F * npix * 2, "render_cols": F * npix * 2 * hb,
+           "render_fused": F * npix * (2 + 2 * hb),
            "project_tc": hread + nwin * npix * 4, "project_simt": hread + nwin * npix * 4}
     roofline = roofline_of(per_kernel, alg, hbm, peak_kind, ms / 1e3)
     parity, cpu = None, None
@@ -681,13 +689,14 @@ def run_uneven(args, ws, rank, local):
 
     hbm, _, peak_kind = measured_peaks()
     hb = 2 if args.precision in ("fp16", "bf16") else 4
-    alg = {"render_rows": 0, "render_cols": 0, "gram_tc": 0, "gram_simt": 0, "project_tc": 0,
-           "project_simt": 0}
+    alg = {"render_rows": 0, "render_cols": 0, "render_fused": 0, "gram_tc": 0, "gram_simt": 0,
+           "project_tc": 0, "project_simt": 0}
     for g, n, _, _ in sizes:
         npix = g.n * g.n
         F = g.frames.shape[0]
         alg["render_rows"] += F * npix * 2
         alg["render_cols"] += F * npix * 2 * hb
+        alg["render_fused"] += F * npix * (2 + 2 * hb)
         hread = sum(n[L] * L * npix * 2 * hb for L in n)
         for k in ("gram_tc", "gram_simt"):
             alg[k] += hread
@@ -952,6 +961,11 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--render-schedule", choices=["auto", "persistent", "chunks"], default="auto",
+                    help="Eq. 1 schedule of the headline plan: auto = the library's autotuner "
+                         "(dh_plan_autotune); else DH_OPT_RENDER_SCHEDULE with ring and lag")
+    ap.add_argument("--render-ring", type=int, default=0, help="DH_OPT_RENDER_RING (0 = automatic)")
+    ap.add_argument("--render-lag", type=int, default=0, help="DH_OPT_RENDER_LAG (0 = automatic)")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="stream time replayed by --workload serving")
     ap.add_argument("--workload", choices=["paper", "sliding", "uneven", "serving", "fourier"],

@@ -102,6 +102,32 @@ dh_status dh_plan_set_precision(dh_plan_t plan, dh_precision prec);
  * Synchronous; previously rendered holograms are discarded when the store grows. */
 dh_status dh_plan_reserve(dh_plan_t plan, int max_frames, int max_windows);
 
+/* Plan options (dh_plan_set_option).
+ * DH_OPT_RENDER_SCHEDULE: how Eq. 1 is scheduled. 0 (default): for square frames from
+ *   256 x 256, every frame of a render call in one persistent launch that interleaves the
+ *   row and column FFT passes of consecutive frames over a small L2-resident ring of
+ *   intermediates (a frame's column work starts as soon as its rows are done; other sizes
+ *   use chunks). 1: chunks of frames, each a row-pass launch then a column-pass launch.
+ *   Both give bitwise the same holograms. */
+#define DH_OPT_RENDER_SCHEDULE 0
+/* DH_OPT_RENDER_RING: frames of intermediate in the persistent schedule's ring, 2..64
+ *   (capped by the plan's intermediate), 0 = automatic (twice the lag).
+ * DH_OPT_RENDER_LAG: frames between a frame's row pass and its column pass in that
+ *   schedule, 1..63 (capped at ring - 1), 0 = automatic (half the ring; the automatic ring
+ *   makes it about 1.5 rounds of the grid's CTAs in work items). */
+#define DH_OPT_RENDER_RING 1
+#define DH_OPT_RENDER_LAG 2
+dh_status dh_plan_set_option(dh_plan_t plan, int option, int value);
+dh_status dh_plan_get_option(dh_plan_t plan, int option, int *value);
+
+/* Autotuner: render n_frames (capped at the plan's slots) zero frames with every candidate
+ * schedule (chunks; the persistent ring at the automatic lag, half and twice it) and keep
+ * the fastest in the plan's options (all candidates give bitwise the same holograms; the
+ * render time does not depend on the frame values). Discards rendered holograms; allocates
+ * and frees a temporary frame buffer; synchronises `stream`. Call it once after
+ * dh_plan_reserve, before any graph capture. */
+dh_status dh_plan_autotune(dh_plan_t plan, int n_frames, void *stream);
+
 /* Bytes of device memory the plan holds now (all buffers). */
 size_t dh_plan_device_bytes(dh_plan_t plan);
 

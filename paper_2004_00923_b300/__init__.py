@@ -94,6 +94,28 @@ class Plan:
     def __exit__(self, *exc):
         self.close()
 
+    def set_render_schedule(self, persistent: bool, ring: int = 0, lag: int = 0) -> None:
+        """DH_OPT_RENDER_SCHEDULE / _RING / _LAG: one persistent launch over an L2 ring (True,
+        the default where it applies; ring and lag 0 = automatic) or chunks of row/column
+        launches (False)."""
+        for opt, val in ((0, 0 if persistent else 1), (1, int(ring)), (2, int(lag))):
+            _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(self._h, opt, val))
+
+    def render_schedule(self) -> dict:
+        """The plan's render options: persistent (bool), ring and lag (0 = automatic)."""
+        v = ctypes.c_int(0)
+        out = {}
+        for opt, key in ((0, "persistent"), (1, "ring"), (2, "lag")):
+            _lib.check("dh_plan_get_option", self._lib.dh_plan_get_option(self._h, opt, ctypes.byref(v)))
+            out[key] = (v.value == 0) if opt == 0 else v.value
+        return out
+
+    def autotune(self, n_frames: int = 256, stream=None) -> dict:
+        """dh_plan_autotune: time the render schedules on zero frames and keep the fastest."""
+        _lib.check("dh_plan_autotune", self._lib.dh_plan_autotune(self._h, int(n_frames),
+                                                                   _stream_ptr(stream)))
+        return self.render_schedule()
+
     @property
     def device_bytes(self) -> int:
         return int(self._lib.dh_plan_device_bytes(self._h))

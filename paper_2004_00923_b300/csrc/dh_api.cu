@@ -343,7 +343,8 @@ dh_status dh_plan_create(dh_plan_t *out, int nx, int ny, double lambda_m, double
         (st = dalloc(p, &p.d_cy, cy.size() * sizeof(float2))) == DH_OK &&
         (st = dalloc(p, &p.d_twx, twx.size() * sizeof(float2))) == DH_OK &&
         (st = dalloc(p, &p.d_twy, twy.size() * sizeof(float2))) == DH_OK &&
-        (st = dalloc(p, &p.d_status, sizeof(uint32_t))) == DH_OK) {
+        (st = dalloc(p, &p.d_status, sizeof(uint32_t))) == DH_OK &&
+        (st = dalloc(p, &p.d_sync, sizeof(unsigned) * (1 + 2 * 64))) == DH_OK) {
       cudaError_t c = cudaMemcpy(p.d_cx, cx.data(), cx.size() * sizeof(float2), cudaMemcpyHostToDevice);
       if (c == cudaSuccess) c = cudaMemcpy(p.d_cy, cy.data(), cy.size() * sizeof(float2), cudaMemcpyHostToDevice);
       if (c == cudaSuccess) c = cudaMemcpy(p.d_twx, twx.data(), twx.size() * sizeof(float2), cudaMemcpyHostToDevice);
@@ -373,7 +374,7 @@ void release(dh_plan_t h) {
     if (p.ev_jac[k]) cudaEventDestroy(p.ev_jac[k]);
   }
   if (p.aux) cudaStreamDestroy(p.aux);
-  dfree(p.d_cx); dfree(p.d_cy); dfree(p.d_twx); dfree(p.d_twy); dfree(p.d_status);
+  dfree(p.d_cx); dfree(p.d_cy); dfree(p.d_twx); dfree(p.d_twy); dfree(p.d_status); dfree(p.d_sync);
   dh_plan *base = h->base;
   delete h;
   if (base) {
@@ -456,6 +457,95 @@ dh_status dh_plan_reserve(dh_plan_t h, int max_frames, int max_windows) {
 }
 
 size_t dh_plan_device_bytes(dh_plan_t h) { return h ? h->p.bytes : 0; }
+
+dh_status dh_plan_get_option(dh_plan_t h, int option, int *value) {
+  if (!h || !value) return DH_ERR_INVALID_ARG;
+  switch (option) {
+    case DH_OPT_RENDER_SCHEDULE: *value = h->p.render_mode; return DH_OK;
+    case DH_OPT_RENDER_RING: *value = h->p.render_ring; return DH_OK;
+    case DH_OPT_RENDER_LAG: *value = h->p.render_lag; return DH_OK;
+  }
+  return DH_ERR_INVALID_ARG;
+}
+
+// Time every candidate render schedule on n_frames zero frames (render time does not depend
+// on the values: no data-dependent control flow) and keep the fastest. Candidates: chunks,
+// and the persistent ring with the automatic lag, half of it and twice it.
+dh_status dh_plan_autotune(dh_plan_t h, int n_frames, void *stream) {
+  if (!h || n_frames < 1) return DH_ERR_INVALID_ARG;
+  Plan &p = h->p;
+  if (p.is_view) return DH_ERR_STATE;
+  if (n_frames > p.max_frames) n_frames = p.max_frames;
+  Busy g(h->busy);
+  if (!g.ok) return DH_ERR_STATE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint16_t *zeros = nullptr;
+  DH_CUDA_TRY(cudaMalloc(&zeros, (size_t)n_frames * p.npix * sizeof(uint16_t)));
+  struct Cand { int mode, ring, lag; };
+  std::vector<Cand> cands = {{1, 0, 0}};
+  {
+    // automatic lag of this plan (grid of 2 CTAs per SM, the persistent kernel's residency)
+    const int items = render_items_per_frame(p);
+    const long long grid = 2ll * p.num_sms;
+    const int lag = (int)((3 * grid + 2ll * items - 1) / (2ll * items));
+    for (int l : {lag, lag / 2, 2 * lag})
+      if (l >= 1 && 2 * l <= 64 && 2 * l <= p.mid_frames) cands.push_back({0, 2 * l, l});
+    if (p.mid_frames >= 3 && lag == 1) cands.push_back({0, 3, 1});
+  }
+  const int saved[3] = {p.render_mode, p.render_ring, p.render_lag};
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = cudaMemsetAsync(zeros, 0, (size_t)n_frames * p.npix * sizeof(uint16_t), s);
+  float best = 1e30f;
+  Cand pick = {saved[0], saved[1], saved[2]};
+  dh_status st = e == cudaSuccess ? DH_OK : fail_cuda(e);
+  for (const Cand &c : cands) {
+    if (st != DH_OK) break;
+    p.render_mode = c.mode; p.render_ring = c.ring; p.render_lag = c.lag;
+    if ((st = launch_render(p, zeros, p.npix, n_frames, 0, s)) != DH_OK) break;  // warm-up
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 3 && st == DH_OK; ++rep) {
+      e = cudaEventRecord(a, s);
+      if (e == cudaSuccess) st = launch_render(p, zeros, p.npix, n_frames, 0, s);
+      if (st == DH_OK && e == cudaSuccess) e = cudaEventRecord(b, s);
+      if (st == DH_OK && e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (st == DH_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      if (e != cudaSuccess && st == DH_OK) st = fail_cuda(e);
+      if (ms < tmin) tmin = ms;
+    }
+    if (st == DH_OK && tmin < best) { best = tmin; pick = c; }
+  }
+  p.render_mode = pick.mode; p.render_ring = pick.ring; p.render_lag = pick.lag;
+  if (st != DH_OK) { p.render_mode = saved[0]; p.render_ring = saved[1]; p.render_lag = saved[2]; }
+  cudaStreamSynchronize(s);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(zeros);
+  return st;
+}
+
+dh_status dh_plan_set_option(dh_plan_t h, int option, int value) {
+  if (!h) return DH_ERR_INVALID_ARG;
+  Busy g(h->busy);
+  if (!g.ok) return DH_ERR_STATE;
+  switch (option) {
+    case DH_OPT_RENDER_SCHEDULE:
+      if (value != 0 && value != 1) return DH_ERR_INVALID_ARG;
+      h->p.render_mode = value;
+      return DH_OK;
+    case DH_OPT_RENDER_RING:
+      if (value < 0 || value > 64 || value == 1) return DH_ERR_INVALID_ARG;
+      h->p.render_ring = value;
+      return DH_OK;
+    case DH_OPT_RENDER_LAG:
+      if (value < 0 || value > 63) return DH_ERR_INVALID_ARG;
+      h->p.render_lag = value;
+      return DH_OK;
+  }
+  return DH_ERR_INVALID_ARG;
+}
 
 size_t dh_plan_footprint(int nx, int ny, int T, dh_precision prec, int max_frames, int max_windows) {
   if (!pow2_in_range(nx) || !pow2_in_range(ny) || !(T == 16 || T == 32 || T == 64) ||

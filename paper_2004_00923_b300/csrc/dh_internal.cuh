@@ -35,6 +35,11 @@ struct Plan {
   // render intermediate (row-pass output): a chunk of frames sized to stay in L2
   float2 *d_mid = nullptr;
   int mid_frames = 0;
+  // render schedule: 0 = one persistent launch over a ring of intermediates where it
+  // applies (square frames from 256^2), else chunks; 1 = always chunks of two launches
+  int render_mode = 0;
+  int render_ring = 0, render_lag = 0;  // persistent schedule: ring frames, lag (0 = automatic)
+  unsigned *d_sync = nullptr;  // ticket and ring counters of the persistent render
   // second stream: the eigensolver of one group of windows overlaps the next group's work
   cudaStream_t aux = nullptr;
   static constexpr int kMaxGroups = 4;
@@ -67,7 +72,7 @@ struct Plan {
 // ---------------------------------------------------------------- tracing
 enum KernelId {
   K_RENDER_ROWS = 0, K_RENDER_COLS, K_GRAM_SIMT, K_GRAM_TC, K_REDUCE_COV, K_JACOBI,
-  K_PROJECT_SIMT, K_PROJECT_TC, K_FOURIER_OP, K_SVD_FOURIER_OP, K_COUNT
+  K_PROJECT_SIMT, K_PROJECT_TC, K_FOURIER_OP, K_SVD_FOURIER_OP, K_RENDER_FUSED, K_COUNT
 };
 const char *kernel_name(int kid);
 dh_status profile_enable(Plan &p, int on);
@@ -98,6 +103,8 @@ dh_status fail_cuda(cudaError_t e);
 dh_status launch_render(Plan &p, const uint16_t *frames, long long frame_stride, int n_frames,
                         int slot0, cudaStream_t s);
 void build_twiddles(int logn, float2 *host_out);  // host, FP64 -> FP32
+// work items per frame and pass of the render (square frames): N / FFTs per CTA
+int render_items_per_frame(const Plan &p);
 int twiddle_len(int logn);
 
 // Partial Gram matrices per window (split-K over pixels), fixed per frame size.

@@ -232,95 +232,197 @@ __device__ __forceinline__ int mid_index(int kx, int y, int ny, int cw_log) {
   return ((t * ny + y) << cw_log) + (c ^ mid_swz(y, cw_log));
 }
 
-// Row pass: FPC consecutive rows of one frame per item. The next item's uint16 rows are
-// prefetched into registers with 16-byte loads while the current rows are transformed;
-// each transform's input row is parked at the head of its own exchange region.
+// ---------------------------------------------------------------- work items
+// Row work: FPC consecutive rows y0.. of one frame. `pf` holds their uint16 samples (16-byte
+// chunks, thread-strided, loaded by row_prefetch); each transform's input row is parked at
+// the head of its own exchange region, then `parked()` runs (the caller issues the next
+// prefetch there, so it overlaps this item's transforms). Output: the frame's intermediate.
 template <int LOGN>
-__global__ void __launch_bounds__(fpc<LOGN>() * Shape<LOGN>::P, (fpc<LOGN>() * Shape<LOGN>::P <= 256 ? 2 : 1))
-k_render_rows(const uint16_t *__restrict__ frames, long long frame_stride, int ny, int cw_log,
-              const float2 *__restrict__ cx, const float2 *__restrict__ cy,
-              const float2 *__restrict__ tw, float2 *__restrict__ mid, int n_items) {
+struct RowCfg {
   using S = Shape<LOGN>;
-  constexpr int FPC = fpc<LOGN>();
-  constexpr int NT = FPC * S::P;                // threads
-  constexpr int CHUNKS = FPC * S::N / 8;        // 16-byte chunks of the uint16 rows
-  constexpr int CPT = CHUNKS / NT;              // chunks per thread (= R / 8)
-  constexpr int CPR = S::N / 8;                 // chunks per row
+  static constexpr int FPC = fpc<LOGN>();
+  static constexpr int NT = FPC * S::P;            // threads
+  static constexpr int CHUNKS = FPC * S::N / 8;    // 16-byte chunks of the uint16 rows
+  static constexpr int CPT = CHUNKS / NT;          // chunks per thread (= R / 8)
+  static constexpr int CPR = S::N / 8;             // chunks per row
+};
+
+template <int LOGN>
+__device__ __forceinline__ void row_prefetch(uint4 (&pf)[RowCfg<LOGN>::CPT], const uint16_t *__restrict__ frame,
+                                             int y0) {
+  using C = RowCfg<LOGN>;
+  const uint4 *src = reinterpret_cast<const uint4 *>(frame + (long long)y0 * Shape<LOGN>::N);
+#pragma unroll
+  for (int k = 0; k < C::CPT; ++k) pf[k] = __ldg(src + threadIdx.x + k * C::NT);
+}
+
+template <int LOGN, typename Parked>
+__device__ __forceinline__ void row_work(const uint4 (&pf)[RowCfg<LOGN>::CPT], float2 *smem, int y0, int ny,
+                                         int cw_log, const float2 *__restrict__ cx,
+                                         const float2 *__restrict__ cy, const float2 *__restrict__ tw,
+                                         float2 *__restrict__ dst, Parked parked) {
+  using S = Shape<LOGN>;
+  using C = RowCfg<LOGN>;
   using E = Engine<LOGN, (S::P > 32)>;
-  extern __shared__ float2 smem[];
   const int fft = threadIdx.x / S::P, j = threadIdx.x % S::P;
   float2 *sm = smem + fft * S::RSTRIDE;
-  const int groups = ny / FPC;
-  const long long npix = (long long)S::N * ny;
-
-  uint4 pf[CPT];
-  auto prefetch = [&](int item) {
-    const int f = item / groups, y0 = (item % groups) * FPC;
-    const uint4 *src = reinterpret_cast<const uint4 *>(frames + (long long)f * frame_stride + (long long)y0 * S::N);
+  const int y = y0 + fft;
+  __syncthreads();  // every transform is done with its region (previous item)
 #pragma unroll
-    for (int k = 0; k < CPT; ++k) pf[k] = __ldg(src + threadIdx.x + k * NT);
-  };
-  if (blockIdx.x < n_items) prefetch(blockIdx.x);
-
-  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    const int f = item / groups, y = (item % groups) * FPC + fft;
-    __syncthreads();  // every transform is done with its region (previous item)
+  for (int k = 0; k < C::CPT; ++k) {
+    const int c = threadIdx.x + k * C::NT, row = c / C::CPR, cr = c % C::CPR;
+    reinterpret_cast<uint4 *>(smem + row * S::RSTRIDE)[cr] = pf[k];
+  }
+  parked();
+  __syncthreads();
+  const uint16_t *row16 = reinterpret_cast<const uint16_t *>(sm);
+  float2 v[S::R];
 #pragma unroll
-    for (int k = 0; k < CPT; ++k) {  // park each row at the head of its transform's region
-      const int c = threadIdx.x + k * NT, row = c / CPR, cr = c % CPR;
-      reinterpret_cast<uint4 *>(smem + row * S::RSTRIDE)[cr] = pf[k];
-    }
-    if (item + (int)gridDim.x < n_items) prefetch(item + gridDim.x);
-    __syncthreads();
-    const uint16_t *row16 = reinterpret_cast<const uint16_t *>(sm);
-    float2 v[S::R];
+  for (int r = 0; r < S::R; ++r) {
+    const int x = j + r * S::P;
+    const float a = (float)row16[x];
+    const float2 c = __ldg(cx + x);
+    v[r] = make_float2(a * c.x, a * c.y);
+  }
+  E::run(v, sm, j, tw);  // its first exchange store is ordered after the reads above
+  const float2 cyy = __ldg(cy + y);
+  if ((S::P & ((1 << cw_log) - 1)) == 0) {
+    // kx = j + i P: the tile column and the swizzle are fixed per thread, and successive
+    // outputs are P n_y elements apart
+    float2 *d = dst + mid_index(j, y, ny, cw_log);
+    const int step = S::P * ny;
 #pragma unroll
-    for (int r = 0; r < S::R; ++r) {
-      const int x = j + r * S::P;
-      const float a = (float)row16[x];
-      const float2 c = __ldg(cx + x);
-      v[r] = make_float2(a * c.x, a * c.y);
-    }
-    E::run(v, sm, j, tw);  // its first exchange store is ordered after the reads above
-    const float2 cyy = __ldg(cy + y);
-    float2 *dst = mid + (long long)f * npix;
-    if ((S::P & ((1 << cw_log) - 1)) == 0) {
-      // kx = j + i P: the tile column and the swizzle are fixed per thread, and successive
-      // outputs are P n_y elements apart
-      float2 *d = dst + mid_index(j, y, ny, cw_log);
-      const int step = S::P * ny;
+    for (int i = 0; i < S::R; ++i) d[i * step] = cmul(v[E::out_reg(i)], cyy);
+  } else {
 #pragma unroll
-      for (int i = 0; i < S::R; ++i) d[i * step] = cmul(v[E::out_reg(i)], cyy);
-    } else {
-#pragma unroll
-      for (int i = 0; i < S::R; ++i)
-        dst[mid_index(j + i * S::P, y, ny, cw_log)] = cmul(v[E::out_reg(i)], cyy);
-    }
+    for (int i = 0; i < S::R; ++i)
+      dst[mid_index(j + i * S::P, y, ny, cw_log)] = cmul(v[E::out_reg(i)], cyy);
   }
 }
 
-// Column pass: one tile of FPC (= CW) columns of one frame per item. The tile (contiguous,
-// CW n_y FP32 complex values) arrives by bulk asynchronous copy into shared memory; each
-// transform (P threads) reads its column, runs in place in the same buffer, and writes the
-// hologram planes in column-major pixel order p = kx n_y + ky (re plane, then im plane, of
-// slot slot0 + f). A bulk copy that does not complete within the wait budget raises
-// DH_FLAG_WAIT_TIMEOUT and the CTA stops.
-template <int LOGN, typename OutT>
-__global__ void __launch_bounds__(fpc<LOGN>() * Shape<LOGN>::P, (fpc<LOGN>() * Shape<LOGN>::P <= 256 ? 3 : 1))
-k_render_cols(const float2 *__restrict__ mid, int nx, const float2 *__restrict__ tw,
-              OutT *__restrict__ H, long long npix, long long rows_total, int slot0, int n_items,
-              uint32_t *__restrict__ status) {
+// Column work: one tile of FPC (= CW) columns [kx0, kx0 + FPC) of one frame. The tile
+// (contiguous, CW n_y FP32 complex values) arrives by bulk asynchronous copy into shared
+// memory (thread 0 issues it; `issued()` then runs on every thread, `landed()` on thread 0
+// once the copy is complete); each transform (P threads) reads its column, runs in place
+// in the same buffer, and writes the hologram planes of `slot` in column-major pixel order
+// p = kx n_y + ky. Returns false (after a barrier) if the copy did not complete within the
+// wait budget; `copy_ok` false on thread 0 skips the copy (a failed wait before it).
+template <int LOGN, typename OutT, typename Issued, typename Landed>
+__device__ __forceinline__ bool col_work(const float2 *__restrict__ src, float2 *smem, uint64_t *bar,
+                                         uint32_t &phase, int *abort_flag, bool copy_ok, int kx0,
+                                         OutT *__restrict__ H, long long npix, long long rows_total,
+                                         int slot, bool &finite, const float2 *__restrict__ tw,
+                                         Issued issued, Landed landed) {
   using S = Shape<LOGN>;
   constexpr int FPC = fpc<LOGN>();
   constexpr int CW_LOG = FPC == 16 ? 4 : FPC == 8 ? 3 : FPC == 4 ? 2 : FPC == 2 ? 1 : 0;
   constexpr int TILE_BYTES = FPC * S::N * (int)sizeof(float2);
   constexpr int CHUNK = TILE_BYTES < 16384 ? TILE_BYTES : 16384;
   using E = Engine<LOGN, (S::P > 32)>;
+  const int fft = threadIdx.x / S::P, j = threadIdx.x % S::P;
+  float2 *sm = smem + fft * S::RSTRIDE;
+  if (threadIdx.x == 0) {
+    if (copy_ok) {
+      tc::mbar_arrive_expect_tx(bar, TILE_BYTES);
+      const char *s8 = reinterpret_cast<const char *>(src);
+#pragma unroll
+      for (int off = 0; off < TILE_BYTES; off += CHUNK)
+        tc::bulk_load(reinterpret_cast<char *>(smem) + off, s8 + off, CHUNK, bar);
+    } else {
+      *abort_flag = 1;
+      tc::mbar_arrive(bar);  // completes the phase without data so no thread waits it out
+    }
+  }
+  issued();
+  if (!tc::mbar_wait(bar, phase)) *abort_flag = 1;
+  phase ^= 1;
+  if (threadIdx.x == 0 && copy_ok && !*abort_flag) landed();
+  __syncthreads();
+  if (*abort_flag) return false;
+  float2 v[S::R];
+  if constexpr (S::P % 16 == 0) {  // y = j + r P keeps the swizzle of j
+    const float2 *col = smem + j * FPC + (fft ^ mid_swz(j, CW_LOG));
+#pragma unroll
+    for (int r = 0; r < S::R; ++r) v[r] = col[r * S::P * FPC];
+  } else {
+#pragma unroll
+    for (int r = 0; r < S::R; ++r) {
+      const int y = j + r * S::P;
+      v[r] = smem[y * FPC + (fft ^ mid_swz(y, CW_LOG))];
+    }
+  }
+  __syncthreads();  // the tile is consumed; its buffer becomes the exchange regions
+  E::run(v, sm, j, tw);
+  const int kx = kx0 + fft;
+  if constexpr (sizeof(OutT) == 4) {  // FP32 planes: [slot][re|im][p]
+    OutT *re = H + (long long)slot * 2 * npix + (long long)kx * S::N;
+    OutT *im = re + npix;
+#pragma unroll
+    for (int i = 0; i < S::R; ++i) {
+      const float2 o = v[E::out_reg(i)];
+      finite &= isfinite(o.x) & isfinite(o.y);
+      re[j + i * S::P] = o.x;
+      im[j + i * S::P] = o.y;
+    }
+  } else {  // 16-bit planes in 64-pixel blocks: [p / 64][row = 2 slot + c][p % 64]
+    const long long pix0 = (long long)kx * S::N;  // a multiple of 64 when n_y >= 64
+    OutT *base = H + (2ll * slot << 6);
+    const long long bstride = rows_total << 6;
+#pragma unroll
+    for (int i = 0; i < S::R; ++i) {
+      const float2 o = v[E::out_reg(i)];
+      const OutT a = to_store<OutT>(o.x), b = to_store<OutT>(o.y);
+      finite &= stored_finite<OutT>(a) & stored_finite<OutT>(b);
+      OutT *q;
+      if constexpr (S::N >= 64) {
+        const int e = j + i * S::P;  // < n_y
+        q = base + ((pix0 >> 6) + (e >> 6)) * bstride + (e & 63);
+      } else {
+        const long long pix = pix0 + j + i * S::P;
+        q = base + (pix >> 6) * bstride + (pix & 63);
+      }
+      q[0] = a;
+      q[64] = b;
+    }
+  }
+  __syncthreads();  // all transforms are done with the buffer before the next copy lands
+  return true;
+}
+
+// Row pass over a chunk of frames: one item = FPC consecutive rows of one frame.
+template <int LOGN>
+__global__ void __launch_bounds__(fpc<LOGN>() * Shape<LOGN>::P, (fpc<LOGN>() * Shape<LOGN>::P <= 256 ? 2 : 1))
+k_render_rows(const uint16_t *__restrict__ frames, long long frame_stride, int ny, int cw_log,
+              const float2 *__restrict__ cx, const float2 *__restrict__ cy,
+              const float2 *__restrict__ tw, float2 *__restrict__ mid, int n_items) {
+  using C = RowCfg<LOGN>;
+  extern __shared__ float2 smem[];
+  const int groups = ny / C::FPC;
+  const long long npix = (long long)Shape<LOGN>::N * ny;
+  uint4 pf[C::CPT];
+  auto frame_of = [&](int item) { return frames + (long long)(item / groups) * frame_stride; };
+  if (blockIdx.x < n_items) row_prefetch<LOGN>(pf, frame_of(blockIdx.x), (blockIdx.x % groups) * C::FPC);
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int f = item / groups, y0 = (item % groups) * C::FPC;
+    const int nxt = item + (int)gridDim.x;
+    row_work<LOGN>(pf, smem, y0, ny, cw_log, cx, cy, tw, mid + (long long)f * npix, [&]() {
+      if (nxt < n_items) row_prefetch<LOGN>(pf, frame_of(nxt), (nxt % groups) * C::FPC);
+    });
+  }
+}
+
+// Column pass over a chunk of frames: one item = one tile of FPC columns of one frame,
+// written to hologram slot slot0 + f. A bulk copy that does not complete within the wait
+// budget raises DH_FLAG_WAIT_TIMEOUT and the CTA stops.
+template <int LOGN, typename OutT>
+__global__ void __launch_bounds__(fpc<LOGN>() * Shape<LOGN>::P, (fpc<LOGN>() * Shape<LOGN>::P <= 256 ? 3 : 1))
+k_render_cols(const float2 *__restrict__ mid, int nx, const float2 *__restrict__ tw,
+              OutT *__restrict__ H, long long npix, long long rows_total, int slot0, int n_items,
+              uint32_t *__restrict__ status) {
+  constexpr int FPC = fpc<LOGN>();
   extern __shared__ float2 smem[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int abort_flag;
-  const int fft = threadIdx.x / S::P, j = threadIdx.x % S::P;
-  float2 *sm = smem + fft * S::RSTRIDE;
   const int groups = nx / FPC;
   if (threadIdx.x == 0) {
     tc::mbar_init(&bar, 1);
@@ -332,63 +434,137 @@ k_render_cols(const float2 *__restrict__ mid, int nx, const float2 *__restrict__
   bool finite = true;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     const int f = item / groups, t = item % groups;
-    if (threadIdx.x == 0) {
-      const char *src = reinterpret_cast<const char *>(mid + (long long)f * npix + (long long)t * FPC * S::N);
-      tc::mbar_arrive_expect_tx(&bar, TILE_BYTES);
-#pragma unroll
-      for (int off = 0; off < TILE_BYTES; off += CHUNK) tc::bulk_load(reinterpret_cast<char *>(smem) + off, src + off, CHUNK, &bar);
-    }
-    if (!tc::mbar_wait(&bar, phase)) abort_flag = 1;
-    phase ^= 1;
+    const float2 *src = mid + (long long)f * npix + (long long)t * FPC * Shape<LOGN>::N;
+    if (!col_work<LOGN, OutT>(src, smem, &bar, phase, &abort_flag, true, t * FPC, H, npix, rows_total,
+                              slot0 + f, finite, tw, []() {}, []() {}))
+      break;
+  }
+  if (abort_flag && threadIdx.x == 0) {
+    atomicOr(status, DH_FLAG_WAIT_TIMEOUT);
+    tc::mbar_wait(&bar, phase ^ 1);  // let a late copy land before the CTA exits
+  }
+  if (!finite) atomicOr(status, DH_FLAG_STORE_OVERFLOW);
+}
+
+// ---------------------------------------------------------------- fused, persistent render
+// One launch renders every frame of a call (square frames whose row and column items both
+// use 256 threads). Work items are taken from a global ticket counter in a fixed order:
+// phase k holds the row items of frame k interleaved with the column items of frame k - lag
+// (0 < lag < ring), so a frame's rows have had lag phases to finish before its columns run.
+// The row-pass output goes to a ring of `ring` frame-sized intermediates, small enough to
+// stay in L2, instead of a chunk of frames:
+//   - a column item of frame f waits until the row items of frame f are complete;
+//   - a row item of frame f waits until the column items of frame f - ring have copied
+//     their tiles out of the ring slot it overwrites.
+// Every item waits only on items with lower tickets, and a ticket is only ever held by a
+// running CTA, so the waits cannot deadlock whatever the residency. Waits are bounded: on
+// expiry the CTA raises DH_FLAG_WAIT_TIMEOUT and stops (CTAs waiting on it then time out
+// too). Ring writes (generic proxy) are fenced against the column items' bulk copies (async
+// proxy) on both sides of the release/acquire pair that publishes them.
+constexpr int kMaxRing = 64;  // ring slots the counter array (1 + 2 kMaxRing words) serves
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned *p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ bool wait_geq(const unsigned *p, unsigned target) {
+  if (ld_acquire(p) >= target) return true;
+  const long long t0 = clock64();
+  while (ld_acquire(p) < target) {
+    if (clock64() - t0 > tc::kWaitBudget) return false;
+    __nanosleep(128);
+  }
+  return true;
+}
+
+template <int LOGN, typename OutT>
+__global__ void __launch_bounds__(256, 2)
+k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int n_frames, int cw_log,
+               const float2 *__restrict__ cx, const float2 *__restrict__ cy, const float2 *__restrict__ tw,
+               float2 *__restrict__ mid, int ring, int lag, OutT *__restrict__ H, long long rows_total,
+               int slot0, unsigned *__restrict__ sync, uint32_t *__restrict__ status) {
+  using S = Shape<LOGN>;
+  using RC = RowCfg<LOGN>;
+  constexpr int FPC = fpc<LOGN>();  // rows per row item = columns per column item
+  constexpr int N = S::N;
+  constexpr int NI = N / FPC;       // row items = column items per frame
+  constexpr long long NPIX = (long long)N * N;
+  static_assert(RC::NT == 256, "fused render needs 256-thread items");
+  extern __shared__ float2 smem[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  __shared__ int tk[2];
+  unsigned *tickets = sync, *rows_done = sync + 1, *cols_done = sync + 1 + ring;
+  const int total = (n_frames + lag) * 2 * NI;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_barrier_init();
+    abort_flag = 0;
+    tk[0] = (int)atomicAdd(tickets, 1u);
+  }
+  __syncthreads();
+  // ticket i: phase k = i / (2 NI); even positions are row items of frame k, odd ones column
+  // items of frame k - lag; the item index is the position / 2
+  auto is_row = [](int i) { return ((i % (2 * NI)) & 1) == 0; };
+  auto frame_of = [&](int i) { return i / (2 * NI) - (is_row(i) ? 0 : lag); };
+  auto item_of = [](int i) { return (i % (2 * NI)) >> 1; };
+  auto valid = [&](int i) { const int f = frame_of(i); return i < total && f >= 0 && f < n_frames; };
+  int cur = tk[0];
+  uint4 pf[RC::CPT];
+  if (valid(cur) && is_row(cur))
+    row_prefetch<LOGN>(pf, frames + (long long)frame_of(cur) * frame_stride, item_of(cur) * FPC);
+  uint32_t phase = 0;
+  bool finite = true;
+  int b = 1;
+  while (cur < total) {
+    if (threadIdx.x == 0) tk[b] = (int)atomicAdd(tickets, 1u);
     __syncthreads();
+    const int nxt = tk[b];
+    b ^= 1;
     if (abort_flag) break;
-    float2 v[S::R];
-    if constexpr (S::P % 16 == 0) {  // y = j + r P keeps the swizzle of j
-      const float2 *col = smem + j * FPC + (fft ^ mid_swz(j, CW_LOG));
-#pragma unroll
-      for (int r = 0; r < S::R; ++r) v[r] = col[r * S::P * FPC];
+    // the next item's uint16 rows are loaded while this item runs (or right away when this
+    // ticket names no item)
+    auto prefetch_next = [&]() {
+      if (valid(nxt) && is_row(nxt))
+        row_prefetch<LOGN>(pf, frames + (long long)frame_of(nxt) * frame_stride, item_of(nxt) * FPC);
+    };
+    if (!valid(cur)) {
+      prefetch_next();
     } else {
-#pragma unroll
-      for (int r = 0; r < S::R; ++r) {
-        const int y = j + r * S::P;
-        v[r] = smem[y * FPC + (fft ^ mid_swz(y, CW_LOG))];
-      }
-    }
-    __syncthreads();  // the tile is consumed; its buffer becomes the exchange regions
-    E::run(v, sm, j, tw);
-    const int kx = t * FPC + fft;
-    if constexpr (sizeof(OutT) == 4) {  // FP32 planes: [slot][re|im][p]
-      OutT *re = H + (long long)(slot0 + f) * 2 * npix + (long long)kx * S::N;
-      OutT *im = re + npix;
-#pragma unroll
-      for (int i = 0; i < S::R; ++i) {
-        const float2 o = v[E::out_reg(i)];
-        finite &= isfinite(o.x) & isfinite(o.y);
-        re[j + i * S::P] = o.x;
-        im[j + i * S::P] = o.y;
-      }
-    } else {  // 16-bit planes in 64-pixel blocks: [p / 64][row = 2 slot + c][p % 64]
-      const long long pix0 = (long long)kx * S::N;  // a multiple of 64 when n_y >= 64
-      OutT *base = H + (2ll * (slot0 + f) << 6);
-      const long long bstride = rows_total << 6;
-#pragma unroll
-      for (int i = 0; i < S::R; ++i) {
-        const float2 o = v[E::out_reg(i)];
-        const OutT a = to_store<OutT>(o.x), b = to_store<OutT>(o.y);
-        finite &= stored_finite<OutT>(a) & stored_finite<OutT>(b);
-        OutT *q;
-        if constexpr (S::N >= 64) {
-          const int e = j + i * S::P;  // < n_y
-          q = base + ((pix0 >> 6) + (e >> 6)) * bstride + (e & 63);
-        } else {
-          const long long pix = pix0 + j + i * S::P;
-          q = base + (pix >> 6) * bstride + (pix & 63);
+      const int f = frame_of(cur), i = item_of(cur), rs = f % ring;
+      float2 *ring_f = mid + (long long)rs * NPIX;
+      if (is_row(cur)) {
+        if (threadIdx.x == 0 && !wait_geq(cols_done + rs, (unsigned)(f / ring) * NI)) abort_flag = 1;
+        __syncthreads();
+        if (abort_flag) break;
+        row_work<LOGN>(pf, smem, i * FPC, N, cw_log, cx, cy, tw, ring_f, prefetch_next);
+        fence_proxy_async_global();  // this thread's ring writes, for later bulk copies
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          __threadfence();
+          red_release_add(rows_done + rs, 1u);
         }
-        q[0] = a;
-        q[64] = b;
+      } else {
+        bool ok = true;
+        if (threadIdx.x == 0) {
+          ok = wait_geq(rows_done + rs, (unsigned)(f / ring + 1) * NI);
+          if (ok) fence_proxy_async_global();
+        }
+        const float2 *src = ring_f + (long long)i * FPC * N;
+        if (!col_work<LOGN, OutT>(src, smem, &bar, phase, &abort_flag, ok, i * FPC, H, NPIX, rows_total,
+                                  slot0 + f, finite, tw, prefetch_next,
+                                  [&]() { red_release_add(cols_done + rs, 1u); }))
+          break;
       }
     }
-    __syncthreads();  // all transforms are done with the buffer before the next copy lands
+    cur = nxt;
   }
   if (abort_flag && threadIdx.x == 0) {
     atomicOr(status, DH_FLAG_WAIT_TIMEOUT);
@@ -526,7 +702,76 @@ dh_status launch_cols_typed(const Plan &p, const float2 *mid, int nf, int slot0,
   return DH_ERR_UNSUPPORTED_SIZE;
 }
 
+// Ring and lag of the persistent schedule, in frames. A column item should find its frame's
+// rows done and a row item its ring slot free, so both distances should span about 1.5
+// rounds of the grid's CTAs, counted in work items (N / FPC per frame and pass): lag =
+// ceil(1.5 grid / items per frame), ring = 2 lag, within the plan's intermediate and the
+// 64 slots of the counters. The plan's choices override both. ring 0: not applicable.
+int fused_ring(const Plan &p, int grid, int items_per_frame) {
+  if (p.render_mode != 0 || p.nx != p.ny || p.lognx < 8 || p.lognx > 12) return 0;
+  // untuned plans use it where it measured faster than chunks (512^2, 1024^2); an explicit
+  // ring or lag (the autotuner's pick) applies it at any square size from 256^2
+  if (p.render_ring == 0 && p.render_lag == 0 && (p.lognx < 9 || p.lognx > 10)) return 0;
+  long long r = p.render_ring;
+  if (r <= 0) r = 2ll * ((3ll * grid + 2ll * items_per_frame - 1) / (2ll * items_per_frame));
+  if (r < 2) r = 2;
+  if (r > kMaxRing) r = kMaxRing;
+  if (r > p.mid_frames) r = p.mid_frames;
+  return r >= 2 ? (int)r : 0;
+}
+int fused_lag(const Plan &p, int ring) {
+  int l = p.render_lag > 0 ? p.render_lag : ring / 2;
+  if (l > ring - 1) l = ring - 1;
+  return l < 1 ? 1 : l;
+}
+
+template <int LOGN, typename OutT>
+dh_status launch_fused_t(Plan &p, const uint16_t *frames, long long fstride, int nf, int slot0,
+                         cudaStream_t s) {
+  using S = Shape<LOGN>;
+  constexpr int FPC = fpc<LOGN>();
+  const size_t row_smem = (size_t)FPC * S::RSTRIDE * sizeof(float2);
+  const size_t tile = (size_t)FPC * S::N * sizeof(float2);
+  const size_t smem = row_smem > tile ? row_smem : tile;
+  auto kern = k_render_fused<LOGN, OutT>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    DH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set = true;
+  }
+  int per_sm = 0;
+  DH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
+  if (per_sm < 1) per_sm = 1;
+  const int items = 2 * nf * (S::N / FPC);
+  int grid = per_sm * p.num_sms;
+  if (grid > items) grid = items;
+  const int ring = fused_ring(p, grid, S::N / FPC);
+  const int lag = fused_lag(p, ring);
+  DH_CUDA_TRY(cudaMemsetAsync(p.d_sync, 0, sizeof(unsigned) * (1 + 2 * ring), s));
+  ProfScope ps(p, K_RENDER_FUSED, s);
+  kern<<<grid, 256, smem, s>>>(frames, fstride, nf, col_tile_log(p.logny), p.d_cx, p.d_cy, p.d_twx, p.d_mid,
+                               ring, lag, static_cast<OutT *>(p.d_H), 2ll * p.max_frames, slot0, p.d_sync,
+                               p.d_status);
+  DH_CUDA_TRY(cudaGetLastError());
+  return DH_OK;
+}
+
+template <typename OutT>
+dh_status launch_fused_typed(Plan &p, const uint16_t *frames, long long fstride, int nf, int slot0,
+                             cudaStream_t s) {
+  switch (p.lognx) {
+    case 8: return launch_fused_t<8, OutT>(p, frames, fstride, nf, slot0, s);
+    case 9: return launch_fused_t<9, OutT>(p, frames, fstride, nf, slot0, s);
+    case 10: return launch_fused_t<10, OutT>(p, frames, fstride, nf, slot0, s);
+    case 11: return launch_fused_t<11, OutT>(p, frames, fstride, nf, slot0, s);
+    case 12: return launch_fused_t<12, OutT>(p, frames, fstride, nf, slot0, s);
+  }
+  return DH_ERR_UNSUPPORTED_SIZE;
+}
+
 }  // namespace
+
+int render_items_per_frame(const Plan &p) { return p.nx >> col_tile_log(p.lognx); }
 
 int twiddle_len(int logn) {
   const int logr = log_radix(logn), R = 1 << logr, L = logn / logr;
@@ -564,6 +809,14 @@ void build_twiddles(int logn, float2 *out) {
 
 dh_status launch_render(Plan &p, const uint16_t *frames, long long frame_stride, int n_frames,
                         int slot0, cudaStream_t s) {
+  // square frames from 256^2: every frame of the call in one persistent launch
+  if (fused_ring(p, 1, 1)) {
+    switch (p.prec) {
+      case DH_PREC_FP32: return launch_fused_typed<float>(p, frames, frame_stride, n_frames, slot0, s);
+      case DH_PREC_FP16: return launch_fused_typed<__half>(p, frames, frame_stride, n_frames, slot0, s);
+      case DH_PREC_BF16: return launch_fused_typed<__nv_bfloat16>(p, frames, frame_stride, n_frames, slot0, s);
+    }
+  }
   // Chunks of mid_frames frames: the row pass fills the L2-sized intermediate, the column
   // pass drains it, back to back on the caller's stream. (Running the column pass of one
   // chunk beside the row pass of the next was measured slower: both passes are issue-bound

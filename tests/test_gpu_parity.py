@@ -223,3 +223,40 @@ def test_eigensolver_reaches_fp64_accuracy(dh, T):
     assert np.linalg.norm(V.conj().T @ V - np.eye(T)) <= 1e-12 * T
     ref = np.linalg.eigvalsh(Ch)[::-1]
     assert np.max(np.abs(lam - ref)) <= 1e-12 * nC
+
+
+# ------------------------------------------------------- persistent render schedule
+@pytest.mark.parametrize("n,F", [(256, 9), (512, 7), (1024, 13), (2048, 5), (4096, 3)])
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+def test_persistent_render_equals_chunked(dh, n, F, prec):
+    """The persistent ring schedule (one launch, rows and columns of consecutive frames
+    interleaved) and the chunked two-launch schedule compute the same transforms: the
+    holograms must be bitwise equal, at every square size it serves, with more frames
+    than the ring holds."""
+    frames = to_gpu(SpeckleStream(SpeckleParams(n, n), seed=n + F).next(F).numpy())
+    out = []
+    # chunks; the persistent ring with an explicit ring and lag (so it runs at every size);
+    # and the automatic choice
+    for sched in ((False, 0, 0), (True, 3, 1), (True, 0, 0)):
+        with dh.Plan(n, n, LAM, Z, PITCH, T=16, precision=prec, max_frames=max(F + 2, 16)) as plan:
+            plan.set_render_schedule(*sched)
+            plan.render_frames(frames, first_slot=2)
+            out.append([plan.debug_hologram(2 + t).cpu() for t in range(F)])
+            assert plan.status() == 0
+    for holo in out[1:]:
+        for a, b in zip(out[0], holo):
+            assert torch.equal(a, b)
+
+
+def test_autotune_keeps_results(dh):
+    """The autotuner only changes the render schedule: the same holograms before and after."""
+    frames = to_gpu(SpeckleStream(SpeckleParams(512, 512), seed=77).next(6).numpy())
+    with dh.Plan(512, 512, LAM, Z, PITCH, T=16, precision="fp16", max_frames=16) as plan:
+        plan.render_frames(frames)
+        before = [plan.debug_hologram(t).cpu() for t in range(6)]
+        pick = plan.autotune(16)
+        assert set(pick) == {"persistent", "ring", "lag"}
+        plan.render_frames(frames)
+        after = [plan.debug_hologram(t).cpu() for t in range(6)]
+    for a, b in zip(before, after):
+        assert torch.equal(a, b)
