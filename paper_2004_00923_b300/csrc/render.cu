@@ -197,10 +197,24 @@ struct Engine {
 };
 
 // FFTs per CTA (256 threads, or one FFT when it needs more threads than that).
+// Threads of a render CTA (FFTs per CTA = kCtaThreads / P, at most 16; one FFT when it needs
+// more threads), and the CTAs per SM the register budget gives each pass.
+#ifndef DH_RENDER_CTA_THREADS
+#define DH_RENDER_CTA_THREADS 256
+#endif
+constexpr int kCtaThreads = DH_RENDER_CTA_THREADS;
 template <int LOGN>
 __host__ __device__ constexpr int fpc() {
-  return Shape<LOGN>::P >= 256 ? 1 : (256 / Shape<LOGN>::P < 16 ? 256 / Shape<LOGN>::P : 16);
+  return Shape<LOGN>::P >= kCtaThreads ? 1
+                                       : (kCtaThreads / Shape<LOGN>::P < 16 ? kCtaThreads / Shape<LOGN>::P : 16);
 }
+template <int LOGN>
+__host__ __device__ constexpr int cta_threads() { return fpc<LOGN>() * Shape<LOGN>::P; }
+// rows: <= 128 registers a thread; columns: <= 80 (3 / 2 of the row residency)
+template <int LOGN>
+__host__ __device__ constexpr int rows_per_sm() { return cta_threads<LOGN>() <= 256 ? 512 / cta_threads<LOGN>() : 1; }
+template <int LOGN>
+__host__ __device__ constexpr int cols_per_sm() { return cta_threads<LOGN>() <= 256 ? 768 / cta_threads<LOGN>() : 1; }
 
 template <typename T> __device__ __forceinline__ T to_store(float x);
 template <> __device__ __forceinline__ float to_store<float>(float x) { return x; }
@@ -208,6 +222,21 @@ template <> __device__ __forceinline__ __half to_store<__half>(float x) { return
 template <> __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(float x) {
   return __float2bfloat16_rn(x);
 }
+// Hologram planes are written once per render and read back by later kernels: store them
+// with the streaming hint so they do not push the intermediate out of L2.
+__device__ __forceinline__ void st_stream(float *p, float v) { __stcs(p, v); }
+__device__ __forceinline__ void st_stream(__half *p, __half v) {
+  asm volatile("st.global.cs.b16 [%0], %1;" ::"l"(p), "h"(__half_as_ushort(v)) : "memory");
+}
+__device__ __forceinline__ void st_stream(__nv_bfloat16 *p, __nv_bfloat16 v) {
+  asm volatile("st.global.cs.b16 [%0], %1;" ::"l"(p), "h"(__bfloat16_as_ushort(v)) : "memory");
+}
+// Drop a 128-byte line of the intermediate from L2 without writing it back (its data is
+// dead once the column pass has copied its tile).
+__device__ __forceinline__ void l2_discard(const void *p) {
+  asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
 template <typename T> __device__ __forceinline__ bool stored_finite(T h);
 template <> __device__ __forceinline__ bool stored_finite<float>(float h) { return isfinite(h); }
 template <> __device__ __forceinline__ bool stored_finite<__half>(__half h) {
@@ -253,7 +282,7 @@ __device__ __forceinline__ void row_prefetch(uint4 (&pf)[RowCfg<LOGN>::CPT], con
   using C = RowCfg<LOGN>;
   const uint4 *src = reinterpret_cast<const uint4 *>(frame + (long long)y0 * Shape<LOGN>::N);
 #pragma unroll
-  for (int k = 0; k < C::CPT; ++k) pf[k] = __ldg(src + threadIdx.x + k * C::NT);
+  for (int k = 0; k < C::CPT; ++k) pf[k] = __ldcs(src + threadIdx.x + k * C::NT);  // read once
 }
 
 template <int LOGN, typename Parked>
@@ -339,6 +368,10 @@ __device__ __forceinline__ bool col_work(const float2 *__restrict__ src, float2 
   if (threadIdx.x == 0 && copy_ok && !*abort_flag) landed();
   __syncthreads();
   if (*abort_flag) return false;
+  // the tile is in shared memory: its lines of the intermediate need no write-back (the
+  // next writer of this part of the intermediate overwrites it whole)
+  for (int off = threadIdx.x * 128; off < TILE_BYTES; off += blockDim.x * 128)
+    l2_discard(reinterpret_cast<const char *>(src) + off);
   float2 v[S::R];
   if constexpr (S::P % 16 == 0) {  // y = j + r P keeps the swizzle of j
     const float2 *col = smem + j * FPC + (fft ^ mid_swz(j, CW_LOG));
@@ -361,8 +394,8 @@ __device__ __forceinline__ bool col_work(const float2 *__restrict__ src, float2 
     for (int i = 0; i < S::R; ++i) {
       const float2 o = v[E::out_reg(i)];
       finite &= isfinite(o.x) & isfinite(o.y);
-      re[j + i * S::P] = o.x;
-      im[j + i * S::P] = o.y;
+      st_stream(re + j + i * S::P, o.x);
+      st_stream(im + j + i * S::P, o.y);
     }
   } else {  // 16-bit planes in 64-pixel blocks: [p / 64][row = 2 slot + c][p % 64]
     const long long pix0 = (long long)kx * S::N;  // a multiple of 64 when n_y >= 64
@@ -381,8 +414,8 @@ __device__ __forceinline__ bool col_work(const float2 *__restrict__ src, float2 
         const long long pix = pix0 + j + i * S::P;
         q = base + (pix >> 6) * bstride + (pix & 63);
       }
-      q[0] = a;
-      q[64] = b;
+      st_stream(q, a);
+      st_stream(q + 64, b);
     }
   }
   __syncthreads();  // all transforms are done with the buffer before the next copy lands
@@ -391,7 +424,7 @@ __device__ __forceinline__ bool col_work(const float2 *__restrict__ src, float2 
 
 // Row pass over a chunk of frames: one item = FPC consecutive rows of one frame.
 template <int LOGN>
-__global__ void __launch_bounds__(fpc<LOGN>() * Shape<LOGN>::P, (fpc<LOGN>() * Shape<LOGN>::P <= 256 ? 2 : 1))
+__global__ void __launch_bounds__(cta_threads<LOGN>(), rows_per_sm<LOGN>())
 k_render_rows(const uint16_t *__restrict__ frames, long long frame_stride, int ny, int cw_log,
               const float2 *__restrict__ cx, const float2 *__restrict__ cy,
               const float2 *__restrict__ tw, float2 *__restrict__ mid, int n_items) {
@@ -415,7 +448,7 @@ k_render_rows(const uint16_t *__restrict__ frames, long long frame_stride, int n
 // written to hologram slot slot0 + f. A bulk copy that does not complete within the wait
 // budget raises DH_FLAG_WAIT_TIMEOUT and the CTA stops.
 template <int LOGN, typename OutT>
-__global__ void __launch_bounds__(fpc<LOGN>() * Shape<LOGN>::P, (fpc<LOGN>() * Shape<LOGN>::P <= 256 ? 3 : 1))
+__global__ void __launch_bounds__(cta_threads<LOGN>(), cols_per_sm<LOGN>())
 k_render_cols(const float2 *__restrict__ mid, int nx, const float2 *__restrict__ tw,
               OutT *__restrict__ H, long long npix, long long rows_total, int slot0, int n_items,
               uint32_t *__restrict__ status) {
@@ -485,7 +518,7 @@ __device__ __forceinline__ bool wait_geq(const unsigned *p, unsigned target) {
 }
 
 template <int LOGN, typename OutT>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(kCtaThreads, 512 / kCtaThreads)
 k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int n_frames, int cw_log,
                const float2 *__restrict__ cx, const float2 *__restrict__ cy, const float2 *__restrict__ tw,
                float2 *__restrict__ mid, int ring, int lag, OutT *__restrict__ H, long long rows_total,
@@ -496,7 +529,7 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
   constexpr int N = S::N;
   constexpr int NI = N / FPC;       // row items = column items per frame
   constexpr long long NPIX = (long long)N * N;
-  static_assert(RC::NT == 256, "fused render needs 256-thread items");
+  static_assert(RC::NT == kCtaThreads, "fused render needs full-size items on both axes");
   extern __shared__ float2 smem[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int abort_flag;
@@ -547,10 +580,7 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
         row_work<LOGN>(pf, smem, i * FPC, N, cw_log, cx, cy, tw, ring_f, prefetch_next);
         fence_proxy_async_global();  // this thread's ring writes, for later bulk copies
         __syncthreads();
-        if (threadIdx.x == 0) {
-          __threadfence();
-          red_release_add(rows_done + rs, 1u);
-        }
+        if (threadIdx.x == 0) red_release_add(rows_done + rs, 1u);  // after the CTA's writes
       } else {
         bool ok = true;
         if (threadIdx.x == 0) {
@@ -702,6 +732,8 @@ dh_status launch_cols_typed(const Plan &p, const float2 *mid, int nf, int slot0,
   return DH_ERR_UNSUPPORTED_SIZE;
 }
 
+int cta_threads_of(int logn);
+
 // Ring and lag of the persistent schedule, in frames. A column item should find its frame's
 // rows done and a row item its ring slot free, so both distances should span about 1.5
 // rounds of the grid's CTAs, counted in work items (N / FPC per frame and pass): lag =
@@ -709,6 +741,7 @@ dh_status launch_cols_typed(const Plan &p, const float2 *mid, int nf, int slot0,
 // 64 slots of the counters. The plan's choices override both. ring 0: not applicable.
 int fused_ring(const Plan &p, int grid, int items_per_frame) {
   if (p.render_mode != 0 || p.nx != p.ny || p.lognx < 8 || p.lognx > 12) return 0;
+  if (cta_threads_of(p.lognx) != kCtaThreads) return 0;
   // untuned plans use it where it measured faster than chunks (512^2, 1024^2); an explicit
   // ring or lag (the autotuner's pick) applies it at any square size from 256^2
   if (p.render_ring == 0 && p.render_lag == 0 && (p.lognx < 9 || p.lognx > 10)) return 0;
@@ -728,6 +761,9 @@ int fused_lag(const Plan &p, int ring) {
 template <int LOGN, typename OutT>
 dh_status launch_fused_t(Plan &p, const uint16_t *frames, long long fstride, int nf, int slot0,
                          cudaStream_t s) {
+  if constexpr (cta_threads<LOGN>() != kCtaThreads) {
+    return DH_ERR_UNSUPPORTED_SIZE;  // an item of this length needs more threads
+  } else {
   using S = Shape<LOGN>;
   constexpr int FPC = fpc<LOGN>();
   const size_t row_smem = (size_t)FPC * S::RSTRIDE * sizeof(float2);
@@ -740,7 +776,7 @@ dh_status launch_fused_t(Plan &p, const uint16_t *frames, long long fstride, int
     attr_set = true;
   }
   int per_sm = 0;
-  DH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
+  DH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCtaThreads, smem));
   if (per_sm < 1) per_sm = 1;
   const int items = 2 * nf * (S::N / FPC);
   int grid = per_sm * p.num_sms;
@@ -749,11 +785,20 @@ dh_status launch_fused_t(Plan &p, const uint16_t *frames, long long fstride, int
   const int lag = fused_lag(p, ring);
   DH_CUDA_TRY(cudaMemsetAsync(p.d_sync, 0, sizeof(unsigned) * (1 + 2 * ring), s));
   ProfScope ps(p, K_RENDER_FUSED, s);
-  kern<<<grid, 256, smem, s>>>(frames, fstride, nf, col_tile_log(p.logny), p.d_cx, p.d_cy, p.d_twx, p.d_mid,
+  kern<<<grid, kCtaThreads, smem, s>>>(frames, fstride, nf, col_tile_log(p.logny), p.d_cx, p.d_cy, p.d_twx, p.d_mid,
                                ring, lag, static_cast<OutT *>(p.d_H), 2ll * p.max_frames, slot0, p.d_sync,
                                p.d_status);
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
+  }
+}
+
+int cta_threads_of(int logn) {
+  switch (logn) {
+    case 8: return cta_threads<8>(); case 9: return cta_threads<9>(); case 10: return cta_threads<10>();
+    case 11: return cta_threads<11>(); case 12: return cta_threads<12>();
+  }
+  return 0;
 }
 
 template <typename OutT>
