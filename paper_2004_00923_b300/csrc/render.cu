@@ -63,8 +63,17 @@ constexpr float kSin64[64] = {
 };
 constexpr float kRsqrt2 = 0.7071067811865475244f;
 
+// Threads of a render CTA (FFTs per CTA = kCtaThreads / P, at most 16; one FFT when it
+// needs more threads).
+#ifndef DH_RENDER_CTA_THREADS
+#define DH_RENDER_CTA_THREADS 256
+#endif
+constexpr int kCtaThreads = DH_RENDER_CTA_THREADS;
+#ifndef DH_LOGR_1024
+#define DH_LOGR_1024 5
+#endif
 __host__ __device__ constexpr int log_radix(int logn) {
-  return logn == 6 ? 3 : (logn == 5 || logn == 9 || logn == 10) ? 5 : 4;
+  return logn == 6 ? 3 : logn == 10 ? DH_LOGR_1024 : (logn == 5 || logn == 9) ? 5 : 4;
 }
 
 __host__ __device__ constexpr int bitrev(int k, int bits) {
@@ -144,8 +153,16 @@ __device__ __forceinline__ void dif_each(float2 (&v)[RR]) {
 template <int LOGN, bool CTA_SYNC>
 struct Engine {
   using S = Shape<LOGN>;
+  // exchanges of a transform spread over several warps synchronise only those warps (a
+  // named barrier per transform), unless the transform is the whole CTA
   static __device__ __forceinline__ void sync() {
-    if constexpr (CTA_SYNC) __syncthreads(); else __syncwarp();
+    if constexpr (!CTA_SYNC) {
+      __syncwarp();
+    } else if constexpr (S::P >= kCtaThreads) {
+      __syncthreads();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)threadIdx.x / S::P), "r"(S::P) : "memory");
+    }
   }
   static __device__ __forceinline__ int pad(int i) { return i + (i >> S::LOGR); }
   static __host__ __device__ constexpr int out_reg(int i) {
@@ -197,12 +214,7 @@ struct Engine {
 };
 
 // FFTs per CTA (256 threads, or one FFT when it needs more threads than that).
-// Threads of a render CTA (FFTs per CTA = kCtaThreads / P, at most 16; one FFT when it needs
-// more threads), and the CTAs per SM the register budget gives each pass.
-#ifndef DH_RENDER_CTA_THREADS
-#define DH_RENDER_CTA_THREADS 256
-#endif
-constexpr int kCtaThreads = DH_RENDER_CTA_THREADS;
+// FFTs per CTA, and the CTAs per SM the register budget gives each pass.
 template <int LOGN>
 __host__ __device__ constexpr int fpc() {
   return Shape<LOGN>::P >= kCtaThreads ? 1
@@ -210,11 +222,22 @@ __host__ __device__ constexpr int fpc() {
 }
 template <int LOGN>
 __host__ __device__ constexpr int cta_threads() { return fpc<LOGN>() * Shape<LOGN>::P; }
-// rows: <= 128 registers a thread; columns: <= 80 (3 / 2 of the row residency)
+// CTAs per SM each pass is compiled for: threads counted in whole warps (a CTA of fewer
+// threads still holds a warp's registers), row items with 32 complex values a thread at
+// 2 x 256 threads (<= 128 registers), 16 values at 3 x 256, 8 at 4 x 256; column items
+// (no uint16 prefetch in flight) one step higher. Measured: the radix-16 lengths (2048,
+// 4096, 256) gain 3-8% over 2 x 256, the radix-32 ones (512, 1024) keep 2 x 256.
 template <int LOGN>
-__host__ __device__ constexpr int rows_per_sm() { return cta_threads<LOGN>() <= 256 ? 512 / cta_threads<LOGN>() : 1; }
+__host__ __device__ constexpr int warp_threads() { return cta_threads<LOGN>() < 32 ? 32 : cta_threads<LOGN>(); }
 template <int LOGN>
-__host__ __device__ constexpr int cols_per_sm() { return cta_threads<LOGN>() <= 256 ? 768 / cta_threads<LOGN>() : 1; }
+__host__ __device__ constexpr int rows_per_sm() {
+  return warp_threads<LOGN>() <= 256
+             ? (Shape<LOGN>::R >= 32 ? 512 : Shape<LOGN>::R >= 16 ? 768 : 1024) / warp_threads<LOGN>() : 1;
+}
+template <int LOGN>
+__host__ __device__ constexpr int cols_per_sm() {
+  return warp_threads<LOGN>() <= 256 ? (Shape<LOGN>::R >= 32 ? 768 : 1024) / warp_threads<LOGN>() : 1;
+}
 
 template <typename T> __device__ __forceinline__ T to_store(float x);
 template <> __device__ __forceinline__ float to_store<float>(float x) { return x; }
@@ -518,7 +541,7 @@ __device__ __forceinline__ bool wait_geq(const unsigned *p, unsigned target) {
 }
 
 template <int LOGN, typename OutT>
-__global__ void __launch_bounds__(kCtaThreads, 512 / kCtaThreads)
+__global__ void __launch_bounds__(kCtaThreads, rows_per_sm<LOGN>())
 k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int n_frames, int cw_log,
                const float2 *__restrict__ cx, const float2 *__restrict__ cy, const float2 *__restrict__ tw,
                float2 *__restrict__ mid, int ring, int lag, OutT *__restrict__ H, long long rows_total,
