@@ -210,6 +210,21 @@ dh_status dh_normalize_images(const float *images_dev, int n_images, int64_t npi
                               float *normalized_dev, uint8_t *display_dev, float display_gain,
                               double *means_dev, void *stream);
 
+/* dh_pca_batch from HOST memory, overlapping the transfers with the computation: frames
+ * (uint16, frame i at frames_host + i * frame_stride_elems) are copied to the device in
+ * groups of windows (up to 256 frames a group) on a copy stream, into two alternating
+ * staging buffers, while the caller's stream renders and demodulates the previous group; the
+ * images (n_windows x n_x n_y FP32) and, if eigvals_host is not NULL, the eigenvalues
+ * (n_windows x T FP64) of each group are copied back on a second copy stream as soon as the
+ * group is done. Use pinned host memory for the copies to overlap (pageable memory works,
+ * with synchronous copies). The host buffers must stay valid until `stream` has passed this
+ * call; `stream` is ordered after every copy. The staging buffers and the device images are
+ * allocated on first use (synchronously) and kept by the plan. Asynchronous otherwise.
+ * The paper's pipeline streams camera frames through a host buffer in the same way. */
+dh_status dh_pca_batch_host(dh_plan_t plan, const uint16_t *frames_host, int64_t frame_stride_elems,
+                            int n_windows, int window_stride_frames, int k0, int k1,
+                            float *images_host, double *eigvals_host, void *stream);
+
 /* Inspection (tests): copy hologram slot `slot` as interleaved FP32 (re, im) pairs,
  * n_x n_y of them, to out_dev. Asynchronous. */
 dh_status dh_debug_hologram(dh_plan_t plan, int slot, float *out_dev, void *stream);

@@ -210,6 +210,29 @@ class Plan:
             _stream_ptr(stream)))
         return images, eigvals
 
+    def pca_batch_host(self, frames_host: torch.Tensor, n_windows: int, window_stride: int,
+                       k0: int, k1: int, images_host: torch.Tensor | None = None,
+                       eigvals_host: torch.Tensor | None = None, want_eigvals: bool = True,
+                       stream=None, sync: bool = True):
+        """dh_pca_batch_host: frames in host memory (pinned to overlap the copies), images and
+        eigenvalues back in host memory; with sync=True the stream is synchronised."""
+        f = frames_host
+        if f.dtype != torch.uint16 or f.is_cuda or f.dim() != 3 or f.shape[1:] != (self.ny, self.nx) \
+                or not f.is_contiguous():
+            raise TypeError(f"frames must be a contiguous host uint16 tensor [F, {self.ny}, {self.nx}]")
+        pin = f.is_pinned()
+        if images_host is None:
+            images_host = torch.empty((n_windows, self.ny, self.nx), dtype=torch.float32, pin_memory=pin)
+        if eigvals_host is None and want_eigvals:
+            eigvals_host = torch.empty((n_windows, self.T), dtype=torch.float64, pin_memory=pin)
+        _lib.check("dh_pca_batch_host", self._lib.dh_pca_batch_host(
+            self._h, _ptr(f), self.nx * self.ny, int(n_windows), int(window_stride), int(k0),
+            int(k1), _ptr(images_host), _ptr(eigvals_host) if eigvals_host is not None else None,
+            _stream_ptr(stream)))
+        if sync:
+            (stream or torch.cuda.current_stream()).synchronize()
+        return images_host, eigvals_host
+
     # -- inspection -----------------------------------------------------------
     def debug_hologram(self, slot: int, stream=None) -> torch.Tensor:
         out = torch.empty((self.ny, self.nx, 2), dtype=torch.float32, device="cuda")

@@ -57,6 +57,7 @@ SIGNATURES = [
     ("dh_render_stack", _i, [_vp, _vp, _i64, _vp]),
     ("dh_pca_window", _i, [_vp, _i, _i, _vp, _vp, _vp]),
     ("dh_pca_batch", _i, [_vp, _vp, _i64, _i, _i, _i, _i, _vp, _vp, _vp]),
+    ("dh_pca_batch_host", _i, [_vp, _vp, _i64, _i, _i, _i, _i, _vp, _vp, _vp]),
     ("dh_normalize_images", _i, [_vp, _i, _i64, _vp, _vp, ctypes.c_float, _vp, _vp]),
     ("dh_debug_hologram", _i, [_vp, _i, _vp, _vp]),
     ("dh_debug_covariance", _i, [_vp, _i, _vp, _vp]),

@@ -145,7 +145,10 @@ dh_status alloc_windows(Plan &p) {
 dh_status alloc_store(Plan &p, const Plan *base = nullptr) {
   free_store(p);
   const StoreSizes z = store_sizes(p);
-  p.bytes = p.is_view ? 0 : z.tables;
+  // the host-buffer pipeline's buffers (kept across reservations) stay counted
+  const size_t pipe = 2 * p.pipe.stage_elems * sizeof(uint16_t) + p.pipe.img_elems * sizeof(float) +
+                      p.pipe.eig_elems * sizeof(double);
+  p.bytes = (p.is_view ? 0 : z.tables) + pipe;
   p.H_elem_bytes = p.prec == DH_PREC_FP32 ? 4 : 2;
   dh_status st;
   if (p.is_view) {
@@ -374,6 +377,12 @@ void release(dh_plan_t h) {
     if (p.ev_jac[k]) cudaEventDestroy(p.ev_jac[k]);
   }
   if (p.aux) cudaStreamDestroy(p.aux);
+  Plan::HostPipe &q = p.pipe;
+  if (q.up) cudaStreamDestroy(q.up);
+  if (q.down) cudaStreamDestroy(q.down);
+  for (cudaEvent_t ev : {q.start, q.done, q.finished, q.copied[0], q.copied[1], q.freed[0], q.freed[1]})
+    if (ev) cudaEventDestroy(ev);
+  dfree(q.stage[0]); dfree(q.stage[1]); dfree(q.img); dfree(q.eig);
   dfree(p.d_cx); dfree(p.d_cy); dfree(p.d_twx); dfree(p.d_twy); dfree(p.d_status); dfree(p.d_sync);
   dh_plan *base = h->base;
   delete h;
@@ -654,6 +663,95 @@ dh_status dh_pca_batch(dh_plan_t h, const uint16_t *frames_dev, int64_t frame_st
   if (!g.ok) return DH_ERR_STATE;
   return pca_impl(p, frames_dev, frame_stride_elems, 0, window_stride_frames, n_windows, k0, k1,
                   images_dev, eigvals_dev, static_cast<cudaStream_t>(stream));
+}
+
+dh_status dh_pca_batch_host(dh_plan_t h, const uint16_t *frames_host, int64_t frame_stride_elems,
+                            int n_windows, int window_stride_frames, int k0, int k1, float *images_host,
+                            double *eigvals_host, void *stream) {
+  if (!h || !frames_host || !images_host || n_windows < 1 || window_stride_frames < 1) return DH_ERR_INVALID_ARG;
+  Plan &p = h->p;
+  if (p.is_view) return DH_ERR_STATE;
+  if (k0 < 0 || k1 < k0 || k1 >= p.T) return DH_ERR_INVALID_ARG;
+  const int ws = window_stride_frames, T = p.T;
+  const long long nf_all = (long long)(n_windows - 1) * ws + T;
+  if (nf_all > p.max_frames || n_windows > p.max_windows || frame_stride_elems < p.npix ||
+      (frame_stride_elems & 7) != 0)
+    return DH_ERR_INVALID_ARG;
+  Busy g(h->busy);
+  if (!g.ok) return DH_ERR_STATE;
+  // groups of windows whose new frames fit a 256-frame staging buffer (one window per group
+  // when windows are further apart than T: only its own frames are copied)
+  const int cap = T > 256 ? T : 256;
+  const int G = ws > T ? 1 : (cap - T) / ws + 1;
+  Plan::HostPipe &q = p.pipe;
+  const size_t stage_elems = (size_t)cap * frame_stride_elems;
+  const size_t img_elems = (size_t)p.max_windows * p.npix, eig_elems = (size_t)p.max_windows * T;
+  if (!q.up) {
+    DH_CUDA_TRY(cudaStreamCreateWithFlags(&q.up, cudaStreamNonBlocking));
+    DH_CUDA_TRY(cudaStreamCreateWithFlags(&q.down, cudaStreamNonBlocking));
+    for (cudaEvent_t *ev : {&q.start, &q.done, &q.finished, &q.copied[0], &q.copied[1], &q.freed[0], &q.freed[1]})
+      DH_CUDA_TRY(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+  }
+  if (q.stage_elems < stage_elems) {
+    DH_CUDA_TRY(cudaDeviceSynchronize());
+    dfree(q.stage[0]); dfree(q.stage[1]);
+    p.bytes -= 2 * q.stage_elems * sizeof(uint16_t);
+    q.stage_elems = 0;
+    dh_status st;
+    if ((st = dalloc(p, &q.stage[0], stage_elems * sizeof(uint16_t))) != DH_OK) return st;
+    if ((st = dalloc(p, &q.stage[1], stage_elems * sizeof(uint16_t))) != DH_OK) return st;
+    q.stage_elems = stage_elems;
+  }
+  if (q.img_elems < img_elems || q.eig_elems < eig_elems) {
+    DH_CUDA_TRY(cudaDeviceSynchronize());
+    dfree(q.img); dfree(q.eig);
+    p.bytes -= q.img_elems * sizeof(float) + q.eig_elems * sizeof(double);
+    q.img_elems = q.eig_elems = 0;
+    dh_status st;
+    if ((st = dalloc(p, &q.img, img_elems * sizeof(float))) != DH_OK) return st;
+    if ((st = dalloc(p, &q.eig, eig_elems * sizeof(double))) != DH_OK) return st;
+    q.img_elems = img_elems; q.eig_elems = eig_elems;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DH_CUDA_TRY(cudaEventRecord(q.start, s));  // copies follow earlier work on the caller's stream
+  DH_CUDA_TRY(cudaStreamWaitEvent(q.up, q.start, 0));
+  DH_CUDA_TRY(cudaStreamWaitEvent(q.down, q.start, 0));
+  long long rendered = 0;  // frames 0 .. rendered-1 are in their slots (ws <= T)
+  for (int w0 = 0, grp = 0; w0 < n_windows; w0 += G, ++grp) {
+    const int nw = n_windows - w0 < G ? n_windows - w0 : G;
+    long long f0, nf;
+    if (ws > T) {
+      f0 = (long long)w0 * ws;
+      nf = T;
+    } else {
+      f0 = rendered;
+      nf = (long long)(w0 + nw - 1) * ws + T - rendered;
+      rendered += nf;
+    }
+    const int b = grp & 1;
+    if (grp >= 2) DH_CUDA_TRY(cudaStreamWaitEvent(q.up, q.freed[b], 0));  // group grp-2 rendered
+    DH_CUDA_TRY(cudaMemcpyAsync(q.stage[b], frames_host + f0 * frame_stride_elems,
+                                (size_t)nf * frame_stride_elems * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                                q.up));
+    DH_CUDA_TRY(cudaEventRecord(q.copied[b], q.up));
+    DH_CUDA_TRY(cudaStreamWaitEvent(s, q.copied[b], 0));
+    dh_status st = launch_render(p, q.stage[b], frame_stride_elems, (int)nf, (int)f0, s);
+    if (st != DH_OK) return st;
+    DH_CUDA_TRY(cudaEventRecord(q.freed[b], s));
+    st = pca_impl(p, nullptr, 0, w0 * ws, ws, nw, k0, k1, q.img + (size_t)w0 * p.npix,
+                  eigvals_host ? q.eig + (size_t)w0 * T : nullptr, s);
+    if (st != DH_OK) return st;
+    DH_CUDA_TRY(cudaEventRecord(q.done, s));
+    DH_CUDA_TRY(cudaStreamWaitEvent(q.down, q.done, 0));
+    DH_CUDA_TRY(cudaMemcpyAsync(images_host + (size_t)w0 * p.npix, q.img + (size_t)w0 * p.npix,
+                                (size_t)nw * p.npix * sizeof(float), cudaMemcpyDeviceToHost, q.down));
+    if (eigvals_host)
+      DH_CUDA_TRY(cudaMemcpyAsync(eigvals_host + (size_t)w0 * T, q.eig + (size_t)w0 * T,
+                                  (size_t)nw * T * sizeof(double), cudaMemcpyDeviceToHost, q.down));
+  }
+  DH_CUDA_TRY(cudaEventRecord(q.finished, q.down));
+  DH_CUDA_TRY(cudaStreamWaitEvent(s, q.finished, 0));  // the caller's stream ends with the results
+  return DH_OK;
 }
 
 dh_status dh_debug_hologram(dh_plan_t h, int slot, float *out_dev, void *stream) {

@@ -63,6 +63,18 @@ struct Plan {
   CUtensorMap tmap_B;
   bool tmaps_ok = false;
 
+  // host-buffer pipeline (dh_pca_batch_host), created on first use: copy streams, two
+  // staging buffers of frames, device images / eigenvalues of the batch
+  struct HostPipe {
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr, finished = nullptr;
+    cudaEvent_t copied[2] = {}, freed[2] = {};
+    uint16_t *stage[2] = {};
+    size_t stage_elems = 0;
+    float *img = nullptr;
+    double *eig = nullptr;
+    size_t img_elems = 0, eig_elems = 0;
+  } pipe;
   size_t bytes = 0;         // device bytes the plan itself allocated
   size_t window_bytes = 0;  // the part of `bytes` in per-window buffers
   int busy = 0;

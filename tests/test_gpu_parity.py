@@ -260,3 +260,21 @@ def test_autotune_keeps_results(dh):
         after = [plan.debug_hologram(t).cpu() for t in range(6)]
     for a, b in zip(before, after):
         assert torch.equal(a, b)
+
+
+# ------------------------------------------------------- host buffers, overlapped copies
+@pytest.mark.parametrize("T,ws,n", [(16, 16, 40), (16, 8, 50), (16, 40, 7), (32, 32, 9)])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_batch_from_host_buffers_equals_device_batch(dh, T, ws, n, pinned):
+    """dh_pca_batch_host (groups of windows copied in while earlier groups compute) gives
+    bitwise the device-buffer batch's images and eigenvalues, for windows apart by T, by
+    less (overlapping) and by more (gaps), from pinned and from pageable memory."""
+    F = (n - 1) * ws + T
+    frames = SpeckleStream(SpeckleParams(128, 64), seed=T + ws + n).next(F)
+    host = frames.pin_memory() if pinned else frames.clone()
+    with dh.Plan(128, 64, LAM, Z, PITCH, T=T, precision="fp16", max_frames=F, max_windows=n) as plan:
+        img_d, lam_d = plan.pca_batch(frames.cuda(), n, ws, 2, T - 1)
+        img_d, lam_d = img_d.cpu(), lam_d.cpu()
+        img_h, lam_h = plan.pca_batch_host(host, n, ws, 2, T - 1)
+        assert plan.status() == 0
+    assert torch.equal(img_h, img_d) and torch.equal(lam_h, lam_d)
