@@ -154,6 +154,7 @@ def algorithmic_bytes(npix, frames, windows, T, hbytes):
         "render_cols": frames * npix * 2 * hbytes,           # Re/Im planes out
         "render_fused": frames * npix * (2 + 2 * hbytes),    # both, one persistent launch
         "gram_tc": windows * T * npix * 2 * hbytes,          # H read once per window
+        "gram_raw": windows * T * npix * 2,                  # uint16 frames read once per window
         "gram_simt": windows * T * npix * 2 * hbytes,
         "project_tc": windows * (T * npix * 2 * hbytes + npix * 4),  # H read + image out
         "project_simt": windows * (T * npix * 2 * hbytes + npix * 4),
@@ -208,6 +209,7 @@ def run_ours(args, ws, rank, local):
 
     plan = dh.Plan(NX, NY, LAM, Z, PITCH, T=T, precision=args.precision, max_frames=nframes,
                    max_windows=nwin)
+    plan.set_covariance_source(args.covariance == "raw")
     if args.render_schedule == "auto":
         tuned = plan.autotune(256)  # setup, outside the timed region
     else:
@@ -334,7 +336,7 @@ def run_ours(args, ws, rank, local):
                        "windows_per_step": nwin, "frames_per_step": nframes, "k0": K0, "k1": K1,
                        "precision": args.precision,
                        "l2": "no flush: 4 GiB of input frames per step exceed the 126 MB L2",
-                       "render_schedule": tuned,
+                       "render_schedule": tuned, "covariance": args.covariance,
                        "parallelism": f"replicas x{ws}"},
             "frames_per_s": value * T,
             "step_ms": {"p50": statistics.median(step_ms), "max": max(step_ms)},
@@ -979,6 +981,9 @@ def main(argv=None):
     ap.add_argument("--render-schedule", choices=["auto", "persistent", "chunks"], default="auto",
                     help="Eq. 1 schedule of the headline plan: auto = the library's autotuner "
                          "(dh_plan_autotune); else DH_OPT_RENDER_SCHEDULE with ring and lag")
+    ap.add_argument("--covariance", choices=["holograms", "raw"], default="holograms",
+                    help="Eq. 4 from the holograms (as written, default) or exactly from the uint16 "
+                         "frames (DH_OPT_COVARIANCE = 1, C = I^T I)")
     ap.add_argument("--render-ring", type=int, default=0, help="DH_OPT_RENDER_RING (0 = automatic)")
     ap.add_argument("--render-lag", type=int, default=0, help="DH_OPT_RENDER_LAG (0 = automatic)")
     ap.add_argument("--serve-seconds", type=float, default=60.0,

@@ -117,6 +117,15 @@ dh_status dh_plan_reserve(dh_plan_t plan, int max_frames, int max_windows);
  *   makes it about 1.5 rounds of the grid's CTAs in work items). */
 #define DH_OPT_RENDER_RING 1
 #define DH_OPT_RENDER_LAG 2
+/* DH_OPT_COVARIANCE: 0 (default): C = H^{t*} H from the holograms, as Eq. 4 is written.
+ *   1: wherever the call has the uint16 frames at hand (dh_pca_batch; dh_pca_batch_host when
+ *   windows are T or more frames apart), C = I^T I from the frames themselves -- equal in
+ *   exact arithmetic because the Fresnel transform of Eq. 1 is unitary per frame -- computed
+ *   exactly on the tensor cores (each value split into two bytes, integer accumulation):
+ *   half the bytes read and no storage rounding in C (exact while sum I^2 < 2^53). 16-bit
+ *   hologram storage only (DH_ERR_STATE for FP32 plans). Holograms are still rendered for
+ *   the projection of Eqs. 6-7. */
+#define DH_OPT_COVARIANCE 3
 dh_status dh_plan_set_option(dh_plan_t plan, int option, int value);
 dh_status dh_plan_get_option(dh_plan_t plan, int option, int *value);
 

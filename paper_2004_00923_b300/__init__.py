@@ -101,6 +101,11 @@ class Plan:
         for opt, val in ((0, 0 if persistent else 1), (1, int(ring)), (2, int(lag))):
             _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(self._h, opt, val))
 
+    def set_covariance_source(self, raw: bool) -> None:
+        """DH_OPT_COVARIANCE: C from the uint16 frames (exact, C = I^T I) where the call has
+        them, or from the holograms (Eq. 4 as written, the default)."""
+        _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(self._h, 3, 1 if raw else 0))
+
     def render_schedule(self) -> dict:
         """The plan's render options: persistent (bool), ring and lag (0 = automatic)."""
         v = ctypes.c_int(0)

@@ -182,10 +182,13 @@ std::vector<float2> chirp_table(int n, double a) {
 // eigensolver of one group beside the next group's rendering was measured slower (both
 // slowed down on the shared SMs).
 // With b0 >= 0 the operand of Eq. 6 is replaced, per window, by the SVD-filter + DFT operand
-// of Eqs. 2-3 and 8-9 (components k0..k1 kept, bins b0..b1).
+// of Eqs. 2-3 and 8-9 (components k0..k1 kept, bins b0..b1). With `raw` (uint16 frames,
+// window w's first frame at raw + w * slot_stride * raw_stride) and the plan's raw-domain
+// option, the covariance is formed from those frames (C = I^T I) instead of the holograms.
 dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int first_slot,
                    int slot_stride, int n_windows, int k0, int k1, float *images, double *eig_user,
-                   cudaStream_t s, int b0 = -1, int b1 = -1) {
+                   cudaStream_t s, int b0 = -1, int b1 = -1, const uint16_t *raw = nullptr,
+                   long long raw_stride = 0) {
   const int G = 1;
   const int nS = b0 >= 0 ? b1 - b0 + 1 : k1 - k0 + 1;  // projected columns
   const int nop = p.prec == DH_PREC_FP32 ? 2 * nS : (2 * nS + 15) / 16 * 16;  // operand rows
@@ -207,10 +210,17 @@ dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int 
     }
     const int fs = first_slot + w0 * slot_stride;
     int parts = 0;
-    st = p.prec == DH_PREC_FP32 ? launch_gram_simt(p, fs, slot_stride, nw, &parts, s)
-                                : launch_gram_tc(p, fs, slot_stride, nw, &parts, s);
-    if (st != DH_OK) return st;
-    if ((st = launch_reduce(p, nw, parts, w0, s)) != DH_OK) return st;
+    if (raw && p.cov_raw) {
+      st = launch_gram_raw(p, raw, raw_stride, (n_windows - 1) * slot_stride + p.T, w0 * slot_stride, slot_stride,
+                           nw, &parts, s);
+      if (st != DH_OK) return st;
+      if ((st = launch_reduce_raw(p, nw, parts, w0, s)) != DH_OK) return st;
+    } else {
+      st = p.prec == DH_PREC_FP32 ? launch_gram_simt(p, fs, slot_stride, nw, &parts, s)
+                                  : launch_gram_tc(p, fs, slot_stride, nw, &parts, s);
+      if (st != DH_OK) return st;
+      if ((st = launch_reduce(p, nw, parts, w0, s)) != DH_OK) return st;
+    }
     DH_CUDA_TRY(cudaEventRecord(p.ev_grp[g], s));
     DH_CUDA_TRY(cudaStreamWaitEvent(p.aux, p.ev_grp[g], 0));
     st = launch_jacobi(p, nw, k0, k1, nop, eig_user ? eig_user + (long long)w0 * p.T : nullptr, w0, p.aux);
@@ -443,6 +453,7 @@ dh_status dh_plan_set_precision(dh_plan_t h, dh_precision prec) {
   if (!g.ok) return DH_ERR_STATE;
   DH_CUDA_TRY(cudaDeviceSynchronize());
   h->p.prec = prec;
+  if (prec == DH_PREC_FP32) h->p.cov_raw = 0;
   return alloc_store(h->p);
 }
 
@@ -473,6 +484,7 @@ dh_status dh_plan_get_option(dh_plan_t h, int option, int *value) {
     case DH_OPT_RENDER_SCHEDULE: *value = h->p.render_mode; return DH_OK;
     case DH_OPT_RENDER_RING: *value = h->p.render_ring; return DH_OK;
     case DH_OPT_RENDER_LAG: *value = h->p.render_lag; return DH_OK;
+    case DH_OPT_COVARIANCE: *value = h->p.cov_raw; return DH_OK;
   }
   return DH_ERR_INVALID_ARG;
 }
@@ -551,6 +563,11 @@ dh_status dh_plan_set_option(dh_plan_t h, int option, int value) {
     case DH_OPT_RENDER_LAG:
       if (value < 0 || value > 63) return DH_ERR_INVALID_ARG;
       h->p.render_lag = value;
+      return DH_OK;
+    case DH_OPT_COVARIANCE:
+      if (value != 0 && value != 1) return DH_ERR_INVALID_ARG;
+      if (value == 1 && h->p.prec == DH_PREC_FP32) return DH_ERR_STATE;  // tensor-core path only
+      h->p.cov_raw = value;
       return DH_OK;
   }
   return DH_ERR_INVALID_ARG;
@@ -662,7 +679,8 @@ dh_status dh_pca_batch(dh_plan_t h, const uint16_t *frames_dev, int64_t frame_st
   Busy g(h->busy);
   if (!g.ok) return DH_ERR_STATE;
   return pca_impl(p, frames_dev, frame_stride_elems, 0, window_stride_frames, n_windows, k0, k1,
-                  images_dev, eigvals_dev, static_cast<cudaStream_t>(stream));
+                  images_dev, eigvals_dev, static_cast<cudaStream_t>(stream), -1, -1, frames_dev,
+                  frame_stride_elems);
 }
 
 dh_status dh_pca_batch_host(dh_plan_t h, const uint16_t *frames_host, int64_t frame_stride_elems,
@@ -737,10 +755,13 @@ dh_status dh_pca_batch_host(dh_plan_t h, const uint16_t *frames_host, int64_t fr
     DH_CUDA_TRY(cudaStreamWaitEvent(s, q.copied[b], 0));
     dh_status st = launch_render(p, q.stage[b], frame_stride_elems, (int)nf, (int)f0, s);
     if (st != DH_OK) return st;
-    DH_CUDA_TRY(cudaEventRecord(q.freed[b], s));
+    // the raw-domain covariance reads the staged frames: only when the group's windows lie
+    // wholly in them (windows T or more frames apart)
     st = pca_impl(p, nullptr, 0, w0 * ws, ws, nw, k0, k1, q.img + (size_t)w0 * p.npix,
-                  eigvals_host ? q.eig + (size_t)w0 * T : nullptr, s);
+                  eigvals_host ? q.eig + (size_t)w0 * T : nullptr, s, -1, -1,
+                  ws >= T ? q.stage[b] : nullptr, frame_stride_elems);
     if (st != DH_OK) return st;
+    DH_CUDA_TRY(cudaEventRecord(q.freed[b], s));
     DH_CUDA_TRY(cudaEventRecord(q.done, s));
     DH_CUDA_TRY(cudaStreamWaitEvent(q.down, q.done, 0));
     DH_CUDA_TRY(cudaMemcpyAsync(images_host + (size_t)w0 * p.npix, q.img + (size_t)w0 * p.npix,

@@ -39,6 +39,7 @@ struct Plan {
   // applies (square frames from 256^2), else chunks; 1 = always chunks of two launches
   int render_mode = 0;
   int render_ring = 0, render_lag = 0;  // persistent schedule: ring frames, lag (0 = automatic)
+  int cov_raw = 0;  // 1: covariance from the uint16 frames (C = I^T I) where the frames are at hand
   unsigned *d_sync = nullptr;  // ticket and ring counters of the persistent render
   // second stream: the eigensolver of one group of windows overlaps the next group's work
   cudaStream_t aux = nullptr;
@@ -84,7 +85,8 @@ struct Plan {
 // ---------------------------------------------------------------- tracing
 enum KernelId {
   K_RENDER_ROWS = 0, K_RENDER_COLS, K_GRAM_SIMT, K_GRAM_TC, K_REDUCE_COV, K_JACOBI,
-  K_PROJECT_SIMT, K_PROJECT_TC, K_FOURIER_OP, K_SVD_FOURIER_OP, K_RENDER_FUSED, K_COUNT
+  K_PROJECT_SIMT, K_PROJECT_TC, K_FOURIER_OP, K_SVD_FOURIER_OP, K_RENDER_FUSED, K_GRAM_RAW,
+  K_REDUCE_RAW, K_COUNT
 };
 const char *kernel_name(int kid);
 dh_status profile_enable(Plan &p, int on);
@@ -122,8 +124,12 @@ int twiddle_len(int logn);
 // Partial Gram matrices per window (split-K over pixels), fixed per frame size.
 int gram_units(long long npix);
 int gram_tc_parts(const Plan &p);
+int gram_raw_parts(const Plan &p);
+// partial Gram matrices a window may need (hologram or raw-domain covariance)
 inline int parts_per_window(const Plan &p) {
-  return p.prec == DH_PREC_FP32 ? gram_units(p.npix) : gram_tc_parts(p);
+  const int h = p.prec == DH_PREC_FP32 ? gram_units(p.npix) : gram_tc_parts(p);
+  const int r = gram_raw_parts(p);
+  return h > r ? h : r;
 }
 // Eq. 4, FP32 CUDA cores: partial real Gram matrices of X = [Re H_t ; Im H_t] rows.
 dh_status launch_gram_simt(Plan &p, int first_slot, int slot_stride, int n_windows,
@@ -131,6 +137,13 @@ dh_status launch_gram_simt(Plan &p, int first_slot, int slot_stride, int n_windo
 // Eq. 4, tensor cores (16-bit storage).
 dh_status launch_gram_tc(Plan &p, int first_slot, int slot_stride, int n_windows,
                          int *parts_per_window, cudaStream_t s);
+// Eq. 4 from the uint16 frames (C = I^T I, exact): partial Gram matrices of the hi / lo byte
+// rows of windows [first_frame + w * window_stride, + T) of `frames` (n_frames frames,
+// frame_stride elements apart), then their FP64 reduction into C.
+dh_status launch_gram_raw(Plan &p, const uint16_t *frames, long long frame_stride, int n_frames,
+                          int first_frame, int window_stride, int n_windows, int *parts_per_window,
+                          cudaStream_t s);
+dh_status launch_reduce_raw(Plan &p, int n_windows, int parts_per_window, int woff, cudaStream_t s);
 // Eq. 4 final FP64 reduction, then Eq. 5 + ordering + operand build for Eq. 6, for windows
 // [woff, woff + n_windows) of the plan's per-window buffers.
 dh_status launch_reduce(Plan &p, int n_windows, int parts_per_window, int woff, cudaStream_t s);

@@ -36,6 +36,31 @@ k_reduce_cov(const double *__restrict__ part, int parts, int n_windows, double *
   if (!isfinite(re) || !isfinite(im)) atomicOr(status, DH_FLAG_NONFINITE_C);
 }
 
+// Raw-domain covariance: rows 2t / 2t+1 of the partial Gram matrices are the high / low bytes
+// of frame t, so C[t][u] = sum over partials of 65536 G[2t][2u] + 256 (G[2t][2u+1] +
+// G[2t+1][2u]) + G[2t+1][2u+1], all integers (exact in FP64 while below 2^53); Im C = 0.
+template <int T>
+__global__ void __launch_bounds__(256)
+k_reduce_raw(const double *__restrict__ part, int parts, int n_windows, double *__restrict__ C,
+             uint32_t *__restrict__ status) {
+  constexpr int M = 2 * T;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_windows * T * T) return;
+  const int w = idx / (T * T), e = idx % (T * T), t = e / T, u = e % T;
+  const double *P = part + (long long)w * parts * M * M;
+  double hh = 0.0, cross = 0.0, ll = 0.0;
+  for (int q = 0; q < parts; ++q) {
+    const double *G = P + (long long)q * M * M;
+    hh += G[(2 * t) * M + 2 * u];
+    cross += G[(2 * t) * M + 2 * u + 1] + G[(2 * t + 1) * M + 2 * u];
+    ll += G[(2 * t + 1) * M + 2 * u + 1];
+  }
+  const double c = 65536.0 * hh + 256.0 * cross + ll;
+  C[2 * ((long long)w * T * T + e)] = c;
+  C[2 * ((long long)w * T * T + e) + 1] = 0.0;
+  if (!isfinite(c)) atomicOr(status, DH_FLAG_NONFINITE_C);
+}
+
 __device__ __forceinline__ double block_sum(double v, double *red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -368,6 +393,22 @@ dh_status launch_reduce_cov_window(const double *part, int parts, int T, double 
     case 16: k_reduce_cov<16><<<blocks, 256, 0, s>>>(part, parts, 1, C, status); break;
     case 32: k_reduce_cov<32><<<blocks, 256, 0, s>>>(part, parts, 1, C, status); break;
     case 64: k_reduce_cov<64><<<blocks, 256, 0, s>>>(part, parts, 1, C, status); break;
+    default: return DH_ERR_UNSUPPORTED_SIZE;
+  }
+  DH_CUDA_TRY(cudaGetLastError());
+  return DH_OK;
+}
+
+dh_status launch_reduce_raw(Plan &p, int n_windows, int parts, int woff, cudaStream_t s) {
+  const int total = n_windows * p.T * p.T;
+  ProfScope ps(p, K_REDUCE_RAW, s);
+  switch (p.T) {
+    case 16: k_reduce_raw<16><<<(total + 255) / 256, 256, 0, s>>>(p.d_part, parts, n_windows,
+                                                                  p.d_C + 2ll * woff * 16 * 16, p.d_status); break;
+    case 32: k_reduce_raw<32><<<(total + 255) / 256, 256, 0, s>>>(p.d_part, parts, n_windows,
+                                                                  p.d_C + 2ll * woff * 32 * 32, p.d_status); break;
+    case 64: k_reduce_raw<64><<<(total + 255) / 256, 256, 0, s>>>(p.d_part, parts, n_windows,
+                                                                  p.d_C + 2ll * woff * 64 * 64, p.d_status); break;
     default: return DH_ERR_UNSUPPORTED_SIZE;
   }
   DH_CUDA_TRY(cudaGetLastError());

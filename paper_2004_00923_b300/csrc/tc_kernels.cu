@@ -226,6 +226,219 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmH, int first_slot, int slot_stri
   }
 }
 
+// ======================================================================= raw-domain covariance
+// The Fresnel transform of Eq. 1 is unitary per frame, so C = H^{t*} H = I^T I exactly: the
+// covariance can be formed from the uint16 frames themselves, exactly, at half the bytes of
+// the 16-bit holograms. Each value is split I = 256 hi + lo (hi, lo < 256, exact in FP16); a
+// converter warpgroup turns each TMA-loaded uint16 tile (T frames x 64 pixels) into the
+// operand rows [hi_0; lo_0; hi_1; lo_1; ...] (2T rows, K-major, 128-byte swizzle: the layout
+// the hologram Gram reads), and the same stacked 128 x 128 MMA forms the 2T x 2T Gram G of
+// those rows. Products are < 2^16 and a stage sums 64 of them per element, so every
+// accumulator value is an exact integer below 2^23; the epilogue adds each drained value to
+// a 32-bit integer sum (through the FP32 mantissa: bits(v + 2^23) = 0x4B000000 + v), which is
+// exact while a unit's sum stays below 2^32 (<= 65536 pixels per unit). The reduction then
+// forms C = 65536 G_hh + 256 (G_hl + G_lh) + G_ll in FP64, exact while sum I^2 < 2^53.
+template <int T>
+struct RawCfg {
+  static constexpr int M2 = 2 * T;
+  static constexpr int R = 128 / M2;               // 64-pixel chunks stacked per stage
+  static constexpr int PIX = 64 * R;               // pixels per stage
+  static constexpr int OP_BYTES = 128 * 128;       // operand stage: 128 rows x 64 pixels, FP16
+  static constexpr int RAW_BYTES = R * T * 128;    // uint16 stage: R boxes of T frames x 64 pixels
+  static constexpr int NCOL = T == 64 ? 64 : 32;
+  static constexpr int EPI_WARPS = 4 * (M2 / NCOL);
+  static constexpr int CONV_THREADS = 128;
+  static constexpr int THREADS = 64 + CONV_THREADS + 32 * EPI_WARPS;
+  static constexpr int CTAS_PER_SM = T == 16 ? 2 : 1;
+  static constexpr int OP_STAGES = CTAS_PER_SM == 2 ? 3 : 6;
+  static constexpr int RAW_STAGES = CTAS_PER_SM == 2 ? 4 : 8;
+  static constexpr int NB = CTAS_PER_SM == 2 ? 2 : 4;
+  static constexpr int TMEM_COLS = 128 * NB;
+  static constexpr size_t SMEM = OP_STAGES * OP_BYTES + RAW_STAGES * RAW_BYTES + 1024 + 512;
+};
+
+// Split-K units per window for the raw-domain covariance: the tensor-core units, more where
+// needed to keep <= 65536 pixels a unit (exact 32-bit sums).
+int gram_raw_units(long long npix) {
+  long long u = gram_tc_units(npix);
+  const long long need = (npix + 65535) / 65536;
+  return (int)(u > need ? u : need);
+}
+
+__device__ __forceinline__ uint32_t byte_pair_to_half2(uint32_t w) {
+  // two bytes in the low byte of each 16-bit lane -> FP16 1024 + b (exact), then - 1024
+  const uint32_t h = w | 0x64006400u;
+  __half2 x = *reinterpret_cast<const __half2 *>(&h);
+  x = __hsub2(x, __half2(__float2half(1024.f), __float2half(1024.f)));
+  return *reinterpret_cast<uint32_t *>(&x);
+}
+
+template <int T>
+__global__ void __launch_bounds__(RawCfg<T>::THREADS, 1)
+k_gram_raw_tc(const __grid_constant__ CUtensorMap tmI, int first_frame, int window_stride, int n_windows,
+              int units_pw, int stages_per_unit, double *__restrict__ part, uint32_t *__restrict__ status) {
+  using C = RawCfg<T>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = align1024(smem_raw);
+  uint8_t *ops = smem;
+  uint8_t *raws = smem + C::OP_STAGES * C::OP_BYTES;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(raws + C::RAW_STAGES * C::RAW_BYTES);
+  uint64_t *raw_full = bars, *raw_empty = raw_full + C::RAW_STAGES;
+  uint64_t *op_full = raw_empty + C::RAW_STAGES, *op_empty = op_full + C::OP_STAGES;
+  uint64_t *acc_full = op_empty + C::OP_STAGES, *acc_empty = acc_full + C::NB;
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(acc_empty + C::NB);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::RAW_STAGES; ++s) { mbar_init(&raw_full[s], 1); mbar_init(&raw_empty[s], C::CONV_THREADS); }
+    for (int s = 0; s < C::OP_STAGES; ++s) { mbar_init(&op_full[s], C::CONV_THREADS); mbar_init(&op_empty[s], 1); }
+    for (int b = 0; b < C::NB; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 32 * C::EPI_WARPS); }
+    *abort_flag = 0;
+    fence_barrier_init();
+    prefetch_tmap(&tmI);
+  }
+  if (warp == 1) { tmem_alloc(tmem_holder, C::TMEM_COLS); tmem_relinquish(); }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tmem_holder;
+  const int total_units = n_windows * units_pw;
+  auto fail = [&]() { atomicOr(status, DH_FLAG_WAIT_TIMEOUT); *abort_flag = 1; };
+  constexpr int CONV_W0 = 2, EPI_W0 = 2 + C::CONV_THREADS / 32;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---------------- TMA producer: uint16 tiles
+      int slot = 0; uint32_t ph = 0;
+      long long issued = 0;
+      for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x) {
+        const int w = u / units_pw, uu = u % units_pw;
+        const int f0 = first_frame + w * window_stride;
+        const long long p0 = (long long)uu * stages_per_unit * C::PIX;
+        for (int st = 0; st < stages_per_unit; ++st) {
+          if (!mbar_wait(&raw_empty[slot], ph ^ 1)) { fail(); break; }
+          mbar_arrive_expect_tx(&raw_full[slot], C::RAW_BYTES);
+          uint8_t *dst = raws + slot * C::RAW_BYTES;
+#pragma unroll
+          for (int c = 0; c < C::R; ++c)
+            tma_load_2d(dst + c * T * 128, &tmI, &raw_full[slot], (int)(p0 + st * C::PIX + c * 64), f0);
+          ++issued;
+          if (++slot == C::RAW_STAGES) { slot = 0; ph ^= 1; }
+        }
+      }
+      if (*abort_flag) {  // let copies still in flight land before the CTA exits
+        for (int k = 0; k < C::RAW_STAGES && k < issued; ++k) {
+          if (--slot < 0) { slot = C::RAW_STAGES - 1; ph ^= 1; }
+          mbar_wait(&raw_full[slot], ph);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---------------- MMA issuer
+      constexpr uint32_t idesc = idesc_f16(false, false, false, 128, 128);
+      int slot = 0; uint32_t ph = 0; int grp = 0;
+      for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x) {
+        for (int st = 0; st < stages_per_unit && !*abort_flag; ++st, ++grp) {
+          const int buf = grp % C::NB;
+          if (!mbar_wait(&acc_empty[buf], ((grp / C::NB) & 1) ^ 1)) { fail(); break; }
+          fence_after_sync();
+          const uint32_t d = tmem + buf * 128;
+          if (!mbar_wait(&op_full[slot], ph)) { fail(); break; }
+          fence_after_sync();
+          const uint32_t base = smem_u32(ops + slot * C::OP_BYTES);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint64_t desc = smem_desc(base + 32 * k, 16, 1024, kSwizzle128);
+            mma_f16(d, desc, desc, idesc, k > 0 ? 1u : 0u);
+          }
+          mma_commit(&op_empty[slot]);
+          mma_commit(&acc_full[buf]);
+          if (++slot == C::OP_STAGES) { slot = 0; ph ^= 1; }
+        }
+      }
+    }
+  } else if (warp < EPI_W0) {  // ---------------- converters: uint16 -> FP16 hi / lo rows
+    const int ct = threadIdx.x - 32 * CONV_W0;
+    int rslot = 0, oslot = 0; uint32_t rph = 0, oph = 0;
+    for (int u = blockIdx.x; u < total_units && !__any_sync(0xffffffffu, *abort_flag); u += gridDim.x) {
+      bool ok = true;
+      for (int st = 0; st < stages_per_unit; ++st) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&raw_full[rslot], rph))) { fail(); ok = false; break; }
+        if (!__all_sync(0xffffffffu, mbar_wait(&op_empty[oslot], oph ^ 1))) { fail(); ok = false; break; }
+        const uint8_t *src = raws + rslot * C::RAW_BYTES;
+        uint8_t *dst = ops + oslot * C::OP_BYTES;
+#pragma unroll
+        for (int it = 0; it < C::R * T * 8 / C::CONV_THREADS; ++it) {
+          const int item = ct + it * C::CONV_THREADS;   // (chunk c, frame t, 16-byte column j)
+          const int j = item & 7, t = (item >> 3) % T, c = (item >> 3) / T;
+          const uint4 v = *reinterpret_cast<const uint4 *>(src + c * T * 128 + t * 128 + ((j ^ (t & 7)) << 4));
+          uint4 hi, lo;
+          hi.x = byte_pair_to_half2((v.x >> 8) & 0x00FF00FFu); lo.x = byte_pair_to_half2(v.x & 0x00FF00FFu);
+          hi.y = byte_pair_to_half2((v.y >> 8) & 0x00FF00FFu); lo.y = byte_pair_to_half2(v.y & 0x00FF00FFu);
+          hi.z = byte_pair_to_half2((v.z >> 8) & 0x00FF00FFu); lo.z = byte_pair_to_half2(v.z & 0x00FF00FFu);
+          hi.w = byte_pair_to_half2((v.w >> 8) & 0x00FF00FFu); lo.w = byte_pair_to_half2(v.w & 0x00FF00FFu);
+          const int rh = c * C::M2 + 2 * t, rl = rh + 1;  // operand rows of hi_t and lo_t
+          *reinterpret_cast<uint4 *>(dst + rh * 128 + ((j ^ (rh & 7)) << 4)) = hi;
+          *reinterpret_cast<uint4 *>(dst + rl * 128 + ((j ^ (rl & 7)) << 4)) = lo;
+        }
+        // the tensor cores read the operand through the async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&raw_empty[rslot]);
+        mbar_arrive(&op_full[oslot]);
+        if (++rslot == C::RAW_STAGES) { rslot = 0; rph ^= 1; }
+        if (++oslot == C::OP_STAGES) { oslot = 0; oph ^= 1; }
+      }
+      if (!ok) break;
+    }
+  } else {  // ------------------------------ epilogue warps
+    const int e = warp - EPI_W0;
+    const int q = warp & 3;                 // TMEM lane quarter this warp may access
+    const int ch = e >> 2;                  // which NCOL-column part of the chunk
+    const int L = 32 * q + lane;            // accumulator row = TMEM lane
+    const int c = L / C::M2, r = L % C::M2;
+    const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
+    int grp = 0;
+    for (int u = blockIdx.x; u < total_units && !__any_sync(0xffffffffu, *abort_flag); u += gridDim.x) {
+      const int w = u / units_pw, uu = u % units_pw;
+      uint32_t acc[C::NCOL];
+#pragma unroll
+      for (int j = 0; j < C::NCOL; ++j) acc[j] = 0u;
+      bool ok = true;
+      for (int st = 0; st < stages_per_unit; ++st, ++grp) {
+        const int buf = grp % C::NB;
+        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (grp / C::NB) & 1))) {
+          fail(); ok = false; break;
+        }
+        fence_after_sync();
+        const uint32_t ta = tmem + lane_addr + buf * 128 + c * C::M2 + ch * C::NCOL;
+#pragma unroll
+        for (int h = 0; h < C::NCOL / 32; ++h) {
+          float v[32];
+          tmem_ld32(ta + 32 * h, v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) acc[32 * h + i] += (uint32_t)__float_as_int(v[i] + 8388608.f);
+        }
+        fence_before_sync();
+        mbar_arrive(&acc_empty[buf]);
+      }
+      if (!ok) break;
+      // remove the 0x4B000000 of every drained value (mod 2^32)
+      const uint32_t bias = (uint32_t)stages_per_unit * 0x4B000000u;
+      double *dst = part + ((long long)(w * units_pw + uu) * C::R + c) * C::M2 * C::M2 +
+                    (long long)r * C::M2 + ch * C::NCOL;
+#pragma unroll
+      for (int j = 0; j < C::NCOL; ++j) dst[j] = (double)(acc[j] - bias);
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if (warp == 1) {
+    __syncwarp();
+    tmem_dealloc(tmem, C::TMEM_COLS);
+  }
+}
+
 // ======================================================================= projection
 template <int T>
 struct ProjCfg {
@@ -557,6 +770,47 @@ dh_status project_t(Plan &p, int first_slot, int slot_stride, int n_windows, int
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
 }
+template <int T>
+dh_status gram_raw_t(Plan &p, const uint16_t *frames, long long frame_stride, int n_frames, int first_frame,
+                     int window_stride, int n_windows, cudaStream_t s) {
+  using C = RawCfg<T>;
+  auto kern = k_gram_raw_tc<T>;
+  static bool attr = false;
+  if (!attr) {
+    DH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+    DH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared));
+    attr = true;
+  }
+  // uint16 frames as a 2-D tensor: npix x n_frames, box 64 pixels x T frames, 128-byte swizzle
+  auto fn = encode_fn();
+  if (!fn) return DH_ERR_CUDA;
+  CUtensorMap tm;
+  const cuuint64_t dims[2] = {(cuuint64_t)p.npix, (cuuint64_t)n_frames};
+  const cuuint64_t strides[1] = {(cuuint64_t)frame_stride * 2};
+  const cuuint32_t box[2] = {64, (cuuint32_t)T};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<uint16_t *>(frames), dims, strides, box,
+                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return DH_ERR_CUDA;
+  const int units_pw = gram_raw_units(p.npix);
+  const int stages_per_unit = (int)(p.npix / units_pw / C::PIX);
+  const int total = n_windows * units_pw;
+  int per_sm = 0;
+  dh_status rs = resident_ctas(kern, C::THREADS, C::SMEM, &per_sm);
+  if (rs != DH_OK) return rs;
+  if (per_sm > C::CTAS_PER_SM) per_sm = C::CTAS_PER_SM;
+  if (per_sm < 1) per_sm = 1;
+  int grid = p.num_sms * per_sm;
+  if (grid > total) grid = total;
+  ProfScope ps(p, K_GRAM_RAW, s);
+  kern<<<grid, C::THREADS, C::SMEM, s>>>(tm, first_frame, window_stride, n_windows, units_pw, stages_per_unit,
+                                          p.d_part, p.d_status);
+  DH_CUDA_TRY(cudaGetLastError());
+  return DH_OK;
+}
+
 
 }  // namespace
 
@@ -588,6 +842,20 @@ dh_status launch_gram_tc(Plan &p, int first_slot, int slot_stride, int n_windows
                          : gram_t<32, false>(p, first_slot, slot_stride, n_windows, s);
     case 64: return bf16 ? gram_t<64, true>(p, first_slot, slot_stride, n_windows, s)
                          : gram_t<64, false>(p, first_slot, slot_stride, n_windows, s);
+  }
+  return DH_ERR_UNSUPPORTED_SIZE;
+}
+
+int gram_raw_parts(const Plan &p) { return gram_raw_units(p.npix) * (128 / (2 * p.T)); }
+
+dh_status launch_gram_raw(Plan &p, const uint16_t *frames, long long frame_stride, int n_frames,
+                          int first_frame, int window_stride, int n_windows, int *parts_per_window,
+                          cudaStream_t s) {
+  *parts_per_window = gram_raw_parts(p);
+  switch (p.T) {
+    case 16: return gram_raw_t<16>(p, frames, frame_stride, n_frames, first_frame, window_stride, n_windows, s);
+    case 32: return gram_raw_t<32>(p, frames, frame_stride, n_frames, first_frame, window_stride, n_windows, s);
+    case 64: return gram_raw_t<64>(p, frames, frame_stride, n_frames, first_frame, window_stride, n_windows, s);
   }
   return DH_ERR_UNSUPPORTED_SIZE;
 }

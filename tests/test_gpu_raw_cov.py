@@ -1,0 +1,88 @@
+"""Covariance from the uint16 frames (DH_OPT_COVARIANCE = 1): C = I^T I, formed exactly on the
+tensor cores. Because the Fresnel transform of Eq. 1 is unitary per frame, this is the
+covariance of Eq. 4 in exact arithmetic; here it must equal the int64 Gram of the frames
+bit for bit, and the windows' images and eigenvalues must match the FP64 oracle."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from dh_synth import SpeckleParams, SpeckleStream
+from parity_helpers import LAM, PITCH, TOL_IMG, Z, boundary_gap, rel, to_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dh():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2004_00923_b300 as m
+    return m
+
+
+def int_gram(frames):
+    X = frames.reshape(frames.shape[0], -1).astype(np.int64)
+    return X @ X.T
+
+
+@pytest.mark.parametrize("nx,ny,T,full16", [(64, 64, 16, False), (256, 128, 32, False),
+                                            (128, 128, 64, False), (1024, 1024, 32, True),
+                                            (512, 512, 64, True), (16, 16, 16, True)])
+def test_raw_covariance_is_the_integer_gram(dh, nx, ny, T, full16):
+    n = 3
+    if full16:  # every bit of the 16-bit range
+        rng = np.random.default_rng(nx + T)
+        frames = rng.integers(0, 65536, size=(n * T, ny, nx), dtype=np.uint16)
+    else:
+        frames = SpeckleStream(SpeckleParams(nx, ny), seed=nx + T).next(n * T).numpy()
+    with dh.Plan(nx, ny, LAM, Z, PITCH, T=T, precision="fp16", max_frames=n * T, max_windows=n) as plan:
+        plan.set_covariance_source(True)
+        plan.pca_batch(to_gpu(frames), n, T, 2, T - 1)
+        C = [plan.debug_covariance(w).cpu().numpy() for w in range(n)]
+        flags = plan.status()
+    # full-range random frames put a DC hologram value (~ mean x sqrt(n_x n_y)) beyond FP16:
+    # the hologram store reports it; the covariance, from the frames, is unaffected
+    assert flags == (1 if full16 else 0)
+    for w in range(n):
+        ref = int_gram(frames[w * T:(w + 1) * T]).astype(np.float64)
+        assert np.array_equal(C[w].real, ref), w
+        assert np.all(C[w].imag == 0.0)
+
+
+@pytest.mark.parametrize("T", [16, 32, 64])
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_raw_covariance_windows_match_oracle(dh, T, prec):
+    frames = SpeckleStream(SpeckleParams(256, 256), seed=100 + T).next(2 * T).numpy()
+    with dh.Plan(256, 256, LAM, Z, PITCH, T=T, precision=prec, max_frames=2 * T, max_windows=2) as plan:
+        plan.set_covariance_source(True)
+        img, lam = plan.pca_batch(to_gpu(frames), 2, T, 2, T - 1)
+        img, lam = img.cpu().numpy(), lam.cpu().numpy()
+    for w in range(2):
+        M, lam_ref, _, _ = oracle.pca_window(frames[w * T:(w + 1) * T], LAM, Z, PITCH, 2, T - 1)
+        # exact C: the eigenvalues carry only the eigensolver's FP64 error
+        assert np.max(np.abs(lam[w] - lam_ref)) <= 1e-11 * lam_ref[0]
+        # the projection still reads the 16-bit holograms: the stated image tolerance holds
+        # for FP16 storage (BF16 storage is documented not to meet it)
+        if prec == "fp16":
+            tol = max(TOL_IMG["fp16"], 1e-5 / boundary_gap(lam_ref, 2, T - 1))
+            assert rel(img[w], M) <= tol, (w, rel(img[w], M))
+
+
+def test_raw_covariance_through_host_buffers(dh):
+    T, n = 32, 12
+    frames = SpeckleStream(SpeckleParams(128, 128), seed=7).next(n * T)
+    with dh.Plan(128, 128, LAM, Z, PITCH, T=T, precision="fp16", max_frames=n * T, max_windows=n) as plan:
+        plan.set_covariance_source(True)
+        img_d, lam_d = plan.pca_batch(frames.cuda(), n, T, 2, T - 1)
+        img_d, lam_d = img_d.cpu(), lam_d.cpu()
+        img_h, lam_h = plan.pca_batch_host(frames.pin_memory(), n, T, 2, T - 1)
+    assert torch.equal(img_h, img_d) and torch.equal(lam_h, lam_d)
+
+
+def test_raw_covariance_option_needs_16bit_storage(dh):
+    with dh.Plan(64, 64, LAM, Z, PITCH, T=16) as plan:
+        with pytest.raises(dh.DHError) as e:
+            plan.set_covariance_source(True)
+        assert e.value.code == 7
