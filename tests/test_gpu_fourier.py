@@ -94,3 +94,21 @@ def test_svd_fourier_windows_match_oracle(dh, T, prec):
         tol = max(TOL_IMG[prec], EPS_C[prec] / boundary_gap(lam_ref, 2, T - 1))
         assert rel(img[w], M) <= tol, (w, rel(img[w], M), tol)
         assert np.max(np.abs(lam[w] - lam_ref)) / lam_ref[0] <= lam_tol(prec, 128 * 128)
+
+
+@pytest.mark.parametrize("T,b0,b1", [(32, 7, 23), (16, 3, 11), (64, 20, 40)])
+def test_fourier_sliding_recurrence_long_run(dh, T, b0, b1):
+    """300 windows a frame apart (several restart segments of the sliding recurrence): each
+    sampled window equals the direct projection onto W (a one-window call) to FP32 rounding,
+    and matches the oracle."""
+    n = 300
+    frames = SpeckleStream(SpeckleParams(64, 64), seed=80 + T).next(n + T - 1).numpy()
+    with dh.Plan(64, 64, LAM, Z, PITCH, T=T, max_frames=n + T - 1) as plan:
+        plan.render_frames(to_gpu(frames))
+        slide = plan.fourier_windows(0, 1, n, b0, b1).cpu().numpy()
+        for w in (0, 1, 127, 128, 129, 255, 256, 299):
+            direct = plan.fourier_windows(w, 1, 1, b0, b1)[0].cpu().numpy()
+            assert rel(slide[w], direct) <= 1e-5, (w, rel(slide[w], direct))
+    for w in (0, 150, 299):
+        M = oracle.fourier_window(frames[w:w + T], LAM, Z, PITCH, b0, b1)
+        assert rel(slide[w], M) <= TOL_IMG["fp32"], (w, rel(slide[w], M))
