@@ -296,14 +296,17 @@ typedef struct {
   double *eigvals_dev;            /* may be NULL */
 } dh_batch_item;
 
-/* Run a batch of items over any mix of frame sizes, window lengths and plans. Items that
- * touch the same hologram store (a plan and its views) run in the given order on one branch
- * stream; branches of different stores run concurrently (up to 8 branches; more stores share
- * them). Branches fork from `stream` and are joined back into it before the call returns,
- * so the batch is ordered after earlier work on `stream` and later work waits for all of it;
- * the whole batch can be captured into one graph (dh_graph_begin). Every item is validated
- * before anything is launched (DH_ERR_INVALID_ARG); a plan in use by another call gives
- * DH_ERR_STATE. The paper runs one frame size; this batches several. Asynchronous. */
+/* Run a batch of up to 64 items over any mix of frame sizes, window lengths and plans, on
+ * branch streams forked from `stream` and joined back into it before the call returns (the
+ * batch is ordered after earlier work on `stream`; later work waits for all of it; the batch
+ * can be captured into one graph with dh_graph_begin). Ordering: the renders of one hologram
+ * store run in the given order; the windows of one plan run in the given order; the windows
+ * of different plans run concurrently, each after the earlier renders of its store (so the
+ * views of one store, and different stores, overlap on the device); a render waits for the
+ * earlier windows that read its store. Up to 8 branch streams (more branches share them,
+ * which only adds ordering). Every item is validated before anything is launched
+ * (DH_ERR_INVALID_ARG); a plan in use by another call gives DH_ERR_STATE. The paper runs
+ * one frame size and one window length; this batches several. Asynchronous. */
 dh_status dh_batch_run(const dh_batch_item *items, int n_items, void *stream);
 
 /* ---------------------------------------------------------------- serving

@@ -248,14 +248,16 @@ struct Busy {
   ~Busy() { if (ok) b.store(0); }
 };
 
-// Branch streams of the batch executor, one set per device: a batch forks one branch per
-// hologram store from the caller's stream and joins them back before returning.
+// Branch streams of the batch executor, one set per device: a batch forks branches from the
+// caller's stream and joins them back before returning.
 struct Executor {
   static constexpr int kBranches = 8;
+  static constexpr int kMaxItems = 64;
   std::mutex mu;
   cudaStream_t st[kBranches] = {};
   cudaEvent_t fork = nullptr;
   cudaEvent_t join[kBranches] = {};
+  cudaEvent_t ev[2 * kMaxItems] = {};  // after each item's render part and windows part
   bool ready = false;
 
   cudaError_t init() {
@@ -265,6 +267,8 @@ struct Executor {
       e = cudaStreamCreateWithFlags(&st[b], cudaStreamNonBlocking);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[b], cudaEventDisableTiming);
     }
+    for (int k = 0; k < 2 * kMaxItems && e == cudaSuccess; ++k)
+      e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
     ready = e == cudaSuccess;
     return e;
   }
@@ -856,15 +860,15 @@ void dh_graph_destroy(dh_graph_t g) {
 
 // ---------------------------------------------------------------- batches
 dh_status dh_batch_run(const dh_batch_item *items, int n_items, void *stream) {
-  if (!items || n_items < 1) return DH_ERR_INVALID_ARG;
+  if (!items || n_items < 1 || n_items > Executor::kMaxItems) return DH_ERR_INVALID_ARG;
   // validate everything before launching anything
-  std::vector<dh_plan *> roots, plans;
-  std::vector<int> branch(n_items);
+  std::vector<dh_plan *> plans, roots(n_items);
   for (int i = 0; i < n_items; ++i) {
     const dh_batch_item &it = items[i];
     if (!it.plan) return DH_ERR_INVALID_ARG;
     dh_plan *root = it.plan;
     while (root->base) root = root->base;
+    roots[i] = root;
     const Plan &p = it.plan->p;
     if (it.frames_dev) {
       if (it.n_frames < 1 || it.render_slot < 0 || it.frame_stride_elems < p.npix ||
@@ -879,13 +883,9 @@ dh_status dh_batch_run(const dh_batch_item *items, int n_items, void *stream) {
           (long long)it.first_slot + (long long)(it.n_windows - 1) * it.slot_stride + p.T > p.max_frames)
         return DH_ERR_INVALID_ARG;
     }
-    int r = 0;
-    while (r < (int)roots.size() && roots[r] != root) ++r;
-    if (r == (int)roots.size()) roots.push_back(root);
-    branch[i] = r % Executor::kBranches;
     for (dh_plan *q : {it.plan, root}) {
       bool seen = false;
-      for (dh_plan *x : plans) seen |= x == q;
+      for (dh_plan *y : plans) seen |= y == q;
       if (!seen) plans.push_back(q);
     }
   }
@@ -901,23 +901,71 @@ dh_status dh_batch_run(const dh_batch_item *items, int n_items, void *stream) {
   std::lock_guard<std::mutex> lk(x.mu);
   DH_CUDA_TRY(x.init());
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int nb = std::min((int)roots.size(), Executor::kBranches);
+  // Branches: one per store for its renders, one per plan for its windows, in order of first
+  // appearance (wrapping onto shared streams beyond kBranches, which only adds ordering).
+  // The windows of different plans over one store (views) run concurrently once the store's
+  // earlier renders are done; a later render of a store waits for its earlier readers.
+  std::vector<const void *> keys;
+  auto branch_of = [&](const void *key) {
+    int k = 0;
+    while (k < (int)keys.size() && keys[k] != key) ++k;
+    if (k == (int)keys.size()) keys.push_back(key);
+    return k % Executor::kBranches;
+  };
   DH_CUDA_TRY(cudaEventRecord(x.fork, s));
-  for (int b = 0; b < nb; ++b) DH_CUDA_TRY(cudaStreamWaitEvent(x.st[b], x.fork, 0));
+  bool forked[Executor::kBranches] = {};
+  auto stream_of = [&](int b) -> cudaStream_t {
+    if (!forked[b]) {
+      forked[b] = true;
+      if (cudaStreamWaitEvent(x.st[b], x.fork, 0) != cudaSuccess) return nullptr;
+    }
+    return x.st[b];
+  };
   dh_status st = DH_OK;
   for (int i = 0; i < n_items && st == DH_OK; ++i) {
     const dh_batch_item &it = items[i];
-    dh_plan *root = it.plan;
-    while (root->base) root = root->base;
-    cudaStream_t bs = x.st[branch[i]];
-    if (it.frames_dev)
+    dh_plan *root = roots[i];
+    int store_render = -1;  // latest earlier render part of this store
+    for (int j = i - 1; j >= 0 && store_render < 0; --j)
+      if (roots[j] == root && items[j].frames_dev) store_render = 2 * j;
+    if (it.frames_dev) {
+      cudaStream_t bs = stream_of(branch_of(root));
+      if (!bs) { st = fail_cuda(cudaGetLastError()); break; }
+      // readers of this store since its last render finish first
+      for (int j = i - 1; j >= 0; --j) {
+        if (roots[j] != root) continue;
+        if (items[j].n_windows > 0) {
+          cudaError_t e = cudaStreamWaitEvent(bs, x.ev[2 * j + 1], 0);
+          if (e != cudaSuccess) { st = fail_cuda(e); break; }
+        }
+        if (items[j].frames_dev) break;  // readers before that render waited for it already
+      }
+      if (st != DH_OK) break;
       st = launch_render(root->p, it.frames_dev, it.frame_stride_elems, it.n_frames, it.render_slot, bs);
-    if (st == DH_OK && it.n_windows > 0)
+      if (st == DH_OK) {
+        cudaError_t e = cudaEventRecord(x.ev[2 * i], bs);
+        if (e != cudaSuccess) st = fail_cuda(e);
+      }
+      store_render = 2 * i;
+    }
+    if (st == DH_OK && it.n_windows > 0) {
+      cudaStream_t bs = stream_of(branch_of(it.plan));
+      if (!bs) { st = fail_cuda(cudaGetLastError()); break; }
+      if (store_render >= 0) {
+        cudaError_t e = cudaStreamWaitEvent(bs, x.ev[store_render], 0);
+        if (e != cudaSuccess) { st = fail_cuda(e); break; }
+      }
       st = pca_impl(it.plan->p, nullptr, 0, it.first_slot, it.slot_stride, it.n_windows, it.k0, it.k1,
                     it.images_dev, it.eigvals_dev, bs);
+      if (st == DH_OK) {
+        cudaError_t e = cudaEventRecord(x.ev[2 * i + 1], bs);
+        if (e != cudaSuccess) st = fail_cuda(e);
+      }
+    }
   }
-  // join every branch, also after an error, so the caller's stream never runs ahead of them
-  for (int b = 0; b < nb; ++b) {
+  // join every forked branch, also after an error, so the caller's stream never runs ahead
+  for (int b = 0; b < Executor::kBranches; ++b) {
+    if (!forked[b]) continue;
     cudaError_t e = cudaEventRecord(x.join[b], x.st[b]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, x.join[b], 0);
     if (e != cudaSuccess && st == DH_OK) st = fail_cuda(e);

@@ -13,6 +13,15 @@
 //   and the retained columns k0..k1 are packed into the operand of Eq. 6.
 #include "dh_internal.cuh"
 
+// FP64 phase of the eigensolver: Lowdin re-orthonormalisation steps, and the off(A) / ||C||_F
+// at which the FP64 sweeps stop.
+#ifndef DH_LOWDIN_PASSES
+#define DH_LOWDIN_PASSES 2
+#endif
+#ifndef DH_EIG_TOL
+#define DH_EIG_TOL 1e-12
+#endif
+
 namespace dh {
 namespace {
 
@@ -230,7 +239,7 @@ k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restr
   // Lowdin re-orthonormalisation of the (nearly orthonormal) columns of V:
   // V <- V (3 I - V^{t*} V) / 2 squares the orthogonality error E = V^{t*} V - I; the FP32
   // sweeps leave |E| ~ 1e-6, so two steps reach FP64 level.
-  for (int pass = 0; pass < 2; ++pass) {
+  for (int pass = 0; pass < DH_LOWDIN_PASSES; ++pass) {
   for (int e = tid; e < T * T; e += blockDim.x) {  // Z = V^{t*} V
     const int i = e / T, j = e % T;
     double sr = 0.0, si = 0.0;
@@ -378,7 +387,7 @@ dh_status launch_jacobi_t(Plan &p, int n_windows, int k0, int k1, int Npad, doub
   ProfScope ps(p, K_JACOBI, s);
   k_jacobi<T><<<n_windows, 256, smem, s>>>(p.d_C + 2ll * woff * T * T, p.d_lam + (long long)woff * T,
                                            p.d_V + 2ll * woff * T * T, eig_user, (int)p.prec, B, B_stride,
-                                           k0, k1, Npad, 5e-14, 30, p.d_status);
+                                           k0, k1, Npad, DH_EIG_TOL, 30, p.d_status);
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
 }

@@ -157,3 +157,49 @@ def test_view_rules(dh):
     torch.cuda.synchronize()
     assert torch.equal(img_before, img_after) and torch.equal(lam_before, lam_after)
     v.close()
+
+
+@pytest.mark.parametrize("prec", ["fp16"])
+def test_views_run_concurrently_in_a_batch(dh, prec):
+    """One batch: render, then the three lengths' windows on concurrent branches (views of one
+    store); bitwise the sequential calls' results."""
+    frames = SpeckleStream(SpeckleParams(128, 128), seed=25).next(96).numpy()
+    f = to_gpu(frames)
+    sl = Sliding(dh, 128, 128, 96, prec)
+    sl.step(f)
+    ref = sl.results()
+    items = [{"plan": sl.base, "frames": f}] + [
+        {"plan": sl.plans[T], "n_windows": sl.n[T], "first_slot": 0, "slot_stride": STRIDE,
+         "k0": 2, "k1": T - 1, "images": sl.images[T], "eigvals": sl.lam[T]} for T in (64, 32, 16)]
+    for T in LENGTHS:
+        sl.images[T].zero_()
+    dh.run_batch(items)
+    got = sl.results()
+    for T in LENGTHS:
+        assert np.array_equal(got[T][0], ref[T][0]) and np.array_equal(got[T][1], ref[T][1])
+    sl.close()
+
+
+def test_batch_orders_a_rerender_after_its_readers(dh):
+    """render A; windows (views); render B into the same slots; windows again: the first
+    windows see A and the second see B (the second render waits for the first readers)."""
+    gen = SpeckleStream(SpeckleParams(64, 64), seed=26)
+    fa, fb = to_gpu(gen.next(48).numpy()), to_gpu(gen.next(48).numpy())
+    base = dh.Plan(64, 64, LAM, Z, PITCH, T=16, precision="fp16", max_frames=48, max_windows=5)
+    v32 = base.view(32, 3)
+    out = {k: torch.empty((3, 64, 64), dtype=torch.float32, device="cuda") for k in ("a", "b")}
+    items = [{"plan": base, "frames": fa},
+             {"plan": v32, "n_windows": 3, "first_slot": 0, "slot_stride": 8, "k0": 2, "k1": 31,
+              "images": out["a"]},
+             {"plan": base, "frames": fb},
+             {"plan": v32, "n_windows": 3, "first_slot": 0, "slot_stride": 8, "k0": 2, "k1": 31,
+              "images": out["b"]}]
+    dh.run_batch(items)
+    torch.cuda.synchronize()
+    for key, fr in (("a", fa), ("b", fb)):
+        with dh.Plan(64, 64, LAM, Z, PITCH, T=32, precision="fp16", max_frames=48, max_windows=3) as own:
+            img, _ = own.pca_batch(fr, 3, 8, 2, 31)
+            torch.cuda.synchronize()
+            assert torch.equal(img, out[key]), key
+    v32.close()
+    base.close()
