@@ -260,14 +260,15 @@ __device__ __forceinline__ void l2_discard(const void *p) {
   asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
 }
 
-template <typename T> __device__ __forceinline__ bool stored_finite(T h);
-template <> __device__ __forceinline__ bool stored_finite<float>(float h) { return isfinite(h); }
-template <> __device__ __forceinline__ bool stored_finite<__half>(__half h) {
-  return isfinite(__half2float(h));
-}
-template <> __device__ __forceinline__ bool stored_finite<__nv_bfloat16>(__nv_bfloat16 h) {
-  return isfinite(__bfloat162float(h));
-}
+// Overflow watch of the stored planes: the largest |value| bits a thread wrote, compared once
+// with the smallest FP32 magnitude that does not store as a finite value of the storage type
+// (FP32: Inf/NaN; FP16: >= 65520, which rounds to Inf; BF16: >= 3.3961775e38). NaN bits
+// exceed every threshold.
+__device__ __forceinline__ uint32_t abs_bits(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+template <typename T> __host__ __device__ constexpr uint32_t overflow_bits();
+template <> __host__ __device__ constexpr uint32_t overflow_bits<float>() { return 0x7f800000u; }
+template <> __host__ __device__ constexpr uint32_t overflow_bits<__half>() { return 0x477ff000u; }
+template <> __host__ __device__ constexpr uint32_t overflow_bits<__nv_bfloat16>() { return 0x7f7f8000u; }
 
 // The row-pass output `mid` of a frame is stored in tiles of CW = fpc(log2 n_y) columns:
 // tile t holds columns [t CW, t CW + CW) for every y, row-major [y][CW], and inside a row of
@@ -332,7 +333,7 @@ __device__ __forceinline__ void row_work(const uint4 (&pf)[RowCfg<LOGN>::CPT], f
 #pragma unroll
   for (int r = 0; r < S::R; ++r) {
     const int x = j + r * S::P;
-    const float a = (float)row16[x];
+    const float a = __uint_as_float(0x4b000000u | row16[x]) - 8388608.f;  // exact: u < 2^23
     const float2 c = __ldg(cx + x);
     v[r] = make_float2(a * c.x, a * c.y);
   }
@@ -363,7 +364,7 @@ template <int LOGN, typename OutT, typename Issued, typename Landed>
 __device__ __forceinline__ bool col_work(const float2 *__restrict__ src, float2 *smem, uint64_t *bar,
                                          uint32_t &phase, int *abort_flag, bool copy_ok, int kx0,
                                          OutT *__restrict__ H, long long npix, long long rows_total,
-                                         int slot, bool &finite, const float2 *__restrict__ tw,
+                                         int slot, uint32_t &maxbits, const float2 *__restrict__ tw,
                                          Issued issued, Landed landed) {
   using S = Shape<LOGN>;
   constexpr int FPC = fpc<LOGN>();
@@ -416,7 +417,7 @@ __device__ __forceinline__ bool col_work(const float2 *__restrict__ src, float2 
 #pragma unroll
     for (int i = 0; i < S::R; ++i) {
       const float2 o = v[E::out_reg(i)];
-      finite &= isfinite(o.x) & isfinite(o.y);
+      maxbits = max(maxbits, max(abs_bits(o.x), abs_bits(o.y)));
       st_stream(re + j + i * S::P, o.x);
       st_stream(im + j + i * S::P, o.y);
     }
@@ -428,7 +429,7 @@ __device__ __forceinline__ bool col_work(const float2 *__restrict__ src, float2 
     for (int i = 0; i < S::R; ++i) {
       const float2 o = v[E::out_reg(i)];
       const OutT a = to_store<OutT>(o.x), b = to_store<OutT>(o.y);
-      finite &= stored_finite<OutT>(a) & stored_finite<OutT>(b);
+      maxbits = max(maxbits, max(abs_bits(o.x), abs_bits(o.y)));
       OutT *q;
       if constexpr (S::N >= 64) {
         const int e = j + i * S::P;  // < n_y
@@ -487,19 +488,19 @@ k_render_cols(const float2 *__restrict__ mid, int nx, const float2 *__restrict__
   }
   __syncthreads();
   uint32_t phase = 0;
-  bool finite = true;
+  uint32_t maxbits = 0;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     const int f = item / groups, t = item % groups;
     const float2 *src = mid + (long long)f * npix + (long long)t * FPC * Shape<LOGN>::N;
     if (!col_work<LOGN, OutT>(src, smem, &bar, phase, &abort_flag, true, t * FPC, H, npix, rows_total,
-                              slot0 + f, finite, tw, []() {}, []() {}))
+                              slot0 + f, maxbits, tw, []() {}, []() {}))
       break;
   }
   if (abort_flag && threadIdx.x == 0) {
     atomicOr(status, DH_FLAG_WAIT_TIMEOUT);
     tc::mbar_wait(&bar, phase ^ 1);  // let a late copy land before the CTA exits
   }
-  if (!finite) atomicOr(status, DH_FLAG_STORE_OVERFLOW);
+  if (maxbits >= overflow_bits<OutT>()) atomicOr(status, DH_FLAG_STORE_OVERFLOW);
 }
 
 // ---------------------------------------------------------------- fused, persistent render
@@ -577,7 +578,7 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
   if (valid(cur) && is_row(cur))
     row_prefetch<LOGN>(pf, frames + (long long)frame_of(cur) * frame_stride, item_of(cur) * FPC);
   uint32_t phase = 0;
-  bool finite = true;
+  uint32_t maxbits = 0;
   int b = 1;
   while (cur < total) {
     if (threadIdx.x == 0) tk[b] = (int)atomicAdd(tickets, 1u);
@@ -612,7 +613,7 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
         }
         const float2 *src = ring_f + (long long)i * FPC * N;
         if (!col_work<LOGN, OutT>(src, smem, &bar, phase, &abort_flag, ok, i * FPC, H, NPIX, rows_total,
-                                  slot0 + f, finite, tw, prefetch_next,
+                                  slot0 + f, maxbits, tw, prefetch_next,
                                   [&]() { red_release_add(cols_done + rs, 1u); }))
           break;
       }
@@ -623,7 +624,7 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
     atomicOr(status, DH_FLAG_WAIT_TIMEOUT);
     tc::mbar_wait(&bar, phase ^ 1);  // let a late copy land before the CTA exits
   }
-  if (!finite) atomicOr(status, DH_FLAG_STORE_OVERFLOW);
+  if (maxbits >= overflow_bits<OutT>()) atomicOr(status, DH_FLAG_STORE_OVERFLOW);
 }
 
 // Inspection: one slot's hologram (column-major pixels p = kx n_y + ky; FP32 as planes,
