@@ -186,7 +186,7 @@ struct Engine {
         for (int r = 0; r < S::R; ++r) v[r] = sm[pad(j + r * S::P)];
         const int m = j & (Ns - 1);
 #pragma unroll
-        for (int r = 1; r < S::R; ++r) v[r] = cmul(v[r], __ldg(&tw[tw_off + (r - 1) * Ns + m]));
+        for (int r = 1; r < S::R; ++r) v[r] = cmul(v[r], tw[tw_off + (r - 1) * Ns + m]);
         tw_off += (S::R - 1) * Ns;
         dif<S::R, 1, 0, S::R>(v);
         if (p == S::L - 1 && S::R2 == 1) return;
@@ -205,7 +205,7 @@ struct Engine {
           const int b = j + q * S::P;
 #pragma unroll
           for (int r2 = 1; r2 < S::R2; ++r2)
-            v[q + S::B * r2] = cmul(v[q + S::B * r2], __ldg(&tw[tw_off + (r2 - 1) * NsE + b]));
+            v[q + S::B * r2] = cmul(v[q + S::B * r2], tw[tw_off + (r2 - 1) * NsE + b]);
         }
         dif_each<S::R2, S::B, 0, S::R>(v);
       }
@@ -334,11 +334,11 @@ __device__ __forceinline__ void row_work(const uint4 (&pf)[RowCfg<LOGN>::CPT], f
   for (int r = 0; r < S::R; ++r) {
     const int x = j + r * S::P;
     const float a = __uint_as_float(0x4b000000u | row16[x]) - 8388608.f;  // exact: u < 2^23
-    const float2 c = __ldg(cx + x);
+    const float2 c = cx[x];
     v[r] = make_float2(a * c.x, a * c.y);
   }
   E::run(v, sm, j, tw);  // its first exchange store is ordered after the reads above
-  const float2 cyy = __ldg(cy + y);
+  const float2 cyy = cy[y];
   if ((S::P & ((1 << cw_log) - 1)) == 0) {
     // kx = j + i P: the tile column and the swizzle are fixed per thread, and successive
     // outputs are P n_y elements apart
@@ -545,6 +545,7 @@ template <int LOGN, typename OutT>
 __global__ void __launch_bounds__(kCtaThreads, rows_per_sm<LOGN>())
 k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int n_frames, int cw_log,
                const float2 *__restrict__ cx, const float2 *__restrict__ cy, const float2 *__restrict__ tw,
+               int tw_len,
                float2 *__restrict__ mid, int ring, int lag, OutT *__restrict__ H, long long rows_total,
                int slot0, unsigned *__restrict__ sync, uint32_t *__restrict__ status) {
   using S = Shape<LOGN>;
@@ -555,6 +556,12 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
   constexpr long long NPIX = (long long)N * N;
   static_assert(RC::NT == kCtaThreads, "fused render needs full-size items on both axes");
   extern __shared__ float2 smem[];
+  // the CTA lives for the whole launch: its twiddle and chirp tables are copied into shared
+  // memory once, after the exchange / tile buffer
+  constexpr int XCHG = (FPC * S::RSTRIDE > FPC * S::N ? FPC * S::RSTRIDE : FPC * S::N);
+  float2 *s_tw = smem + XCHG, *s_cx = s_tw + tw_len, *s_cy = s_cx + N;
+  for (int e = threadIdx.x; e < tw_len; e += blockDim.x) s_tw[e] = tw[e];
+  for (int e = threadIdx.x; e < N; e += blockDim.x) { s_cx[e] = cx[e]; s_cy[e] = cy[e]; }
   __shared__ __align__(8) uint64_t bar;
   __shared__ int abort_flag;
   __shared__ int tk[2];
@@ -601,7 +608,7 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
         if (threadIdx.x == 0 && !wait_geq(cols_done + rs, (unsigned)(f / ring) * NI)) abort_flag = 1;
         __syncthreads();
         if (abort_flag) break;
-        row_work<LOGN>(pf, smem, i * FPC, N, cw_log, cx, cy, tw, ring_f, prefetch_next);
+        row_work<LOGN>(pf, smem, i * FPC, N, cw_log, s_cx, s_cy, s_tw, ring_f, prefetch_next);
         fence_proxy_async_global();  // this thread's ring writes, for later bulk copies
         __syncthreads();
         if (threadIdx.x == 0) red_release_add(rows_done + rs, 1u);  // after the CTA's writes
@@ -613,7 +620,7 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
         }
         const float2 *src = ring_f + (long long)i * FPC * N;
         if (!col_work<LOGN, OutT>(src, smem, &bar, phase, &abort_flag, ok, i * FPC, H, NPIX, rows_total,
-                                  slot0 + f, maxbits, tw, prefetch_next,
+                                  slot0 + f, maxbits, s_tw, prefetch_next,
                                   [&]() { red_release_add(cols_done + rs, 1u); }))
           break;
       }
@@ -792,7 +799,9 @@ dh_status launch_fused_t(Plan &p, const uint16_t *frames, long long fstride, int
   constexpr int FPC = fpc<LOGN>();
   const size_t row_smem = (size_t)FPC * S::RSTRIDE * sizeof(float2);
   const size_t tile = (size_t)FPC * S::N * sizeof(float2);
-  const size_t smem = row_smem > tile ? row_smem : tile;
+  const int tw_len = twiddle_len(LOGN);
+  // exchange / tile buffer, then the twiddle and the two chirp tables
+  const size_t smem = (row_smem > tile ? row_smem : tile) + (size_t)(tw_len + 2 * S::N) * sizeof(float2);
   auto kern = k_render_fused<LOGN, OutT>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -809,7 +818,8 @@ dh_status launch_fused_t(Plan &p, const uint16_t *frames, long long fstride, int
   const int lag = fused_lag(p, ring);
   DH_CUDA_TRY(cudaMemsetAsync(p.d_sync, 0, sizeof(unsigned) * (1 + 2 * ring), s));
   ProfScope ps(p, K_RENDER_FUSED, s);
-  kern<<<grid, kCtaThreads, smem, s>>>(frames, fstride, nf, col_tile_log(p.logny), p.d_cx, p.d_cy, p.d_twx, p.d_mid,
+  kern<<<grid, kCtaThreads, smem, s>>>(frames, fstride, nf, col_tile_log(p.logny), p.d_cx, p.d_cy, p.d_twx, tw_len,
+                                      p.d_mid,
                                ring, lag, static_cast<OutT *>(p.d_H), 2ll * p.max_frames, slot0, p.d_sync,
                                p.d_status);
   DH_CUDA_TRY(cudaGetLastError());
