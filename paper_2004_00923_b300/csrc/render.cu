@@ -309,7 +309,7 @@ __device__ __forceinline__ void row_prefetch(uint4 (&pf)[RowCfg<LOGN>::CPT], con
   for (int k = 0; k < C::CPT; ++k) pf[k] = __ldcs(src + threadIdx.x + k * C::NT);  // read once
 }
 
-template <int LOGN, typename Parked>
+template <int LOGN, bool LEAD_SYNC = true, typename Parked>
 __device__ __forceinline__ void row_work(const uint4 (&pf)[RowCfg<LOGN>::CPT], float2 *smem, int y0, int ny,
                                          int cw_log, const float2 *__restrict__ cx,
                                          const float2 *__restrict__ cy, const float2 *__restrict__ tw,
@@ -320,7 +320,7 @@ __device__ __forceinline__ void row_work(const uint4 (&pf)[RowCfg<LOGN>::CPT], f
   const int fft = threadIdx.x / S::P, j = threadIdx.x % S::P;
   float2 *sm = smem + fft * S::RSTRIDE;
   const int y = y0 + fft;
-  __syncthreads();  // every transform is done with its region (previous item)
+  if constexpr (LEAD_SYNC) __syncthreads();  // every transform is done with its region (previous item)
 #pragma unroll
   for (int k = 0; k < C::CPT; ++k) {
     const int c = threadIdx.x + k * C::NT, row = c / C::CPR, cr = c % C::CPR;
@@ -360,7 +360,7 @@ __device__ __forceinline__ void row_work(const uint4 (&pf)[RowCfg<LOGN>::CPT], f
 // in the same buffer, and writes the hologram planes of `slot` in column-major pixel order
 // p = kx n_y + ky. Returns false (after a barrier) if the copy did not complete within the
 // wait budget; `copy_ok` false on thread 0 skips the copy (a failed wait before it).
-template <int LOGN, typename OutT, typename Issued, typename Landed>
+template <int LOGN, typename OutT, bool TAIL_SYNC = true, typename Issued, typename Landed>
 __device__ __forceinline__ bool col_work(const float2 *__restrict__ src, float2 *smem, uint64_t *bar,
                                          uint32_t &phase, int *abort_flag, bool copy_ok, int kx0,
                                          OutT *__restrict__ H, long long npix, long long rows_total,
@@ -442,7 +442,7 @@ __device__ __forceinline__ bool col_work(const float2 *__restrict__ src, float2 
       st_stream(q + 64, b);
     }
   }
-  __syncthreads();  // all transforms are done with the buffer before the next copy lands
+  if constexpr (TAIL_SYNC) __syncthreads();  // all transforms are done with the buffer before the next copy
   return true;
 }
 
@@ -588,7 +588,15 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
   uint32_t maxbits = 0;
   int b = 1;
   while (cur < total) {
-    if (threadIdx.x == 0) tk[b] = (int)atomicAdd(tickets, 1u);
+    // one barrier per item start: thread 0 takes the next ticket and, for a row item, waits for
+    // its ring slot; the barrier also ends the previous item's use of shared memory
+    if (threadIdx.x == 0) {
+      tk[b] = (int)atomicAdd(tickets, 1u);
+      if (valid(cur) && is_row(cur)) {
+        const int f = frame_of(cur);
+        if (!wait_geq(cols_done + f % ring, (unsigned)(f / ring) * NI)) abort_flag = 1;
+      }
+    }
     __syncthreads();
     const int nxt = tk[b];
     b ^= 1;
@@ -605,10 +613,7 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
       const int f = frame_of(cur), i = item_of(cur), rs = f % ring;
       float2 *ring_f = mid + (long long)rs * NPIX;
       if (is_row(cur)) {
-        if (threadIdx.x == 0 && !wait_geq(cols_done + rs, (unsigned)(f / ring) * NI)) abort_flag = 1;
-        __syncthreads();
-        if (abort_flag) break;
-        row_work<LOGN>(pf, smem, i * FPC, N, cw_log, s_cx, s_cy, s_tw, ring_f, prefetch_next);
+        row_work<LOGN, false>(pf, smem, i * FPC, N, cw_log, s_cx, s_cy, s_tw, ring_f, prefetch_next);
         fence_proxy_async_global();  // this thread's ring writes, for later bulk copies
         __syncthreads();
         if (threadIdx.x == 0) red_release_add(rows_done + rs, 1u);  // after the CTA's writes
@@ -619,7 +624,7 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
           if (ok) fence_proxy_async_global();
         }
         const float2 *src = ring_f + (long long)i * FPC * N;
-        if (!col_work<LOGN, OutT>(src, smem, &bar, phase, &abort_flag, ok, i * FPC, H, NPIX, rows_total,
+        if (!col_work<LOGN, OutT, false>(src, smem, &bar, phase, &abort_flag, ok, i * FPC, H, NPIX, rows_total,
                                   slot0 + f, maxbits, s_tw, prefetch_next,
                                   [&]() { red_release_add(cols_done + rs, 1u); }))
           break;
