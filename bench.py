@@ -207,8 +207,11 @@ def run_ours(args, ws, rank, local):
     frames = SpeckleStream(SpeckleParams(NX, NY), seed=1000 + rank, device=dev).next(nframes)
     npix = NX * NY
 
-    plan = dh.Plan(NX, NY, LAM, Z, PITCH, T=T, precision=args.precision, max_frames=nframes,
-                   max_windows=nwin)
+    # pipelined steps use two halves of hologram slots: batch k+1 renders into one half while
+    # batch k's covariance, eigensolver and projection read the other
+    pipeline = args.pipeline and args.covariance != "raw"
+    plan = dh.Plan(NX, NY, LAM, Z, PITCH, T=T, precision=args.precision,
+                   max_frames=nframes * (2 if pipeline else 1), max_windows=nwin)
     plan.set_covariance_source(args.covariance == "raw")
     if args.render_schedule == "auto":
         tuned = plan.autotune(256)  # setup, outside the timed region
@@ -221,32 +224,75 @@ def run_ours(args, ws, rank, local):
     def step(p):
         p.pca_batch(frames, nwin, T, K0, K1, images, eig)
 
-    for _ in range(max(args.warmup, 0)):
-        step(plan)
+    s_render, s_pca = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    ev_rendered = [torch.cuda.Event() for _ in range(2)]
+    ev_done = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    done_marks = []
+
+    def pipelined(k_first, n):
+        """Steps k_first .. k_first + n - 1: render of step k on one stream, Eqs. 4-7 of step k
+        on another; half k % 2 is re-rendered only after its previous PCA (step k - 2)."""
+        for k in range(k_first, k_first + n):
+            h = k % 2
+            s_render.wait_event(ev_done[h])
+            plan.render_frames(frames, first_slot=h * nframes, stream=s_render)
+            ev_rendered[h].record(s_render)
+            s_pca.wait_event(ev_rendered[h])
+            plan.pca_windows(h * nframes, T, nwin, K0, K1, images, eig, stream=s_pca)
+            mark = torch.cuda.Event(enable_timing=True)
+            mark.record(s_pca)
+            done_marks.append(mark)
+            ev_done[h].record(s_pca)
+
+    if pipeline:
+        pipelined(0, max(args.warmup, 0))
+    else:
+        for _ in range(max(args.warmup, 0)):
+            step(plan)
     torch.cuda.synchronize()
 
     # ---------------------------------------------------------------- timed region
     clocks = ClockSampler(local)
-    plan.profile(True)
     barrier(ws)
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    ev[0].record(stream)
-    for k in range(args.steps):
-        step(plan)
-        ev[k + 1].record(stream)
-    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if pipeline:
+        start.record(stream)
+        s_render.wait_stream(stream)
+        s_pca.wait_stream(stream)
+        done_marks.clear()
+        pipelined(args.warmup, args.steps)
+        stream.wait_stream(s_render)
+        stream.wait_stream(s_pca)
+        end.record(stream)
+        torch.cuda.synchronize()
+        step_ms = [start.elapsed_time(done_marks[0])] + [
+            done_marks[k - 1].elapsed_time(done_marks[k]) for k in range(1, len(done_marks))]
+    else:
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        start.record(stream)
+        for k in range(args.steps):
+            step(plan)
+            marks[k].record(stream)
+        end.record(stream)
+        torch.cuda.synchronize()
+        step_ms = [start.elapsed_time(marks[0])] + [marks[k - 1].elapsed_time(marks[k])
+                                                    for k in range(1, args.steps)]
     barrier(ws)
     clock_info = clocks.stop()
-    prof = plan.profile_read()
-    plan.profile(False)
-    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    ms = ev[0].elapsed_time(ev[-1]) / args.steps
+    ms = start.elapsed_time(end) / args.steps
     ms_max = max_over_ranks(ms, ws)
     value = whole_job_rate(nwin, ws, ms_max)
     flags = plan.status()
+    # per-kernel breakdown: the same number of steps again, one after another with the
+    # library's tracer on (overlapped steps would mix their event intervals); not timed
+    plan.profile(True)
+    for _ in range(args.steps):
+        step(plan)
+    prof = plan.profile_read()
+    plan.profile(False)
 
     # ---------------------------------------------------------------- roofline
     hbm, bf16_peak, peak_kind = measured_peaks()
@@ -337,6 +383,7 @@ def run_ours(args, ws, rank, local):
                        "precision": args.precision,
                        "l2": "no flush: 4 GiB of input frames per step exceed the 126 MB L2",
                        "render_schedule": tuned, "covariance": args.covariance,
+                       "pipelined_steps": pipeline,
                        "parallelism": f"replicas x{ws}"},
             "frames_per_s": value * T,
             "step_ms": {"p50": statistics.median(step_ms), "max": max(step_ms)},
@@ -986,6 +1033,10 @@ def main(argv=None):
     ap.add_argument("--render-schedule", choices=["auto", "persistent", "chunks"], default="auto",
                     help="Eq. 1 schedule of the headline plan: auto = the library's autotuner "
                          "(dh_plan_autotune); else DH_OPT_RENDER_SCHEDULE with ring and lag")
+    ap.add_argument("--pipeline", action=argparse.BooleanOptionalAction, default=False,
+                    help="overlap the render of batch k+1 with Eqs. 4-7 of batch k (two halves of "
+                         "hologram slots, two streams; measured no faster: the persistent render "
+                         "holds every SM's registers); default: batches back to back")
     ap.add_argument("--covariance", choices=["holograms", "raw"], default="holograms",
                     help="Eq. 4 from the holograms (as written, default) or exactly from the uint16 "
                          "frames (DH_OPT_COVARIANCE = 1, C = I^T I)")
