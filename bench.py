@@ -212,7 +212,7 @@ def run_ours(args, ws, rank, local):
     pipeline = args.pipeline and args.covariance != "raw"
     plan = dh.Plan(NX, NY, LAM, Z, PITCH, T=T, precision=args.precision,
                    max_frames=nframes * (2 if pipeline else 1), max_windows=nwin)
-    plan.set_covariance_source(args.covariance == "raw")
+    plan.set_covariance_source(args.covariance)
     if args.render_schedule == "auto":
         tuned = plan.autotune(256)  # setup, outside the timed region
     else:
@@ -539,15 +539,37 @@ def run_sliding(args, ws, rank, local):
     per_kernel = merge_tables(tables)
     launches = sum(v["launches"] for v in per_kernel.values())
 
-    # timed form: one batch per step, the three window lengths (views of one store) running
-    # concurrently after the shared render, longest first
-    items = [{"plan": base, "frames": frames}] + [
-        {"plan": plans[L], "n_windows": n[L], "first_slot": 0, "slot_stride": SLIDE_STRIDE,
-         "k0": 2, "k1": L - 1, "images": images[L], "eigvals": eig[L]} for L in (64, 32, 16)]
+    # timed form: render, the banded covariance of the whole sequence (each frame read three
+    # times instead of once per window holding it), then one batch with the three window
+    # lengths (views of one store) running concurrently, longest first
+    if args.band:
+        for p in plans.values():
+            p.set_covariance_source("band")
+    items = [{"plan": plans[L], "n_windows": n[L], "first_slot": 0, "slot_stride": SLIDE_STRIDE,
+              "k0": 2, "k1": L - 1, "images": images[L], "eigvals": eig[L]} for L in (64, 32, 16)]
+
+    def timed_step():
+        base.render_frames(frames)
+        if args.band:
+            base.band_gram(0, F)
+        dh.run_batch(items)
+
+    # traced once more in the timed form's covariance mode, one stage after the other
+    if args.band:
+        for p in plans.values():
+            p.profile(True)
+        base.render_frames(frames)
+        base.band_gram(0, F)
+        for L in SLIDE_LENGTHS:
+            plans[L].pca_windows(0, SLIDE_STRIDE, n[L], 2, L - 1, images[L], eig[L])
+        per_kernel = merge_tables([kernel_table(p.profile_read())[0] for p in plans.values()])
+        for p in plans.values():
+            p.profile(False)
+        launches = sum(v["launches"] for v in per_kernel.values())
     s = torch.cuda.Stream(device=dev)
     torch.cuda.synchronize()
     with dh.capture(s) as g:
-        dh.run_batch(items)
+        timed_step()
     for _ in range(max(args.warmup, 0)):
         g.launch(s)
     ms, step_ms, clock_info = timed_graph(g, s, args.steps, ws, local)
@@ -560,7 +582,8 @@ def run_sliding(args, ws, rank, local):
     npix = NX * NY
     gram = sum(n[L] * L * npix * 4 for L in SLIDE_LENGTHS)
     alg = {"render_rows": F * npix * 2, "render_cols": F * npix * 4, "render_fused": F * npix * 6,
-           "gram_tc": gram, "project_tc": gram + nwin * npix * 4}
+           "gram_tc": gram, "project_tc": gram + nwin * npix * 4,
+           "band_gram": 3 * F * npix * 4}  # each frame read as block b (twice) and as b + 1
     fl = render_flops(npix, NX, NY, F)
     roofline = roofline_of(per_kernel, alg, hbm, peak_kind, ms / 1e3, {k: fl for k in RENDER_KERNELS})
 
@@ -587,6 +610,8 @@ def run_sliding(args, ws, rank, local):
             "config": {"workload": "sliding: 2048 frames of 1024x1024 uint16, 16/32/64-frame "
                                    "windows at stride 8, each frame rendered once (FP16), "
                                    "the lengths run concurrently, one CUDA graph per step",
+                       "covariance": "banded Gram of the store (dh_band_gram)" if args.band
+                       else "one Gram per window",
                        "windows_per_step": n, "k0": 2, "k1": "T-1",
                        "l2": "no flush: 4 GiB of frames and 8 GiB of holograms per step",
                        "parallelism": f"replicas x{ws}"},
@@ -1037,6 +1062,9 @@ def main(argv=None):
                     help="overlap the render of batch k+1 with Eqs. 4-7 of batch k (two halves of "
                          "hologram slots, two streams; measured no faster: the persistent render "
                          "holds every SM's registers); default: batches back to back")
+    ap.add_argument("--band", action=argparse.BooleanOptionalAction, default=True,
+                    help="sliding workload: windows take C from the store's banded Gram "
+                         "(dh_band_gram) instead of one Gram per window")
     ap.add_argument("--covariance", choices=["holograms", "raw"], default="holograms",
                     help="Eq. 4 from the holograms (as written, default) or exactly from the uint16 "
                          "frames (DH_OPT_COVARIANCE = 1, C = I^T I)")

@@ -125,6 +125,9 @@ dh_status dh_plan_reserve(dh_plan_t plan, int max_frames, int max_windows);
  *   half the bytes read and no storage rounding in C (exact while sum I^2 < 2^53). 16-bit
  *   hologram storage only (DH_ERR_STATE for FP32 plans). Holograms are still rendered for
  *   the projection of Eqs. 6-7. */
+/*   2: C from the banded Gram of the store computed by dh_band_gram (below): windows of any
+ *   length and stride inside the band take their C from it without reading the holograms
+ *   again (DH_ERR_STATE for windows outside the band). 16-bit storage only. */
 #define DH_OPT_COVARIANCE 3
 dh_status dh_plan_set_option(dh_plan_t plan, int option, int value);
 dh_status dh_plan_get_option(dh_plan_t plan, int option, int *value);
@@ -163,6 +166,22 @@ dh_status dh_render_frames(dh_plan_t plan, const uint16_t *frames_dev,
 dh_status dh_pca_windows(dh_plan_t plan, int first_slot, int slot_stride, int n_windows,
                          int k0, int k1, float *images_dev, double *eigvals_dev,
                          void *stream);
+
+/* Banded covariance of a hologram store (16-bit storage): the real Gram of the rows Re H_f,
+ * Im H_f for every pair of frames fewer than 64 apart among slots [first_slot, first_slot +
+ * n_frames), computed once on the tensor cores (64-frame blocks b; the products X_b X_b^T and
+ * X_b X_{b+1}^T, so each frame is read three times). Every
+ * window of T <= 64 frames inside those slots -- any start, any stride, any plan over the
+ * store (a view, or the plan itself) with DH_OPT_COVARIANCE = 2 -- then takes its Eq. 4
+ * covariance from the band instead of reading its T frames again: for overlapping windows
+ * (sliding windows of several lengths) this replaces re-reading each frame once per window
+ * containing it. Call it on any plan of the store after rendering; it replaces the store's
+ * previous band (stream-ordered: windows enqueued before it on other streams must have
+ * finished). The first call (and a longer band) allocates the band buffers synchronously,
+ * so make it once before a graph capture; asynchronous otherwise. DH_ERR_STATE for FP32
+ * storage, DH_ERR_INVALID_ARG for slots outside the reservation. The paper computes C per
+ * window; this computes the whole sequence's band at once. */
+dh_status dh_band_gram(dh_plan_t plan, int first_slot, int n_frames, void *stream);
 
 /* Eqs. 8-9, the paper's Fourier alternative to Eqs. 4-7: temporal demodulation of each
  * window by the unitary DFT W, w_{t,k} = exp(-2 pi i t k / T) / sqrt(T) (t, k counted from

@@ -101,10 +101,17 @@ class Plan:
         for opt, val in ((0, 0 if persistent else 1), (1, int(ring)), (2, int(lag))):
             _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(self._h, opt, val))
 
-    def set_covariance_source(self, raw: bool) -> None:
-        """DH_OPT_COVARIANCE: C from the uint16 frames (exact, C = I^T I) where the call has
-        them, or from the holograms (Eq. 4 as written, the default)."""
-        _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(self._h, 3, 1 if raw else 0))
+    def set_covariance_source(self, source) -> None:
+        """DH_OPT_COVARIANCE: "holograms" (Eq. 4 as written, the default; also False), "raw"
+        (exact C = I^T I from the uint16 frames where the call has them; also True) or "band"
+        (the store's banded Gram, see band_gram)."""
+        mode = {False: 0, True: 1, "holograms": 0, "raw": 1, "band": 2}[source]
+        _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(self._h, 3, mode))
+
+    def band_gram(self, first_slot: int, n_frames: int, stream=None) -> None:
+        """dh_band_gram: the banded covariance of slots [first_slot, first_slot + n_frames)."""
+        _lib.check("dh_band_gram", self._lib.dh_band_gram(self._h, int(first_slot), int(n_frames),
+                                                           _stream_ptr(stream)))
 
     def render_schedule(self) -> dict:
         """The plan's render options: persistent (bool), ring and lag (0 = automatic)."""
@@ -263,7 +270,7 @@ class Plan:
 
     def profile_read(self) -> dict:
         """{kernel name: (launches, total device ms)} since the last read (synchronises)."""
-        n = 16
+        n = 64  # more than the library's kernel kinds (the call returns how many it has)
         names = (ctypes.c_char_p * n)()
         launches = (ctypes.c_int * n)()
         ms = (ctypes.c_double * n)()

@@ -53,6 +53,7 @@ SIGNATURES = [
     ("dh_render_frames", _i, [_vp, _vp, _i64, _i, _i, _vp]),
     ("dh_pca_windows", _i, [_vp, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
     ("dh_fourier_windows", _i, [_vp, _i, _i, _i, _i, _i, _vp, _vp]),
+    ("dh_band_gram", _i, [_vp, _i, _i, _vp]),
     ("dh_svd_fourier_windows", _i, [_vp, _i, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
     ("dh_render_stack", _i, [_vp, _vp, _i64, _vp]),
     ("dh_pca_window", _i, [_vp, _i, _i, _vp, _vp, _vp]),

@@ -144,6 +144,7 @@ dh_status alloc_windows(Plan &p) {
 // takes the store of `base` instead of allocating one.
 dh_status alloc_store(Plan &p, const Plan *base = nullptr) {
   free_store(p);
+  p.band_frames = 0;  // a new store has no band yet
   const StoreSizes z = store_sizes(p);
   // the host-buffer pipeline's buffers (kept across reservations) stay counted
   const size_t pipe = 2 * p.pipe.stage_elems * sizeof(uint16_t) + p.pipe.img_elems * sizeof(float) +
@@ -210,11 +211,17 @@ dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int 
     }
     const int fs = first_slot + w0 * slot_stride;
     int parts = 0;
-    if (raw && p.cov_raw) {
+    if (raw && p.cov_mode == 1) {
       st = launch_gram_raw(p, raw, raw_stride, (n_windows - 1) * slot_stride + p.T, w0 * slot_stride, slot_stride,
                            nw, &parts, s);
       if (st != DH_OK) return st;
       if ((st = launch_reduce_raw(p, nw, parts, w0, s)) != DH_OK) return st;
+    } else if (p.cov_mode == 2) {
+      const Plan *o = p.band_owner;
+      if (!o || o->band_frames == 0 || fs < o->band_first ||
+          (long long)fs + (long long)(nw - 1) * slot_stride + p.T > (long long)o->band_first + o->band_frames)
+        return DH_ERR_STATE;  // the windows are not inside the store's current band
+      if ((st = launch_band_cov(p, *o, fs, slot_stride, nw, w0, s)) != DH_OK) return st;
     } else {
       st = p.prec == DH_PREC_FP32 ? launch_gram_simt(p, fs, slot_stride, nw, &parts, s)
                                   : launch_gram_tc(p, fs, slot_stride, nw, &parts, s);
@@ -343,6 +350,7 @@ dh_status dh_plan_create(dh_plan_t *out, int nx, int ny, double lambda_m, double
   p.a = pitch_m * pitch_m / (lambda_m * z_m);
   p.max_frames = T;
   p.max_windows = 1;
+  p.band_owner = &p;
   cudaError_t e = cudaGetDevice(&p.device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p.aux, cudaStreamNonBlocking);
@@ -397,6 +405,7 @@ void release(dh_plan_t h) {
   for (cudaEvent_t ev : {q.start, q.done, q.finished, q.copied[0], q.copied[1], q.freed[0], q.freed[1]})
     if (ev) cudaEventDestroy(ev);
   dfree(q.stage[0]); dfree(q.stage[1]); dfree(q.img); dfree(q.eig);
+  dfree(p.d_band); dfree(p.d_band_part);
   dfree(p.d_cx); dfree(p.d_cy); dfree(p.d_twx); dfree(p.d_twy); dfree(p.d_status); dfree(p.d_sync);
   dh_plan *base = h->base;
   delete h;
@@ -430,6 +439,7 @@ dh_status dh_plan_create_view(dh_plan_t *out, dh_plan_t base_h, int T) {
   base_h->refs.fetch_add(1);
   base_h->views.fetch_add(1);
   h->base = base_h;
+  p.band_owner = &base_h->p;
   cudaError_t e = cudaStreamCreateWithFlags(&p.aux, cudaStreamNonBlocking);
   for (int k = 0; k < Plan::kMaxGroups && e == cudaSuccess; ++k) {
     e = cudaEventCreateWithFlags(&p.ev_grp[k], cudaEventDisableTiming);
@@ -457,7 +467,7 @@ dh_status dh_plan_set_precision(dh_plan_t h, dh_precision prec) {
   if (!g.ok) return DH_ERR_STATE;
   DH_CUDA_TRY(cudaDeviceSynchronize());
   h->p.prec = prec;
-  if (prec == DH_PREC_FP32) h->p.cov_raw = 0;
+  if (prec == DH_PREC_FP32) h->p.cov_mode = 0;
   return alloc_store(h->p);
 }
 
@@ -488,7 +498,7 @@ dh_status dh_plan_get_option(dh_plan_t h, int option, int *value) {
     case DH_OPT_RENDER_SCHEDULE: *value = h->p.render_mode; return DH_OK;
     case DH_OPT_RENDER_RING: *value = h->p.render_ring; return DH_OK;
     case DH_OPT_RENDER_LAG: *value = h->p.render_lag; return DH_OK;
-    case DH_OPT_COVARIANCE: *value = h->p.cov_raw; return DH_OK;
+    case DH_OPT_COVARIANCE: *value = h->p.cov_mode; return DH_OK;
   }
   return DH_ERR_INVALID_ARG;
 }
@@ -569,9 +579,9 @@ dh_status dh_plan_set_option(dh_plan_t h, int option, int value) {
       h->p.render_lag = value;
       return DH_OK;
     case DH_OPT_COVARIANCE:
-      if (value != 0 && value != 1) return DH_ERR_INVALID_ARG;
-      if (value == 1 && h->p.prec == DH_PREC_FP32) return DH_ERR_STATE;  // tensor-core path only
-      h->p.cov_raw = value;
+      if (value < 0 || value > 2) return DH_ERR_INVALID_ARG;
+      if (value != 0 && h->p.prec == DH_PREC_FP32) return DH_ERR_STATE;  // tensor-core paths only
+      h->p.cov_mode = value;
       return DH_OK;
   }
   return DH_ERR_INVALID_ARG;
@@ -648,6 +658,34 @@ dh_status dh_fourier_windows(dh_plan_t h, int first_slot, int slot_stride, int n
   if (!g.ok) return DH_ERR_STATE;
   return launch_fourier(p, first_slot, slot_stride, n_windows, k0, k1, images_dev,
                         static_cast<cudaStream_t>(stream));
+}
+
+dh_status dh_band_gram(dh_plan_t h, int first_slot, int n_frames, void *stream) {
+  if (!h || first_slot < 0 || n_frames < 1) return DH_ERR_INVALID_ARG;
+  dh_plan *root = h;
+  while (root->base) root = root->base;
+  Plan &p = root->p;
+  if (p.prec == DH_PREC_FP32) return DH_ERR_STATE;
+  if ((long long)first_slot + n_frames > p.max_frames) return DH_ERR_INVALID_ARG;
+  Busy g(root->busy);
+  if (!g.ok) return DH_ERR_STATE;
+  const int blocks = (n_frames + 63) / 64;
+  if (blocks > p.band_cap) {  // first use (or a longer band): allocate
+    DH_CUDA_TRY(cudaDeviceSynchronize());
+    dfree(p.d_band); dfree(p.d_band_part);
+    const size_t cell = 2ull * 128 * 128 * sizeof(double);
+    p.bytes -= (size_t)p.band_cap * cell * (1 + band_units(p.npix));
+    p.band_cap = 0;
+    dh_status st;
+    if ((st = dalloc(p, &p.d_band, (size_t)blocks * cell)) != DH_OK) return st;
+    if ((st = dalloc(p, &p.d_band_part, (size_t)blocks * band_units(p.npix) * cell)) != DH_OK) return st;
+    p.band_cap = blocks;
+  }
+  dh_status st = launch_band_gram(p, first_slot, n_frames, static_cast<cudaStream_t>(stream));
+  if (st != DH_OK) return st;
+  p.band_first = first_slot;
+  p.band_frames = n_frames;
+  return DH_OK;
 }
 
 dh_status dh_render_stack(dh_plan_t h, const uint16_t *frames_dev, int64_t frame_stride_elems,

@@ -39,7 +39,9 @@ struct Plan {
   // applies (square frames from 256^2), else chunks; 1 = always chunks of two launches
   int render_mode = 0;
   int render_ring = 0, render_lag = 0;  // persistent schedule: ring frames, lag (0 = automatic)
-  int cov_raw = 0;  // 1: covariance from the uint16 frames (C = I^T I) where the frames are at hand
+  // covariance source: 0 holograms (Eq. 4 as written), 1 the uint16 frames (C = I^T I) where
+  // the call has them, 2 the banded Gram of the store (dh_band_gram)
+  int cov_mode = 0;
   unsigned *d_sync = nullptr;  // ticket and ring counters of the persistent render
   // second stream: the eigensolver of one group of windows overlaps the next group's work
   cudaStream_t aux = nullptr;
@@ -62,7 +64,13 @@ struct Plan {
   // tensor maps for the tensor-core kernels (16-bit storage only)
   CUtensorMap tmap_H;
   CUtensorMap tmap_B;
+  CUtensorMap tmap_band;  // 64 pixels x 128 rows (64 frames) boxes, for the banded Gram
   bool tmaps_ok = false;
+  // banded Gram of the store (held by the plan that owns the store; views read the owner's)
+  const Plan *band_owner = nullptr;
+  double *d_band = nullptr, *d_band_part = nullptr;
+  int band_cap = 0;                     // 64-frame blocks the buffers hold
+  int band_first = 0, band_frames = 0;  // slots the current band covers
 
   // host-buffer pipeline (dh_pca_batch_host), created on first use: copy streams, two
   // staging buffers of frames, device images / eigenvalues of the batch
@@ -86,7 +94,7 @@ struct Plan {
 enum KernelId {
   K_RENDER_ROWS = 0, K_RENDER_COLS, K_GRAM_SIMT, K_GRAM_TC, K_REDUCE_COV, K_JACOBI,
   K_PROJECT_SIMT, K_PROJECT_TC, K_FOURIER_OP, K_SVD_FOURIER_OP, K_RENDER_FUSED, K_GRAM_RAW,
-  K_REDUCE_RAW, K_FOURIER_SLIDING, K_COUNT
+  K_REDUCE_RAW, K_FOURIER_SLIDING, K_BAND_GRAM, K_BAND_REDUCE, K_BAND_COV, K_COUNT
 };
 const char *kernel_name(int kid);
 dh_status profile_enable(Plan &p, int on);
@@ -144,6 +152,12 @@ dh_status launch_gram_raw(Plan &p, const uint16_t *frames, long long frame_strid
                           int first_frame, int window_stride, int n_windows, int *parts_per_window,
                           cudaStream_t s);
 dh_status launch_reduce_raw(Plan &p, int n_windows, int parts_per_window, int woff, cudaStream_t s);
+// Banded Gram of slots [first_slot, first_slot + n_frames) into p.d_band (16-bit storage), and
+// the covariance of windows [woff, woff + n_windows) of plan p assembled from owner's band.
+int band_units(long long npix);
+dh_status launch_band_gram(Plan &p, int first_slot, int n_frames, cudaStream_t s);
+dh_status launch_band_cov(Plan &p, const Plan &owner, int first_slot, int slot_stride, int n_windows, int woff,
+                          cudaStream_t s);
 // Eq. 4 final FP64 reduction, then Eq. 5 + ordering + operand build for Eq. 6, for windows
 // [woff, woff + n_windows) of the plan's per-window buffers.
 dh_status launch_reduce(Plan &p, int n_windows, int parts_per_window, int woff, cudaStream_t s);

@@ -826,6 +826,8 @@ dh_status make_tensor_maps(Plan &p) {
   const uint32_t box[3] = {64, (uint32_t)(2 * p.T), 1};
   dh_status st = encode_3d(&p.tmap_H, p.d_H, bf16, dims, strides, box);
   if (st != DH_OK) return st;
+  const uint32_t box_band[3] = {64, 128, 1};  // one 64-frame block of the banded Gram
+  if ((st = encode_3d(&p.tmap_band, p.d_H, bf16, dims, strides, box_band)) != DH_OK) return st;
   p.tmaps_ok = true;
   return DH_OK;
 }

@@ -203,3 +203,62 @@ def test_batch_orders_a_rerender_after_its_readers(dh):
             assert torch.equal(img, out[key]), key
     v32.close()
     base.close()
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_band_covariance_serves_every_length(dh, prec):
+    """dh_band_gram once over the store, then 16/32/64-frame windows at stride 8 (and one
+    window at an odd offset) take C from it: equal to the per-window Gram within FP32
+    accumulation (3e-6), and the windows' images and eigenvalues match the oracle."""
+    F = 200
+    frames = SpeckleStream(SpeckleParams(128, 128), seed=27).next(F).numpy()
+    base = dh.Plan(128, 128, LAM, Z, PITCH, T=16, precision=prec, max_frames=F, max_windows=24)
+    base.render_frames(to_gpu(frames))
+    base.band_gram(0, F)
+    for T in LENGTHS:
+        n = (F - T) // STRIDE + 1
+        band_plan = base if T == 16 else base.view(T, n)
+        ref_plan = base.view(T, n)
+        band_plan.set_covariance_source("band")
+        img_b, lam_b = band_plan.pca_windows(0, STRIDE, n, 2, T - 1)
+        Cb = [band_plan.debug_covariance(w).cpu().numpy() for w in range(n)]
+        img_r, lam_r = ref_plan.pca_windows(0, STRIDE, n, 2, T - 1)
+        Cr = [ref_plan.debug_covariance(w).cpu().numpy() for w in range(n)]
+        for w in range(n):
+            assert np.linalg.norm(Cb[w] - Cr[w]) <= 3e-6 * np.linalg.norm(Cr[w]), (T, w)
+        if prec == "fp16":
+            img_b, lam_b = img_b.cpu().numpy(), lam_b.cpu().numpy()
+            for w in (0, n // 2, n - 1):
+                check_window(img_b[w], lam_b[w], Cb[w], frames[w * STRIDE:w * STRIDE + T], 2, T - 1,
+                             prec)
+        # a window at an offset that is not a multiple of 8, inside the band
+        img1, _ = band_plan.pca_windows(37, 1, 1, 2, T - 1)
+        C1 = band_plan.debug_covariance(0).cpu().numpy()
+        ref1, _ = ref_plan.pca_windows(37, 1, 1, 2, T - 1)
+        C1r = ref_plan.debug_covariance(0).cpu().numpy()
+        assert np.linalg.norm(C1 - C1r) <= 3e-6 * np.linalg.norm(C1r)
+        if band_plan is not base:
+            band_plan.close()
+        ref_plan.close()
+    assert base.status() == 0
+    base.close()
+
+
+def test_band_rules(dh):
+    frames = to_gpu(SpeckleStream(SpeckleParams(64, 64), seed=28).next(96).numpy())
+    base = dh.Plan(64, 64, LAM, Z, PITCH, T=32, precision="fp16", max_frames=96, max_windows=4)
+    base.render_frames(frames)
+    base.set_covariance_source("band")
+    with pytest.raises(dh.DHError) as e:      # no band yet
+        base.pca_windows(0, 8, 2, 2, 31)
+    assert e.value.code == 7
+    base.band_gram(0, 64)
+    base.pca_windows(0, 8, 2, 2, 31)          # frames 0..39: inside
+    with pytest.raises(dh.DHError) as e:      # frames 40..71 reach past the band
+        base.pca_windows(40, 8, 1, 2, 31)
+    assert e.value.code == 7
+    base.close()
+    with dh.Plan(64, 64, LAM, Z, PITCH, T=16) as p32:
+        with pytest.raises(dh.DHError) as e:
+            p32.band_gram(0, 16)
+        assert e.value.code == 7
