@@ -504,6 +504,18 @@ def timed_graph(graph, stream, steps, ws, local):
 SLIDE_FRAMES, SLIDE_STRIDE, SLIDE_LENGTHS = 2048, 8, (16, 32, 64)
 
 
+def span_bytes(F, npix):
+    """Hologram bytes the grouped projection reads per step: groups of 8 windows at stride 8,
+    each group's span of T + 56 frames once (4 bytes a pixel: Re, Im FP16)."""
+    total = 0
+    for L in SLIDE_LENGTHS:
+        n = (F - L) // SLIDE_STRIDE + 1
+        for g0 in range(0, n, 8):
+            gw = min(8, n - g0)
+            total += (L + (gw - 1) * SLIDE_STRIDE) * npix * 4
+    return total
+
+
 def run_sliding(args, ws, rank, local):
     """16-, 32- and 64-frame windows at stride 8 over 2048 frames of 1024^2: each frame is
     rendered once into a FP16 store read by all three window lengths (views), and the whole
@@ -545,6 +557,8 @@ def run_sliding(args, ws, rank, local):
     if args.band:
         for p in plans.values():
             p.set_covariance_source("band")
+    for p in plans.values():
+        p.set_projection(args.projection == "grouped")
     items = [{"plan": plans[L], "n_windows": n[L], "first_slot": 0, "slot_stride": SLIDE_STRIDE,
               "k0": 2, "k1": L - 1, "images": images[L], "eigvals": eig[L]} for L in (64, 32, 16)]
 
@@ -554,12 +568,13 @@ def run_sliding(args, ws, rank, local):
             base.band_gram(0, F)
         dh.run_batch(items)
 
-    # traced once more in the timed form's covariance mode, one stage after the other
-    if args.band:
+    # traced once more in the timed form's covariance and projection modes, stage by stage
+    if args.band or args.projection == "grouped":
         for p in plans.values():
             p.profile(True)
         base.render_frames(frames)
-        base.band_gram(0, F)
+        if args.band:
+            base.band_gram(0, F)
         for L in SLIDE_LENGTHS:
             plans[L].pca_windows(0, SLIDE_STRIDE, n[L], 2, L - 1, images[L], eig[L])
         per_kernel = merge_tables([kernel_table(p.profile_read())[0] for p in plans.values()])
@@ -583,7 +598,8 @@ def run_sliding(args, ws, rank, local):
     gram = sum(n[L] * L * npix * 4 for L in SLIDE_LENGTHS)
     alg = {"render_rows": F * npix * 2, "render_cols": F * npix * 4, "render_fused": F * npix * 6,
            "gram_tc": gram, "project_tc": gram + nwin * npix * 4,
-           "band_gram": 3 * F * npix * 4}  # each frame read as block b (twice) and as b + 1
+           "band_gram": 3 * F * npix * 4,
+           "project_span": span_bytes(F, npix) + nwin * npix * 4}  # each frame read as block b (twice) and as b + 1
     fl = render_flops(npix, NX, NY, F)
     roofline = roofline_of(per_kernel, alg, hbm, peak_kind, ms / 1e3, {k: fl for k in RENDER_KERNELS})
 
@@ -612,6 +628,9 @@ def run_sliding(args, ws, rank, local):
                                    "the lengths run concurrently, one CUDA graph per step",
                        "covariance": "banded Gram of the store (dh_band_gram)" if args.band
                        else "one Gram per window",
+                       "projection": "grouped: 8 windows per tile load, energy minus discarded "
+                                     "components" if args.projection == "grouped"
+                       else "per window (Eq. 7 over the kept components)",
                        "windows_per_step": n, "k0": 2, "k1": "T-1",
                        "l2": "no flush: 4 GiB of frames and 8 GiB of holograms per step",
                        "parallelism": f"replicas x{ws}"},
@@ -1065,6 +1084,8 @@ def main(argv=None):
     ap.add_argument("--band", action=argparse.BooleanOptionalAction, default=True,
                     help="sliding workload: windows take C from the store's banded Gram "
                          "(dh_band_gram) instead of one Gram per window")
+    ap.add_argument("--projection", choices=["grouped", "per-window"], default="grouped",
+                    help="sliding workload: DH_OPT_PROJECTION (grouped = 0, per-window = 1)")
     ap.add_argument("--covariance", choices=["holograms", "raw"], default="holograms",
                     help="Eq. 4 from the holograms (as written, default) or exactly from the uint16 "
                          "frames (DH_OPT_COVARIANCE = 1, C = I^T I)")

@@ -108,6 +108,12 @@ class Plan:
         mode = {False: 0, True: 1, "holograms": 0, "raw": 1, "band": 2}[source]
         _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(self._h, 3, mode))
 
+    def set_projection(self, grouped: bool = True) -> None:
+        """DH_OPT_PROJECTION: grouped (the default: overlapping windows share their tile loads
+        and take the power as energy minus the discarded components' power, where that
+        applies) or per window (False: Eq. 7 over the kept components, always)."""
+        _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(self._h, 4, 0 if grouped else 1))
+
     def band_gram(self, first_slot: int, n_frames: int, stream=None) -> None:
         """dh_band_gram: the banded covariance of slots [first_slot, first_slot + n_frames)."""
         _lib.check("dh_band_gram", self._lib.dh_band_gram(self._h, int(first_slot), int(n_frames),

@@ -114,7 +114,8 @@ StoreSizes store_sizes(const Plan &p) {
   // operand of Eq. 6 per window: FP32 [2T][2T], or 16-bit hi and lo [2][2T][2T]
   const size_t bw = p.prec == DH_PREC_FP32 ? (size_t)M * M * 4 : (size_t)2 * M * M * 2;
   z.B_window = (bw + 1023) / 1024 * 1024;
-  z.B = z.B_window * p.max_windows;
+  // + room for the last group's operand of the grouped projection (at most 64 KiB)
+  z.B = z.B_window * p.max_windows + (p.prec == DH_PREC_FP32 ? 0 : (64u << 10));
   z.W = z.B_window;  // one operand shared by every window (Eq. 8)
   return z;
 }
@@ -193,6 +194,8 @@ dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int 
   const int G = 1;
   const int nS = b0 >= 0 ? b1 - b0 + 1 : k1 - k0 + 1;  // projected columns
   const int nop = p.prec == DH_PREC_FP32 ? 2 * nS : (2 * nS + 15) / 16 * 16;  // operand rows
+  // overlapping windows: grouped projection (one group layout for the whole call)
+  const SpanLayout span = b0 < 0 ? span_layout(p, slot_stride, n_windows, k0, k1) : SpanLayout{};
   int w0s[Plan::kMaxGroups], nws[Plan::kMaxGroups];
   int rendered = 0;  // frames (slots relative to first_slot) already rendered
   dh_status st;
@@ -230,7 +233,8 @@ dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int 
     }
     DH_CUDA_TRY(cudaEventRecord(p.ev_grp[g], s));
     DH_CUDA_TRY(cudaStreamWaitEvent(p.aux, p.ev_grp[g], 0));
-    st = launch_jacobi(p, nw, k0, k1, nop, eig_user ? eig_user + (long long)w0 * p.T : nullptr, w0, p.aux);
+    st = launch_jacobi(p, nw, k0, k1, nop, eig_user ? eig_user + (long long)w0 * p.T : nullptr, w0, p.aux,
+                       span.G > 0 ? &span : nullptr);
     if (st != DH_OK) return st;
     if (b0 >= 0 && (st = launch_svd_fourier_operand(p, nw, k0, k1, b0, b1, nop, w0, p.aux)) != DH_OK)
       return st;
@@ -241,8 +245,11 @@ dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int 
     DH_CUDA_TRY(cudaStreamWaitEvent(s, p.ev_jac[g], 0));
     const int fs = first_slot + w0s[g] * slot_stride;
     float *img = images + (long long)w0s[g] * p.npix;
-    st = p.prec == DH_PREC_FP32 ? launch_project_simt(p, fs, slot_stride, nws[g], nop, img, w0s[g], s)
-                                : launch_project_tc(p, fs, slot_stride, nws[g], nop, img, w0s[g], s);
+    if (span.G > 0)
+      st = launch_project_span(p, span, fs, nws[g], img, w0s[g], s);
+    else
+      st = p.prec == DH_PREC_FP32 ? launch_project_simt(p, fs, slot_stride, nws[g], nop, img, w0s[g], s)
+                                  : launch_project_tc(p, fs, slot_stride, nws[g], nop, img, w0s[g], s);
     if (st != DH_OK) return st;
   }
   return DH_OK;
@@ -499,6 +506,7 @@ dh_status dh_plan_get_option(dh_plan_t h, int option, int *value) {
     case DH_OPT_RENDER_RING: *value = h->p.render_ring; return DH_OK;
     case DH_OPT_RENDER_LAG: *value = h->p.render_lag; return DH_OK;
     case DH_OPT_COVARIANCE: *value = h->p.cov_mode; return DH_OK;
+    case DH_OPT_PROJECTION: *value = h->p.proj_mode; return DH_OK;
   }
   return DH_ERR_INVALID_ARG;
 }
@@ -582,6 +590,10 @@ dh_status dh_plan_set_option(dh_plan_t h, int option, int value) {
       if (value < 0 || value > 2) return DH_ERR_INVALID_ARG;
       if (value != 0 && h->p.prec == DH_PREC_FP32) return DH_ERR_STATE;  // tensor-core paths only
       h->p.cov_mode = value;
+      return DH_OK;
+    case DH_OPT_PROJECTION:
+      if (value != 0 && value != 1) return DH_ERR_INVALID_ARG;
+      h->p.proj_mode = value;
       return DH_OK;
   }
   return DH_ERR_INVALID_ARG;

@@ -42,6 +42,9 @@ struct Plan {
   // covariance source: 0 holograms (Eq. 4 as written), 1 the uint16 frames (C = I^T I) where
   // the call has them, 2 the banded Gram of the store (dh_band_gram)
   int cov_mode = 0;
+  // projection of Eqs. 6-7: 0 = automatic (overlapping windows share their tile loads and use
+  // the complement of the discarded components where that applies), 1 = per window always
+  int proj_mode = 0;
   unsigned *d_sync = nullptr;  // ticket and ring counters of the persistent render
   // second stream: the eigensolver of one group of windows overlaps the next group's work
   cudaStream_t aux = nullptr;
@@ -94,7 +97,7 @@ struct Plan {
 enum KernelId {
   K_RENDER_ROWS = 0, K_RENDER_COLS, K_GRAM_SIMT, K_GRAM_TC, K_REDUCE_COV, K_JACOBI,
   K_PROJECT_SIMT, K_PROJECT_TC, K_FOURIER_OP, K_SVD_FOURIER_OP, K_RENDER_FUSED, K_GRAM_RAW,
-  K_REDUCE_RAW, K_FOURIER_SLIDING, K_BAND_GRAM, K_BAND_REDUCE, K_BAND_COV, K_COUNT
+  K_REDUCE_RAW, K_FOURIER_SLIDING, K_BAND_GRAM, K_BAND_REDUCE, K_BAND_COV, K_PROJECT_SPAN, K_COUNT
 };
 const char *kernel_name(int kid);
 dh_status profile_enable(Plan &p, int on);
@@ -161,8 +164,27 @@ dh_status launch_band_cov(Plan &p, const Plan &owner, int first_slot, int slot_s
 // Eq. 4 final FP64 reduction, then Eq. 5 + ordering + operand build for Eq. 6, for windows
 // [woff, woff + n_windows) of the plan's per-window buffers.
 dh_status launch_reduce(Plan &p, int n_windows, int parts_per_window, int woff, cudaStream_t s);
+// Layout of the grouped projection of overlapping windows (csrc/project_span.cu): G windows
+// of slot stride `stride` per group, each group's banded operand (hi + lo 16-bit images of
+// n_pad x k_pad, 128-byte swizzled, `img_bytes` in all) stored in the operand slots of its
+// windows; G = 0 when the per-window projection is used.
+// 3-D tiled tensor map over 16-bit data (128-byte swizzle, zero fill out of bounds).
+dh_status encode_3d(CUtensorMap *map, void *base, bool bf16, const uint64_t dims[3],
+                    const uint64_t strides_bytes[2], const uint32_t box[3]);
+// Scale of the grouped projection's operand entries (a power of two; see k_span_operand).
+constexpr double kSpanOperandScale = 1024.0;
+struct SpanLayout {
+  int G = 0, cpw = 0, rows = 0, n_pad = 0, k_pad = 0, stride = 0, img_bytes = 0, stages = 0;
+  int nacc = 0, tmem_cols = 0;  // partial accumulators per buffer; TMEM columns allocated
+  int scr_bytes = 0;            // shared scratch of per-pixel chunk energies
+};
+SpanLayout span_layout(const Plan &p, int slot_stride, int n_windows, int k0, int k1);
+dh_status launch_project_span(Plan &p, const SpanLayout &sl, int first_slot, int n_windows, float *images,
+                              int woff, cudaStream_t s);
+// With span (G > 0) the eigensolver writes the discarded components' banded group operand
+// instead of the per-window operand of Eq. 6.
 dh_status launch_jacobi(Plan &p, int n_windows, int k0, int k1, int Npad, double *eig_user, int woff,
-                        cudaStream_t s);
+                        cudaStream_t s, const SpanLayout *span = nullptr);
 // Eqs. 6-7 (and 8-9).
 // images points at window woff's image; woff selects the windows' operands, unless
 // shared_op is given: then every window projects onto that one operand (one window's

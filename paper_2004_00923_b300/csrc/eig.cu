@@ -363,6 +363,46 @@ k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restr
   }
 }
 
+// Operand of the grouped projection of overlapping windows (csrc/project_span.cu): window w's
+// CPW columns of its group's banded operand (group of G windows, slot stride s), from its
+// sorted eigenvectors V (FP64, [T][T] re/im). Column 2d + c of the window holds discarded
+// component d (k < k0 first, then k > k1; zero past the last) as the real embedding row of
+// Eq. 6 (c = 0: Re, c = 1: Im) at span rows 2 (s g + t) + {0, 1}, zeros elsewhere; stored as
+// hi + lo 16-bit images of n_pad x k_pad in the K-major 128-byte-swizzled order the tensor
+// cores read (64-element sub-blocks; the 16-byte chunk index XOR row % 8). The values are
+// scaled by 2^10 (kSpanOperandScale) so that the lo part of an entry near 1/sqrt(T) stays a
+// normal FP16 number: unscaled, it falls below 2^-14 and keeps only a few bits, which limits
+// V to ~21 bits; the projection multiplies the squared products back by 2^-20, exactly.
+__global__ void k_span_operand(const double *__restrict__ V, int T, int n_windows, int k0, int k1, SpanLayout sp,
+                               int bf16, void *__restrict__ Bop, long long B_stride) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int per = sp.cpw * sp.k_pad;
+  if (idx >= n_windows * per) return;
+  const int w = idx / per, e = idx % per;
+  const int g = w % sp.G;
+  const int nD = k0 + (T - 1 - k1);
+  const int nl = e / sp.k_pad, r = e % sp.k_pad;
+  const int d = nl >> 1, c = nl & 1;                 // discarded component d; Re / Im column
+  const int t = (r >> 1) - sp.stride * g, cc = r & 1;  // window frame t; Re / Im row
+  double v = 0.0;
+  if (d < nD && t >= 0 && t < T) {
+    const int k = d < k0 ? d : k1 + 1 + (d - k0);
+    const double re = V[2 * ((long long)w * T * T + t * T + k)], im = V[2 * ((long long)w * T * T + t * T + k) + 1];
+    v = (c == 0 ? (cc == 0 ? re : -im) : (cc == 0 ? im : re)) * kSpanOperandScale;
+  }
+  const int n = g * sp.cpw + nl, sub = r >> 6, kk = r & 63;
+  const long long i =
+      ((long long)sub * sp.n_pad * 128 + n * 128 + (((kk >> 3) ^ (n & 7)) << 4) + ((kk & 7) << 1)) >> 1;
+  const long long img = (long long)sp.n_pad * sp.k_pad;  // elements of one of hi / lo
+  if (bf16) {
+    __nv_bfloat16 *hi = static_cast<__nv_bfloat16 *>(Bop) + (long long)(w - g) * B_stride;
+    put_split<__nv_bfloat16>(hi, hi + img, i, v);
+  } else {
+    __half *hi = static_cast<__half *>(Bop) + (long long)(w - g) * B_stride;
+    put_split<__half>(hi, hi + img, i, v);
+  }
+}
+
 template <int T>
 dh_status launch_reduce_t(Plan &p, int n_windows, int parts, int woff, cudaStream_t s) {
   const int total = n_windows * T * T;
@@ -375,7 +415,8 @@ dh_status launch_reduce_t(Plan &p, int n_windows, int parts, int woff, cudaStrea
 
 template <int T>
 dh_status launch_jacobi_t(Plan &p, int n_windows, int k0, int k1, int Npad, double *eig_user, int woff,
-                          cudaStream_t s) {
+                          cudaStream_t s, const SpanLayout *span) {
+  if (span) Npad = 0;  // the grouped projection's operand is written below instead
   const size_t smem = 6ull * T * (T + 1) * sizeof(double);
   static bool attr = false;
   if (!attr) {
@@ -389,6 +430,14 @@ dh_status launch_jacobi_t(Plan &p, int n_windows, int k0, int k1, int Npad, doub
                                            p.d_V + 2ll * woff * T * T, eig_user, (int)p.prec, B, B_stride,
                                            k0, k1, Npad, DH_EIG_TOL, 30, p.d_status);
   DH_CUDA_TRY(cudaGetLastError());
+  if (span) {
+    const int total = n_windows * span->cpw * span->k_pad;
+    const long long B_stride = (long long)(p.B_window_bytes / 2);
+    void *B = static_cast<char *>(p.d_B) + (size_t)woff * p.B_window_bytes;
+    k_span_operand<<<(total + 255) / 256, 256, 0, s>>>(p.d_V + 2ll * woff * T * T, T, n_windows, k0, k1,
+                                                       *span, p.prec == DH_PREC_BF16, B, B_stride);
+    DH_CUDA_TRY(cudaGetLastError());
+  }
   return DH_OK;
 }
 
@@ -437,11 +486,11 @@ dh_status launch_reduce(Plan &p, int n_windows, int parts, int woff, cudaStream_
 // Eq. 5 + ordering + operand build for windows [woff, woff + n_windows); eig_user (if not
 // NULL) already points at window woff's eigenvalues.
 dh_status launch_jacobi(Plan &p, int n_windows, int k0, int k1, int Npad, double *eig_user, int woff,
-                        cudaStream_t s) {
+                        cudaStream_t s, const SpanLayout *span) {
   switch (p.T) {
-    case 16: return launch_jacobi_t<16>(p, n_windows, k0, k1, Npad, eig_user, woff, s);
-    case 32: return launch_jacobi_t<32>(p, n_windows, k0, k1, Npad, eig_user, woff, s);
-    case 64: return launch_jacobi_t<64>(p, n_windows, k0, k1, Npad, eig_user, woff, s);
+    case 16: return launch_jacobi_t<16>(p, n_windows, k0, k1, Npad, eig_user, woff, s, span);
+    case 32: return launch_jacobi_t<32>(p, n_windows, k0, k1, Npad, eig_user, woff, s, span);
+    case 64: return launch_jacobi_t<64>(p, n_windows, k0, k1, Npad, eig_user, woff, s, span);
   }
   return DH_ERR_UNSUPPORTED_SIZE;
 }

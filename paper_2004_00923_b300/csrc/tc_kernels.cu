@@ -670,19 +670,6 @@ dh_status encode_2d(CUtensorMap *map, void *base, bool bf16, uint64_t inner, uin
   return r == CUDA_SUCCESS ? DH_OK : DH_ERR_CUDA;
 }
 
-dh_status encode_3d(CUtensorMap *map, void *base, bool bf16, const uint64_t dims[3],
-                    const uint64_t strides_bytes[2], const uint32_t box[3]) {
-  auto fn = encode_fn();
-  if (!fn) return DH_ERR_CUDA;
-  const cuuint64_t d[3] = {dims[0], dims[1], dims[2]};
-  const cuuint64_t st[2] = {strides_bytes[0], strides_bytes[1]};
-  const cuuint32_t b[3] = {box[0], box[1], box[2]};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, d,
-                  st, b, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? DH_OK : DH_ERR_CUDA;
-}
 
 // CTAs of `kern` that fit on one SM by shared memory (with the maximum carveout, which these
 // kernels request) and by registers. The runtime's occupancy query assumes the default
@@ -813,6 +800,20 @@ dh_status gram_raw_t(Plan &p, const uint16_t *frames, long long frame_stride, in
 
 
 }  // namespace
+
+dh_status encode_3d(CUtensorMap *map, void *base, bool bf16, const uint64_t dims[3],
+                    const uint64_t strides_bytes[2], const uint32_t box[3]) {
+  auto fn = encode_fn();
+  if (!fn) return DH_ERR_CUDA;
+  const cuuint64_t d[3] = {dims[0], dims[1], dims[2]};
+  const cuuint64_t st[2] = {strides_bytes[0], strides_bytes[1]};
+  const cuuint32_t b[3] = {box[0], box[1], box[2]};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, d,
+                  st, b, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? DH_OK : DH_ERR_CUDA;
+}
 
 int gram_tc_parts(const Plan &p) { return gram_tc_units(p.npix) * (128 / (2 * p.T)); }
 
