@@ -13,11 +13,7 @@
 //   and the retained columns k0..k1 are packed into the operand of Eq. 6.
 #include "dh_internal.cuh"
 
-// FP64 phase of the eigensolver: Lowdin re-orthonormalisation steps, and the off(A) / ||C||_F
-// at which the FP64 sweeps stop.
-#ifndef DH_LOWDIN_PASSES
-#define DH_LOWDIN_PASSES 2
-#endif
+// FP64 phase of the eigensolver: the off(A) / ||C||_F at which the FP64 sweeps stop.
 #ifndef DH_EIG_TOL
 #define DH_EIG_TOL 1e-12
 #endif
@@ -101,6 +97,17 @@ __device__ __forceinline__ void put_split(T16 *hi, T16 *lo, long long i, double 
   lo[i] = from_f32<T16>((float)(v - (double)to_f32<T16>(h)));
 }
 
+// Upper-triangle element e (row-major, rows of T - i elements) -> (i, j), i <= j.
+__device__ __forceinline__ void tri_ij(int e, int T, int &i, int &j) {
+  const float b = 2.0f * T + 1.0f;
+  int r = (int)((b - sqrtf(b * b - 8.0f * e)) * 0.5f);
+  int start = r * T - r * (r - 1) / 2;
+  if (start > e) { --r; start = r * T - r * (r - 1) / 2; }
+  else if (start + (T - r) <= e) { start += T - r; ++r; }
+  i = r;
+  j = r + (e - start);
+}
+
 // Parallel-order two-sided complex Jacobi sweeps on the Hermitian matrix (ar, ai) (row
 // stride LD), accumulating the rotations into (vr, vi). Real = float or double. Returns the
 // number of sweeps taken, or -1 if off(A) > tol ||A||_F after max_sweeps.
@@ -111,7 +118,16 @@ __device__ int jacobi_sweeps(Real *ar, Real *ai, Real *vr, Real *vi, double tol,
   constexpr int LD = T + 1;
   __shared__ Real rc[NP], rwr[NP], rwi[NP];
   __shared__ int rp[NP], rq[NP];
+  __shared__ unsigned short blk[NP * (NP + 1) / 2];  // pair blocks (P << 8 | Q), P <= Q
   const int tid = threadIdx.x;
+  if constexpr (sizeof(Real) == 8 && T == 64) {
+    for (int e = tid; e < NP * (NP + 1) / 2; e += blockDim.x) {
+      int P, Q;
+      tri_ij(e, NP, P, Q);
+      blk[e] = (unsigned short)(P << 8 | Q);
+    }
+    __syncthreads();
+  }
   for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
     double off2 = 0.0;
     for (int e = tid; e < T * T; e += blockDim.x) {
@@ -131,8 +147,20 @@ __device__ int jacobi_sweeps(Real *ar, Real *ai, Real *vr, Real *vi, double tol,
         else { a = (step + tid) % (T - 1); b = (step - tid + T - 1) % (T - 1); }
         const int p = a < b ? a : b, q = a < b ? b : a;
         const Real gr = ar[p * LD + q], gi = ai[p * LD + q];
-        const Real g = sqrt(gr * gr + gi * gi);
         Real c = 1, wr = 0, wi = 0;
+        if constexpr (sizeof(Real) == 4) {
+          const float g2 = gr * gr + gi * gi;
+          if (g2 > (float)(1e-2 * tol * fro / T) * (float)(1e-2 * tol * fro / T)) {
+            const float rg = rsqrtf(g2);
+            const float tau = (ar[q * LD + q] - ar[p * LD + p]) * 0.5f * rg;
+            const float t = __fdividef(copysignf(1.f, tau), fabsf(tau) + sqrtf(1.f + tau * tau));
+            c = rsqrtf(1.f + t * t);
+            const float sn = t * c * rg;
+            wr = sn * gr;
+            wi = sn * gi;
+          }
+        } else {
+        const Real g = sqrt(gr * gr + gi * gi);
         // rotations this small cannot hold off(A) above tol ||A||_F; they are skipped
         if (g > (Real)(1e-2 * tol * fro / T)) {
           const Real tau = (ar[q * LD + q] - ar[p * LD + p]) / (2 * g);
@@ -142,46 +170,110 @@ __device__ int jacobi_sweeps(Real *ar, Real *ai, Real *vr, Real *vi, double tol,
           wr = sn * gr / g;
           wi = sn * gi / g;
         }
+        }
         rp[tid] = p; rq[tid] = q; rc[tid] = c; rwr[tid] = wr; rwi[tid] = wi;
       }
       __syncthreads();
-      // columns of A and V: X_ip' = c X_ip - conj(w) X_iq ;  X_iq' = w X_ip + c X_iq
-      for (int it = tid; it < NP * T; it += blockDim.x) {
-        const int k = it / T, i = it % T;
-        const Real c = rc[k], wr = rwr[k], wi = rwi[k];
-        if (wr == 0 && wi == 0) continue;
-        const int p = rp[k], q = rq[k];
-        Real xpr = ar[i * LD + p], xpi = ai[i * LD + p], xqr = ar[i * LD + q], xqi = ai[i * LD + q];
-        ar[i * LD + p] = c * xpr - (wr * xqr + wi * xqi);
-        ai[i * LD + p] = c * xpi - (wr * xqi - wi * xqr);
-        ar[i * LD + q] = (wr * xpr - wi * xpi) + c * xqr;
-        ai[i * LD + q] = (wr * xpi + wi * xpr) + c * xqi;
-        xpr = vr[i * LD + p]; xpi = vi[i * LD + p]; xqr = vr[i * LD + q]; xqi = vi[i * LD + q];
-        vr[i * LD + p] = c * xpr - (wr * xqr + wi * xqi);
-        vi[i * LD + p] = c * xpi - (wr * xqi - wi * xqr);
-        vr[i * LD + q] = (wr * xpr - wi * xpi) + c * xqr;
-        vi[i * LD + q] = (wr * xpi + wi * xpr) + c * xqi;
+      if constexpr (sizeof(Real) == 4 || T < 64) {
+        // FP32 (latency-bound), and FP64 below T = 64 (too little work per step for the block
+        // form's bookkeeping to pay; measured): a column pass over A and V, then a row pass.
+        // columns of A and V: X_ip' = c X_ip - conj(w) X_iq ;  X_iq' = w X_ip + c X_iq
+        for (int it = tid; it < NP * T; it += blockDim.x) {
+          const int k = it / T, i = it % T;
+          const Real c = rc[k], wr = rwr[k], wi = rwi[k];
+          if (wr == 0 && wi == 0) continue;
+          const int p = rp[k], q = rq[k];
+          Real xpr = ar[i * LD + p], xpi = ai[i * LD + p], xqr = ar[i * LD + q], xqi = ai[i * LD + q];
+          ar[i * LD + p] = c * xpr - (wr * xqr + wi * xqi);
+          ai[i * LD + p] = c * xpi - (wr * xqi - wi * xqr);
+          ar[i * LD + q] = (wr * xpr - wi * xpi) + c * xqr;
+          ai[i * LD + q] = (wr * xpi + wi * xpr) + c * xqi;
+          xpr = vr[i * LD + p]; xpi = vi[i * LD + p]; xqr = vr[i * LD + q]; xqi = vi[i * LD + q];
+          vr[i * LD + p] = c * xpr - (wr * xqr + wi * xqi);
+          vi[i * LD + p] = c * xpi - (wr * xqi - wi * xqr);
+          vr[i * LD + q] = (wr * xpr - wi * xpi) + c * xqr;
+          vi[i * LD + q] = (wr * xpi + wi * xpr) + c * xqi;
+        }
+        __syncthreads();
+        // rows of A: A_pj' = c A_pj - w A_qj ;  A_qj' = conj(w) A_pj + c A_qj
+        for (int it = tid; it < NP * T; it += blockDim.x) {
+          const int k = it / T, j = it % T;
+          const Real c = rc[k], wr = rwr[k], wi = rwi[k];
+          if (wr == 0 && wi == 0) continue;
+          const int p = rp[k], q = rq[k];
+          const Real xpr = ar[p * LD + j], xpi = ai[p * LD + j], xqr = ar[q * LD + j], xqi = ai[q * LD + j];
+          ar[p * LD + j] = c * xpr - (wr * xqr - wi * xqi);
+          ai[p * LD + j] = c * xpi - (wr * xqi + wi * xqr);
+          ar[q * LD + j] = (wr * xpr + wi * xpi) + c * xqr;
+          ai[q * LD + j] = (wr * xpi - wi * xpr) + c * xqi;
+        }
+        __syncthreads();
+        if (tid < NP) {
+          const int p = rp[tid], q = rq[tid];
+          ar[p * LD + q] = ai[p * LD + q] = ar[q * LD + p] = ai[q * LD + p] = 0;
+          ai[p * LD + p] = ai[q * LD + q] = 0;
+        }
+        __syncthreads();
+      } else {
+        // FP64 at T = 64 (bound by the FP64 pipe): half the arithmetic on A (measured 13% off
+        // the FP64 sweeps).
+        // A <- K^H A K and V <- V K, K the T/2 disjoint rotations of this step: column op
+        // x_p' = c x_p - conj(w) x_q, x_q' = w x_p + c x_q; row op the conjugate transpose.
+        // A is Hermitian, so only the upper triangle of 2x2 pair blocks B(P,Q) =
+        // A[{p_P, q_P}][{p_Q, q_Q}] (P <= Q) is updated, B -> B K_Q by rows (with V's columns),
+        // then -> K_P^H (B K_Q) by columns, each block written with its mirror: every element of
+        // A is computed once instead of once per pass.
+        for (int it = tid; it < NP * (NP + 1) + NP * T; it += blockDim.x) {
+          if (it < NP * (NP + 1)) {  // (block, row): B_r <- B_r K_Q
+            const int P = blk[it >> 1] >> 8, Q = blk[it >> 1] & 255;
+            const Real c = rc[Q], wr = rwr[Q], wi = rwi[Q];
+            if (wr == 0 && wi == 0) continue;
+            const int row = (it & 1) ? rq[P] : rp[P], p = rp[Q], q = rq[Q];
+            const Real xpr = ar[row * LD + p], xpi = ai[row * LD + p], xqr = ar[row * LD + q], xqi = ai[row * LD + q];
+            ar[row * LD + p] = c * xpr - (wr * xqr + wi * xqi);
+            ai[row * LD + p] = c * xpi - (wr * xqi - wi * xqr);
+            ar[row * LD + q] = (wr * xpr - wi * xpi) + c * xqr;
+            ai[row * LD + q] = (wr * xpi + wi * xpr) + c * xqi;
+          } else {  // columns of V
+            const int k = (it - NP * (NP + 1)) / T, i = (it - NP * (NP + 1)) % T;
+            const Real c = rc[k], wr = rwr[k], wi = rwi[k];
+            if (wr == 0 && wi == 0) continue;
+            const int p = rp[k], q = rq[k];
+            const Real xpr = vr[i * LD + p], xpi = vi[i * LD + p], xqr = vr[i * LD + q], xqi = vi[i * LD + q];
+            vr[i * LD + p] = c * xpr - (wr * xqr + wi * xqi);
+            vi[i * LD + p] = c * xpi - (wr * xqi - wi * xqr);
+            vr[i * LD + q] = (wr * xpr - wi * xpi) + c * xqr;
+            vi[i * LD + q] = (wr * xpi + wi * xpr) + c * xqi;
+          }
+        }
+        __syncthreads();
+        for (int it = tid; it < NP * (NP + 1); it += blockDim.x) {  // (block, column): K_P^H B
+          const int P = blk[it >> 1] >> 8, Q = blk[it >> 1] & 255;
+          const Real c = rc[P], wr = rwr[P], wi = rwi[P];
+          const bool rotP = !(wr == 0 && wi == 0);
+          if (!rotP && !(rwr[Q] != 0 || rwi[Q] != 0)) continue;  // block unchanged
+          const int cc = (it & 1) ? rq[Q] : rp[Q], r0 = rp[P], r1 = rq[P];
+          const Real m0r = ar[r0 * LD + cc], m0i = ai[r0 * LD + cc], m1r = ar[r1 * LD + cc], m1i = ai[r1 * LD + cc];
+          Real b0r = m0r, b0i = m0i, b1r = m1r, b1i = m1i;
+          if (rotP) {  // row 0' = c M_0 - w M_1, row 1' = conj(w) M_0 + c M_1
+            b0r = c * m0r - (wr * m1r - wi * m1i);
+            b0i = c * m0i - (wr * m1i + wi * m1r);
+            b1r = (wr * m0r + wi * m0i) + c * m1r;
+            b1i = (wr * m0i - wi * m0r) + c * m1i;
+          }
+          if (P == Q) {  // the pair's own block: diagonal afterwards
+            if ((it & 1) == 0) { b1r = 0; b1i = 0; b0i = 0; }
+            else { b0r = 0; b0i = 0; b1i = 0; }
+          }
+          ar[r0 * LD + cc] = b0r; ai[r0 * LD + cc] = b0i;
+          ar[r1 * LD + cc] = b1r; ai[r1 * LD + cc] = b1i;
+          if (P != Q) {
+            ar[cc * LD + r0] = b0r; ai[cc * LD + r0] = -b0i;
+            ar[cc * LD + r1] = b1r; ai[cc * LD + r1] = -b1i;
+          }
+        }
+        __syncthreads();
       }
-      __syncthreads();
-      // rows of A: A_pj' = c A_pj - w A_qj ;  A_qj' = conj(w) A_pj + c A_qj
-      for (int it = tid; it < NP * T; it += blockDim.x) {
-        const int k = it / T, j = it % T;
-        const Real c = rc[k], wr = rwr[k], wi = rwi[k];
-        if (wr == 0 && wi == 0) continue;
-        const int p = rp[k], q = rq[k];
-        const Real xpr = ar[p * LD + j], xpi = ai[p * LD + j], xqr = ar[q * LD + j], xqi = ai[q * LD + j];
-        ar[p * LD + j] = c * xpr - (wr * xqr - wi * xqi);
-        ai[p * LD + j] = c * xpi - (wr * xqi + wi * xqr);
-        ar[q * LD + j] = (wr * xpr + wi * xpi) + c * xqr;
-        ai[q * LD + j] = (wr * xpi - wi * xpr) + c * xqi;
-      }
-      __syncthreads();
-      if (tid < NP) {
-        const int p = rp[tid], q = rq[tid];
-        ar[p * LD + q] = ai[p * LD + q] = ar[q * LD + p] = ai[q * LD + p] = 0;
-        ai[p * LD + p] = ai[q * LD + q] = 0;
-      }
-      __syncthreads();
     }
   }
   return -1;
@@ -190,7 +282,7 @@ __device__ int jacobi_sweeps(Real *ar, Real *ai, Real *vr, Real *vi, double tol,
 // Eq. 5 for one window per CTA, in two precisions:
 //  1. FP32 Jacobi sweeps on C until off(A) <= 1e-6 ||C||_F (the FP32 pipe is ~64x the FP64
 //     pipe on this part);
-//  2. FP64: the FP32 eigenvectors are re-orthonormalised (modified Gram-Schmidt), C is
+//  2. FP64: the FP32 eigenvectors are re-orthonormalised (one second-order Lowdin step), C is
 //     rotated into their basis (A = V^{t*} C V, the Rayleigh quotient), and FP64 Jacobi
 //     sweeps finish A to off(A) <= tol ||C||_F, accumulating into V.
 // The result is the FP64 eigendecomposition of C; phase 1 only supplies a good start.
@@ -236,23 +328,60 @@ k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restr
     vi[i * LD + j] = (double)vi32[i * LD + j];
   }
   __syncthreads();
-  // Lowdin re-orthonormalisation of the (nearly orthonormal) columns of V:
-  // V <- V (3 I - V^{t*} V) / 2 squares the orthogonality error E = V^{t*} V - I; the FP32
-  // sweeps leave |E| ~ 1e-6, so two steps reach FP64 level.
-  for (int pass = 0; pass < DH_LOWDIN_PASSES; ++pass) {
-  for (int e = tid; e < T * T; e += blockDim.x) {  // Z = V^{t*} V
-    const int i = e / T, j = e % T;
+  // Lowdin re-orthonormalisation of the (nearly orthonormal) columns of V, second order in
+  // one pass: with E = V^{t*} V - I (|E| ~ 1e-6 after the FP32 sweeps),
+  // (V^{t*} V)^{-1/2} = I - E/2 + 3E^2/8 - ..., so V <- V (I - E/2 + 3E^2/8) leaves an
+  // orthogonality error O(|E|^3), below FP64 rounding. E and E^2 are Hermitian: only their
+  // upper triangles are computed.
+  constexpr int NTRI = T * (T + 1) / 2;
+  constexpr int TPT = (NTRI + 255) / 256;  // upper-triangle elements per thread
+  for (int e = tid; e < NTRI; e += blockDim.x) {  // Z = E = V^{t*} V - I
+    int i, j;
+    tri_ij(e, T, i, j);
     double sr = 0.0, si = 0.0;
     for (int k = 0; k < T; ++k) {
       const double ar_ = vr[k * LD + i], ai_ = -vi[k * LD + i], br = vr[k * LD + j], bi = vi[k * LD + j];
       sr += ar_ * br - ai_ * bi;
       si += ar_ * bi + ai_ * br;
     }
-    zr[i * LD + j] = (i == j ? 1.5 : 0.0) - 0.5 * sr;
-    zi[i * LD + j] = -0.5 * si;
+    if (i == j) { sr -= 1.0; si = 0.0; }
+    zr[i * LD + j] = sr; zi[i * LD + j] = si;
+    zr[j * LD + i] = sr; zi[j * LD + i] = -si;
   }
   __syncthreads();
   {
+    double yr[TPT], yi[TPT];
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+      const int e = tid + u * 256;
+      yr[u] = yi[u] = 0.0;
+      if (e < NTRI) {
+        int i, j;
+        tri_ij(e, T, i, j);
+        double sr = 0.0, si = 0.0;  // (E^2)_ij
+        for (int k = 0; k < T; ++k) {
+          const double ar_ = zr[i * LD + k], ai_ = zi[i * LD + k], br = zr[k * LD + j], bi = zi[k * LD + j];
+          sr += ar_ * br - ai_ * bi;
+          si += ar_ * bi + ai_ * br;
+        }
+        yr[u] = (i == j ? 1.0 : 0.0) - 0.5 * zr[i * LD + j] + 0.375 * sr;
+        yi[u] = -0.5 * zi[i * LD + j] + 0.375 * si;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+      const int e = tid + u * 256;
+      if (e < NTRI) {
+        int i, j;
+        tri_ij(e, T, i, j);
+        zr[i * LD + j] = yr[u]; zi[i * LD + j] = i == j ? 0.0 : yi[u];
+        zr[j * LD + i] = yr[u]; zi[j * LD + i] = i == j ? 0.0 : -yi[u];
+      }
+    }
+    __syncthreads();
+  }
+  {  // V <- V Y
     constexpr int NPR = 256 / T;   // threads per row of V
     constexpr int CPT = T / NPR;   // output columns per thread
     const int i = tid / NPR, j0 = (tid % NPR) * CPT;
@@ -277,7 +406,6 @@ k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restr
     }
     __syncthreads();
   }
-  }
 
   // Z = C V
   for (int e = tid; e < T * T; e += blockDim.x) {
@@ -292,29 +420,19 @@ k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restr
     zi[i * LD + j] = si;
   }
   __syncthreads();
-  // X = V^{t*} Z (Hermitian up to rounding: computed in full, then symmetrised)
-  for (int e = tid; e < T * T; e += blockDim.x) {
-    const int i = e / T, j = e % T;
+  // X = V^{t*} Z, Hermitian: the upper triangle, mirrored (C is not needed any more)
+  for (int e = tid; e < NTRI; e += blockDim.x) {
+    int i, j;
+    tri_ij(e, T, i, j);
     double sr = 0.0, si = 0.0;
     for (int k = 0; k < T; ++k) {
       const double ar_ = vr[k * LD + i], ai_ = -vi[k * LD + i], br = zr[k * LD + j], bi = zi[k * LD + j];
       sr += ar_ * br - ai_ * bi;
       si += ar_ * bi + ai_ * br;
     }
-    xr[i * LD + j] = sr;
-    xi[i * LD + j] = si;
-  }
-  __syncthreads();
-  for (int e = tid; e < T * T; e += blockDim.x) {
-    const int i = e / T, j = e % T;
-    if (i < j) {
-      const double r = 0.5 * (xr[i * LD + j] + xr[j * LD + i]);
-      const double m = 0.5 * (xi[i * LD + j] - xi[j * LD + i]);
-      xr[i * LD + j] = r; xi[i * LD + j] = m;
-      xr[j * LD + i] = r; xi[j * LD + i] = -m;
-    } else if (i == j) {
-      xi[i * LD + i] = 0.0;
-    }
+    if (i == j) si = 0.0;
+    xr[i * LD + j] = sr; xi[i * LD + j] = si;
+    xr[j * LD + i] = sr; xi[j * LD + i] = -si;
   }
   __syncthreads();
   const int sweeps = jacobi_sweeps<T, double>(xr, xi, vr, vi, tol, max_sweeps, fro, red);
