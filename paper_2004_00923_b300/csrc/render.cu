@@ -103,6 +103,12 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
+// Complex sum and difference with the paired FP32 instructions of this architecture (one
+// instruction for both components; each component rounds exactly as the scalar FADD does,
+// a - b being fma(b, -1, a)).
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
 // x * w_N^I with w_N = exp(+2 pi i / N), N <= 64, I < N/2: compile-time constants.
 template <int N, int I>
 __device__ __forceinline__ float2 tw_mul(float2 x) {
@@ -117,7 +123,9 @@ __device__ __forceinline__ float2 tw_mul(float2 x) {
     return make_float2(-(x.x + x.y) * kRsqrt2, (x.x - x.y) * kRsqrt2);
   } else {
     constexpr float c = kCos64[M], s = kSin64[M];
-    return make_float2(fmaf(x.x, c, -x.y * s), fmaf(x.x, s, x.y * c));
+    // (x.x c - x.y s, x.x s + x.y c): the products x.y (-s, c) rounded, then one paired FMA,
+    // the same roundings as fmaf(x.x, c, -x.y * s), fmaf(x.x, s, x.y * c)
+    return __ffma2_rn(make_float2(x.x, x.x), make_float2(c, s), __fmul2_rn(make_float2(x.y, x.y), make_float2(-s, c)));
   }
 }
 
@@ -127,8 +135,8 @@ template <int N, int S, int O, int I, int RR>
 __device__ __forceinline__ void dif_level(float2 (&v)[RR]) {
   if constexpr (I < N / 2) {
     const float2 a = v[O + I * S], b = v[O + (I + N / 2) * S];
-    v[O + I * S] = make_float2(a.x + b.x, a.y + b.y);
-    v[O + (I + N / 2) * S] = tw_mul<N, I>(make_float2(a.x - b.x, a.y - b.y));
+    v[O + I * S] = cadd(a, b);
+    v[O + (I + N / 2) * S] = tw_mul<N, I>(csub(a, b));
     dif_level<N, S, O, I + 1, RR>(v);
   }
 }
