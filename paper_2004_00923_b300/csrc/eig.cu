@@ -286,8 +286,13 @@ __device__ int jacobi_sweeps(Real *ar, Real *ai, Real *vr, Real *vi, double tol,
 //     rotated into their basis (A = V^{t*} C V, the Rayleigh quotient), and FP64 Jacobi
 //     sweeps finish A to off(A) <= tol ||C||_F, accumulating into V.
 // The result is the FP64 eigendecomposition of C; phase 1 only supplies a good start.
+// Threads of the eigensolver's CTA: 512 at T = 64, where the FP64 phase has the most
+// independent work per step and more warps keep the FP64 pipe busier; 256 below.
 template <int T>
-__global__ void __launch_bounds__(256)
+__host__ __device__ constexpr int kJacThreads() { return T == 64 ? 512 : 256; }
+
+template <int T>
+__global__ void __launch_bounds__(kJacThreads<T>())
 k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restrict__ Vout,
          double *__restrict__ eig_user, int prec, void *__restrict__ Bop, long long B_stride,
          int k0, int k1, int Npad, double tol, int max_sweeps, uint32_t *__restrict__ status) {
@@ -298,7 +303,7 @@ k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restr
   // X: C, later A (FP64); Y: V (FP64); Z: FP32 A and V in phase 1, FP64 scratch in phase 2
   double *xr = sm, *xi = xr + SZ, *vr = xi + SZ, *vi = vr + SZ, *zr = vi + SZ, *zi = zr + SZ;
   float *ar32 = reinterpret_cast<float *>(zr), *ai32 = ar32 + SZ, *vr32 = ai32 + SZ, *vi32 = vr32 + SZ;
-  __shared__ double red[8], dsort[T];
+  __shared__ double red[16], dsort[T];
   __shared__ int perm[T];
   const int w = blockIdx.x, tid = threadIdx.x;
   const double *Cw = C + 2ll * w * T * T;
@@ -334,7 +339,8 @@ k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restr
   // orthogonality error O(|E|^3), below FP64 rounding. E and E^2 are Hermitian: only their
   // upper triangles are computed.
   constexpr int NTRI = T * (T + 1) / 2;
-  constexpr int TPT = (NTRI + 255) / 256;  // upper-triangle elements per thread
+  constexpr int NT = kJacThreads<T>();
+  constexpr int TPT = (NTRI + NT - 1) / NT;  // upper-triangle elements per thread
   for (int e = tid; e < NTRI; e += blockDim.x) {  // Z = E = V^{t*} V - I
     int i, j;
     tri_ij(e, T, i, j);
@@ -353,7 +359,7 @@ k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restr
     double yr[TPT], yi[TPT];
 #pragma unroll
     for (int u = 0; u < TPT; ++u) {
-      const int e = tid + u * 256;
+      const int e = tid + u * NT;
       yr[u] = yi[u] = 0.0;
       if (e < NTRI) {
         int i, j;
@@ -371,7 +377,7 @@ k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restr
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < TPT; ++u) {
-      const int e = tid + u * 256;
+      const int e = tid + u * NT;
       if (e < NTRI) {
         int i, j;
         tri_ij(e, T, i, j);
@@ -382,7 +388,7 @@ k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restr
     __syncthreads();
   }
   {  // V <- V Y
-    constexpr int NPR = 256 / T;   // threads per row of V
+    constexpr int NPR = NT / T;    // threads per row of V
     constexpr int CPT = T / NPR;   // output columns per thread
     const int i = tid / NPR, j0 = (tid % NPR) * CPT;
     double nr[CPT], ni[CPT];
@@ -544,7 +550,7 @@ dh_status launch_jacobi_t(Plan &p, int n_windows, int k0, int k1, int Npad, doub
   const long long B_stride = (long long)(p.B_window_bytes / (p.prec == DH_PREC_FP32 ? 4 : 2));
   void *B = static_cast<char *>(p.d_B) + (size_t)woff * p.B_window_bytes;
   ProfScope ps(p, K_JACOBI, s);
-  k_jacobi<T><<<n_windows, 256, smem, s>>>(p.d_C + 2ll * woff * T * T, p.d_lam + (long long)woff * T,
+  k_jacobi<T><<<n_windows, kJacThreads<T>(), smem, s>>>(p.d_C + 2ll * woff * T * T, p.d_lam + (long long)woff * T,
                                            p.d_V + 2ll * woff * T * T, eig_user, (int)p.prec, B, B_stride,
                                            k0, k1, Npad, DH_EIG_TOL, 30, p.d_status);
   DH_CUDA_TRY(cudaGetLastError());
