@@ -13,7 +13,11 @@
 //   and the retained columns k0..k1 are packed into the operand of Eq. 6.
 #include "dh_internal.cuh"
 
-// FP64 phase of the eigensolver: the off(A) / ||C||_F at which the FP64 sweeps stop.
+// Refinement phase of the eigensolver: the off(A) / ||C||_F at which its sweeps stop, and its
+// arithmetic (1: double-FP32, 0: FP64).
+#ifndef DH_EIG_DF
+#define DH_EIG_DF 1
+#endif
 #ifndef DH_EIG_TOL
 #define DH_EIG_TOL 1e-12
 #endif
@@ -286,6 +290,213 @@ __device__ int jacobi_sweeps(Real *ar, Real *ai, Real *vr, Real *vi, double tol,
 //     rotated into their basis (A = V^{t*} C V, the Rayleigh quotient), and FP64 Jacobi
 //     sweeps finish A to off(A) <= tol ||C||_F, accumulating into V.
 // The result is the FP64 eigendecomposition of C; phase 1 only supplies a good start.
+// ---- double-FP32 ("df") arithmetic for the refinement phase. A value is h + l, two FP32
+// numbers with |l| <= ulp(h)/2: a 48-bit significand. This part's FP64 pipe runs at about
+// 1/100 of its FP32 rate, so the refinement's products and rotations are carried out with
+// error-free transformations on FP32 (Knuth's TwoSum; the FMA-based exact product
+// a b = p + fma(a, b, -p)), every operation an explicitly rounded intrinsic so that no
+// contraction or reassociation changes it. Sums of products are accumulated unnormalised
+// (h the running sum's leading part, l the collected errors) and normalised once at the end.
+__device__ __forceinline__ float2 df_of(double d) {
+  const float h = __double2float_rn(d);
+  return make_float2(h, __double2float_rn(d - (double)h));
+}
+__device__ __forceinline__ double df_dbl(float2 a) { return (double)a.x + (double)a.y; }
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 df_fin(float h, float l) {  // TwoSum(h, l)
+  const float s = __fadd_rn(h, l);
+  const float bb = __fsub_rn(s, h);
+  return make_float2(s, __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(l, bb)));
+}
+// (h, l) += a b
+__device__ __forceinline__ void df_acc(float &h, float &l, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float s = __fadd_rn(h, p);
+  const float bb = __fsub_rn(s, h);
+  const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  h = s;
+  l = __fadd_rn(l, __fadd_rn(err, e));
+}
+__device__ __forceinline__ float2 df_dot3(float2 a0, float2 b0, float2 a1, float2 b1, float2 a2, float2 b2) {
+  float h = 0.f, l = 0.f;
+  df_acc(h, l, a0, b0);
+  df_acc(h, l, a1, b1);
+  df_acc(h, l, a2, b2);
+  return df_fin(h, l);
+}
+// sum_k op(a_k) b_k over k < T (op = conj when CONJ), complex df; a_k at index a0 + k sa,
+// b_k at b0 + k sb of the re / im planes
+template <int T, bool CONJ>
+__device__ __forceinline__ void df_cdot(const float2 *ar, const float2 *ai, int a0, int sa, const float2 *br,
+                                        const float2 *bi, int b0, int sb, float2 &outr, float2 &outi) {
+  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+#pragma unroll 4
+  for (int k = 0; k < T; ++k) {
+    const float2 xr_ = ar[a0 + k * sa], yr = br[b0 + k * sb], yi = bi[b0 + k * sb];
+    const float2 xi_ = CONJ ? df_neg(ai[a0 + k * sa]) : ai[a0 + k * sa];
+    df_acc(rh, rl, xr_, yr);
+    df_acc(rh, rl, df_neg(xi_), yi);
+    df_acc(ih, il, xr_, yi);
+    df_acc(ih, il, xi_, yr);
+  }
+  outr = df_fin(rh, rl);
+  outi = df_fin(ih, il);
+}
+
+// Parallel-order complex Jacobi sweeps in df arithmetic on the Hermitian (ar, ai), rotations
+// accumulated into (vr, vi); the rotation angles are computed in FP64 from the df entries.
+// Same ordering, skip threshold and stopping rule as jacobi_sweeps.
+template <int T>
+__device__ int jacobi_sweeps_df(float2 *ar, float2 *ai, float2 *vr, float2 *vi, double tol, int max_sweeps,
+                                double fro, double *red) {
+  constexpr int NP = T / 2;
+  constexpr int LD = T + 1;
+  __shared__ float2 rc[NP], rwr[NP], rwi[NP];
+  __shared__ int rp[NP], rq[NP], rskip[NP];
+  __shared__ unsigned short blk[NP * (NP + 1) / 2];  // pair blocks (P << 8 | Q), P <= Q
+  const int tid = threadIdx.x;
+  if constexpr (T == 64) {
+    for (int e = tid; e < NP * (NP + 1) / 2; e += blockDim.x) {
+      int P, Q;
+      tri_ij(e, NP, P, Q);
+      blk[e] = (unsigned short)(P << 8 | Q);
+    }
+    __syncthreads();
+  }
+  for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
+    double off2 = 0.0;
+    for (int e = tid; e < T * T; e += blockDim.x) {
+      const int i = e / T, j = e % T;
+      if (i != j) {
+        const double x = df_dbl(ar[i * LD + j]), y = df_dbl(ai[i * LD + j]);
+        off2 += x * x + y * y;
+      }
+    }
+    off2 = block_sum(off2, red);
+    if (sqrt(off2) <= tol * fro) return sweep;
+    if (sweep == max_sweeps) break;
+    for (int step = 0; step < T - 1; ++step) {
+      if (tid < NP) {
+        int a, b;
+        if (tid == 0) { a = step; b = T - 1; }
+        else { a = (step + tid) % (T - 1); b = (step - tid + T - 1) % (T - 1); }
+        const int p = a < b ? a : b, q = a < b ? b : a;
+        const double gr = df_dbl(ar[p * LD + q]), gi = df_dbl(ai[p * LD + q]);
+        const double g = sqrt(gr * gr + gi * gi);
+        double c = 1, wr = 0, wi = 0;
+        int skip = 1;
+        if (g > 1e-2 * tol * fro / T) {  // smaller rotations cannot hold off(A) above tol ||A||_F
+          const double tau = (df_dbl(ar[q * LD + q]) - df_dbl(ar[p * LD + p])) / (2 * g);
+          const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1 + tau * tau));
+          c = 1 / sqrt(1 + t * t);
+          const double sn = t * c;
+          wr = sn * gr / g;
+          wi = sn * gi / g;
+          skip = 0;
+        }
+        rp[tid] = p; rq[tid] = q; rc[tid] = df_of(c); rwr[tid] = df_of(wr); rwi[tid] = df_of(wi);
+        rskip[tid] = skip;
+      }
+      __syncthreads();
+      if constexpr (T == 64) {  // measured: 8% off the sweeps at T = 64, none below
+        // A <- K^H A K on the upper triangle of 2x2 pair blocks (P <= Q; rows of each block by
+        // K_Q, with V's columns, then its columns by K_P^H, written with the mirror), so every
+        // element of A is computed once; see jacobi_sweeps for the column and row operations.
+        for (int it = tid; it < NP * (NP + 1) + NP * T; it += blockDim.x) {
+          if (it < NP * (NP + 1)) {  // (block, row): B_r <- B_r K_Q
+            const int P = blk[it >> 1] >> 8, Q = blk[it >> 1] & 255;
+            if (rskip[Q]) continue;
+            const float2 c = rc[Q], wr = rwr[Q], wi = rwi[Q];
+            const int row = (it & 1) ? rq[P] : rp[P], p = rp[Q], q = rq[Q];
+            const float2 xpr = ar[row * LD + p], xpi = ai[row * LD + p], xqr = ar[row * LD + q], xqi = ai[row * LD + q];
+            ar[row * LD + p] = df_dot3(c, xpr, df_neg(wr), xqr, df_neg(wi), xqi);
+            ai[row * LD + p] = df_dot3(c, xpi, df_neg(wr), xqi, wi, xqr);
+            ar[row * LD + q] = df_dot3(wr, xpr, df_neg(wi), xpi, c, xqr);
+            ai[row * LD + q] = df_dot3(wr, xpi, wi, xpr, c, xqi);
+          } else {  // columns of V
+            const int k = (it - NP * (NP + 1)) / T, i = (it - NP * (NP + 1)) % T;
+            if (rskip[k]) continue;
+            const float2 c = rc[k], wr = rwr[k], wi = rwi[k];
+            const int p = rp[k], q = rq[k];
+            const float2 xpr = vr[i * LD + p], xpi = vi[i * LD + p], xqr = vr[i * LD + q], xqi = vi[i * LD + q];
+            vr[i * LD + p] = df_dot3(c, xpr, df_neg(wr), xqr, df_neg(wi), xqi);
+            vi[i * LD + p] = df_dot3(c, xpi, df_neg(wr), xqi, wi, xqr);
+            vr[i * LD + q] = df_dot3(wr, xpr, df_neg(wi), xpi, c, xqr);
+            vi[i * LD + q] = df_dot3(wr, xpi, wi, xpr, c, xqi);
+          }
+        }
+        __syncthreads();
+        for (int it = tid; it < NP * (NP + 1); it += blockDim.x) {  // (block, column): K_P^H B
+          const int P = blk[it >> 1] >> 8, Q = blk[it >> 1] & 255;
+          if (rskip[P] && rskip[Q]) continue;  // block unchanged
+          const int cc = (it & 1) ? rq[Q] : rp[Q], r0 = rp[P], r1 = rq[P];
+          float2 b0r = ar[r0 * LD + cc], b0i = ai[r0 * LD + cc], b1r = ar[r1 * LD + cc], b1i = ai[r1 * LD + cc];
+          if (!rskip[P]) {  // row 0' = c M_0 - w M_1, row 1' = conj(w) M_0 + c M_1
+            const float2 c = rc[P], wr = rwr[P], wi = rwi[P];
+            const float2 m0r = b0r, m0i = b0i, m1r = b1r, m1i = b1i;
+            b0r = df_dot3(c, m0r, df_neg(wr), m1r, wi, m1i);
+            b0i = df_dot3(c, m0i, df_neg(wr), m1i, df_neg(wi), m1r);
+            b1r = df_dot3(wr, m0r, wi, m0i, c, m1r);
+            b1i = df_dot3(wr, m0i, df_neg(wi), m0r, c, m1i);
+          }
+          if (P == Q) {  // the pair's own block: diagonal afterwards
+            const float2 z = make_float2(0.f, 0.f);
+            if ((it & 1) == 0) { b1r = z; b1i = z; b0i = z; }
+            else { b0r = z; b0i = z; b1i = z; }
+          }
+          ar[r0 * LD + cc] = b0r; ai[r0 * LD + cc] = b0i;
+          ar[r1 * LD + cc] = b1r; ai[r1 * LD + cc] = b1i;
+          if (P != Q) {
+            ar[cc * LD + r0] = b0r; ai[cc * LD + r0] = df_neg(b0i);
+            ar[cc * LD + r1] = b1r; ai[cc * LD + r1] = df_neg(b1i);
+          }
+        }
+        __syncthreads();
+      } else {
+        // columns of A and V: X_ip' = c X_ip - conj(w) X_iq ;  X_iq' = w X_ip + c X_iq
+        for (int it = tid; it < 2 * NP * T; it += blockDim.x) {
+          const bool isv = it >= NP * T;
+          const int k = (isv ? it - NP * T : it) / T, i = (isv ? it - NP * T : it) % T;
+          if (rskip[k]) continue;
+          const float2 c = rc[k], wr = rwr[k], wi = rwi[k];
+          float2 *xr_ = isv ? vr : ar, *xi_ = isv ? vi : ai;
+          const int p = rp[k], q = rq[k];
+          const float2 xpr = xr_[i * LD + p], xpi = xi_[i * LD + p], xqr = xr_[i * LD + q], xqi = xi_[i * LD + q];
+          xr_[i * LD + p] = df_dot3(c, xpr, df_neg(wr), xqr, df_neg(wi), xqi);
+          xi_[i * LD + p] = df_dot3(c, xpi, df_neg(wr), xqi, wi, xqr);
+          xr_[i * LD + q] = df_dot3(wr, xpr, df_neg(wi), xpi, c, xqr);
+          xi_[i * LD + q] = df_dot3(wr, xpi, wi, xpr, c, xqi);
+        }
+        __syncthreads();
+        // rows of A: A_pj' = c A_pj - w A_qj ;  A_qj' = conj(w) A_pj + c A_qj
+        for (int it = tid; it < NP * T; it += blockDim.x) {
+          const int k = it / T, j = it % T;
+          if (rskip[k]) continue;
+          const float2 c = rc[k], wr = rwr[k], wi = rwi[k];
+          const int p = rp[k], q = rq[k];
+          const float2 xpr = ar[p * LD + j], xpi = ai[p * LD + j], xqr = ar[q * LD + j], xqi = ai[q * LD + j];
+          ar[p * LD + j] = df_dot3(c, xpr, df_neg(wr), xqr, wi, xqi);
+          ai[p * LD + j] = df_dot3(c, xpi, df_neg(wr), xqi, df_neg(wi), xqr);
+          ar[q * LD + j] = df_dot3(wr, xpr, wi, xpi, c, xqr);
+          ai[q * LD + j] = df_dot3(wr, xpi, df_neg(wi), xpr, c, xqi);
+        }
+        __syncthreads();
+        if (tid < NP && !rskip[tid]) {
+          const int p = rp[tid], q = rq[tid];
+          const float2 z = make_float2(0.f, 0.f);
+          ar[p * LD + q] = z; ai[p * LD + q] = z; ar[q * LD + p] = z; ai[q * LD + p] = z;
+          ai[p * LD + p] = z; ai[q * LD + q] = z;
+        }
+        __syncthreads();
+      }
+    }
+  }
+  return -1;
+}
+
 // Threads of the eigensolver's CTA: 512 at T = 64, where the FP64 phase has the most
 // independent work per step and more warps keep the FP64 pipe busier; 256 below.
 template <int T>
@@ -326,6 +537,127 @@ k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restr
   // ---- phase 1: FP32
   jacobi_sweeps<T, float>(ar32, ai32, vr32, vi32, 1e-6, 20, fro, red);
 
+#if DH_EIG_DF
+  // ---- phase 2: double-FP32 refinement (see df_acc); C, V and A in df form in the same
+  // 8-byte slots as the FP64 arrays, converted back to FP64 at the end
+  {
+    constexpr int NTRI = T * (T + 1) / 2;
+    constexpr int NT = kJacThreads<T>();
+    constexpr int TPT = (NTRI + NT - 1) / NT;  // upper-triangle elements per thread
+    float2 *XR = reinterpret_cast<float2 *>(xr), *XI = reinterpret_cast<float2 *>(xi);
+    float2 *VR = reinterpret_cast<float2 *>(vr), *VI = reinterpret_cast<float2 *>(vi);
+    float2 *ZR = reinterpret_cast<float2 *>(zr), *ZI = reinterpret_cast<float2 *>(zi);
+    for (int e = tid; e < T * T; e += blockDim.x) {
+      const int i = e / T, j = e % T;
+      const float a = vr32[i * LD + j], b = vi32[i * LD + j];  // read before the C slots change
+      VR[i * LD + j] = make_float2(a, 0.f);
+      VI[i * LD + j] = make_float2(b, 0.f);
+      XR[i * LD + j] = df_of(xr[i * LD + j]);
+      XI[i * LD + j] = df_of(xi[i * LD + j]);
+    }
+    __syncthreads();
+    // Lowdin re-orthonormalisation, second order in one step: E = V^{t*} V - I (Hermitian,
+    // |E| ~ 1e-6 after the FP32 sweeps), V <- V (I - E/2 + 3E^2/8), orthogonality error
+    // O(|E|^3). Y's small terms are formed in FP64.
+    for (int e = tid; e < NTRI; e += blockDim.x) {
+      int i, j;
+      tri_ij(e, T, i, j);
+      float2 sr, si;
+      df_cdot<T, true>(VR, VI, i, LD, VR, VI, j, LD, sr, si);
+      if (i == j) { sr = df_of(df_dbl(sr) - 1.0); si = make_float2(0.f, 0.f); }
+      ZR[i * LD + j] = sr; ZI[i * LD + j] = si;
+      ZR[j * LD + i] = sr; ZI[j * LD + i] = df_neg(si);
+    }
+    __syncthreads();
+    {
+      double yr[TPT], yi[TPT];
+#pragma unroll
+      for (int u = 0; u < TPT; ++u) {
+        const int e = tid + u * NT;
+        yr[u] = yi[u] = 0.0;
+        if (e < NTRI) {
+          int i, j;
+          tri_ij(e, T, i, j);
+          float2 sr, si;  // (E^2)_ij
+          df_cdot<T, false>(ZR, ZI, i * LD, 1, ZR, ZI, j, LD, sr, si);
+          yr[u] = (i == j ? 1.0 : 0.0) - 0.5 * df_dbl(ZR[i * LD + j]) + 0.375 * df_dbl(sr);
+          yi[u] = -0.5 * df_dbl(ZI[i * LD + j]) + 0.375 * df_dbl(si);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < TPT; ++u) {
+        const int e = tid + u * NT;
+        if (e < NTRI) {
+          int i, j;
+          tri_ij(e, T, i, j);
+          ZR[i * LD + j] = df_of(yr[u]); ZI[i * LD + j] = i == j ? make_float2(0.f, 0.f) : df_of(yi[u]);
+          ZR[j * LD + i] = df_of(yr[u]); ZI[j * LD + i] = i == j ? make_float2(0.f, 0.f) : df_of(-yi[u]);
+        }
+      }
+      __syncthreads();
+    }
+    {  // V <- V Y: thread (row i, CPT columns)
+      constexpr int NPR = NT / T;
+      constexpr int CPT = T / NPR;
+      const int i = tid / NPR, j0 = (tid % NPR) * CPT;
+      float rh[CPT], rl[CPT], ih[CPT], il[CPT];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) rh[c] = rl[c] = ih[c] = il[c] = 0.f;
+      if (i < T) {
+        for (int k = 0; k < T; ++k) {
+          const float2 ar_ = VR[i * LD + k], ai_ = VI[i * LD + k];
+#pragma unroll
+          for (int c = 0; c < CPT; ++c) {
+            const float2 br = ZR[k * LD + j0 + c], bi = ZI[k * LD + j0 + c];
+            df_acc(rh[c], rl[c], ar_, br);
+            df_acc(rh[c], rl[c], df_neg(ai_), bi);
+            df_acc(ih[c], il[c], ar_, bi);
+            df_acc(ih[c], il[c], ai_, br);
+          }
+        }
+      }
+      __syncthreads();
+      if (i < T) {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          VR[i * LD + j0 + c] = df_fin(rh[c], rl[c]);
+          VI[i * LD + j0 + c] = df_fin(ih[c], il[c]);
+        }
+      }
+      __syncthreads();
+    }
+    // Rayleigh quotient A = V^{t*} (C V): Z = C V in full, then A's upper triangle (Hermitian)
+    for (int e = tid; e < T * T; e += blockDim.x) {
+      const int i = e / T, j = e % T;
+      float2 sr, si;
+      df_cdot<T, false>(XR, XI, i * LD, 1, VR, VI, j, LD, sr, si);
+      ZR[i * LD + j] = sr; ZI[i * LD + j] = si;
+    }
+    __syncthreads();
+    for (int e = tid; e < NTRI; e += blockDim.x) {
+      int i, j;
+      tri_ij(e, T, i, j);
+      float2 sr, si;
+      df_cdot<T, true>(VR, VI, i, LD, ZR, ZI, j, LD, sr, si);
+      if (i == j) si = make_float2(0.f, 0.f);
+      XR[i * LD + j] = sr; XI[i * LD + j] = si;
+      XR[j * LD + i] = sr; XI[j * LD + i] = df_neg(si);
+    }
+    __syncthreads();
+    const int sweeps = jacobi_sweeps_df<T>(XR, XI, VR, VI, tol, max_sweeps, fro, red);
+    if (sweeps < 0 && tid == 0) atomicOr(status, DH_FLAG_EIG_NOT_CONVERGED);
+    // back to FP64 in place (each slot read and written by the same thread)
+    for (int e = tid; e < T * T; e += blockDim.x) {
+      const int i = e / T, j = e % T;
+      const double a = df_dbl(XR[i * LD + j]), b = df_dbl(VR[i * LD + j]), c = df_dbl(VI[i * LD + j]);
+      xr[i * LD + j] = a;
+      vr[i * LD + j] = b;
+      vi[i * LD + j] = c;
+    }
+    __syncthreads();
+  }
+#else
   // ---- phase 2: FP64
   for (int e = tid; e < T * T; e += blockDim.x) {
     const int i = e / T, j = e % T;
@@ -443,6 +775,8 @@ k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restr
   __syncthreads();
   const int sweeps = jacobi_sweeps<T, double>(xr, xi, vr, vi, tol, max_sweeps, fro, red);
   if (sweeps < 0 && tid == 0) atomicOr(status, DH_FLAG_EIG_NOT_CONVERGED);
+
+#endif
 
   // decreasing order, ties by original index
   if (tid < T) dsort[tid] = xr[tid * LD + tid];
