@@ -525,7 +525,7 @@ def run_sliding(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    F = SLIDE_FRAMES
+    F = args.frames or SLIDE_FRAMES
     n = {L: (F - L) // SLIDE_STRIDE + 1 for L in SLIDE_LENGTHS}
     frames = SpeckleStream(SpeckleParams(NX, NY), seed=2000 + rank, device=dev).next(F)
     base = dh.Plan(NX, NY, LAM, Z, PITCH, T=16, precision="fp16", max_frames=F, max_windows=n[16])
@@ -623,7 +623,7 @@ def run_sliding(args, ws, rank, local):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "mixed: f32 FFT, f16 tensor-core products (f32 accumulate), f64 eig",
             "data": "synthetic",
-            "config": {"workload": "sliding: 2048 frames of 1024x1024 uint16, 16/32/64-frame "
+            "config": {"workload": f"sliding: {F} frames of 1024x1024 uint16, 16/32/64-frame "
                                    "windows at stride 8, each frame rendered once (FP16), "
                                    "the lengths run concurrently, one CUDA graph per step",
                        "covariance": "banded Gram of the store (dh_band_gram)" if args.band
@@ -1084,6 +1084,8 @@ def main(argv=None):
     ap.add_argument("--band", action=argparse.BooleanOptionalAction, default=True,
                     help="sliding workload: windows take C from the store's banded Gram "
                          "(dh_band_gram) instead of one Gram per window")
+    ap.add_argument("--frames", type=int, default=0,
+                    help="sliding workload: frames per step (default 2048; smaller for ncu captures)")
     ap.add_argument("--projection", choices=["grouped", "per-window"], default="grouped",
                     help="sliding workload: DH_OPT_PROJECTION (grouped = 0, per-window = 1)")
     ap.add_argument("--covariance", choices=["holograms", "raw"], default="holograms",
