@@ -302,7 +302,7 @@ def run_ours(args, ws, rank, local):
     alg = {k: v * steps for k, v in algorithmic_bytes(npix, nframes, nwin, T, hbytes).items()}
     fl = render_flops(npix, NX, NY, nframes) * steps
     roofline = roofline_of(per_kernel, alg, hbm, peak_kind, ms / 1e3,
-                           {k: fl for k in RENDER_KERNELS})
+                           {k: fl for k in RENDER_KERNELS}, alg_steps=steps)
 
     # ---------------------------------------------------------------- end to end (host buffers)
     # dh_pca_batch_host: pinned host frames in, host images and eigenvalues out; the library
@@ -446,7 +446,7 @@ def fp32_peak_tflops() -> float:
 
 
 def roofline_of(per_kernel: dict, alg: dict, hbm: float, peak_kind: str, step_s: float,
-                flops: dict | None = None) -> dict:
+                flops: dict | None = None, alg_steps: int = 1) -> dict:
     """Roofline of the kernel with the most device time among those with algorithmic bytes;
     `alg` (and `flops`) and `per_kernel` cover the same traced steps. The FFT kernels of
     Eq. 1 are bound by FP32 arithmetic (their DRAM traffic is the algorithmic minimum at a
@@ -466,7 +466,8 @@ def roofline_of(per_kernel: dict, alg: dict, hbm: float, peak_kind: str, step_s:
                "frac": tf / peak, "traffic": traffic_record(dom),
                "peak_kind": "FP32 FMA peak: SMs x 128 lanes x 2 flops x 2032 MHz",
                "hbm_view": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}}
-    out["step_hbm_frac"] = sum(alg[k] for k in per_kernel if k in alg) / step_s / 1e9 / hbm
+    # `alg` covers `alg_steps` traced steps; the fraction is per step
+    out["step_hbm_frac"] = sum(alg[k] for k in per_kernel if k in alg) / alg_steps / step_s / 1e9 / hbm
     out["kernels"] = per_kernel
     return out
 
