@@ -41,9 +41,6 @@ constexpr int kNacc = 4;  // partial accumulators per buffer (k-step kk goes to 
 constexpr size_t kSpanSmemLimit = 232448;
 constexpr float kInvScale2 = (float)(1.0 / (kSpanOperandScale * kSpanOperandScale));
 
-__device__ __forceinline__ uint8_t *align1024p(uint8_t *p) {
-  return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
-}
 
 // the two 16-bit values of a 32-bit word (lower address first) as floats
 template <bool BF16>
@@ -56,27 +53,30 @@ __device__ __forceinline__ float2 word_to_f32x2(uint32_t w) {
     return __half22float2(hv);
   }
 }
-template <int OFF>
-__device__ __forceinline__ uint32_t lds_u32_at(uint32_t addr) {
-  uint32_t v;
-  asm volatile("ld.shared.b32 %0, [%1+%2];" : "=r"(v) : "r"(addr), "n"(OFF));
-  return v;
+// acc + x^2 for each FP16 half of w (x: lower address, y: upper), with the mixed-precision
+// FMA (FP16 inputs, FP32 accumulator, one rounding): no separate conversion to FP32
+__device__ __forceinline__ float2 sq_acc_f16x2(uint32_t w, float2 acc) {
+  asm("{\n\t.reg .f16 lo, hi;\n\t"
+      "mov.b32 {lo, hi}, %2;\n\t"
+      "fma.rn.f32.f16 %0, lo, lo, %0;\n\t"
+      "fma.rn.f32.f16 %1, hi, hi, %1;\n\t}"
+      : "+f"(acc.x), "+f"(acc.y)
+      : "r"(w));
+  return acc;
 }
 // energies of one 4-frame chunk of this lane's row type for its pixel pair (x: even pixel,
-// y: odd pixel) from the chunk's four 32-bit words, packed FP32 arithmetic
+// y: odd pixel) from the chunk's four 32-bit words
 template <bool BF16>
 __device__ __forceinline__ float2 chunk_sq(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3) {
-  const float2 f0 = word_to_f32x2<BF16>(w0), f1 = word_to_f32x2<BF16>(w1);
-  const float2 f2 = word_to_f32x2<BF16>(w2), f3 = word_to_f32x2<BF16>(w3);
-  return __fadd2_rn(__ffma2_rn(f0, f0, __fmul2_rn(f1, f1)), __ffma2_rn(f2, f2, __fmul2_rn(f3, f3)));
-}
-__device__ __forceinline__ float lds_f32(uint32_t addr) {
-  float v;
-  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
-  return v;
-}
-__device__ __forceinline__ void sts_f32(uint32_t addr, float v) {
-  asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+  if constexpr (BF16) {
+    const float2 f0 = word_to_f32x2<BF16>(w0), f1 = word_to_f32x2<BF16>(w1);
+    const float2 f2 = word_to_f32x2<BF16>(w2), f3 = word_to_f32x2<BF16>(w3);
+    return __fadd2_rn(__ffma2_rn(f0, f0, __fmul2_rn(f1, f1)), __ffma2_rn(f2, f2, __fmul2_rn(f3, f3)));
+  } else {  // (w0^2 + w1^2) + (w2^2 + w3^2), the same pairing
+    const float2 a = sq_acc_f16x2(w1, sq_acc_f16x2(w0, make_float2(0.f, 0.f)));
+    const float2 b = sq_acc_f16x2(w3, sq_acc_f16x2(w2, make_float2(0.f, 0.f)));
+    return __fadd2_rn(a, b);
+  }
 }
 // Barrier `id` of the 64 threads of one lane quarter's two epilogue warps, returning whether
 // any of them passed true (both warps see the same answer and take the same branch).
@@ -100,7 +100,9 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
                int tmem_cols, int stages, int cpg, float *__restrict__ images, int nx, int ny,
                uint32_t *__restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t *smem = align1024p(smem_raw);
+  // aligned by indexing the shared array itself, so that pointers derived from it stay in the
+  // shared address space and plain loads and stores compile to shared-memory instructions
+  uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int stage_bytes = rows * 256;  // two 64-pixel boxes of `rows` rows
   uint8_t *stage0 = smem;
   uint8_t *bsm = smem + stages * stage_bytes;
@@ -247,8 +249,7 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
     const int c_half = (nch + 1) / 2;
     const int c_lo = h == 0 ? 0 : c_half, c_hi = h == 0 ? c_half : nch;
     const int dch = s / 4, mch = T / 4;     // window step and window length in chunks
-    const uint32_t scr_s = smem_u32(scratch);
-    const uint32_t box_s = (uint32_t)((L >> 6) * rows * 128);
+    const int box_off = (L >> 6) * rows * 128;  // this pixel's 64-pixel box within a stage
     int slot = 0, it = 0;
     uint32_t ph = 0;
     bool stop = false;
@@ -292,10 +293,12 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
           fence_before_sync();
           mbar_arrive(&acc_empty[buf]);
           // phase 1: this warp's chunks of the tile
-          const uint32_t a_s = smem_u32(stage0 + slot * stage_bytes) + box_s;
-          uint32_t ws = scr_s + (uint32_t)((buf * nch + c_lo) * 512 + L * 4);
-          uint32_t pk0 = a_s + off[0] + c_lo * 1024, pk1 = a_s + off[1] + c_lo * 1024;
-          uint32_t pk2 = a_s + off[2] + c_lo * 1024, pk3 = a_s + off[3] + c_lo * 1024;
+          const uint8_t *a_b = stage0 + slot * stage_bytes + box_off + c_lo * 1024;
+          const uint32_t *pk0 = reinterpret_cast<const uint32_t *>(a_b + off[0]);
+          const uint32_t *pk1 = reinterpret_cast<const uint32_t *>(a_b + off[1]);
+          const uint32_t *pk2 = reinterpret_cast<const uint32_t *>(a_b + off[2]);
+          const uint32_t *pk3 = reinterpret_cast<const uint32_t *>(a_b + off[3]);
+          float *ws = scratch + (buf * nch + c_lo) * 128 + L;
           // the pair's chunk energy: own row type of own pixel + partner's of the same pixel
           auto pair_sum = [&](float2 e) -> float {
             const float keep = odd ? e.y : e.x, send = odd ? e.x : e.y;
@@ -303,20 +306,17 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
           };
           int c = c_lo;
           for (; c + 1 < c_hi; c += 2) {
-            const uint32_t w0 = lds_u32_at<0>(pk0), w1 = lds_u32_at<0>(pk1);
-            const uint32_t w2 = lds_u32_at<0>(pk2), w3 = lds_u32_at<0>(pk3);
-            const uint32_t x0 = lds_u32_at<1024>(pk0), x1 = lds_u32_at<1024>(pk1);
-            const uint32_t x2 = lds_u32_at<1024>(pk2), x3 = lds_u32_at<1024>(pk3);
+            // 1024 bytes = 256 words per chunk
+            const uint32_t w0 = pk0[0], w1 = pk1[0], w2 = pk2[0], w3 = pk3[0];
+            const uint32_t x0 = pk0[256], x1 = pk1[256], x2 = pk2[256], x3 = pk3[256];
             const float e0 = pair_sum(chunk_sq<BF16>(w0, w1, w2, w3));
             const float e1 = pair_sum(chunk_sq<BF16>(x0, x1, x2, x3));
-            sts_f32(ws, e0);
-            sts_f32(ws + 512, e1);
-            pk0 += 2048; pk1 += 2048; pk2 += 2048; pk3 += 2048; ws += 1024;
+            ws[0] = e0;
+            ws[128] = e1;
+            pk0 += 512; pk1 += 512; pk2 += 512; pk3 += 512; ws += 256;
           }
           if (c < c_hi) {
-            const float e0 = pair_sum(chunk_sq<BF16>(lds_u32_at<0>(pk0), lds_u32_at<0>(pk1), lds_u32_at<0>(pk2),
-                                                     lds_u32_at<0>(pk3)));
-            sts_f32(ws, e0);
+            ws[0] = pair_sum(chunk_sq<BF16>(pk0[0], pk1[0], pk2[0], pk3[0]));
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[slot]);  // the stage's reads are done
@@ -325,17 +325,26 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
         if (pair_sync_or(1 + q, bad)) { fail(); stop = true; break; }
         // phase 2: the windows of this half
         if (j_n > 0) {
-          const uint32_t col = scr_s + (uint32_t)((buf * nch) * 512 + L * 4);
+          const float *col = scratch + buf * nch * 128 + L;  // chunk c at col[c * 128]
           int a = 4 * h * dch;
-          float E = 0.f;
-          for (int c = a; c < a + mch; ++c) E += lds_f32(col + c * 512);
+          float E;
+          {  // the first window's chunks (a multiple of 4 of them): four independent sums
+            float e4[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int c = a; c < a + mch; c += 4) {
+#pragma unroll
+              for (int k = 0; k < 4; ++k) e4[k] += col[(c + k) * 128];
+            }
+            E = (e4[0] + e4[1]) + (e4[2] + e4[3]);
+          }
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             if (j < j_n) {
               if (j > 0) {
                 float in = 0.f, outg = 0.f;
-                for (int c = a + mch; c < a + mch + dch; ++c) in += lds_f32(col + c * 512);
-                for (int c = a; c < a + dch; ++c) outg += lds_f32(col + c * 512);
+                for (int c = 0; c < dch; ++c) {
+                  in += col[(a + mch + c) * 128];
+                  outg += col[(a + c) * 128];
+                }
                 E += in - outg;
                 a += dch;
               }
