@@ -177,6 +177,7 @@ struct SpanLayout {
   int G = 0, cpw = 0, rows = 0, n_pad = 0, k_pad = 0, stride = 0, img_bytes = 0, stages = 0;
   int nacc = 0, tmem_cols = 0;  // partial accumulators per buffer; TMEM columns allocated
   int scr_bytes = 0;            // shared scratch of per-pixel chunk energies
+  int nbuf = 0;                 // TMEM accumulator buffers (2 or 4)
 };
 SpanLayout span_layout(const Plan &p, int slot_stride, int n_windows, int k0, int k1);
 dh_status launch_project_span(Plan &p, const SpanLayout &sl, int first_slot, int n_windows, float *images,

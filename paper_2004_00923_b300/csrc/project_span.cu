@@ -97,7 +97,7 @@ template <int CPW, bool BF16>
 __global__ void __launch_bounds__(kSpanThreads, 1)
 k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restrict__ Bimg, long long group_bytes,
                int img_bytes, int first_slot, int s, int T, int n_windows, int G, int rows, int n_pad,
-               int tmem_cols, int stages, int cpg, float *__restrict__ images, int nx, int ny,
+               int tmem_cols, int nbuf, int stages, int cpg, float *__restrict__ images, int nx, int ny,
                uint32_t *__restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   // aligned by indexing the shared array itself, so that pointers derived from it stay in the
@@ -111,8 +111,8 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
   uint64_t *full = reinterpret_cast<uint64_t *>(bsm + img_bytes + 2 * (rows_used / 8) * 512);
   uint64_t *empty = full + kSpanMaxStages;
   uint64_t *acc_full = empty + kSpanMaxStages;
-  uint64_t *acc_empty = acc_full + 2;
-  uint64_t *bfull = acc_empty + 2;
+  uint64_t *acc_empty = acc_full + 4;
+  uint64_t *bfull = acc_empty + 4;
   uint64_t *bempty = bfull + 1;
   uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bempty + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
@@ -128,14 +128,14 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < stages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1 + kSpanEpiWarps); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 32 * kSpanEpiWarps); }
+    for (int b = 0; b < nbuf; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 32 * kSpanEpiWarps); }
     mbar_init(bfull, 1);
     mbar_init(bempty, 1);
     *abort_flag = 0;
     fence_barrier_init();
     prefetch_tmap(&tmA);
   }
-  // two accumulator buffers, each kNacc partial accumulators of n_pad columns
+  // nbuf (2 or 4) accumulator buffers, each kNacc partial accumulators of n_pad columns
   const int acc_stride = kNacc * n_pad;
   if (warp == 1) { tmem_alloc(tmem_holder, tmem_cols); tmem_relinquish(); }
   fence_before_sync();
@@ -197,8 +197,8 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
           cur = grp;
         }
         for (int i = 0; i < 8; ++i, ++it) {
-          const int buf = it & 1;
-          if (!mbar_wait(&acc_empty[buf], ((it >> 1) & 1) ^ 1)) { fail(); ok = false; break; }
+          const int buf = it % nbuf;
+          if (!mbar_wait(&acc_empty[buf], ((it / nbuf) & 1) ^ 1)) { fail(); ok = false; break; }
           if (!mbar_wait(&full[slot], ph)) { fail(); ok = false; break; }
           fence_after_sync();
           const uint32_t d = tmem + buf * acc_stride;
@@ -261,10 +261,11 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
       float out[4][8];
       const bool aborted = __any_sync(0xffffffffu, *abort_flag != 0);
       for (int i = 0; i < 8; ++i, ++it) {
-        const int buf = it & 1;
+        const int buf = it % nbuf;   // accumulator buffer
+        const int sbuf = it & 1;     // scratch buffer (the pair's barrier separates its reuse)
         bool bad = aborted;
         if (!bad)
-          bad = !__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (it >> 1) & 1)) ||
+          bad = !__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (it / nbuf) & 1)) ||
                 !__all_sync(0xffffffffu, mbar_wait(&full[slot], ph));
         float v[4 * CPW];
         if (!bad) {
@@ -298,25 +299,26 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
           const uint32_t *pk1 = reinterpret_cast<const uint32_t *>(a_b + off[1]);
           const uint32_t *pk2 = reinterpret_cast<const uint32_t *>(a_b + off[2]);
           const uint32_t *pk3 = reinterpret_cast<const uint32_t *>(a_b + off[3]);
-          float *ws = scratch + (buf * nch + c_lo) * 128 + L;
+          float *ws = scratch + (sbuf * nch + c_lo) * 128 + L;
           // the pair's chunk energy: own row type of own pixel + partner's of the same pixel
           auto pair_sum = [&](float2 e) -> float {
             const float keep = odd ? e.y : e.x, send = odd ? e.x : e.y;
             return keep + __shfl_xor_sync(0xffffffffu, send, 1);
           };
           int c = c_lo;
-          for (; c + 1 < c_hi; c += 2) {
-            // 1024 bytes = 256 words per chunk
-            const uint32_t w0 = pk0[0], w1 = pk1[0], w2 = pk2[0], w3 = pk3[0];
-            const uint32_t x0 = pk0[256], x1 = pk1[256], x2 = pk2[256], x3 = pk3[256];
-            const float e0 = pair_sum(chunk_sq<BF16>(w0, w1, w2, w3));
-            const float e1 = pair_sum(chunk_sq<BF16>(x0, x1, x2, x3));
-            ws[0] = e0;
-            ws[128] = e1;
-            pk0 += 512; pk1 += 512; pk2 += 512; pk3 += 512; ws += 256;
+          for (; c + 3 < c_hi; c += 4) {  // 4 chunks (1024 bytes = 256 words each) in flight
+            uint32_t w[4][4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              w[k][0] = pk0[256 * k]; w[k][1] = pk1[256 * k]; w[k][2] = pk2[256 * k]; w[k][3] = pk3[256 * k];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) ws[128 * k] = pair_sum(chunk_sq<BF16>(w[k][0], w[k][1], w[k][2], w[k][3]));
+            pk0 += 1024; pk1 += 1024; pk2 += 1024; pk3 += 1024; ws += 512;
           }
-          if (c < c_hi) {
+          for (; c < c_hi; ++c) {
             ws[0] = pair_sum(chunk_sq<BF16>(pk0[0], pk1[0], pk2[0], pk3[0]));
+            pk0 += 256; pk1 += 256; pk2 += 256; pk3 += 256; ws += 128;
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[slot]);  // the stage's reads are done
@@ -325,7 +327,7 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
         if (pair_sync_or(1 + q, bad)) { fail(); stop = true; break; }
         // phase 2: the windows of this half
         if (j_n > 0) {
-          const float *col = scratch + buf * nch * 128 + L;  // chunk c at col[c * 128]
+          const float *col = scratch + sbuf * nch * 128 + L;  // chunk c at col[c * 128]
           int a = 4 * h * dch;
           float E;
           {  // the first window's chunks (a multiple of 4 of them): four independent sums
@@ -409,7 +411,7 @@ dh_status project_span_t(Plan &p, const SpanLayout &sl, int first_slot, int n_wi
   ProfScope ps(p, K_PROJECT_SPAN, s);
   kern<<<grid, kSpanThreads, smem, s>>>(tmA, B, (long long)sl.G * (long long)p.B_window_bytes, sl.img_bytes,
                                         first_slot, sl.stride, p.T, n_windows, sl.G, sl.rows, sl.n_pad,
-                                        sl.tmem_cols, sl.stages, cpg, images, p.nx, p.ny, p.d_status);
+                                        sl.tmem_cols, sl.nbuf, sl.stages, cpg, images, p.nx, p.ny, p.d_status);
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
 }
@@ -438,8 +440,11 @@ SpanLayout span_layout(const Plan &p, int slot_stride, int n_windows, int k0, in
     // the FP32 rounding of the energy and of the subtracted power); each needs a k-step
     if (rows < 16 * kNacc) continue;
     const int nacc = kNacc;
+    // accumulator buffers: 4 where tensor memory has room (the MMAs run further ahead of the
+    // epilogue), else 2
+    const int nbuf = 4 * nacc * n_pad <= 512 ? 4 : 2;
     int tmem_cols = 32;
-    while (tmem_cols < 2 * nacc * n_pad) tmem_cols *= 2;
+    while (tmem_cols < nbuf * nacc * n_pad) tmem_cols *= 2;
     const int k_pad = (rows + 63) / 64 * 64;
     const int img = 2 * n_pad * k_pad * 2;
     // a group's operand lives in the operand slots of its G windows
@@ -451,6 +456,7 @@ SpanLayout span_layout(const Plan &p, int slot_stride, int n_windows, int k0, in
     if (stages > kSpanMaxStages) stages = kSpanMaxStages;
     sl.G = G; sl.cpw = cpw; sl.rows = rows; sl.n_pad = n_pad; sl.k_pad = k_pad; sl.stride = s;
     sl.img_bytes = img; sl.stages = stages; sl.nacc = nacc; sl.tmem_cols = tmem_cols; sl.scr_bytes = scr;
+    sl.nbuf = nbuf;
     return sl;
   }
   return sl;
