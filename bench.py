@@ -660,7 +660,7 @@ def run_fourier(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    F = FOURIER_FRAMES
+    F = args.frames or FOURIER_FRAMES
     nwin = F - T + 1
     k0, k1 = FOURIER_BINS
     frames = SpeckleStream(SpeckleParams(NX, NY), seed=5000 + rank, device=dev).next(F)
@@ -720,8 +720,8 @@ def run_fourier(args, ws, rank, local):
             "dtype": ("mixed: f32 FFT, f16 tensor-core products (f32 accumulate)"
                       if hb == 2 else "f32"),
             "data": "synthetic",
-            "config": {"workload": "fourier: 2048 frames of 1024x1024 uint16, a 32-frame window "
-                                   "per frame (2017 windows), DFT bins 7..23, one CUDA graph "
+            "config": {"workload": f"fourier: {F} frames of 1024x1024 uint16, a 32-frame window "
+                                   f"per frame ({nwin} windows), DFT bins 7..23, one CUDA graph "
                                    "per step", "precision": args.precision,
                        "l2": "no flush: 4 GiB of frames and 8 GiB of holograms per step",
                        "parallelism": f"replicas x{ws}"},
@@ -1086,7 +1086,8 @@ def main(argv=None):
                     help="sliding workload: windows take C from the store's banded Gram "
                          "(dh_band_gram) instead of one Gram per window")
     ap.add_argument("--frames", type=int, default=0,
-                    help="sliding workload: frames per step (default 2048; smaller for ncu captures)")
+                    help="sliding and fourier workloads: frames per step (default 2048; smaller for "
+                         "ncu captures)")
     ap.add_argument("--projection", choices=["grouped", "per-window"], default="grouped",
                     help="sliding workload: DH_OPT_PROJECTION (grouped = 0, per-window = 1)")
     ap.add_argument("--covariance", choices=["holograms", "raw"], default="holograms",

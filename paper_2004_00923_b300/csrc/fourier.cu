@@ -5,6 +5,8 @@
 // projection operand, built once per call in the layout the eigensolver writes for Eq. 6,
 // and every window is projected onto it by the same kernels, |.|^2 summed in the epilogue:
 //   M[p] = sum_{k=k0..k1} |sum_t H[t][p] w_{t,k}|^2.
+#include <type_traits>
+
 #include "dh_internal.cuh"
 
 namespace dh {
@@ -167,15 +169,196 @@ k_fourier_sliding(const HT *__restrict__ H, long long rows_total, int nx, int ny
   }
 }
 
+// The same recurrence with two pixels a thread (adjacent rows of one image column, pixels p and
+// p + 1): their real parts share one register pair and their imaginary parts another, so every
+// operation of the recurrence is a paired FP32 instruction (__fadd2_rn, __fmul2_rn, __ffma2_rn)
+// with per-bin constant pairs from shared memory; each pixel keeps the same operations in the
+// same order as the one-pixel form, so the powers are bitwise those. A pixel pair's stored
+// values come in one 32-bit (16-bit storage) or 64-bit (FP32) load. A CTA covers 8 image
+// columns x 64 rows.
+template <typename HT> __device__ __forceinline__ void load_h2(const HT *H, long long rows_total, long long npix,
+                                                               int slot, long long p, float2 &re, float2 &im);
+template <> __device__ __forceinline__ void load_h2<float>(const float *H, long long, long long npix, int slot,
+                                                           long long p, float2 &re, float2 &im) {
+  const float *b = H + (long long)slot * 2 * npix + p;
+  re = *reinterpret_cast<const float2 *>(b);
+  im = *reinterpret_cast<const float2 *>(b + npix);
+}
+template <> __device__ __forceinline__ void load_h2<__half>(const __half *H, long long rows_total, long long,
+                                                            int slot, long long p, float2 &re, float2 &im) {
+  const __half *b = H + (p >> 6) * (rows_total << 6) + (2ll * slot << 6) + (p & 63);
+  re = __half22float2(*reinterpret_cast<const __half2 *>(b));
+  im = __half22float2(*reinterpret_cast<const __half2 *>(b + 64));
+}
+template <> __device__ __forceinline__ void load_h2<__nv_bfloat16>(const __nv_bfloat16 *H, long long rows_total,
+                                                                   long long, int slot, long long p, float2 &re,
+                                                                   float2 &im) {
+  const __nv_bfloat16 *b = H + (p >> 6) * (rows_total << 6) + (2ll * slot << 6) + (p & 63);
+  re = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(b));
+  im = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(b + 64));
+}
+constexpr int kSlide2Rows = 64;
+constexpr int kSlideDepth = 8;  // window steps prefetched ahead (cp.async ring per thread)
+// address of the Re (c = 0) or Im (c = 1) values of pixels p, p + 1 in slot `slot`
+template <typename HT> __device__ __forceinline__ const HT *pair_addr(const HT *H, long long rows_total,
+                                                                      long long npix, int slot, long long p, int c) {
+  if constexpr (sizeof(HT) == 4) return H + ((long long)slot * 2 + c) * npix + p;
+  else return H + (p >> 6) * (rows_total << 6) + ((2ll * slot + c) << 6) + (p & 63);
+}
+template <typename HT> __device__ __forceinline__ float2 pair_val(const void *v) {
+  if constexpr (sizeof(HT) == 4) return *reinterpret_cast<const float2 *>(v);
+  else if constexpr (std::is_same<HT, __half>::value) return __half22float2(*reinterpret_cast<const __half2 *>(v));
+  else return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(v));
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_bytes(uint32_t dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+template <typename HT, int NBM>
+__global__ void __launch_bounds__(kSlideThreads)
+k_fourier_sliding2(const HT *__restrict__ H, long long rows_total, int nx, int ny, int T, int k0, int nb,
+                   int first_slot, int n_windows, int seg, float *__restrict__ images) {
+  // pair tables: w[t][j] as (Re, Re), (Im, Im), (-Im, -Im); step factors e[j] likewise
+  extern __shared__ float2 tab2[];
+  __shared__ float out[2][kSlide2Rows][kSlideCols + 1];
+  // this thread's prefetch ring (kSlideDepth steps x 4 values of 2 pixels), after the tables
+  float2 *ring_sm = tab2 + 3 * (T * NBM + NBM);
+  const long long npix = (long long)nx * ny;
+  const double rs = 1.0 / sqrt((double)T);
+  const int nt = T * NBM + NBM;
+  for (int e = threadIdx.x; e < nt; e += blockDim.x) {
+    double sn = 0.0, cs = 0.0;
+    float re, im;
+    if (e < T * NBM) {
+      const int t = e / NBM, j = e % NBM, k = k0 + j;
+      if (j < nb) sincospi(-2.0 * (double)((t * k) % T) / (double)T, &sn, &cs);
+      re = (float)(cs * rs); im = (float)(sn * rs);
+    } else {
+      const int j = e - T * NBM, k = k0 + j;
+      if (j < nb) sincospi(2.0 * (double)(k % T) / (double)T, &sn, &cs);
+      re = (float)cs; im = (float)sn;
+    }
+    tab2[3 * e] = make_float2(re, re);
+    tab2[3 * e + 1] = make_float2(im, im);
+    tab2[3 * e + 2] = make_float2(-im, -im);
+  }
+  __syncthreads();
+  const float2 *w = tab2, *step = tab2 + 3 * T * NBM;
+  const int tiles_y = ny / kSlide2Rows;
+  const int kx0 = (blockIdx.x / tiles_y) * kSlideCols, ky0 = (blockIdx.x % tiles_y) * kSlide2Rows;
+  const int c = threadIdx.x / 32, r2 = threadIdx.x % 32;  // pixels at rows ky0 + 2 r2, + 1
+  const long long p = (long long)(kx0 + c) * ny + ky0 + 2 * r2;
+  const int w0 = blockIdx.y * seg, w1 = min(w0 + seg, n_windows);
+  const float scale = (float)rs;
+  const float2 sc2 = make_float2(scale, scale), m1 = make_float2(-1.f, -1.f);
+  float2 XR[NBM], XI[NBM];
+#pragma unroll
+  for (int j = 0; j < NBM; ++j) XR[j] = XI[j] = make_float2(0.f, 0.f);
+  for (int t = 0; t < T; ++t) {  // direct sum over the segment's first window
+    float2 hr, hi;
+    load_h2<HT>(H, rows_total, npix, first_slot + w0 + t, p, hr, hi);
+#pragma unroll
+    for (int j = 0; j < NBM; ++j) {
+      const float2 qr = w[3 * (t * NBM + j)], qi = w[3 * (t * NBM + j) + 1], qn = w[3 * (t * NBM + j) + 2];
+      XR[j] = __ffma2_rn(hr, qr, __ffma2_rn(hi, qn, XR[j]));  // fmaf(h.x, q.x, fmaf(-h.y, q.y, X.x))
+      XI[j] = __ffma2_rn(hr, qi, __ffma2_rn(hi, qr, XI[j]));  // fmaf(h.x, q.y, fmaf(h.y, q.x, X.y))
+    }
+  }
+  // The frames entering and leaving at window step sq (window sq advances from sq - 1) are
+  // copied kSlideDepth steps ahead into this thread's ring in shared memory (cp.async, one
+  // commit group per step, completed in order): slot sq % kSlideDepth holds in Re, in Im,
+  // out Re, out Im of the pixel pair. Only the thread reads its slots: no barrier is needed.
+  constexpr int EB = sizeof(HT) * 2;  // bytes of a pair's Re or Im values
+  const uint32_t ring0 = (uint32_t)__cvta_generic_to_shared(ring_sm);
+  auto ring_addr = [&](int slot, int j) -> uint32_t {
+    return ring0 + (uint32_t)(((slot * 4 + j) * kSlideThreads + threadIdx.x) * EB);
+  };
+  auto issue = [&](int sq) {  // always commits a group, empty past the segment
+    if (sq > w0 && sq < w1) {
+      const int sl = sq % kSlideDepth;
+      cp_async_bytes<EB>(ring_addr(sl, 0), pair_addr<HT>(H, rows_total, npix, first_slot + sq - 1 + T, p, 0));
+      cp_async_bytes<EB>(ring_addr(sl, 1), pair_addr<HT>(H, rows_total, npix, first_slot + sq - 1 + T, p, 1));
+      cp_async_bytes<EB>(ring_addr(sl, 2), pair_addr<HT>(H, rows_total, npix, first_slot + sq - 1, p, 0));
+      cp_async_bytes<EB>(ring_addr(sl, 3), pair_addr<HT>(H, rows_total, npix, first_slot + sq - 1, p, 1));
+    }
+    cp_async_commit();
+  };
+  for (int k = 0; k < kSlideDepth; ++k) issue(w0 + k);
+  for (int s = w0; s < w1; s += 2) {
+    float2 m[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (s + q >= w1) break;
+      cp_async_wait<kSlideDepth - 1>();  // step s + q's group has landed
+      if (s + q > w0) {  // advance by one frame
+        const int sl = (s + q) % kSlideDepth;
+        const uint8_t *rb = reinterpret_cast<const uint8_t *>(ring_sm);
+        const float2 hin_r = pair_val<HT>(rb + (ring_addr(sl, 0) - ring0));
+        const float2 hin_i = pair_val<HT>(rb + (ring_addr(sl, 1) - ring0));
+        const float2 hout_r = pair_val<HT>(rb + (ring_addr(sl, 2) - ring0));
+        const float2 hout_i = pair_val<HT>(rb + (ring_addr(sl, 3) - ring0));
+        const float2 dr = __fmul2_rn(__ffma2_rn(hout_r, m1, hin_r), sc2);
+        const float2 di = __fmul2_rn(__ffma2_rn(hout_i, m1, hin_i), sc2);
+#pragma unroll
+        for (int j = 0; j < NBM; ++j) {
+          const float2 ar = __fadd2_rn(XR[j], dr), ai = __fadd2_rn(XI[j], di);
+          const float2 er = step[3 * j], ei = step[3 * j + 1], en = step[3 * j + 2];
+          XR[j] = __ffma2_rn(ar, er, __fmul2_rn(ai, en));  // fmaf(a.x, e.x, -a.y * e.y)
+          XI[j] = __ffma2_rn(ar, ei, __fmul2_rn(ai, er));  // fmaf(a.x, e.y, a.y * e.x)
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NBM; ++j) m[q] = __ffma2_rn(XR[j], XR[j], __ffma2_rn(XI[j], XI[j], m[q]));
+      issue(s + q + kSlideDepth);  // the slot just read is refilled for a later step
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      out[q][2 * r2][c] = m[q].x;
+      out[q][2 * r2 + 1][c] = m[q].y;
+    }
+    __syncthreads();
+    // image rows ky0 .. ky0 + 63, columns kx0 .. kx0 + 7: 32 contiguous bytes per row
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (s + q >= w1) break;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int i = threadIdx.x + hh * kSlideThreads, ry = i / kSlideCols, cx = i % kSlideCols;
+        images[(long long)(s + q) * npix + (long long)(ky0 + ry) * nx + kx0 + cx] = out[q][ry][cx];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <typename HT, int NBM>
 dh_status launch_sliding_t(Plan &p, int first_slot, int n_windows, int k0, int nb, float *images, cudaStream_t s) {
   const int seg = 128;
-  const size_t smem = (size_t)(p.T * NBM + NBM) * sizeof(float2);
-  dim3 grid((unsigned)((p.nx / kSlideCols) * (p.ny / kSlideRows)), (unsigned)((n_windows + seg - 1) / seg));
   ProfScope ps(p, K_FOURIER_SLIDING, s);
-  k_fourier_sliding<HT, NBM><<<grid, kSlideThreads, smem, s>>>(
-      static_cast<const HT *>(p.d_H), 2ll * p.max_frames, p.nx, p.ny, p.T, k0, nb, first_slot, n_windows, seg,
-      images);
+  if (p.ny % kSlide2Rows == 0 && NBM <= 24) {  // two pixels a thread (32 bins would spill)
+    const size_t smem = (size_t)3 * (p.T * NBM + NBM) * sizeof(float2) +
+                        (size_t)kSlideDepth * 4 * kSlideThreads * 2 * sizeof(HT);
+    static bool attr = false;
+    if (!attr) {
+      DH_CUDA_TRY(cudaFuncSetAttribute(k_fourier_sliding2<HT, NBM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));  // tables (<= 37 KB at T = 64) + ring (<= 64 KB)
+      attr = true;
+    }
+    dim3 grid((unsigned)((p.nx / kSlideCols) * (p.ny / kSlide2Rows)), (unsigned)((n_windows + seg - 1) / seg));
+    k_fourier_sliding2<HT, NBM><<<grid, kSlideThreads, smem, s>>>(
+        static_cast<const HT *>(p.d_H), 2ll * p.max_frames, p.nx, p.ny, p.T, k0, nb, first_slot, n_windows, seg,
+        images);
+  } else {
+    const size_t smem = (size_t)(p.T * NBM + NBM) * sizeof(float2);
+    dim3 grid((unsigned)((p.nx / kSlideCols) * (p.ny / kSlideRows)), (unsigned)((n_windows + seg - 1) / seg));
+    k_fourier_sliding<HT, NBM><<<grid, kSlideThreads, smem, s>>>(
+        static_cast<const HT *>(p.d_H), 2ll * p.max_frames, p.nx, p.ny, p.T, k0, nb, first_slot, n_windows, seg,
+        images);
+  }
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
 }
