@@ -116,7 +116,10 @@ StoreSizes store_sizes(const Plan &p) {
   z.B_window = (bw + 1023) / 1024 * 1024;
   // + room for the last group's operand of the grouped projection (at most 64 KiB)
   z.B = z.B_window * p.max_windows + (p.prec == DH_PREC_FP32 ? 0 : (64u << 10));
-  z.W = z.B_window;  // one operand shared by every window (Eq. 8)
+  // one operand shared by every window (Eq. 8); 16-bit plans also hold there the banded group
+  // operand of the tensor-core sliding DFT (at most 2 x 240 x 256 16-bit values)
+  z.W = z.B_window;
+  if (p.prec != DH_PREC_FP32 && z.W < (256u << 10)) z.W = 256u << 10;
   return z;
 }
 
@@ -133,6 +136,7 @@ dh_status alloc_windows(Plan &p) {
   if ((st = dalloc(p, &p.d_V, z.V)) != DH_OK) return st;
   if ((st = dalloc(p, &p.d_B, z.B)) != DH_OK) return st;
   if ((st = dalloc(p, &p.d_W, z.W)) != DH_OK) return st;
+  p.W_bytes = z.W;
   p.window_bytes = z.windows();
   DH_CUDA_TRY(cudaMemset(p.d_B, 0, z.B));
   if (p.prec != DH_PREC_FP32) {

@@ -62,6 +62,7 @@ struct Plan {
   void *d_B = nullptr;      // projection operand per window
   size_t B_window_bytes = 0;
   void *d_W = nullptr;      // projection operand shared by all windows (Eq. 8's DFT columns)
+  size_t W_bytes = 0;
   uint32_t *d_status = nullptr;
 
   // tensor maps for the tensor-core kernels (16-bit storage only)
@@ -97,7 +98,7 @@ struct Plan {
 enum KernelId {
   K_RENDER_ROWS = 0, K_RENDER_COLS, K_GRAM_SIMT, K_GRAM_TC, K_REDUCE_COV, K_JACOBI,
   K_PROJECT_SIMT, K_PROJECT_TC, K_FOURIER_OP, K_SVD_FOURIER_OP, K_RENDER_FUSED, K_GRAM_RAW,
-  K_REDUCE_RAW, K_FOURIER_SLIDING, K_BAND_GRAM, K_BAND_REDUCE, K_BAND_COV, K_PROJECT_SPAN, K_COUNT
+  K_REDUCE_RAW, K_FOURIER_SLIDING, K_BAND_GRAM, K_BAND_REDUCE, K_BAND_COV, K_PROJECT_SPAN, K_FOURIER_SPAN, K_COUNT
 };
 const char *kernel_name(int kid);
 dh_status profile_enable(Plan &p, int on);
@@ -194,6 +195,12 @@ dh_status launch_project_simt(Plan &p, int first_slot, int slot_stride, int n_wi
                               float *images, int woff, cudaStream_t s, const void *shared_op = nullptr);
 dh_status launch_project_tc(Plan &p, int first_slot, int slot_stride, int n_windows, int Npad,
                             float *images, int woff, cudaStream_t s, const void *shared_op = nullptr);
+// Eqs. 8-9 for overlapping windows on the tensor cores, 7 windows per span load (FP16 storage,
+// 17 kept bins, slot stride < T, n_y >= 128): whether it applies, and the launch (operand
+// built into d_W first).
+bool fourier_span_applies(const Plan &p, int slot_stride, int n_windows, int nS);
+dh_status launch_fourier_span(Plan &p, int first_slot, int slot_stride, int n_windows, int k0, int nS,
+                              float *images, cudaStream_t s);
 // Eqs. 2-3 then 8-9: per window, the operand Q = V_S V_S^{t*} W_band from the sorted
 // eigenvectors of windows [woff, woff + n_windows), replacing the Eq. 6 operand.
 dh_status launch_svd_fourier_operand(Plan &p, int n_windows, int k0, int k1, int b0, int b1, int Npad,

@@ -383,6 +383,9 @@ dh_status launch_sliding(Plan &p, int first_slot, int n_windows, int k0, int nb,
 dh_status launch_fourier(Plan &p, int first_slot, int slot_stride, int n_windows, int k0, int k1,
                          float *images, cudaStream_t s) {
   const int nS = k1 - k0 + 1;
+  // overlapping windows on the tensor cores: 7 windows per load of their frames
+  if (fourier_span_applies(p, slot_stride, n_windows, nS))
+    return launch_fourier_span(p, first_slot, slot_stride, n_windows, k0, nS, images, s);
   // a window per frame: the sliding recurrence (each frame read twice instead of T times)
   if (slot_stride == 1 && n_windows >= 8 && nS <= 32 && p.ny % kSlideRows == 0 && p.nx % kSlideCols == 0) {
     switch (p.prec) {

@@ -112,3 +112,27 @@ def test_fourier_sliding_recurrence_long_run(dh, T, b0, b1):
     for w in (0, 150, 299):
         M = oracle.fourier_window(frames[w:w + T], LAM, Z, PITCH, b0, b1)
         assert rel(slide[w], M) <= TOL_IMG["fp32"], (w, rel(slide[w], M))
+
+
+@pytest.mark.parametrize("stride,n", [(1, 16), (2, 9), (5, 3)])
+def test_fourier_span_equals_single_window_projection(dh, stride, n):
+    """Overlapping windows on the tensor-core span path (7 windows per load of their frames,
+    FP16, 17 bins): equal to one-window calls (the per-window projection onto W) to FP32
+    rounding, over full and ragged groups, and to the oracle."""
+    T, b0, b1 = 32, 7, 23
+    F = (n - 1) * stride + T
+    frames = SpeckleStream(SpeckleParams(256, 128), seed=90 + stride).next(F).numpy()
+    with dh.Plan(256, 128, LAM, Z, PITCH, T=T, precision="fp16", max_frames=F) as plan:
+        plan.render_frames(to_gpu(frames))
+        plan.profile(True)
+        span = plan.fourier_windows(0, stride, n, b0, b1).cpu().numpy()
+        prof = plan.profile_read()
+        plan.profile(False)
+        assert prof["fourier_span"][0] == 1, prof
+        for w in range(n):
+            one = plan.fourier_windows(w * stride, 1, 1, b0, b1)[0].cpu().numpy()
+            assert rel(span[w], one) <= 1e-5, (w, rel(span[w], one))
+        assert plan.status() == 0
+    for w in (0, n - 1):
+        M = oracle.fourier_window(frames[w * stride:w * stride + T], LAM, Z, PITCH, b0, b1)
+        assert rel(span[w], M) <= TOL_IMG["fp16"], (w, rel(span[w], M))
