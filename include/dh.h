@@ -129,9 +129,9 @@ dh_status dh_plan_reserve(dh_plan_t plan, int max_frames, int max_windows);
  *   length and stride inside the band take their C from it without reading the holograms
  *   again (DH_ERR_STATE for windows outside the band). 16-bit storage only. */
 #define DH_OPT_COVARIANCE 3
-/* DH_OPT_PROJECTION: 0 (default): overlapping windows (slot stride s < T, s a multiple of 4;
- *   FP16 storage, n_y >= 128, n_x a multiple of 8) with at most 4 discarded components (k0 + T - 1 - k1 <= 4)
- *   are projected in groups of up to 8: each pixel tile of a group's span of frames is read
+/* DH_OPT_PROJECTION: 0 (default): overlapping windows (slot stride s < T, s a multiple of
+ *   4; FP16 storage, n_y >= 128, n_x a multiple of 8) with at most 4 discarded components
+ *   (k0 + T - 1 - k1 <= 4) are projected in groups of up to 8: each pixel tile of a group's span of frames is read
  *   once for all its windows, and each window's power is taken as its energy sum_t |H_t|^2
  *   minus its discarded components' power (equal to Eq. 7 because V is unitary). Other
  *   calls project per window. 1: per window always (Eq. 7 over the kept components). */
@@ -199,7 +199,10 @@ dh_status dh_band_gram(dh_plan_t plan, int first_slot, int n_frames, void *strea
  * [first_slot + w * slot_stride, + T). No covariance or eigendecomposition is computed;
  * windows of any number and stride (stride 1 = a new window per frame) share the rendered
  * holograms. Runs on the tensor cores for 16-bit storage (the DFT operand split into hi +
- * lo 16-bit parts), on FP32 CUDA cores for FP32 storage. Asynchronous. */
+ * lo 16-bit parts), on FP32 CUDA cores for FP32 storage. Overlapping windows (stride < T)
+ * are computed together where possible: 7 at a time from one load of their frames on the
+ * tensor cores (FP16 storage, 17 bins as the paper's 7..23 at T = 32, n_y >= 128), else one
+ * frame read twice per window by a sliding DFT recurrence (stride 1). Asynchronous. */
 dh_status dh_fourier_windows(dh_plan_t plan, int first_slot, int slot_stride, int n_windows,
                              int k0, int k1, float *images_dev, void *stream);
 
