@@ -131,10 +131,11 @@ dh_status dh_plan_reserve(dh_plan_t plan, int max_frames, int max_windows);
 #define DH_OPT_COVARIANCE 3
 /* DH_OPT_PROJECTION: 0 (default): overlapping windows (slot stride s < T, s a multiple of
  *   4; FP16 storage, n_y >= 128, n_x a multiple of 8) with at most 4 discarded components
- *   (k0 + T - 1 - k1 <= 4) are projected in groups of up to 8: each pixel tile of a group's span of frames is read
- *   once for all its windows, and each window's power is taken as its energy sum_t |H_t|^2
- *   minus its discarded components' power (equal to Eq. 7 because V is unitary). Other
- *   calls project per window. 1: per window always (Eq. 7 over the kept components). */
+ *   (k0 + T - 1 - k1 <= 4) are projected in groups of up to 8: each pixel tile of a group's
+ *   span of frames is read once for all its windows, and each window's power is taken as
+ *   its energy sum_t |H_t|^2 minus its discarded components' power (equal to Eq. 7 because
+ *   V is unitary). Other calls project per window. 1: per window always (Eq. 7 over the
+ *   kept components). */
 #define DH_OPT_PROJECTION 4
 dh_status dh_plan_set_option(dh_plan_t plan, int option, int value);
 dh_status dh_plan_get_option(dh_plan_t plan, int option, int *value);
