@@ -1,7 +1,9 @@
 // Eq. 4 on FP32 CUDA cores (the plain path): partial real Gram matrices
 //   G = X X^T,  X = the 2T rows [Re H_0; Im H_0; Re H_1; Im H_1; ...] over a pixel range.
 // Each CTA owns one (window, pixel range) unit and accumulates products in FP32 over
-// 256-pixel runs, then in FP64; units are summed in FP64 by the reduction kernel.
+// 256-pixel runs, then in FP64; units are summed in FP64 by the reduction kernel. Chunks of
+// 32 pixels are double-buffered in shared memory: the next chunk's copy (cp.async, 8-byte
+// pieces) is in flight while the current one is multiplied.
 // C[t][u] = (G[2t][2u] + G[2t+1][2u+1]) + i (G[2t][2u+1] - G[2t+1][2u]).
 #include "dh_internal.cuh"
 
@@ -16,7 +18,7 @@ k_gram_simt(const float *__restrict__ H, long long npix, int first_slot, int slo
   constexpr int TM = M / 16;
   constexpr int KC = 32;
   constexpr int LD = KC + 2;  // row stride: 8-byte aligned pairs, conflict-free columns
-  __shared__ __align__(16) float xs[M * LD];
+  __shared__ __align__(16) float xs[2][M * LD];
   const int w = blockIdx.x / units, u = blockIdx.x % units;
   const float *X = H + (long long)(first_slot + w * slot_stride) * 2 * npix + u * pix_per_unit;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -26,20 +28,32 @@ k_gram_simt(const float *__restrict__ H, long long npix, int first_slot, int slo
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int k = 0; k < TM; ++k) acc[i][k] = 0.f, acc64[i][k] = 0.0;
+  // copy of chunk `pc` into buffer `b`: 8-byte pieces, consecutive threads along a row
+  auto issue = [&](long long pc, int b) {
+    if (pc < pix_per_unit) {
+      for (int e = threadIdx.x; e < M * (KC / 2); e += 256) {
+        const int r = e / (KC / 2), k = 2 * (e % (KC / 2));
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&xs[b][r * LD + k]);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(X + (long long)r * npix + pc + k)
+                     : "memory");
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  issue(0, 0);
   int chunk = 0;
   for (long long pc = 0; pc < pix_per_unit; pc += KC, ++chunk) {
-    for (int e = threadIdx.x; e < M * KC; e += 256) {
-      const int r = e / KC, k = e % KC;
-      xs[r * LD + k] = X[(long long)r * npix + pc + k];
-    }
+    const int cb = chunk & 1;
+    issue(pc + KC, cb ^ 1);  // the other buffer: its readers passed the barrier below
+    asm volatile("cp.async.wait_group 1;" ::: "memory");  // this chunk's copy has landed
     __syncthreads();
 #pragma unroll 4
     for (int k = 0; k < KC; k += 2) {
       float2 a[TM], b[TM];
 #pragma unroll
       for (int i = 0; i < TM; ++i) {
-        a[i] = *reinterpret_cast<const float2 *>(&xs[(ty + 16 * i) * LD + k]);
-        b[i] = *reinterpret_cast<const float2 *>(&xs[(tx + 16 * i) * LD + k]);
+        a[i] = *reinterpret_cast<const float2 *>(&xs[cb][(ty + 16 * i) * LD + k]);
+        b[i] = *reinterpret_cast<const float2 *>(&xs[cb][(tx + 16 * i) * LD + k]);
       }
 #pragma unroll
       for (int i = 0; i < TM; ++i)
