@@ -308,16 +308,25 @@ struct RowCfg {
   static constexpr int CPR = S::N / 8;             // chunks per row
 };
 
-template <int LOGN>
+// PER_WARP (transforms of one warp each, P = 32): warp w loads the chunks of row y0 + w only,
+// so it can stage them in its own exchange region without a CTA barrier.
+template <int LOGN, bool PER_WARP = false>
 __device__ __forceinline__ void row_prefetch(uint4 (&pf)[RowCfg<LOGN>::CPT], const uint16_t *__restrict__ frame,
                                              int y0) {
   using C = RowCfg<LOGN>;
   const uint4 *src = reinterpret_cast<const uint4 *>(frame + (long long)y0 * Shape<LOGN>::N);
+  if constexpr (PER_WARP) {
+    static_assert(Shape<LOGN>::P == 32 && C::CPR == 32 * C::CPT, "one row a warp");
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int k = 0; k < C::CPT; ++k) pf[k] = __ldcs(src + threadIdx.x + k * C::NT);  // read once
+    for (int k = 0; k < C::CPT; ++k) pf[k] = __ldcs(src + w * C::CPR + lane + 32 * k);  // read once
+  } else {
+#pragma unroll
+    for (int k = 0; k < C::CPT; ++k) pf[k] = __ldcs(src + threadIdx.x + k * C::NT);  // read once
+  }
 }
 
-template <int LOGN, bool LEAD_SYNC = true, typename Parked>
+template <int LOGN, bool LEAD_SYNC = true, bool PER_WARP = false, typename Parked>
 __device__ __forceinline__ void row_work(const uint4 (&pf)[RowCfg<LOGN>::CPT], float2 *smem, int y0, int ny,
                                          int cw_log, const float2 *__restrict__ cx,
                                          const float2 *__restrict__ cy, const float2 *__restrict__ tw,
@@ -329,13 +338,20 @@ __device__ __forceinline__ void row_work(const uint4 (&pf)[RowCfg<LOGN>::CPT], f
   float2 *sm = smem + fft * S::RSTRIDE;
   const int y = y0 + fft;
   if constexpr (LEAD_SYNC) __syncthreads();  // every transform is done with its region (previous item)
+  if constexpr (PER_WARP) {  // this warp's row, into its own region
 #pragma unroll
-  for (int k = 0; k < C::CPT; ++k) {
-    const int c = threadIdx.x + k * C::NT, row = c / C::CPR, cr = c % C::CPR;
-    reinterpret_cast<uint4 *>(smem + row * S::RSTRIDE)[cr] = pf[k];
+    for (int k = 0; k < C::CPT; ++k) reinterpret_cast<uint4 *>(sm)[(threadIdx.x & 31) + 32 * k] = pf[k];
+    parked();
+    __syncwarp();
+  } else {
+#pragma unroll
+    for (int k = 0; k < C::CPT; ++k) {
+      const int c = threadIdx.x + k * C::NT, row = c / C::CPR, cr = c % C::CPR;
+      reinterpret_cast<uint4 *>(smem + row * S::RSTRIDE)[cr] = pf[k];
+    }
+    parked();
+    __syncthreads();
   }
-  parked();
-  __syncthreads();
   const uint16_t *row16 = reinterpret_cast<const uint16_t *>(sm);
   float2 v[S::R];
 #pragma unroll
@@ -563,6 +579,10 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
   constexpr int NI = N / FPC;       // row items = column items per frame
   constexpr long long NPIX = (long long)N * N;
   static_assert(RC::NT == kCtaThreads, "fused render needs full-size items on both axes");
+  // one transform a warp (n = 1024): a row item's warps stage and release their rows each on
+  // their own (rows_done counts rows), with no CTA barrier inside the item
+  constexpr bool PW = S::P == 32;
+  constexpr unsigned ROWS_PER_FRAME = PW ? (unsigned)N : (unsigned)NI;
   extern __shared__ float2 smem[];
   // the CTA lives for the whole launch: its twiddle and chirp tables are copied into shared
   // memory once, after the exchange / tile buffer
@@ -591,7 +611,7 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
   int cur = tk[0];
   uint4 pf[RC::CPT];
   if (valid(cur) && is_row(cur))
-    row_prefetch<LOGN>(pf, frames + (long long)frame_of(cur) * frame_stride, item_of(cur) * FPC);
+    row_prefetch<LOGN, PW>(pf, frames + (long long)frame_of(cur) * frame_stride, item_of(cur) * FPC);
   uint32_t phase = 0;
   uint32_t maxbits = 0;
   int b = 1;
@@ -613,7 +633,7 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
     // ticket names no item)
     auto prefetch_next = [&]() {
       if (valid(nxt) && is_row(nxt))
-        row_prefetch<LOGN>(pf, frames + (long long)frame_of(nxt) * frame_stride, item_of(nxt) * FPC);
+        row_prefetch<LOGN, PW>(pf, frames + (long long)frame_of(nxt) * frame_stride, item_of(nxt) * FPC);
     };
     if (!valid(cur)) {
       prefetch_next();
@@ -621,14 +641,19 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
       const int f = frame_of(cur), i = item_of(cur), rs = f % ring;
       float2 *ring_f = mid + (long long)rs * NPIX;
       if (is_row(cur)) {
-        row_work<LOGN, false>(pf, smem, i * FPC, N, cw_log, s_cx, s_cy, s_tw, ring_f, prefetch_next);
+        row_work<LOGN, false, PW>(pf, smem, i * FPC, N, cw_log, s_cx, s_cy, s_tw, ring_f, prefetch_next);
         fence_proxy_async_global();  // this thread's ring writes, for later bulk copies
-        __syncthreads();
-        if (threadIdx.x == 0) red_release_add(rows_done + rs, 1u);  // after the CTA's writes
+        if constexpr (PW) {
+          __syncwarp();
+          if ((threadIdx.x & 31) == 0) red_release_add(rows_done + rs, 1u);  // after the warp's writes
+        } else {
+          __syncthreads();
+          if (threadIdx.x == 0) red_release_add(rows_done + rs, 1u);  // after the CTA's writes
+        }
       } else {
         bool ok = true;
         if (threadIdx.x == 0) {
-          ok = wait_geq(rows_done + rs, (unsigned)(f / ring + 1) * NI);
+          ok = wait_geq(rows_done + rs, (unsigned)(f / ring + 1) * ROWS_PER_FRAME);
           if (ok) fence_proxy_async_global();
         }
         const float2 *src = ring_f + (long long)i * FPC * N;
