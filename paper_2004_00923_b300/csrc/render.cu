@@ -156,8 +156,13 @@ __device__ __forceinline__ void dif_each(float2 (&v)[RR]) {
   }
 }
 
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
 // One length-N transform spread over P threads (index j). On entry v[r] = x[j + r P];
-// on exit element j + i P of the transform is v[out_reg(i)].
+// on exit element j + i P of the transform is v[out_reg(i)]. `freed()` runs on every thread
+// once it has made its last read of `sm` (for the column tile: of the whole buffer).
 template <int LOGN, bool CTA_SYNC>
 struct Engine {
   using S = Shape<LOGN>;
@@ -178,8 +183,10 @@ struct Engine {
                       : (i % S::B) + S::B * bitrev(i / S::B, S::LOGR2);
   }
 
+  template <typename Freed = NoHook>
   static __device__ __forceinline__ void run(float2 (&v)[S::R], float2 *sm, int j,
-                                             const float2 *__restrict__ tw) {
+                                             const float2 *__restrict__ tw, Freed freed = Freed()) {
+    if constexpr (S::NPASS == 1) freed();
     dif<S::R, 1, 0, S::R>(v);  // pass 0 (span 1): no inter-pass twiddles
     if constexpr (S::NPASS > 1) {
       sync();  // earlier readers of sm are done
@@ -192,6 +199,7 @@ struct Engine {
         const int Ns = 1 << (p * S::LOGR);
 #pragma unroll
         for (int r = 0; r < S::R; ++r) v[r] = sm[pad(j + r * S::P)];
+        if (p == S::L - 1 && S::R2 == 1) freed();
         const int m = j & (Ns - 1);
 #pragma unroll
         for (int r = 1; r < S::R; ++r) v[r] = cmul(v[r], tw[tw_off + (r - 1) * Ns + m]);
@@ -208,6 +216,7 @@ struct Engine {
         constexpr int NsE = 1 << (S::L * S::LOGR);
 #pragma unroll
         for (int i = 0; i < S::R; ++i) v[i] = sm[pad(j + i * S::P)];
+        freed();
 #pragma unroll
         for (int q = 0; q < S::B; ++q) {
           const int b = j + q * S::P;
@@ -297,7 +306,8 @@ __device__ __forceinline__ int mid_index(int kx, int y, int ny, int cw_log) {
 // Row work: FPC consecutive rows y0.. of one frame. `pf` holds their uint16 samples (16-byte
 // chunks, thread-strided, loaded by row_prefetch); each transform's input row is parked at
 // the head of its own exchange region, then `parked()` runs (the caller issues the next
-// prefetch there, so it overlaps this item's transforms). Output: the frame's intermediate.
+// prefetch there, so it overlaps this item's transforms); `freed()` runs on each thread after
+// its last read of shared memory. Output: the frame's intermediate.
 template <int LOGN>
 struct RowCfg {
   using S = Shape<LOGN>;
@@ -326,11 +336,11 @@ __device__ __forceinline__ void row_prefetch(uint4 (&pf)[RowCfg<LOGN>::CPT], con
   }
 }
 
-template <int LOGN, bool LEAD_SYNC = true, bool PER_WARP = false, typename Parked>
+template <int LOGN, bool LEAD_SYNC = true, bool PER_WARP = false, typename Parked, typename Freed = NoHook>
 __device__ __forceinline__ void row_work(const uint4 (&pf)[RowCfg<LOGN>::CPT], float2 *smem, int y0, int ny,
                                          int cw_log, const float2 *__restrict__ cx,
                                          const float2 *__restrict__ cy, const float2 *__restrict__ tw,
-                                         float2 *__restrict__ dst, Parked parked) {
+                                         float2 *__restrict__ dst, Parked parked, Freed freed = Freed()) {
   using S = Shape<LOGN>;
   using C = RowCfg<LOGN>;
   using E = Engine<LOGN, (S::P > 32)>;
@@ -361,7 +371,7 @@ __device__ __forceinline__ void row_work(const uint4 (&pf)[RowCfg<LOGN>::CPT], f
     const float2 c = cx[x];
     v[r] = make_float2(a * c.x, a * c.y);
   }
-  E::run(v, sm, j, tw);  // its first exchange store is ordered after the reads above
+  E::run(v, sm, j, tw, freed);  // its first exchange store is ordered after the reads above
   const float2 cyy = cy[y];
   if ((S::P & ((1 << cw_log) - 1)) == 0) {
     // kx = j + i P: the tile column and the swizzle are fixed per thread, and successive
@@ -377,49 +387,66 @@ __device__ __forceinline__ void row_work(const uint4 (&pf)[RowCfg<LOGN>::CPT], f
   }
 }
 
+// Bytes of one column tile (FPC columns of the intermediate, contiguous), and the bulk copy
+// of one into shared memory that completes on `bar` (one thread issues it).
+template <int LOGN>
+__host__ __device__ constexpr int tile_bytes() { return fpc<LOGN>() * Shape<LOGN>::N * (int)sizeof(float2); }
+
+template <int LOGN>
+__device__ __forceinline__ void issue_tile(const float2 *__restrict__ src, float2 *smem, uint64_t *bar) {
+  constexpr int TILE_BYTES = tile_bytes<LOGN>();
+  constexpr int CHUNK = TILE_BYTES < 16384 ? TILE_BYTES : 16384;
+  tc::mbar_arrive_expect_tx(bar, TILE_BYTES);
+  const char *s8 = reinterpret_cast<const char *>(src);
+#pragma unroll
+  for (int off = 0; off < TILE_BYTES; off += CHUNK)
+    tc::bulk_load(reinterpret_cast<char *>(smem) + off, s8 + off, CHUNK, bar);
+}
+
 // Column work: one tile of FPC (= CW) columns [kx0, kx0 + FPC) of one frame. The tile
 // (contiguous, CW n_y FP32 complex values) arrives by bulk asynchronous copy into shared
-// memory (thread 0 issues it; `issued()` then runs on every thread, `landed()` on thread 0
-// once the copy is complete); each transform (P threads) reads its column, runs in place
-// in the same buffer, and writes the hologram planes of `slot` in column-major pixel order
-// p = kx n_y + ky. Returns false (after a barrier) if the copy did not complete within the
-// wait budget; `copy_ok` false on thread 0 skips the copy (a failed wait before it).
-template <int LOGN, typename OutT, bool TAIL_SYNC = true, typename Issued, typename Landed>
+// memory (thread 0 issues it; `issued()` then runs on every thread); each transform
+// (P threads) reads its column, runs in place in the same buffer, and writes the hologram
+// planes of `slot` in column-major pixel order p = kx n_y + ky. `landed()` runs on thread 0
+// once every thread has read the tile and dropped its lines from L2; `freed()` runs on each
+// thread after its last read of the buffer. Returns false (after a barrier) if the copy did
+// not complete within the wait budget; `copy_ok` false on thread 0 skips the copy (a failed
+// wait before it); `preissued` (the same on every thread) says the copy is already in flight
+// on `bar` (issue_tile).
+template <int LOGN, typename OutT, bool TAIL_SYNC = true, typename Issued, typename Landed,
+          typename Freed = NoHook>
 __device__ __forceinline__ bool col_work(const float2 *__restrict__ src, float2 *smem, uint64_t *bar,
-                                         uint32_t &phase, int *abort_flag, bool copy_ok, int kx0,
-                                         OutT *__restrict__ H, long long npix, long long rows_total,
+                                         uint32_t &phase, int *abort_flag, bool copy_ok, bool preissued,
+                                         int kx0, OutT *__restrict__ H, long long npix, long long rows_total,
                                          int slot, uint32_t &maxbits, const float2 *__restrict__ tw,
-                                         Issued issued, Landed landed) {
+                                         Issued issued, Landed landed, Freed freed = Freed()) {
   using S = Shape<LOGN>;
   constexpr int FPC = fpc<LOGN>();
   constexpr int CW_LOG = FPC == 16 ? 4 : FPC == 8 ? 3 : FPC == 4 ? 2 : FPC == 2 ? 1 : 0;
-  constexpr int TILE_BYTES = FPC * S::N * (int)sizeof(float2);
-  constexpr int CHUNK = TILE_BYTES < 16384 ? TILE_BYTES : 16384;
+  constexpr int TILE_BYTES = tile_bytes<LOGN>();
   using E = Engine<LOGN, (S::P > 32)>;
   const int fft = threadIdx.x / S::P, j = threadIdx.x % S::P;
   float2 *sm = smem + fft * S::RSTRIDE;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && !preissued) {
     if (copy_ok) {
-      tc::mbar_arrive_expect_tx(bar, TILE_BYTES);
-      const char *s8 = reinterpret_cast<const char *>(src);
-#pragma unroll
-      for (int off = 0; off < TILE_BYTES; off += CHUNK)
-        tc::bulk_load(reinterpret_cast<char *>(smem) + off, s8 + off, CHUNK, bar);
+      issue_tile<LOGN>(src, smem, bar);
     } else {
       *abort_flag = 1;
       tc::mbar_arrive(bar);  // completes the phase without data so no thread waits it out
     }
   }
   issued();
-  if (!tc::mbar_wait(bar, phase)) *abort_flag = 1;
+  const bool got = tc::mbar_wait(bar, phase);
+  if (!got) *abort_flag = 1;
   phase ^= 1;
-  if (threadIdx.x == 0 && copy_ok && !*abort_flag) landed();
-  __syncthreads();
-  if (*abort_flag) return false;
   // the tile is in shared memory: its lines of the intermediate need no write-back (the
-  // next writer of this part of the intermediate overwrites it whole)
-  for (int off = threadIdx.x * 128; off < TILE_BYTES; off += blockDim.x * 128)
-    l2_discard(reinterpret_cast<const char *>(src) + off);
+  // next writer of this part of the intermediate overwrites it whole, and may start only
+  // after `landed()`, which the barrier below orders after every thread's discards). A
+  // thread 0 that skips the copy sets the abort flag before its arrival, so the wait orders
+  // that write before this read.
+  if (got && !*abort_flag)
+    for (int off = threadIdx.x * 128; off < TILE_BYTES; off += blockDim.x * 128)
+      l2_discard(reinterpret_cast<const char *>(src) + off);
   float2 v[S::R];
   if constexpr (S::P % 16 == 0) {  // y = j + r P keeps the swizzle of j
     const float2 *col = smem + j * FPC + (fft ^ mid_swz(j, CW_LOG));
@@ -433,7 +460,9 @@ __device__ __forceinline__ bool col_work(const float2 *__restrict__ src, float2 
     }
   }
   __syncthreads();  // the tile is consumed; its buffer becomes the exchange regions
-  E::run(v, sm, j, tw);
+  if (*abort_flag) return false;
+  if (threadIdx.x == 0 && copy_ok) landed();
+  E::run(v, sm, j, tw, freed);
   const int kx = kx0 + fft;
   if constexpr (sizeof(OutT) == 4) {  // FP32 planes: [slot][re|im][p]
     OutT *re = H + (long long)slot * 2 * npix + (long long)kx * S::N;
@@ -516,7 +545,7 @@ k_render_cols(const float2 *__restrict__ mid, int nx, const float2 *__restrict__
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     const int f = item / groups, t = item % groups;
     const float2 *src = mid + (long long)f * npix + (long long)t * FPC * Shape<LOGN>::N;
-    if (!col_work<LOGN, OutT>(src, smem, &bar, phase, &abort_flag, true, t * FPC, H, npix, rows_total,
+    if (!col_work<LOGN, OutT>(src, smem, &bar, phase, &abort_flag, true, false, t * FPC, H, npix, rows_total,
                               slot0 + f, maxbits, tw, []() {}, []() {}))
       break;
   }
@@ -554,6 +583,17 @@ __device__ __forceinline__ void red_release_add(unsigned *p, unsigned v) {
 }
 __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// shared-memory counter: the release orders this thread's earlier accesses before the add,
+// the acquire orders those of the adds read before this one ahead of what follows
+__device__ __forceinline__ int atom_add_acq_rel_shared(int *p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;"
+               : "=r"(old) : "r"(tc::smem_u32(p)), "r"(v) : "memory");
+  return old;
 }
 __device__ __forceinline__ bool wait_geq(const unsigned *p, unsigned target) {
   if (ld_acquire(p) >= target) return true;
@@ -593,13 +633,25 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
   __shared__ __align__(8) uint64_t bar;
   __shared__ int abort_flag;
   __shared__ int tk[2];
+  // The next item's tile copy, when the next item is a column item, is issued during the
+  // current item by the last warp to make its final read of the buffer (n_freed counts them),
+  // so it lands while the current item finishes; `preissued` is the ticket it was issued for.
+  __shared__ int n_freed, preissued;
   unsigned *tickets = sync, *rows_done = sync + 1, *cols_done = sync + 1 + ring;
   const int total = (n_frames + lag) * 2 * NI;
+  // thread 0 takes tickets two items ahead: the one it takes at an item's start is published
+  // at the next item's start, so the atomic's round trip overlaps a whole item. Every ticket a
+  // CTA holds is larger than the one it runs and the items only wait on smaller tickets, so
+  // the smallest unfinished item can always proceed.
+  int pending = 0;
   if (threadIdx.x == 0) {
     tc::mbar_init(&bar, 1);
     tc::fence_barrier_init();
     abort_flag = 0;
+    n_freed = 0;
+    preissued = -1;
     tk[0] = (int)atomicAdd(tickets, 1u);
+    pending = (int)atomicAdd(tickets, 1u);
   }
   __syncthreads();
   // ticket i: phase k = i / (2 NI); even positions are row items of frame k, odd ones column
@@ -615,11 +667,14 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
   uint32_t phase = 0;
   uint32_t maxbits = 0;
   int b = 1;
+  bool pre_unwaited = false;  // a copy issued early for `cur` that no one has waited on
   while (cur < total) {
-    // one barrier per item start: thread 0 takes the next ticket and, for a row item, waits for
-    // its ring slot; the barrier also ends the previous item's use of shared memory
+    // one barrier per item start: thread 0 publishes the next ticket, takes the one after it
+    // and, for a row item, waits for its ring slot; the barrier also ends the previous item's
+    // use of shared memory
     if (threadIdx.x == 0) {
-      tk[b] = (int)atomicAdd(tickets, 1u);
+      tk[b] = pending;
+      pending = (int)atomicAdd(tickets, 1u);
       if (valid(cur) && is_row(cur)) {
         const int f = frame_of(cur);
         if (!wait_geq(cols_done + f % ring, (unsigned)(f / ring) * NI)) abort_flag = 1;
@@ -628,6 +683,8 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
     __syncthreads();
     const int nxt = tk[b];
     b ^= 1;
+    const bool pre = preissued == cur;  // read before any write of this item (see freed)
+    pre_unwaited = pre;
     if (abort_flag) break;
     // the next item's uint16 rows are loaded while this item runs (or right away when this
     // ticket names no item)
@@ -635,13 +692,35 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
       if (valid(nxt) && is_row(nxt))
         row_prefetch<LOGN, PW>(pf, frames + (long long)frame_of(nxt) * frame_stride, item_of(nxt) * FPC);
     };
+    // every warp of the CTA calls this once, after its last read of the buffer; the last one
+    // issues the next column item's tile copy if that item's rows are done. Each warp has read
+    // `preissued` for this item before its call, and the counter's acquire-release orders
+    // all those reads, and all the warps' buffer reads, before the copy and the new value.
+    const bool early = valid(nxt) && !is_row(nxt);
+    auto freed = [&]() {
+      if (!early) return;
+      __syncwarp();
+      if ((threadIdx.x & 31) == 0 && atom_add_acq_rel_shared(&n_freed, 1) == kCtaThreads / 32 - 1) {
+        n_freed = 0;  // the next item's adds follow the next item-start barrier
+        // one look, no wait: the current item may be a row item of the same frame, whose rows
+        // are released only after it ends; if they are not all done the column item issues
+        // its own copy
+        const int fn = frame_of(nxt), rn = fn % ring;
+        if (ld_acquire(rows_done + rn) >= (unsigned)(fn / ring + 1) * ROWS_PER_FRAME) {
+          fence_proxy_async_global();  // the rows' ring writes, for the copy
+          fence_proxy_async_shared();  // the buffer's reads, before the copy's writes
+          issue_tile<LOGN>(mid + (long long)rn * NPIX + (long long)item_of(nxt) * FPC * N, smem, &bar);
+          preissued = nxt;
+        }
+      }
+    };
     if (!valid(cur)) {
       prefetch_next();
     } else {
       const int f = frame_of(cur), i = item_of(cur), rs = f % ring;
       float2 *ring_f = mid + (long long)rs * NPIX;
       if (is_row(cur)) {
-        row_work<LOGN, false, PW>(pf, smem, i * FPC, N, cw_log, s_cx, s_cy, s_tw, ring_f, prefetch_next);
+        row_work<LOGN, false, PW>(pf, smem, i * FPC, N, cw_log, s_cx, s_cy, s_tw, ring_f, prefetch_next, freed);
         fence_proxy_async_global();  // this thread's ring writes, for later bulk copies
         if constexpr (PW) {
           __syncwarp();
@@ -652,14 +731,15 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
         }
       } else {
         bool ok = true;
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && !pre) {
           ok = wait_geq(rows_done + rs, (unsigned)(f / ring + 1) * ROWS_PER_FRAME);
           if (ok) fence_proxy_async_global();
         }
+        pre_unwaited = false;
         const float2 *src = ring_f + (long long)i * FPC * N;
-        if (!col_work<LOGN, OutT, false>(src, smem, &bar, phase, &abort_flag, ok, i * FPC, H, NPIX, rows_total,
-                                  slot0 + f, maxbits, s_tw, prefetch_next,
-                                  [&]() { red_release_add(cols_done + rs, 1u); }))
+        if (!col_work<LOGN, OutT, false>(src, smem, &bar, phase, &abort_flag, ok, pre, i * FPC, H, NPIX,
+                                         rows_total, slot0 + f, maxbits, s_tw, prefetch_next,
+                                         [&]() { red_release_add(cols_done + rs, 1u); }, freed))
           break;
       }
     }
@@ -667,7 +747,10 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
   }
   if (abort_flag && threadIdx.x == 0) {
     atomicOr(status, DH_FLAG_WAIT_TIMEOUT);
-    tc::mbar_wait(&bar, phase ^ 1);  // let a late copy land before the CTA exits
+    // let a late copy land before the CTA exits: the last one waited on, and one issued early
+    // for an item the CTA stopped before
+    tc::mbar_wait(&bar, phase ^ 1);
+    if (pre_unwaited) tc::mbar_wait(&bar, phase);
   }
   if (maxbits >= overflow_bits<OutT>()) atomicOr(status, DH_FLAG_STORE_OVERFLOW);
 }
