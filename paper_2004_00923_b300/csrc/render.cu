@@ -281,7 +281,6 @@ __device__ __forceinline__ void l2_discard(const void *p) {
 // with the smallest FP32 magnitude that does not store as a finite value of the storage type
 // (FP32: Inf/NaN; FP16: >= 65520, which rounds to Inf; BF16: >= 3.3961775e38). NaN bits
 // exceed every threshold.
-__device__ __forceinline__ uint32_t abs_bits(float x) { return __float_as_uint(x) & 0x7fffffffu; }
 template <typename T> __host__ __device__ constexpr uint32_t overflow_bits();
 template <> __host__ __device__ constexpr uint32_t overflow_bits<float>() { return 0x7f800000u; }
 template <> __host__ __device__ constexpr uint32_t overflow_bits<__half>() { return 0x477ff000u; }
@@ -464,13 +463,16 @@ __device__ __forceinline__ bool col_work(const float2 *__restrict__ src, float2 
   if (threadIdx.x == 0 && copy_ok) landed();
   E::run(v, sm, j, tw, freed);
   const int kx = kx0 + fft;
+  // largest |component| stored, for the overflow flag: `maxbits` holds a non-negative float's
+  // bits, which order as the values do (the values are finite: finite inputs and tables)
+  float mx = __uint_as_float(maxbits);
   if constexpr (sizeof(OutT) == 4) {  // FP32 planes: [slot][re|im][p]
     OutT *re = H + (long long)slot * 2 * npix + (long long)kx * S::N;
     OutT *im = re + npix;
 #pragma unroll
     for (int i = 0; i < S::R; ++i) {
       const float2 o = v[E::out_reg(i)];
-      maxbits = max(maxbits, max(abs_bits(o.x), abs_bits(o.y)));
+      mx = fmaxf(mx, fmaxf(fabsf(o.x), fabsf(o.y)));
       st_stream(re + j + i * S::P, o.x);
       st_stream(im + j + i * S::P, o.y);
     }
@@ -482,7 +484,7 @@ __device__ __forceinline__ bool col_work(const float2 *__restrict__ src, float2 
     for (int i = 0; i < S::R; ++i) {
       const float2 o = v[E::out_reg(i)];
       const OutT a = to_store<OutT>(o.x), b = to_store<OutT>(o.y);
-      maxbits = max(maxbits, max(abs_bits(o.x), abs_bits(o.y)));
+      mx = fmaxf(mx, fmaxf(fabsf(o.x), fabsf(o.y)));
       OutT *q;
       if constexpr (S::N >= 64) {
         const int e = j + i * S::P;  // < n_y
@@ -495,6 +497,7 @@ __device__ __forceinline__ bool col_work(const float2 *__restrict__ src, float2 
       st_stream(q + 64, b);
     }
   }
+  maxbits = __float_as_uint(mx);
   if constexpr (TAIL_SYNC) __syncthreads();  // all transforms are done with the buffer before the next copy
   return true;
 }
