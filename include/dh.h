@@ -137,6 +137,14 @@ dh_status dh_plan_reserve(dh_plan_t plan, int max_frames, int max_windows);
  *   V is unitary). Other calls project per window. 1: per window always (Eq. 7 over the
  *   kept components). */
 #define DH_OPT_PROJECTION 4
+/* DH_OPT_WINDOW_GROUPS: 0 (default): a call whose covariance comes from the holograms
+ *   through the tensor cores (16-bit storage, DH_OPT_COVARIANCE 0) and whose windows are
+ *   projected one by one, with 32 to (SMs) windows, runs in two groups of windows: the
+ *   eigensolver of one group (one CTA per window) runs beside the covariance of the next
+ *   group, and the eigensolver of that group beside the projection of the first, each pair
+ *   on disjoint SMs (the covariance and projection launches leave one SM per eigensolver
+ *   CTA). 1: one group always. Both give bitwise the same results. */
+#define DH_OPT_WINDOW_GROUPS 5
 dh_status dh_plan_set_option(dh_plan_t plan, int option, int value);
 dh_status dh_plan_get_option(dh_plan_t plan, int option, int *value);
 

@@ -114,6 +114,12 @@ class Plan:
         applies) or per window (False: Eq. 7 over the kept components, always)."""
         _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(self._h, 4, 0 if grouped else 1))
 
+    def set_window_groups(self, automatic: bool = True) -> None:
+        """DH_OPT_WINDOW_GROUPS: automatic (the default: two groups of windows, each one's
+        eigensolver beside the other's covariance or projection, where that applies) or one
+        group (False). Both give bitwise the same results."""
+        _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(self._h, 5, 0 if automatic else 1))
+
     def band_gram(self, first_slot: int, n_frames: int, stream=None) -> None:
         """dh_band_gram: the banded covariance of slots [first_slot, first_slot + n_frames)."""
         _lib.check("dh_band_gram", self._lib.dh_band_gram(self._h, int(first_slot), int(n_frames),

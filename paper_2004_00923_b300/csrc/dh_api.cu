@@ -184,9 +184,9 @@ std::vector<float2> chirp_table(int n, double a) {
 // they need first. The windows can be processed in groups: each group's covariance runs on
 // the caller's stream, its eigensolver on the plan's aux stream, and the projections follow
 // on the caller's stream once each group's eigenvectors are ready; the call ends with the
-// caller's stream joined to everything it launched. One group is used: running the
-// eigensolver of one group beside the next group's rendering was measured slower (both
-// slowed down on the shared SMs).
+// caller's stream joined to everything it launched. Two groups are used only with every
+// frame rendered first: an eigensolver beside the persistent render, which fills every SM,
+// was measured slower (both slowed down on the shared SMs).
 // With b0 >= 0 the operand of Eq. 6 is replaced, per window, by the SVD-filter + DFT operand
 // of Eqs. 2-3 and 8-9 (components k0..k1 kept, bins b0..b1). With `raw` (uint16 frames,
 // window w's first frame at raw + w * slot_stride * raw_stride) and the plan's raw-domain
@@ -195,20 +195,33 @@ dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int 
                    int slot_stride, int n_windows, int k0, int k1, float *images, double *eig_user,
                    cudaStream_t s, int b0 = -1, int b1 = -1, const uint16_t *raw = nullptr,
                    long long raw_stride = 0) {
-  const int G = 1;
   const int nS = b0 >= 0 ? b1 - b0 + 1 : k1 - k0 + 1;  // projected columns
   const int nop = p.prec == DH_PREC_FP32 ? 2 * nS : (2 * nS + 15) / 16 * 16;  // operand rows
   // overlapping windows: grouped projection (one group layout for the whole call)
   const SpanLayout span = b0 < 0 ? span_layout(p, slot_stride, n_windows, k0, k1) : SpanLayout{};
+  // Two groups where the eigensolver (one CTA per window) can run beside the other group's
+  // tensor-core covariance and projection: those launches then leave one SM per eigensolver
+  // CTA (their own CTAs, by registers or shared memory, cannot share an SM with it), and
+  // every frame is rendered first, since the persistent render fills all SMs.
+  const bool two = p.group_mode == 0 && b0 < 0 && span.G == 0 && p.cov_mode == 0 &&
+                   p.prec != DH_PREC_FP32 && n_windows >= 32 && n_windows <= p.num_sms;
+  const int G = two ? 2 : 1;
+  struct Budget {  // the SM budget applies to one launch at a time
+    Plan &p;
+    ~Budget() { p.sm_budget = 0; }
+  } budget{p};
   int w0s[Plan::kMaxGroups], nws[Plan::kMaxGroups];
+  for (int g = 0, w0 = 0; g < G; ++g) {
+    nws[g] = n_windows / G + (g < n_windows % G ? 1 : 0);
+    w0s[g] = w0;
+    w0 += nws[g];
+  }
   int rendered = 0;  // frames (slots relative to first_slot) already rendered
   dh_status st;
-  for (int g = 0, w0 = 0; g < G; ++g) {
-    const int nw = n_windows / G + (g < n_windows % G ? 1 : 0);
-    w0s[g] = w0;
-    nws[g] = nw;
+  for (int g = 0; g < G; ++g) {
+    const int w0 = w0s[g], nw = nws[g];
     if (frames) {
-      const int need = (w0 + nw - 1) * slot_stride + p.T;
+      const int need = (G > 1 ? n_windows - 1 : w0 + nw - 1) * slot_stride + p.T;
       if (need > rendered) {
         st = launch_render(p, frames + (long long)rendered * frame_stride, frame_stride, need - rendered,
                            first_slot + rendered, s);
@@ -230,8 +243,10 @@ dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int 
         return DH_ERR_STATE;  // the windows are not inside the store's current band
       if ((st = launch_band_cov(p, *o, fs, slot_stride, nw, w0, s)) != DH_OK) return st;
     } else {
+      p.sm_budget = g > 0 ? p.num_sms - nws[g - 1] : 0;  // beside the previous group's eigensolver
       st = p.prec == DH_PREC_FP32 ? launch_gram_simt(p, fs, slot_stride, nw, &parts, s)
                                   : launch_gram_tc(p, fs, slot_stride, nw, &parts, s);
+      p.sm_budget = 0;
       if (st != DH_OK) return st;
       if ((st = launch_reduce(p, nw, parts, w0, s)) != DH_OK) return st;
     }
@@ -243,17 +258,18 @@ dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int 
     if (b0 >= 0 && (st = launch_svd_fourier_operand(p, nw, k0, k1, b0, b1, nop, w0, p.aux)) != DH_OK)
       return st;
     DH_CUDA_TRY(cudaEventRecord(p.ev_jac[g], p.aux));
-    w0 += nw;
   }
   for (int g = 0; g < G; ++g) {
     DH_CUDA_TRY(cudaStreamWaitEvent(s, p.ev_jac[g], 0));
     const int fs = first_slot + w0s[g] * slot_stride;
     float *img = images + (long long)w0s[g] * p.npix;
+    p.sm_budget = g + 1 < G ? p.num_sms - nws[g + 1] : 0;  // beside the next group's eigensolver
     if (span.G > 0)
       st = launch_project_span(p, span, fs, nws[g], img, w0s[g], s);
     else
       st = p.prec == DH_PREC_FP32 ? launch_project_simt(p, fs, slot_stride, nws[g], nop, img, w0s[g], s)
                                   : launch_project_tc(p, fs, slot_stride, nws[g], nop, img, w0s[g], s);
+    p.sm_budget = 0;
     if (st != DH_OK) return st;
   }
   return DH_OK;
@@ -511,6 +527,7 @@ dh_status dh_plan_get_option(dh_plan_t h, int option, int *value) {
     case DH_OPT_RENDER_LAG: *value = h->p.render_lag; return DH_OK;
     case DH_OPT_COVARIANCE: *value = h->p.cov_mode; return DH_OK;
     case DH_OPT_PROJECTION: *value = h->p.proj_mode; return DH_OK;
+    case DH_OPT_WINDOW_GROUPS: *value = h->p.group_mode; return DH_OK;
   }
   return DH_ERR_INVALID_ARG;
 }
@@ -598,6 +615,10 @@ dh_status dh_plan_set_option(dh_plan_t h, int option, int value) {
     case DH_OPT_PROJECTION:
       if (value != 0 && value != 1) return DH_ERR_INVALID_ARG;
       h->p.proj_mode = value;
+      return DH_OK;
+    case DH_OPT_WINDOW_GROUPS:
+      if (value != 0 && value != 1) return DH_ERR_INVALID_ARG;
+      h->p.group_mode = value;
       return DH_OK;
   }
   return DH_ERR_INVALID_ARG;

@@ -45,6 +45,12 @@ struct Plan {
   // projection of Eqs. 6-7: 0 = automatic (overlapping windows share their tile loads and use
   // the complement of the discarded components where that applies), 1 = per window always
   int proj_mode = 0;
+  // window groups of one call: 0 = automatic (two where the eigensolver can overlap the
+  // covariance and projection of the other group), 1 = one group
+  int group_mode = 0;
+  // SMs the next tensor-core covariance or projection launch may fill (0 = all): the rest
+  // are left to an eigensolver running beside it
+  int sm_budget = 0;
   unsigned *d_sync = nullptr;  // ticket and ring counters of the persistent render
   // second stream: the eigensolver of one group of windows overlaps the next group's work
   cudaStream_t aux = nullptr;

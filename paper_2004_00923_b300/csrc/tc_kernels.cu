@@ -690,6 +690,12 @@ dh_status resident_ctas(K kern, int threads, size_t smem, int *out) {
   return DH_OK;
 }
 
+// SMs a persistent covariance or projection launch spreads over: all, or the plan's budget
+// when an eigensolver runs beside it
+int sm_share(const Plan &p) {
+  return p.sm_budget > 0 && p.sm_budget < p.num_sms ? p.sm_budget : p.num_sms;
+}
+
 template <int T, bool BF16>
 dh_status gram_t(Plan &p, int first_slot, int slot_stride, int n_windows, cudaStream_t s) {
   using C = GramCfg<T>;
@@ -709,7 +715,7 @@ dh_status gram_t(Plan &p, int first_slot, int slot_stride, int n_windows, cudaSt
   if (rs != DH_OK) return rs;
   if (per_sm > C::CTAS_PER_SM) per_sm = C::CTAS_PER_SM;  // tensor memory: 512 columns per SM
   if (per_sm < 1) per_sm = 1;
-  int grid = p.num_sms * per_sm;
+  int grid = sm_share(p) * per_sm;
   if (grid > total) grid = total;
   ProfScope ps(p, K_GRAM_TC, s);
   kern<<<grid, C::THREADS, C::SMEM, s>>>(p.tmap_H, first_slot, slot_stride, n_windows, units_pw,
@@ -747,7 +753,7 @@ dh_status project_t(Plan &p, int first_slot, int slot_stride, int n_windows, int
   if (rs != DH_OK) return rs;
   if (per_sm < 1) per_sm = 1;
   if (per_sm * C::TMEM_COLS > 512) per_sm = 512 / C::TMEM_COLS;  // tensor memory per SM
-  int grid = p.num_sms * per_sm;
+  int grid = sm_share(p) * per_sm;
   if (grid > total) grid = (int)total;
   ProfScope ps(p, K_PROJECT_TC, s);
   kern<<<grid, C::THREADS, C::SMEM, s>>>(p.tmap_H, tmB, first_slot, slot_stride, n_windows, tiles_pw, Npad,

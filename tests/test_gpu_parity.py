@@ -146,6 +146,31 @@ def test_window_alone_equals_in_batch(dh, prec):
         assert np.array_equal(lam_1[0], lam_b[w])
 
 
+@pytest.mark.parametrize("T,n,ws", [(32, 40, 32), (16, 33, 16), (64, 32, 64), (32, 48, 40)])
+def test_two_window_groups_equal_one(dh, T, n, ws):
+    """The two-group schedule (each group's eigensolver beside the other group's covariance
+    or projection, on SM budgets) gives bitwise the one-group results, with the frames
+    rendered inside the call, for an odd split, every window length, and gaps between
+    windows; the two-group batch matches the oracle on its first and last window."""
+    F = (n - 1) * ws + T
+    frames = SpeckleStream(SpeckleParams(128, 128), seed=T + n).next(F)
+    out = []
+    for automatic in (False, True):
+        with dh.Plan(128, 128, LAM, Z, PITCH, T=T, precision="fp16", max_frames=F, max_windows=n) as plan:
+            plan.set_window_groups(automatic)
+            img, lam = plan.pca_batch(to_gpu(frames.numpy()), n, ws, 2, T - 1)
+            torch.cuda.synchronize()
+            assert plan.status() == 0
+            out.append((img.cpu().numpy(), lam.cpu().numpy()))
+            if automatic:
+                for w in (0, n - 1):
+                    C = plan.debug_covariance(w).cpu().numpy()
+                    check_window(out[-1][0][w].astype(np.float64), out[-1][1][w], C,
+                                 frames[w * ws:w * ws + T].numpy(), 2, T - 1, "fp16")
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
 def test_overlapping_sliding_windows(dh, prec):
     """Windows at stride 8 < T share rendered holograms; each matches the oracle."""
