@@ -263,7 +263,12 @@ dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int 
     DH_CUDA_TRY(cudaStreamWaitEvent(s, p.ev_jac[g], 0));
     const int fs = first_slot + w0s[g] * slot_stride;
     float *img = images + (long long)w0s[g] * p.npix;
-    p.sm_budget = g + 1 < G ? p.num_sms - nws[g + 1] : 0;  // beside the next group's eigensolver
+    // beside the next group's eigensolver. At T = 32 an eigensolver CTA (50.7 KB of shared
+    // memory) fits beside one projection CTA (99.6 KB, two per SM otherwise), so whichever
+    // launch comes first, 2 x SMs - (eigensolver CTAs) projection CTAs stay resident: a
+    // budget of SMs - CTAs / 2 (measured: 1.75 -> 1.64 ms for the two projections of a
+    // 64-window step). Elsewhere each eigensolver CTA keeps a whole SM.
+    p.sm_budget = g + 1 < G ? p.num_sms - (p.T == 32 ? nws[g + 1] / 2 : nws[g + 1]) : 0;
     if (span.G > 0)
       st = launch_project_span(p, span, fs, nws[g], img, w0s[g], s);
     else
