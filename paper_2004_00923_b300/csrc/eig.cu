@@ -132,16 +132,31 @@ __device__ int jacobi_sweeps(Real *ar, Real *ai, Real *vr, Real *vi, double tol,
     }
     __syncthreads();
   }
+  const double inv_fro = fro > 0.0 ? 1.0 / fro : 0.0;
   for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
-    double off2 = 0.0;
-    for (int e = tid; e < T * T; e += blockDim.x) {
-      const int i = e / T, j = e % T;
-      if (i != j) {
-        const double x = (double)ar[i * LD + j], y = (double)ai[i * LD + j];
-        off2 += x * x + y * y;
+    double off2;
+    if constexpr (sizeof(Real) == 4) {  // a threshold test: FP32 on the entries over ||A||_F
+      const float sc = (float)inv_fro;
+      float o = 0.f;
+      for (int e = tid; e < T * T; e += blockDim.x) {
+        const int i = e / T, j = e % T;
+        if (i != j) {
+          const float x = (float)ar[i * LD + j] * sc, y = (float)ai[i * LD + j] * sc;
+          o = fmaf(x, x, fmaf(y, y, o));
+        }
       }
+      off2 = block_sum((double)o, red) * fro * fro;
+    } else {
+      off2 = 0.0;
+      for (int e = tid; e < T * T; e += blockDim.x) {
+        const int i = e / T, j = e % T;
+        if (i != j) {
+          const double x = (double)ar[i * LD + j], y = (double)ai[i * LD + j];
+          off2 += x * x + y * y;
+        }
+      }
+      off2 = block_sum(off2, red);
     }
-    off2 = block_sum(off2, red);
     if (sqrt(off2) <= tol * fro) return sweep;
     if (sweep == max_sweeps) break;
     for (int step = 0; step < T - 1; ++step) {
@@ -346,8 +361,22 @@ __device__ __forceinline__ void df_cdot(const float2 *ar, const float2 *ai, int 
   outi = df_fin(ih, il);
 }
 
+// 1/sqrt(x) in FP64 from an estimate r0 within ~2^-22 (an FP32 reciprocal square root):
+// two steps of Newton's iteration r <- r + r (1 - x r^2) / 2, each squaring the relative
+// error, reach FP64 rounding
+__device__ __forceinline__ double rsqrt_newton(double x, double r0) {
+  double r = r0;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const double e = fma(-x * r, r, 1.0);
+    r = fma(0.5 * r, e, r);
+  }
+  return r;
+}
+
 // Parallel-order complex Jacobi sweeps in df arithmetic on the Hermitian (ar, ai), rotations
-// accumulated into (vr, vi); the rotation angles are computed in FP64 from the df entries.
+// accumulated into (vr, vi); the rotation is formed in FP64 from the df entries (its tangent
+// from an FP32 estimate).
 // Same ordering, skip threshold and stopping rule as jacobi_sweeps.
 template <int T>
 __device__ int jacobi_sweeps_df(float2 *ar, float2 *ai, float2 *vr, float2 *vi, double tol, int max_sweeps,
@@ -366,16 +395,20 @@ __device__ int jacobi_sweeps_df(float2 *ar, float2 *ai, float2 *vr, float2 *vi, 
     }
     __syncthreads();
   }
+  const double inv_fro = fro > 0.0 ? 1.0 / fro : 0.0;
   for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
-    double off2 = 0.0;
+    // a threshold test: FP32 on the leading parts over ||A||_F (the trailing parts change
+    // each square by less than 2^-23 of itself)
+    const float sc = (float)inv_fro;
+    float o = 0.f;
     for (int e = tid; e < T * T; e += blockDim.x) {
       const int i = e / T, j = e % T;
       if (i != j) {
-        const double x = df_dbl(ar[i * LD + j]), y = df_dbl(ai[i * LD + j]);
-        off2 += x * x + y * y;
+        const float x = ar[i * LD + j].x * sc, y = ai[i * LD + j].x * sc;
+        o = fmaf(x, x, fmaf(y, y, o));
       }
     }
-    off2 = block_sum(off2, red);
+    const double off2 = block_sum((double)o, red) * fro * fro;
     if (sqrt(off2) <= tol * fro) return sweep;
     if (sweep == max_sweeps) break;
     for (int step = 0; step < T - 1; ++step) {
@@ -385,16 +418,25 @@ __device__ int jacobi_sweeps_df(float2 *ar, float2 *ai, float2 *vr, float2 *vi, 
         else { a = (step + tid) % (T - 1); b = (step - tid + T - 1) % (T - 1); }
         const int p = a < b ? a : b, q = a < b ? b : a;
         const double gr = df_dbl(ar[p * LD + q]), gi = df_dbl(ai[p * LD + q]);
-        const double g = sqrt(gr * gr + gi * gi);
+        const double g2 = gr * gr + gi * gi, thr = 1e-2 * tol * fro / T;
         double c = 1, wr = 0, wi = 0;
         int skip = 1;
-        if (g > 1e-2 * tol * fro / T) {  // smaller rotations cannot hold off(A) above tol ||A||_F
-          const double tau = (df_dbl(ar[q * LD + q]) - df_dbl(ar[p * LD + p])) / (2 * g);
-          const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1 + tau * tau));
-          c = 1 / sqrt(1 + t * t);
-          const double sn = t * c;
-          wr = sn * gr / g;
-          wi = sn * gi / g;
+        if (g2 > thr * thr) {  // smaller rotations cannot hold off(A) above tol ||A||_F
+          // The tangent t in FP32, in units of ||A||_F (relative error ~1e-7: the rotation
+          // leaves ~1e-7 of the entry, far below the stopping level after one sweep); then a
+          // rotation unitary to FP64 rounding for that t: c = 1/sqrt(1 + t^2) and
+          // w = t c g / |g|, both reciprocal square roots by Newton's iteration.
+          // (g2s >= (1e-2 tol / T)^2: a normal FP32 value for tol >= 1e-15; the kernel runs
+          // with tol = 1e-12)
+          const float g2s = (float)(g2 * inv_fro * inv_fro);
+          const float rgs = rsqrtf(g2s);
+          const float tau = (float)((df_dbl(ar[q * LD + q]) - df_dbl(ar[p * LD + p])) * inv_fro) * 0.5f * rgs;
+          const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+          const double td = (double)t;
+          c = rsqrt_newton(fma(td, td, 1.0), (double)rsqrtf(fmaf(t, t, 1.f)));
+          const double sn = td * c * rsqrt_newton(g2, (double)rgs * inv_fro);
+          wr = sn * gr;
+          wi = sn * gi;
           skip = 0;
         }
         rp[tid] = p; rq[tid] = q; rc[tid] = df_of(c); rwr[tid] = df_of(wr); rwi[tid] = df_of(wi);
