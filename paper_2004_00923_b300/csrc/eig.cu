@@ -214,23 +214,29 @@ __device__ int jacobi_sweeps(Real *ar, Real *ai, Real *vr, Real *vi, double tol,
           vi[i * LD + q] = (wr * xpi + wi * xpr) + c * xqi;
         }
         __syncthreads();
-        // rows of A: A_pj' = c A_pj - w A_qj ;  A_qj' = conj(w) A_pj + c A_qj
+        // rows of A: A_pj' = c A_pj - w A_qj ;  A_qj' = conj(w) A_pj + c A_qj. The pair's own
+        // entries come out exact: A_pq = A_qp = 0 and real diagonal entries (also for a
+        // skipped rotation, whose A_pq is below the skip level).
         for (int it = tid; it < NP * T; it += blockDim.x) {
           const int k = it / T, j = it % T;
           const Real c = rc[k], wr = rwr[k], wi = rwi[k];
-          if (wr == 0 && wi == 0) continue;
           const int p = rp[k], q = rq[k];
+          if (wr == 0 && wi == 0) {
+            if (j == p) { ai[p * LD + p] = 0; ar[q * LD + p] = ai[q * LD + p] = 0; }
+            if (j == q) { ar[p * LD + q] = ai[p * LD + q] = 0; ai[q * LD + q] = 0; }
+            continue;
+          }
           const Real xpr = ar[p * LD + j], xpi = ai[p * LD + j], xqr = ar[q * LD + j], xqi = ai[q * LD + j];
-          ar[p * LD + j] = c * xpr - (wr * xqr - wi * xqi);
-          ai[p * LD + j] = c * xpi - (wr * xqi + wi * xqr);
-          ar[q * LD + j] = (wr * xpr + wi * xpi) + c * xqr;
-          ai[q * LD + j] = (wr * xpi - wi * xpr) + c * xqi;
-        }
-        __syncthreads();
-        if (tid < NP) {
-          const int p = rp[tid], q = rq[tid];
-          ar[p * LD + q] = ai[p * LD + q] = ar[q * LD + p] = ai[q * LD + p] = 0;
-          ai[p * LD + p] = ai[q * LD + q] = 0;
+          Real ypr = c * xpr - (wr * xqr - wi * xqi);
+          Real ypi = c * xpi - (wr * xqi + wi * xqr);
+          Real yqr = (wr * xpr + wi * xpi) + c * xqr;
+          Real yqi = (wr * xpi - wi * xpr) + c * xqi;
+          if (j == p) { ypi = 0; yqr = yqi = 0; }
+          if (j == q) { ypr = ypi = 0; yqi = 0; }
+          ar[p * LD + j] = ypr;
+          ai[p * LD + j] = ypi;
+          ar[q * LD + j] = yqr;
+          ai[q * LD + j] = yqi;
         }
         __syncthreads();
       } else {
@@ -513,24 +519,23 @@ __device__ int jacobi_sweeps_df(float2 *ar, float2 *ai, float2 *vr, float2 *vi, 
           xi_[i * LD + q] = df_dot3(wr, xpi, wi, xpr, c, xqi);
         }
         __syncthreads();
-        // rows of A: A_pj' = c A_pj - w A_qj ;  A_qj' = conj(w) A_pj + c A_qj
+        // rows of A: A_pj' = c A_pj - w A_qj ;  A_qj' = conj(w) A_pj + c A_qj; a rotated
+        // pair's own entries come out exact (A_pq = A_qp = 0, real diagonal entries)
         for (int it = tid; it < NP * T; it += blockDim.x) {
           const int k = it / T, j = it % T;
           if (rskip[k]) continue;
           const float2 c = rc[k], wr = rwr[k], wi = rwi[k];
           const int p = rp[k], q = rq[k];
           const float2 xpr = ar[p * LD + j], xpi = ai[p * LD + j], xqr = ar[q * LD + j], xqi = ai[q * LD + j];
-          ar[p * LD + j] = df_dot3(c, xpr, df_neg(wr), xqr, wi, xqi);
-          ai[p * LD + j] = df_dot3(c, xpi, df_neg(wr), xqi, df_neg(wi), xqr);
-          ar[q * LD + j] = df_dot3(wr, xpr, wi, xpi, c, xqr);
-          ai[q * LD + j] = df_dot3(wr, xpi, df_neg(wi), xpr, c, xqi);
-        }
-        __syncthreads();
-        if (tid < NP && !rskip[tid]) {
-          const int p = rp[tid], q = rq[tid];
           const float2 z = make_float2(0.f, 0.f);
-          ar[p * LD + q] = z; ai[p * LD + q] = z; ar[q * LD + p] = z; ai[q * LD + p] = z;
-          ai[p * LD + p] = z; ai[q * LD + q] = z;
+          float2 ypr = df_dot3(c, xpr, df_neg(wr), xqr, wi, xqi);
+          float2 ypi = df_dot3(c, xpi, df_neg(wr), xqi, df_neg(wi), xqr);
+          float2 yqr = df_dot3(wr, xpr, wi, xpi, c, xqr);
+          float2 yqi = df_dot3(wr, xpi, df_neg(wi), xpr, c, xqi);
+          if (j == p) { ypi = z; yqr = z; yqi = z; }
+          if (j == q) { ypr = z; ypi = z; yqi = z; }
+          ar[p * LD + j] = ypr; ai[p * LD + j] = ypi;
+          ar[q * LD + j] = yqr; ai[q * LD + j] = yqi;
         }
         __syncthreads();
       }
