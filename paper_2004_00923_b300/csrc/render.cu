@@ -64,16 +64,12 @@ constexpr float kSin64[64] = {
 constexpr float kRsqrt2 = 0.7071067811865475244f;
 
 // Threads of a render CTA (FFTs per CTA = kCtaThreads / P, at most 16; one FFT when it
-// needs more threads).
-#ifndef DH_RENDER_CTA_THREADS
-#define DH_RENDER_CTA_THREADS 256
-#endif
-constexpr int kCtaThreads = DH_RENDER_CTA_THREADS;
-#ifndef DH_LOGR_1024
-#define DH_LOGR_1024 5
-#endif
+// needs more threads). 128 threads measured faster at 512^2 and much slower at 2048^2.
+constexpr int kCtaThreads = 256;
+// log2 of the radix of an FFT length's passes. Measured: radix 32 at 1024 (two passes; radix
+// 16, three passes, was 22% slower) and at 2048 (32 x 32 x 2; 21% faster than 16 x 16 x 8).
 __host__ __device__ constexpr int log_radix(int logn) {
-  return logn == 6 ? 3 : logn == 10 ? DH_LOGR_1024 : (logn == 5 || logn == 9) ? 5 : 4;
+  return logn == 6 ? 3 : (logn == 5 || logn == 9 || logn == 10 || logn == 11) ? 5 : 4;
 }
 
 __host__ __device__ constexpr int bitrev(int k, int bits) {
@@ -242,8 +238,10 @@ __host__ __device__ constexpr int cta_threads() { return fpc<LOGN>() * Shape<LOG
 // CTAs per SM each pass is compiled for: threads counted in whole warps (a CTA of fewer
 // threads still holds a warp's registers), row items with 32 complex values a thread at
 // 2 x 256 threads (<= 128 registers), 16 values at 3 x 256, 8 at 4 x 256; column items
-// (no uint16 prefetch in flight) one step higher. Measured: the radix-16 lengths (2048,
-// 4096, 256) gain 3-8% over 2 x 256, the radix-32 ones (512, 1024) keep 2 x 256.
+// (no uint16 prefetch in flight) one step higher, except 32 values from 2048 up, which
+// spill at 3 x 256 (2048: 15.1 ms for 512 frames at 2 x 256 against 17.0 at 3 x 256).
+// Measured: the radix-16 lengths (4096, 256) gain 3-8% over 2 x 256, the radix-32 ones
+// (512, 1024) keep 2 x 256.
 template <int LOGN>
 __host__ __device__ constexpr int warp_threads() { return cta_threads<LOGN>() < 32 ? 32 : cta_threads<LOGN>(); }
 template <int LOGN>
@@ -253,7 +251,8 @@ __host__ __device__ constexpr int rows_per_sm() {
 }
 template <int LOGN>
 __host__ __device__ constexpr int cols_per_sm() {
-  return warp_threads<LOGN>() <= 256 ? (Shape<LOGN>::R >= 32 ? 768 : 1024) / warp_threads<LOGN>() : 1;
+  return warp_threads<LOGN>() <= 256
+             ? (Shape<LOGN>::R >= 32 ? (LOGN >= 11 ? 512 : 768) : 1024) / warp_threads<LOGN>() : 1;
 }
 
 template <typename T> __device__ __forceinline__ T to_store(float x);
