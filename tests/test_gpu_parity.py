@@ -7,6 +7,8 @@ FP32 holograms are compared at 3e-6 relative L2 (a few FP32 ulps times log2 N st
 covariances at 5e-6 relative Frobenius (plain) and 2e-4 (16-bit storage).
 """
 
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -199,6 +201,13 @@ def test_invalid_calls_return_errors(dh):
             plan.pca_windows(0, 16, 2, 0, 15)  # more windows than reserved
         with pytest.raises(dh.DHError):
             plan.render_frames(f, first_slot=8)  # slots beyond the reservation
+        lib = plan._lib
+        for opt, bad in ((0, 2), (1, 1), (1, 65), (2, 64), (3, 3), (4, 2), (5, 2), (5, -1), (6, 0)):
+            assert lib.dh_plan_set_option(plan._h, opt, bad) == 1, (opt, bad)  # DH_ERR_INVALID_ARG
+        v = ctypes.c_int(-1)
+        assert lib.dh_plan_get_option(plan._h, 5, ctypes.byref(v)) == 0 and v.value == 0
+        plan.set_window_groups(False)
+        assert lib.dh_plan_get_option(plan._h, 5, ctypes.byref(v)) == 0 and v.value == 1
         img, lam = plan.pca_window(2, 15)
         assert np.all(np.diff(lam.numpy()) <= 0)
 
