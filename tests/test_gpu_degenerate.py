@@ -1,0 +1,91 @@
+"""Degenerate windows through the C ABI: all-zero frames (C = 0: no rotation, no division
+by ||C||) and identical frames (C of rank one, T - 1 equal zero eigenvalues), per window and
+through the grouped projection of overlapping windows.
+
+For identical frames h_t = h, C = T h^H h 1 1^T: lambda_0 = T ||h||^2, the other eigenvalues
+are 0, V_0 = 1 / sqrt(T), and every other eigenvector is orthogonal to 1, so H V_k = h (1^T
+V_k) = 0: the power of components 1..T-1 vanishes and components 0..T-1 give T |h|^2 per pixel
+(Eq. 7 with V unitary). The same identities hold for the stored 16-bit holograms, which are
+identical too.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from dh_synth import speckle_window
+from parity_helpers import LAM, PITCH, TOL_IMG, Z, rel, to_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dh():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2004_00923_b300 as m
+    return m
+
+
+@pytest.mark.parametrize("T", [16, 32, 64])
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_all_zero_windows(dh, T, prec):
+    """Zero frames: zero eigenvalues and images, no NaN, no flag."""
+    n = 3
+    frames = np.zeros((n * T, 64, 128), dtype=np.uint16)
+    with dh.Plan(128, 64, LAM, Z, PITCH, T=T, precision=prec, max_frames=n * T, max_windows=n) as plan:
+        img, lam = plan.pca_batch(to_gpu(frames), n, T, 0, T - 1)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        img, lam = img.cpu().numpy(), lam.cpu().numpy()
+    assert np.all(img == 0.0) and np.all(lam == 0.0)
+
+
+@pytest.mark.parametrize("T", [16, 32, 64])
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_identical_frames(dh, T, prec):
+    """Rank-one C: one eigenvalue T ||h||^2 (the oracle's), T - 1 zeros to 1e-6 of it (the
+    covariance's own rounding, ~1e-7 of ||C||, bounds them by Weyl); the discarded-first image
+    (components 1..T-1) has no power; the full range gives T |h|^2."""
+    one = speckle_window(128, 64, 1, seed=T).numpy()
+    frames = np.repeat(one, T, axis=0)
+    with dh.Plan(128, 64, LAM, Z, PITCH, T=T, precision=prec, max_frames=T, max_windows=1) as plan:
+        plan.render_stack(to_gpu(frames))
+        full, lam = plan.pca_window(0, T - 1)
+        rest, _ = plan.pca_window(1, T - 1)
+        assert plan.status() == 0
+        full, rest, lam = full.double().cpu().numpy(), rest.double().cpu().numpy(), lam.numpy()
+        hs = plan.debug_hologram(0).cpu().numpy().astype(np.complex128)
+    M, lam_ref, _, _ = oracle.pca_window(frames, LAM, Z, PITCH, 0, T - 1)
+    if prec == "fp32":
+        assert abs(lam[0] - lam_ref[0]) <= 1e-5 * lam_ref[0]
+    else:
+        # the frames' 16-bit storage rounding is the same in every frame, so it does not
+        # average out over the window as it does for distinct frames: pin lambda_0 to the
+        # stored hologram instead, T ||h_stored||^2 in FP64
+        lam0 = T * float(np.sum(np.abs(hs) ** 2))
+        assert abs(lam[0] - lam0) <= 1e-6 * lam0
+        assert abs(lam[0] - lam_ref[0]) <= 1e-4 * lam_ref[0]
+    assert np.all(np.abs(lam[1:]) <= 1e-6 * lam[0])
+    assert rel(full, M) <= TOL_IMG[prec]
+    assert np.max(rest) <= 1e-6 * np.mean(full)
+
+
+def test_identical_frames_grouped_projection(dh):
+    """Overlapping windows over constant frames (the grouped projection, which takes the power
+    as the window's energy minus its discarded components'): with k0 = 1 the single discarded
+    component holds all of the energy, and the images vanish to the rounding of it (energy and
+    discarded power are each accurate to ~1e-6; speckle energies reach ~10x their mean)."""
+    T, s, n = 32, 8, 9
+    F = (n - 1) * s + T
+    one = speckle_window(128, 128, 1, seed=7).numpy()
+    frames = np.repeat(one, F, axis=0)
+    with dh.Plan(128, 128, LAM, Z, PITCH, T=T, precision="fp16", max_frames=F, max_windows=n) as plan:
+        img, lam = plan.pca_batch(to_gpu(frames), n, s, 1, T - 1)
+        full, _ = plan.pca_batch(to_gpu(frames), n, s, 0, T - 1)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        img, full = img.double().cpu().numpy(), full.double().cpu().numpy()
+    for w in range(n):
+        assert np.max(img[w]) <= 1e-4 * np.mean(full[w]), w
