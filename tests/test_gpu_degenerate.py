@@ -1,6 +1,7 @@
-"""Degenerate windows through the C ABI: all-zero frames (C = 0: no rotation, no division
-by ||C||) and identical frames (C of rank one, T - 1 equal zero eigenvalues), per window and
-through the grouped projection of overlapping windows.
+"""Degenerate and boundary windows through the C ABI: all-zero frames (C = 0: no rotation,
+no division by ||C||), identical frames (C of rank one, T - 1 equal zero eigenvalues), per
+window and through the grouped projection of overlapping windows; an empty batch; more
+windows than SMs (one group, several CTA rounds of the eigensolver).
 
 For identical frames h_t = h, C = T h^H h 1 1^T: lambda_0 = T ||h||^2, the other eigenvalues
 are 0, V_0 = 1 / sqrt(T), and every other eigenvector is orthogonal to 1, so H V_k = h (1^T
@@ -89,3 +90,29 @@ def test_identical_frames_grouped_projection(dh):
         img, full = img.double().cpu().numpy(), full.double().cpu().numpy()
     for w in range(n):
         assert np.max(img[w]) <= 1e-4 * np.mean(full[w]), w
+
+
+def test_empty_batch_is_an_argument_error(dh):
+    """A batch of no windows is rejected before anything launches."""
+    frames = to_gpu(speckle_window(64, 64, 16, seed=3).numpy())
+    with dh.Plan(64, 64, LAM, Z, PITCH, T=16, precision="fp16") as plan:
+        with pytest.raises(dh.DHError) as e:
+            plan.pca_batch(frames, 0, 16, 2, 15)
+        assert e.value.code == 1
+        assert plan.status() == 0
+
+
+def test_more_windows_than_sms(dh):
+    """160 windows (more than the SMs: one group, the eigensolver in several CTA rounds),
+    first, middle and last against the oracle."""
+    T, n = 16, 160
+    frames = np.concatenate([speckle_window(128, 64, T, seed=500 + w).numpy() for w in range(n)])
+    with dh.Plan(128, 64, LAM, Z, PITCH, T=T, precision="fp16", max_frames=n * T, max_windows=n) as plan:
+        img, lam = plan.pca_batch(to_gpu(frames), n, T, 2, T - 1)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        img, lam = img.cpu().numpy(), lam.cpu().numpy()
+    for w in (0, n // 2, n - 1):
+        M, lam_ref, _, _ = oracle.pca_window(frames[w * T:(w + 1) * T], LAM, Z, PITCH, 2, T - 1)
+        assert rel(img[w], M) <= TOL_IMG["fp16"], w
+        assert np.max(np.abs(lam[w] - lam_ref)) <= 1e-5 * lam_ref[0], w
