@@ -137,8 +137,8 @@ dh_status dh_plan_reserve(dh_plan_t plan, int max_frames, int max_windows);
  *   V is unitary). Other calls project per window. 1: per window always (Eq. 7 over the
  *   kept components). */
 #define DH_OPT_PROJECTION 4
-/* DH_OPT_WINDOW_GROUPS: 0 (default): a call whose covariance comes from the holograms
- *   through the tensor cores (16-bit storage, DH_OPT_COVARIANCE 0) and whose windows are
+/* DH_OPT_WINDOW_GROUPS: 0 (default): a call whose covariance comes from the tensor cores
+ *   (16-bit storage; DH_OPT_COVARIANCE 0, or 1 with the frames at hand) and whose windows are
  *   projected one by one, with 32 to (SMs) windows, runs in two groups of windows: the
  *   eigensolver of one group (one CTA per window) runs beside the covariance of the next
  *   group, and the eigensolver of that group beside the projection of the first, each pair

@@ -203,7 +203,7 @@ dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int 
   // tensor-core covariance and projection: those launches then leave one SM per eigensolver
   // CTA (their own CTAs, by registers or shared memory, cannot share an SM with it), and
   // every frame is rendered first, since the persistent render fills all SMs.
-  const bool two = p.group_mode == 0 && b0 < 0 && span.G == 0 && p.cov_mode == 0 &&
+  const bool two = p.group_mode == 0 && b0 < 0 && span.G == 0 && (p.cov_mode == 0 || p.cov_mode == 1) &&
                    p.prec != DH_PREC_FP32 && n_windows >= 32 && n_windows <= p.num_sms;
   const int G = two ? 2 : 1;
   struct Budget {  // the SM budget applies to one launch at a time
@@ -232,8 +232,10 @@ dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int 
     const int fs = first_slot + w0 * slot_stride;
     int parts = 0;
     if (raw && p.cov_mode == 1) {
+      p.sm_budget = g > 0 ? p.num_sms - nws[g - 1] : 0;  // beside the previous group's eigensolver
       st = launch_gram_raw(p, raw, raw_stride, (n_windows - 1) * slot_stride + p.T, w0 * slot_stride, slot_stride,
                            nw, &parts, s);
+      p.sm_budget = 0;
       if (st != DH_OK) return st;
       if ((st = launch_reduce_raw(p, nw, parts, w0, s)) != DH_OK) return st;
     } else if (p.cov_mode == 2) {

@@ -795,7 +795,7 @@ dh_status gram_raw_t(Plan &p, const uint16_t *frames, long long frame_stride, in
   if (rs != DH_OK) return rs;
   if (per_sm > C::CTAS_PER_SM) per_sm = C::CTAS_PER_SM;
   if (per_sm < 1) per_sm = 1;
-  int grid = p.num_sms * per_sm;
+  int grid = sm_share(p) * per_sm;
   if (grid > total) grid = total;
   ProfScope ps(p, K_GRAM_RAW, s);
   kern<<<grid, C::THREADS, C::SMEM, s>>>(tm, first_frame, window_stride, n_windows, units_pw, stages_per_unit,

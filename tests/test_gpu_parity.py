@@ -173,6 +173,29 @@ def test_two_window_groups_equal_one(dh, T, n, ws):
     assert np.array_equal(out[0][1], out[1][1])
 
 
+def test_two_window_groups_equal_one_raw_covariance(dh):
+    """The two-group schedule with the covariance taken from the uint16 frames (C = I^T I)
+    gives bitwise the one-group results, and matches the oracle on its first and last window."""
+    T, n = 32, 36
+    F = n * T
+    frames = SpeckleStream(SpeckleParams(128, 128), seed=77).next(F)
+    out = []
+    for automatic in (False, True):
+        with dh.Plan(128, 128, LAM, Z, PITCH, T=T, precision="fp16", max_frames=F, max_windows=n) as plan:
+            plan.set_covariance_source("raw")
+            plan.set_window_groups(automatic)
+            img, lam = plan.pca_batch(to_gpu(frames.numpy()), n, T, 2, T - 1)
+            torch.cuda.synchronize()
+            assert plan.status() == 0
+            out.append((img.cpu().numpy(), lam.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    for w in (0, n - 1):
+        M, lam_ref, _, _ = oracle.pca_window(frames[w * T:(w + 1) * T].numpy(), LAM, Z, PITCH, 2, T - 1)
+        assert rel(out[1][0][w], M) <= TOL_IMG["fp16"]
+        assert np.max(np.abs(out[1][1][w] - lam_ref)) <= TOL_LAM * lam_ref[0]
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
 def test_overlapping_sliding_windows(dh, prec):
     """Windows at stride 8 < T share rendered holograms; each matches the oracle."""
