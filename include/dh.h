@@ -149,7 +149,8 @@ dh_status dh_plan_set_option(dh_plan_t plan, int option, int value);
 dh_status dh_plan_get_option(dh_plan_t plan, int option, int *value);
 
 /* Autotuner: render n_frames (capped at the plan's slots) zero frames with every candidate
- * schedule (chunks; the persistent ring at the automatic lag, half and twice it) and keep
+ * schedule (chunks; the persistent ring at the automatic lag, half and twice it, and the
+ * automatic ring with one frame more lag) and keep
  * the fastest in the plan's options (all candidates give bitwise the same holograms; the
  * render time does not depend on the frame values). Discards rendered holograms; allocates
  * and frees a temporary frame buffer; synchronises `stream`. Call it once after

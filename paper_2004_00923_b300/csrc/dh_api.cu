@@ -541,7 +541,8 @@ dh_status dh_plan_get_option(dh_plan_t h, int option, int *value) {
 
 // Time every candidate render schedule on n_frames zero frames (render time does not depend
 // on the values: no data-dependent control flow) and keep the fastest. Candidates: chunks,
-// and the persistent ring with the automatic lag, half of it and twice it.
+// and the persistent ring with the automatic lag, half of it and twice it (ring twice the
+// lag), and the automatic ring with one frame more lag.
 dh_status dh_plan_autotune(dh_plan_t h, int n_frames, void *stream) {
   if (!h || n_frames < 1) return DH_ERR_INVALID_ARG;
   Plan &p = h->p;
@@ -561,6 +562,8 @@ dh_status dh_plan_autotune(dh_plan_t h, int n_frames, void *stream) {
     const int lag = (int)((3 * grid + 2ll * items - 1) / (2ll * items));
     for (int l : {lag, lag / 2, 2 * lag})
       if (l >= 1 && 2 * l <= 64 && 2 * l <= p.mid_frames) cands.push_back({0, 2 * l, l});
+    // one frame more lag in the same ring (a larger ring spills the intermediate from L2)
+    if (lag >= 2 && 2 * lag <= 64 && 2 * lag <= p.mid_frames) cands.push_back({0, 2 * lag, lag + 1});
     if (p.mid_frames >= 3 && lag == 1) cands.push_back({0, 3, 1});
   }
   const int saved[3] = {p.render_mode, p.render_ring, p.render_lag};
