@@ -16,6 +16,7 @@ host cores, one window per step.
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -77,9 +78,11 @@ def whole_job_rate(units_per_rank: int, ws: int, ms_per_step_max: float) -> floa
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms from before the timed region
+    to after it; the samples stamped between begin() and end() (the timed region, host clock)
+    are the ones reported, all of them if none falls inside."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -87,6 +90,13 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.t_begin = self.t_end = None
+
+    def begin(self):
+        self.t_begin = datetime.datetime.now()
+
+    def end(self):
+        self.t_end = datetime.datetime.now()
 
     def start(self):
         fd, self.path = tempfile.mkstemp(prefix="dh_clocks_", suffix=".csv")
@@ -94,7 +104,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (FileNotFoundError, OSError):
             self.proc = None
@@ -110,17 +120,29 @@ class ClockSampler:
         rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
+            if len(parts) >= 10:
                 rows.append(parts)
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+
+        def stamp(r):
+            try:
+                return datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f")
+            except ValueError:
+                return None
+        inside = rows
+        if self.t_begin is not None and self.t_end is not None:
+            kept = [r for r in rows if stamp(r) is not None and self.t_begin <= stamp(r) <= self.t_end]
+            if kept:
+                inside = kept
+        sm = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in inside if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[6 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(inside),
+                "in_timed_region": inside is not rows}
 
 
 def measured_peaks():
@@ -258,6 +280,7 @@ def run_ours(args, ws, rank, local):
     clocks.start()
     time.sleep(0.3)
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.begin()
     if pipeline:
         start.record(stream)
         s_render.wait_stream(stream)
@@ -280,6 +303,7 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         step_ms = [start.elapsed_time(marks[0])] + [marks[k - 1].elapsed_time(marks[k])
                                                     for k in range(1, args.steps)]
+    clocks.end()
     barrier(ws)
     clock_info = clocks.stop()
     ms = start.elapsed_time(end) / args.steps
@@ -490,11 +514,13 @@ def timed_graph(graph, stream, steps, ws, local):
     clocks.start()
     time.sleep(0.3)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    clocks.begin()
     ev[0].record(stream)
     for k in range(steps):
         graph.launch(stream)
         ev[k + 1].record(stream)
     torch.cuda.synchronize()
+    clocks.end()
     barrier(ws)
     clock_info = clocks.stop()
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
@@ -976,7 +1002,9 @@ def run_serving(args, ws, rank, local):
     run(1.0, clocked=False)
     clocks = ClockSampler(local)
     clocks.start()
+    clocks.begin()
     n_win, wall, lat, lat_push, late = run(args.serve_seconds, clocked=True)
+    clocks.end()
     clock_info = clocks.stop()
     n_sat, wall_sat, _, lat_sat, _ = run(min(10.0, args.serve_seconds), clocked=False)
 
