@@ -5,8 +5,9 @@
 // k_jacobi: one CTA per window. Hermitian eigendecomposition C = V Lambda V^{t*} by the
 //   two-sided complex Jacobi method (Forsythe & Henrici 1960; Golub & Van Loan Sec. 8.5)
 //   with the parallel round-robin ordering: each of the T-1 steps of a sweep rotates T/2
-//   disjoint pairs at once (Brent & Luk 1985); FP32 sweeps first, then FP64 sweeps from the
-//   Rayleigh quotient of the re-orthonormalised FP32 eigenvectors. For a pair with
+//   disjoint pairs at once (Brent & Luk 1985); FP32 sweeps first, then refinement sweeps
+//   from the Rayleigh quotient of the re-orthonormalised FP32 eigenvectors, in double-FP32
+//   arithmetic with each rotation formed in FP64 (FP64 sweeps with DH_EIG_DF=0). For a pair with
 //   C_pq = g e^{i alpha}, the real 2x2 Schur rotation (c, s) of [[C_pp, g], [g, C_qq]] is
 //   combined with the phase: J_pp = J_qq = c, J_pq = s e^{i alpha}, J_qp = -s e^{-i alpha},
 //   C <- J^{t*} C J, V <- V J. Eigenvalues are then ordered decreasing (ties by index)
