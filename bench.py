@@ -318,6 +318,9 @@ def run_ours(args, ws, rank, local):
     prof = plan.profile_read()
     plan.profile(False)
 
+    # ---------------------------------------------------------------- measured FMA rates
+    rates = None if args.no_peaks else measure_rates(local)
+
     # ---------------------------------------------------------------- roofline
     hbm, bf16_peak, peak_kind = measured_peaks()
     hbytes = 2 if args.precision in ("fp16", "bf16") else 4
@@ -326,7 +329,8 @@ def run_ours(args, ws, rank, local):
     alg = {k: v * steps for k, v in algorithmic_bytes(npix, nframes, nwin, T, hbytes).items()}
     fl = render_flops(npix, NX, NY, nframes) * steps
     roofline = roofline_of(per_kernel, alg, hbm, peak_kind, ms / 1e3,
-                           {k: fl for k in RENDER_KERNELS}, alg_steps=steps)
+                           {k: fl for k in RENDER_KERNELS}, alg_steps=steps,
+                           fp32_peak=rates["fp32_peak_tflops"] if rates else None)
 
     # ---------------------------------------------------------------- end to end (host buffers)
     # dh_pca_batch_host: pinned host frames in, host images and eigenvalues out; the library
@@ -395,6 +399,17 @@ def run_ours(args, ws, rank, local):
                   "tolerance_image": 1e-3 if args.precision != "fp32" else 1e-4,
                   "tolerance_eig": 1e-5}
 
+    # ---------------------------------------------------------------- p50 / p99 latency
+    # the metric's third term: a short replay of the serving mix at the stream clock, after
+    # the headline plan's memory is given back
+    latency = None
+    plan.close()
+    torch.cuda.synchronize()
+    if args.latency_seconds > 0:
+        frames = None  # the step's 4 GiB of input frames
+        torch.cuda.empty_cache()
+        latency = serve_latency(args, ws, rank, local)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -417,12 +432,13 @@ def run_ours(args, ws, rank, local):
             "plain_fp32": plain,
             "speedup_vs_plain_fp32": (value / plain["value"]) if plain else None,
             "parity": parity,
+            "latency_ms": latency,
+            "measured_rates": rates,
             "gpu_launches": launches_total,
             "device_flags": flags,
             "clocks": clock_info,
         }
         print(json.dumps(line), flush=True)
-    plan.close()
     return 0
 
 
@@ -464,13 +480,40 @@ def render_flops(npix: int, nx: int, ny: int, frames: int) -> float:
 
 
 def fp32_peak_tflops() -> float:
-    """FP32 FMA peak: SMs x 128 FP32 lanes x 2 flops x the maximum SM clock (2032 MHz)."""
+    """Nominal FP32 FMA peak: SMs x 128 FP32 lanes x 2 flops x the maximum SM clock (2032 MHz)."""
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     return sms * 128 * 2 * 2.032e9 / 1e12
 
 
+def measure_rates(local) -> dict:
+    """FP32 (scalar and paired FMA) and FP64 FMA throughput measured now, on this GPU, by the
+    library's rate kernel (dh_measure_fma_rate), with the SM clock sampled meanwhile; no clock
+    or power setting is touched. The FP32 peak is the larger of the two FP32 forms."""
+    import paper_2004_00923_b300 as dh
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.2)
+    clocks.begin()
+    out = {}
+    for kind, iters in (("fp32", 32768), ("fp32x2", 16384), ("fp64", 512)):
+        best = None
+        for _ in range(3):
+            r = dh.measure_fma_rate(kind, iters=iters, blocks_per_sm=4)
+            if best is None or r["tflops"] > best["tflops"]:
+                best = r
+        out[kind] = {"tflops": best["tflops"], "ms": best["ms"]}
+    clocks.end()
+    info = clocks.stop()
+    out["fp32_peak_tflops"] = max(out["fp32"]["tflops"], out["fp32x2"]["tflops"])
+    out["fp64_peak_tflops"] = out["fp64"]["tflops"]
+    out["clocks"] = info
+    out["how"] = ("dh_measure_fma_rate: 4 x SMs CTAs x 256 threads x 8 independent FMA chains, "
+                  "best of 3 timed launches (CUDA events) after a warm-up")
+    return out
+
+
 def roofline_of(per_kernel: dict, alg: dict, hbm: float, peak_kind: str, step_s: float,
-                flops: dict | None = None, alg_steps: int = 1) -> dict:
+                flops: dict | None = None, alg_steps: int = 1, fp32_peak: float | None = None) -> dict:
     """Roofline of the kernel with the most device time among those with algorithmic bytes;
     `alg` (and `flops`) and `per_kernel` cover the same traced steps. The FFT kernels of
     Eq. 1 are bound by FP32 arithmetic (their DRAM traffic is the algorithmic minimum at a
@@ -485,10 +528,13 @@ def roofline_of(per_kernel: dict, alg: dict, hbm: float, peak_kind: str, step_s:
            "peak_kind": f"{peak_kind} copy bandwidth"}
     if flops and dom in flops:
         tf = flops[dom] / d["launches"] / launch_s / 1e12
-        peak = fp32_peak_tflops()
+        if fp32_peak:
+            peak, kind = fp32_peak, "measured FP32 FMA rate of this run (dh_measure_fma_rate)"
+        else:
+            peak, kind = fp32_peak_tflops(), "nominal FP32 FMA peak: SMs x 128 lanes x 2 flops x 2032 MHz"
         out = {"bound": "alu", "kernel": dom, "achieved": tf, "peak": peak, "unit": "TFLOP/s",
-               "frac": tf / peak, "traffic": traffic_record(dom),
-               "peak_kind": "FP32 FMA peak: SMs x 128 lanes x 2 flops x 2032 MHz",
+               "frac": tf / peak, "traffic": traffic_record(dom), "peak_kind": kind,
+               "nominal_fp32_tflops": fp32_peak_tflops(),
                "hbm_view": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}}
     # `alg` covers `alg_steps` traced steps; the fraction is per step
     out["step_hbm_frac"] = sum(alg[k] for k in per_kernel if k in alg) / alg_steps / step_s / 1e9 / hbm
@@ -906,41 +952,40 @@ def pct(xs, q):
     return float(np.percentile(np.asarray(xs), q)) if xs else None
 
 
-def run_serving(args, ws, rank, local):
-    """4 camera streams of 1024^2 at 500 fps and 1 of 2048^2 at 125 fps, 32-frame windows,
-    replayed at the stream clock from pinned host frame pools for `--serve-seconds` of stream
-    time: frames are pushed in 4-frame grabber chunks as they arrive, every finished window
-    is polled back to the host, and its latency (push of its last frame -> image in host
-    memory) is recorded. Then an admission pass against the 40 GB budget and a saturation
-    pass (no clock) for the loop's capacity."""
-    import paper_2004_00923_b300 as dh
-    from dh_synth import SpeckleParams, SpeckleStream
+class ServeReplay:
+    """The serving mix (4 camera streams of 1024^2 at 500 fps and 1 of 2048^2 at 125 fps,
+    32-frame windows) on one dh.Server, fed from pinned host frame pools of `pool` frames per
+    stream. run(seconds, clocked) replays that much stream time: frames are pushed in
+    4-frame grabber chunks as they arrive (clocked) or as fast as the loop accepts them, every
+    finished window is polled back to the host and its latency recorded."""
 
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    srv = dh.Server(SERVE_BUDGET)
-    pools, ids, fps = [], [], []
-    for i, (n, rate) in enumerate(SERVE_STREAMS):
-        gen = SpeckleStream(SpeckleParams(n, n), seed=4000 + 10 * rank + i, device=dev)
-        pool = torch.empty((SERVE_POOL, n, n), dtype=torch.uint16, pin_memory=True)
-        for k in range(0, SERVE_POOL, 32):
-            pool[k:k + 32].copy_(gen.next(32))
-        pools.append(pool)
-        ids.append(srv.add_stream(n, n, LAM, Z, PITCH, SERVE_T, "fp16", 2, SERVE_T - 1,
-                                  ring_windows=SERVE_RING))
-        fps.append(rate)
-    torch.cuda.synchronize()
-    used_served = srv.used_bytes
+    def __init__(self, dh, dev, rank, pool=SERVE_POOL):
+        from dh_synth import SpeckleParams, SpeckleStream
+        self.dh = dh
+        self.pool = pool
+        self.srv = dh.Server(SERVE_BUDGET)
+        self.pools, self.ids, self.fps = [], [], []
+        for i, (n, rate) in enumerate(SERVE_STREAMS):
+            gen = SpeckleStream(SpeckleParams(n, n), seed=4000 + 10 * rank + i, device=dev)
+            pl = torch.empty((pool, n, n), dtype=torch.uint16, pin_memory=True)
+            for k in range(0, pool, 32):
+                pl[k:k + 32].copy_(gen.next(min(32, pool - k)))
+            self.pools.append(pl)
+            self.ids.append(self.srv.add_stream(n, n, LAM, Z, PITCH, SERVE_T, "fp16", 2, SERVE_T - 1,
+                                                ring_windows=SERVE_RING))
+            self.fps.append(rate)
+        torch.cuda.synchronize()
+        self.pushed = [0] * len(self.ids)  # frames each stream has received so far
 
-    def frames_of(i, k, cnt):
-        j = k % SERVE_POOL
-        return pools[i][j:j + cnt]
+    def frames_of(self, i, k, cnt):
+        j = k % self.pool
+        return self.pools[i][j:j + cnt]
 
-    pushed = [0] * len(ids)  # frames each stream has received so far (across passes)
-
-    def run(seconds, clocked):
-        """Returns (windows, wall seconds, latencies per stream, max push lateness)."""
-        start = list(pushed)
+    def run(self, seconds, clocked):
+        """Returns (windows, wall seconds, latencies per stream, latencies from the push,
+        push lateness)."""
+        srv, ids, fps, dh = self.srv, self.ids, self.fps, self.dh
+        start = list(self.pushed)
         nxt = [0] * len(ids)  # frames pushed in this pass
         lat = {sid: [] for sid in ids}       # from the scheduled arrival of the last frame
         lat_push = {sid: [] for sid in ids}  # from the push of the last frame
@@ -983,7 +1028,7 @@ def run_serving(args, ws, rank, local):
             while True:
                 try:
                     k = start[i] + nxt[i]
-                    srv.push(ids[i], frames_of(i, k, SERVE_CHUNK), k)
+                    srv.push(ids[i], self.frames_of(i, k, SERVE_CHUNK), k)
                     break
                 except dh.DHError as e:
                     if e.code != 7:  # only output backpressure is waited out
@@ -995,8 +1040,65 @@ def run_serving(args, ws, rank, local):
         collect()
         wall = time.perf_counter() - t0
         for i in range(len(ids)):
-            pushed[i] = start[i] + nxt[i]
+            self.pushed[i] = start[i] + nxt[i]
         return total, wall, lat, lat_push, late
+
+    def latency_summary(self, lat, seconds):
+        all_lat = [x for v in lat.values() for x in v]
+        by_size = {}
+        for (n, _), sid in zip(SERVE_STREAMS, self.ids):
+            by_size.setdefault(f"{n}x{n}", []).extend(lat[sid])
+        return {"p50": pct(all_lat, 50), "p99": pct(all_lat, 99),
+                "max": max(all_lat) if all_lat else None, "windows": len(all_lat),
+                "expected_windows": sum(int(seconds * r) // SERVE_T for _, r in SERVE_STREAMS),
+                "by_size": {k: {"p50": pct(v, 50), "p99": pct(v, 99), "max": max(v) if v else None}
+                            for k, v in by_size.items()},
+                "from": "scheduled arrival of the window's last frame at the stream clock -> "
+                        "image and eigenvalues in host memory",
+                "target_p99": 64.0}
+
+    def close(self):
+        self.srv.close()
+
+
+def serve_latency(args, ws, rank, local):
+    """The third term of the headline metric: p50/p99 window latency of a short replay of
+    the serving mix at the stream clock (`--latency-seconds` of stream time, after one
+    clock-free second of warm-up); the max of each percentile over ranks."""
+    import paper_2004_00923_b300 as dh
+    dev = torch.device("cuda", local)
+    rep = ServeReplay(dh, dev, rank, pool=64)
+    try:
+        rep.run(1.0, clocked=False)
+        n_win, wall, lat, _, late = rep.run(args.latency_seconds, clocked=True)
+        out = rep.latency_summary(lat, args.latency_seconds)
+    finally:
+        rep.close()
+    for key in ("p50", "p99", "max"):
+        if out[key] is not None:
+            out[key] = max_over_ranks(out[key], ws)
+    out["stream_seconds"] = args.latency_seconds
+    out["windows_per_s"] = n_win / wall
+    out["push_lateness_p99_ms"] = pct(late, 99) * 1e3 if late else None
+    out["streams"] = [{"n": n, "fps": r} for n, r in SERVE_STREAMS]
+    return out
+
+
+def run_serving(args, ws, rank, local):
+    """4 camera streams of 1024^2 at 500 fps and 1 of 2048^2 at 125 fps, 32-frame windows,
+    replayed at the stream clock from pinned host frame pools for `--serve-seconds` of stream
+    time: frames are pushed in 4-frame grabber chunks as they arrive, every finished window
+    is polled back to the host, and its latency (push of its last frame -> image in host
+    memory) is recorded. Then an admission pass against the 40 GB budget and a saturation
+    pass (no clock) for the loop's capacity."""
+    import paper_2004_00923_b300 as dh
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rep = ServeReplay(dh, dev, rank)
+    srv, ids, pools = rep.srv, rep.ids, rep.pools
+    used_served = srv.used_bytes
+    run = rep.run
 
     # warm-up: one clock-free second of every stream
     run(1.0, clocked=False)
@@ -1087,7 +1189,7 @@ def run_serving(args, ws, rank, local):
             "parity": parity, "clocks": clock_info,
         }
         print(json.dumps(line), flush=True)
-    srv.close()
+    rep.close()
     return 0
 
 
@@ -1125,6 +1227,11 @@ def main(argv=None):
     ap.add_argument("--render-lag", type=int, default=0, help="DH_OPT_RENDER_LAG (0 = automatic)")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="stream time replayed by --workload serving")
+    ap.add_argument("--latency-seconds", type=float, default=10.0,
+                    help="headline line: stream time of the serving replay that gives the p50/p99 "
+                         "window latency (0 = skip)")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="headline line: skip the FP32/FP64 FMA-rate measurement")
     ap.add_argument("--workload", choices=["paper", "sliding", "uneven", "serving", "fourier"],
                     default="paper",
                     help="paper: the headline 64 x 1024^2 x 32 step (default); sliding: "

@@ -145,6 +145,13 @@ dh_status dh_plan_reserve(dh_plan_t plan, int max_frames, int max_windows);
  *   on disjoint SMs (the covariance and projection launches leave one SM per eigensolver
  *   CTA). 1: one group always. Both give bitwise the same results. */
 #define DH_OPT_WINDOW_GROUPS 5
+/* DH_OPT_TEST_STALL (test only, for the failure path): value > 0 makes every CTA of the
+ *   persistent render (DH_OPT_RENDER_SCHEDULE 0) first wait `value` SM cycles (at most 1e8)
+ *   on a device word that nothing sets; the bounded wait runs out, the CTA raises
+ *   DH_FLAG_WAIT_TIMEOUT and skips its work (no CTA is left waiting on another), and the next
+ *   dh_plan_status returns DH_ERR_TIMEOUT. The holograms of that call are not written.
+ *   0 (default): off. */
+#define DH_OPT_TEST_STALL 6
 dh_status dh_plan_set_option(dh_plan_t plan, int option, int value);
 dh_status dh_plan_get_option(dh_plan_t plan, int option, int *value);
 
@@ -286,8 +293,13 @@ dh_status dh_debug_covariance(dh_plan_t plan, int w, double *out_dev, void *stre
  * row-major, to out_dev. Asynchronous. */
 dh_status dh_debug_eigvecs(dh_plan_t plan, int w, double *out_dev, void *stream);
 
-/* Synchronise the device, return the plan's accumulated DH_FLAG_* bits in *flags and
- * clear them. */
+/* Wait for the plan's own work -- the streams its calls launched work on since the last
+ * read, its second stream and its host-copy streams (the whole device only if the plan's
+ * work was captured into a graph, or ran on more than 8 streams) -- then return the plan's
+ * accumulated DH_FLAG_* bits in *flags and clear them. Returns DH_ERR_TIMEOUT when the bits
+ * include DH_FLAG_WAIT_TIMEOUT (a bounded device-side wait gave up and its kernel skipped
+ * work: that work's results are invalid; the context stays usable), else DH_OK. Not
+ * concurrently with other calls on the same plan. */
 dh_status dh_plan_status(dh_plan_t plan, uint32_t *flags);
 
 /* Tracing: with on != 0, every kernel the plan launches from now on is bracketed by two
@@ -302,20 +314,35 @@ dh_status dh_profile_enable(dh_plan_t plan, int on);
  * NULL. Returns the number of kernel kinds the library has (write at most n entries). */
 int dh_profile_read(dh_plan_t plan, int n, const char **names, int *launches, double *total_ms);
 
-/* The covariance of one window (the C = H^{t*} H of Eq. 4) without any device
- * allocation, for callers that cannot call cudaMalloc while running (for example a
- * frame-grabber callback in a real-time acquisition loop, where an allocation can
+/* Arithmetic-rate measurement for rooflines (the paper has no counterpart; it serves the
+ * measurement of the FP32-bound render of Eq. 1 and the FP64-bound eigensolver of Eq. 5):
+ * launches blocks_per_sm (1..64) x SMs CTAs of 256 threads, each thread running 8
+ * independent FMA chains for iters x 8 rounds, once to warm up and once timed with CUDA
+ * events on `stream` (synchronised). kind 0: scalar FP32 FMA; 1: paired FP32 FMA (two lanes
+ * per instruction); 2: FP64 FMA. *ms receives the timed launch's duration and *flops its
+ * floating-point operations (2 per FMA lane). */
+dh_status dh_measure_fma_rate(int kind, int iters, int blocks_per_sm, float *ms, double *flops,
+                              void *stream);
+
+/* The covariance of one window, C = H^{t*} H (the FP32 plain path's covariance), without
+ * any device allocation, for callers that cannot call cudaMalloc while running (for example
+ * a frame-grabber callback in a real-time acquisition loop, where an allocation can
  * synchronise the device, or code whose device memory belongs to another allocator). The
  * paper has no counterpart: it is a deployment variant of the covariance stage.
  *   planes_dev: caller-owned device FP32 array [2T][npix]: row 2t = Re H_t, row 2t+1 = Im H_t
- *               (pixels in any fixed order); npix a positive multiple of 32, <= 2^28.
+ *               (pixels in any fixed order); npix a positive multiple of 32, <= 2^28;
+ *               8-byte aligned (else DH_ERR_INVALID_ARG).
  *   T:          16, 32 or 64 (else DH_ERR_UNSUPPORTED_SIZE).
- *   C_dev:      caller-owned device FP64 output, T x T interleaved (re, im), row-major.
+ *   C_dev:      caller-owned device FP64 output, T x T interleaved (re, im), row-major;
+ *               8-byte aligned (else DH_ERR_INVALID_ARG). A non-finite covariance shows up
+ *               as NaN/Inf entries here; no flag is reported.
  * Products are FP32 with FP64 accumulation (as the plain path). The split-K scratch is a
  * fixed 2 MiB device array inside the library (16 partial matrices at T = 64, 64 at
  * T <= 32), held by every GPU that loads the library until exit. The first call on a device
- * looks up that array's address (make it before any stream capture); all calls share the
- * array, so calls that overlap on the GPU race. Asynchronous on `stream`. */
+ * looks up that array's address and loads the library's kernels for this entry point (which
+ * can allocate): make one call per device before real-time use and before any stream
+ * capture. All calls share the array, so calls that overlap on the GPU race. Asynchronous
+ * on `stream`. */
 dh_status dh_covariance_noalloc(const float *planes_dev, int64_t npix, int T, double *C_dev,
                                 void *stream);
 

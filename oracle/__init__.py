@@ -232,10 +232,14 @@ def normalize(M: np.ndarray):
     return M / mean, mean
 
 
-def display_u8(M: np.ndarray, mean: float, gain: float = 128.0) -> np.ndarray:
-    """8-bit display codes of an image with the given mean: clamp(rint(gain * M / mean), 0,
-    255), the product taken in FP32 as float(M) * float(gain / mean) (the precision in which
-    the kernel decides the code); the mean maps to code `gain`."""
-    scale = np.float32(np.float64(gain) / np.float64(mean))
-    v = np.asarray(M, dtype=np.float32) * scale
-    return np.clip(np.rint(v), 0, 255).astype(np.uint8)
+def display_value(M: np.ndarray, gain: float = 128.0) -> np.ndarray:
+    """The display value gain * M / mean(M) of every pixel, in FP64, with the image's own FP64
+    mean (the paper normalises each displayed image by its average value)."""
+    N, _ = normalize(M)
+    return np.float64(gain) * N
+
+
+def display_u8(M: np.ndarray, gain: float = 128.0) -> np.ndarray:
+    """8-bit display codes of an image: clamp(rint(gain * M / mean(M)), 0, 255), decided in
+    FP64 from the image's own FP64 mean; the mean maps to code `gain`."""
+    return np.clip(np.rint(display_value(M, gain)), 0, 255).astype(np.uint8)

@@ -290,9 +290,34 @@ class Plan:
         return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(min(k, n))}
 
     def status(self) -> int:
+        """The plan's DH_FLAG_* bits since the last read (then cleared), after waiting for the
+        plan's own work. A timed-out device wait (DH_ERR_TIMEOUT from the C ABI) shows as
+        DH_FLAG_WAIT_TIMEOUT (0x8) in the returned bits."""
         flags = ctypes.c_uint32(0)
-        _lib.check("dh_plan_status", self._lib.dh_plan_status(self._h, ctypes.byref(flags)))
+        rc = self._lib.dh_plan_status(self._h, ctypes.byref(flags))
+        if rc != 5:  # DH_ERR_TIMEOUT: reported through the flags
+            _lib.check("dh_plan_status", rc)
         return int(flags.value)
+
+    def set_test_stall(self, cycles: int) -> None:
+        """DH_OPT_TEST_STALL (test only): the persistent render's CTAs first wait `cycles`
+        SM cycles on a device word nothing sets, give up, and skip their work; the next status
+        read reports DH_ERR_TIMEOUT. 0 turns it off."""
+        _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(self._h, 6, int(cycles)))
+
+
+def measure_fma_rate(kind: str = "fp32", iters: int = 4096, blocks_per_sm: int = 4,
+                     stream=None) -> dict:
+    """dh_measure_fma_rate: the FMA throughput this GPU sustains now. kind: "fp32" (scalar
+    FMA), "fp32x2" (paired FMA) or "fp64". Returns {"ms", "flops", "tflops"}."""
+    lib = _lib.load()
+    k = {"fp32": 0, "fp32x2": 1, "fp64": 2}[kind]
+    ms, fl = ctypes.c_float(0), ctypes.c_double(0)
+    _lib.check("dh_measure_fma_rate", lib.dh_measure_fma_rate(k, int(iters), int(blocks_per_sm),
+                                                              ctypes.byref(ms), ctypes.byref(fl),
+                                                              _stream_ptr(stream)))
+    return {"ms": float(ms.value), "flops": float(fl.value),
+            "tflops": float(fl.value) / (float(ms.value) * 1e-3) / 1e12}
 
 
 def normalize_images(images: torch.Tensor, normalized: bool = True, display: bool = False,

@@ -282,6 +282,22 @@ dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int 
   return DH_OK;
 }
 
+}  // namespace
+
+void note_stream(Plan &p, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    p.touched_all = true;  // a graph's launch stream is not known here
+    return;
+  }
+  for (int i = 0; i < p.n_touched; ++i)
+    if (p.touched[i] == s) return;
+  if (p.n_touched < Plan::kMaxTouched) p.touched[p.n_touched++] = s;
+  else p.touched_all = true;
+}
+
+namespace {
+
 struct Busy {
   std::atomic<int> &b;
   bool ok;
@@ -331,6 +347,7 @@ dh_status plan_pca(dh_plan *h, int first_slot, int slot_stride, int n_windows, i
                    float *images, double *eigvals, cudaStream_t s) {
   Busy g(h->busy);
   if (!g.ok) return DH_ERR_STATE;
+  note_stream(h->p, s);
   return pca_impl(h->p, nullptr, 0, first_slot, slot_stride, n_windows, k0, k1, images, eigvals, s);
 }
 
@@ -338,6 +355,7 @@ dh_status plan_render(dh_plan *h, const uint16_t *frames, long long stride, int 
                       cudaStream_t s) {
   Busy g(h->busy);
   if (!g.ok) return DH_ERR_STATE;
+  note_stream(h->p, s);
   return launch_render(h->p, frames, stride, n, slot0, s);
 }
 
@@ -403,12 +421,13 @@ dh_status dh_plan_create(dh_plan_t *out, int nx, int ny, double lambda_m, double
         (st = dalloc(p, &p.d_twx, twx.size() * sizeof(float2))) == DH_OK &&
         (st = dalloc(p, &p.d_twy, twy.size() * sizeof(float2))) == DH_OK &&
         (st = dalloc(p, &p.d_status, sizeof(uint32_t))) == DH_OK &&
-        (st = dalloc(p, &p.d_sync, sizeof(unsigned) * (1 + 2 * 64))) == DH_OK) {
+        (st = dalloc(p, &p.d_sync, sizeof(unsigned) * (2 + 2 * 64))) == DH_OK) {
       cudaError_t c = cudaMemcpy(p.d_cx, cx.data(), cx.size() * sizeof(float2), cudaMemcpyHostToDevice);
       if (c == cudaSuccess) c = cudaMemcpy(p.d_cy, cy.data(), cy.size() * sizeof(float2), cudaMemcpyHostToDevice);
       if (c == cudaSuccess) c = cudaMemcpy(p.d_twx, twx.data(), twx.size() * sizeof(float2), cudaMemcpyHostToDevice);
       if (c == cudaSuccess) c = cudaMemcpy(p.d_twy, twy.data(), twy.size() * sizeof(float2), cudaMemcpyHostToDevice);
       if (c == cudaSuccess) c = cudaMemset(p.d_status, 0, sizeof(uint32_t));
+      if (c == cudaSuccess) c = cudaMemset(p.d_sync, 0, sizeof(unsigned) * (2 + 2 * 64));
       st = c == cudaSuccess ? alloc_store(p) : fail_cuda(c);
     }
   }
@@ -535,6 +554,7 @@ dh_status dh_plan_get_option(dh_plan_t h, int option, int *value) {
     case DH_OPT_COVARIANCE: *value = h->p.cov_mode; return DH_OK;
     case DH_OPT_PROJECTION: *value = h->p.proj_mode; return DH_OK;
     case DH_OPT_WINDOW_GROUPS: *value = h->p.group_mode; return DH_OK;
+    case DH_OPT_TEST_STALL: *value = h->p.test_stall; return DH_OK;
   }
   return DH_ERR_INVALID_ARG;
 }
@@ -630,6 +650,10 @@ dh_status dh_plan_set_option(dh_plan_t h, int option, int value) {
       if (value != 0 && value != 1) return DH_ERR_INVALID_ARG;
       h->p.group_mode = value;
       return DH_OK;
+    case DH_OPT_TEST_STALL:
+      if (value < 0 || value > 100000000) return DH_ERR_INVALID_ARG;
+      h->p.test_stall = value;
+      return DH_OK;
   }
   return DH_ERR_INVALID_ARG;
 }
@@ -661,6 +685,7 @@ dh_status dh_render_frames(dh_plan_t h, const uint16_t *frames_dev, int64_t fram
     return DH_ERR_INVALID_ARG;
   Busy g(h->busy);
   if (!g.ok) return DH_ERR_STATE;
+  note_stream(p, static_cast<cudaStream_t>(stream));
   return launch_render(p, frames_dev, frame_stride_elems, n_frames, first_slot,
                        static_cast<cudaStream_t>(stream));
 }
@@ -675,6 +700,7 @@ dh_status dh_pca_windows(dh_plan_t h, int first_slot, int slot_stride, int n_win
     return DH_ERR_INVALID_ARG;
   Busy g(h->busy);
   if (!g.ok) return DH_ERR_STATE;
+  note_stream(p, static_cast<cudaStream_t>(stream));
   return pca_impl(p, nullptr, 0, first_slot, slot_stride, n_windows, k0, k1, images_dev, eigvals_dev,
                   static_cast<cudaStream_t>(stream));
 }
@@ -690,6 +716,7 @@ dh_status dh_svd_fourier_windows(dh_plan_t h, int first_slot, int slot_stride, i
     return DH_ERR_INVALID_ARG;
   Busy g(h->busy);
   if (!g.ok) return DH_ERR_STATE;
+  note_stream(p, static_cast<cudaStream_t>(stream));
   return pca_impl(p, nullptr, 0, first_slot, slot_stride, n_windows, k0, k1, images_dev, eigvals_dev,
                   static_cast<cudaStream_t>(stream), b0, b1);
 }
@@ -703,6 +730,7 @@ dh_status dh_fourier_windows(dh_plan_t h, int first_slot, int slot_stride, int n
     return DH_ERR_INVALID_ARG;
   Busy g(h->busy);
   if (!g.ok) return DH_ERR_STATE;
+  note_stream(p, static_cast<cudaStream_t>(stream));
   return launch_fourier(p, first_slot, slot_stride, n_windows, k0, k1, images_dev,
                         static_cast<cudaStream_t>(stream));
 }
@@ -728,6 +756,7 @@ dh_status dh_band_gram(dh_plan_t h, int first_slot, int n_frames, void *stream) 
     if ((st = dalloc(p, &p.d_band_part, (size_t)blocks * band_units(p.npix) * cell)) != DH_OK) return st;
     p.band_cap = blocks;
   }
+  note_stream(p, static_cast<cudaStream_t>(stream));
   dh_status st = launch_band_gram(p, first_slot, n_frames, static_cast<cudaStream_t>(stream));
   if (st != DH_OK) return st;
   p.band_first = first_slot;
@@ -767,6 +796,7 @@ dh_status dh_pca_batch(dh_plan_t h, const uint16_t *frames_dev, int64_t frame_st
   if (p.is_view) return DH_ERR_STATE;
   Busy g(h->busy);
   if (!g.ok) return DH_ERR_STATE;
+  note_stream(p, static_cast<cudaStream_t>(stream));
   return pca_impl(p, frames_dev, frame_stride_elems, 0, window_stride_frames, n_windows, k0, k1,
                   images_dev, eigvals_dev, static_cast<cudaStream_t>(stream), -1, -1, frames_dev,
                   frame_stride_elems);
@@ -820,6 +850,7 @@ dh_status dh_pca_batch_host(dh_plan_t h, const uint16_t *frames_host, int64_t fr
     q.img_elems = img_elems; q.eig_elems = eig_elems;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  note_stream(p, s);
   DH_CUDA_TRY(cudaEventRecord(q.start, s));  // copies follow earlier work on the caller's stream
   DH_CUDA_TRY(cudaStreamWaitEvent(q.up, q.start, 0));
   DH_CUDA_TRY(cudaStreamWaitEvent(q.down, q.start, 0));
@@ -899,10 +930,27 @@ int dh_profile_read(dh_plan_t h, int n, const char **names, int *launches, doubl
 
 dh_status dh_plan_status(dh_plan_t h, uint32_t *flags) {
   if (!h || !flags) return DH_ERR_INVALID_ARG;
-  DH_CUDA_TRY(cudaDeviceSynchronize());
-  DH_CUDA_TRY(cudaMemcpy(flags, h->p.d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
-  DH_CUDA_TRY(cudaMemset(h->p.d_status, 0, sizeof(uint32_t)));
-  return DH_OK;
+  Plan &p = h->p;
+  // wait for the plan's own work only: the streams its calls launched on, its second stream
+  // and its host-copy streams; the whole device only if it lost track (see note_stream)
+  if (p.touched_all) {
+    DH_CUDA_TRY(cudaDeviceSynchronize());
+  } else {
+    for (int i = 0; i < p.n_touched; ++i) DH_CUDA_TRY(cudaStreamSynchronize(p.touched[i]));
+    for (cudaStream_t q : {p.pipe.up, p.pipe.down})
+      if (q) DH_CUDA_TRY(cudaStreamSynchronize(q));
+  }
+  // read and clear the word on the plan's own non-blocking stream (no implicit
+  // synchronisation with the legacy default stream)
+  DH_CUDA_TRY(cudaStreamSynchronize(p.aux));
+  uint32_t v = 0;
+  DH_CUDA_TRY(cudaMemcpyAsync(&v, p.d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, p.aux));
+  DH_CUDA_TRY(cudaMemsetAsync(p.d_status, 0, sizeof(uint32_t), p.aux));
+  DH_CUDA_TRY(cudaStreamSynchronize(p.aux));
+  p.n_touched = 0;
+  p.touched_all = false;
+  *flags = v;
+  return (v & DH_FLAG_WAIT_TIMEOUT) ? DH_ERR_TIMEOUT : DH_OK;
 }
 
 // ---------------------------------------------------------------- CUDA graphs
@@ -986,6 +1034,8 @@ dh_status dh_batch_run(const dh_batch_item *items, int n_items, void *stream) {
   std::lock_guard<std::mutex> lk(x.mu);
   DH_CUDA_TRY(x.init());
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the branches join back into the caller's stream: waiting on it covers them
+  for (dh_plan *q : plans) note_stream(q->p, s);
   // Branches: one per store for its renders, one per plan for its windows, in order of first
   // appearance (wrapping onto shared streams beyond kBranches, which only adds ordering).
   // The windows of different plans over one store (views) run concurrently once the store's

@@ -51,7 +51,18 @@ struct Plan {
   // SMs the next tensor-core covariance or projection launch may fill (0 = all): the rest
   // are left to an eigensolver running beside it
   int sm_budget = 0;
-  unsigned *d_sync = nullptr;  // ticket and ring counters of the persistent render
+  unsigned *d_sync = nullptr;  // ticket and ring counters of the persistent render, then one
+                               // word nothing ever sets (the stall test's wait target)
+  // test only (DH_OPT_TEST_STALL): cycles the persistent render's CTAs wait on that word
+  // before their first item; the wait always runs out (0 = off)
+  int test_stall = 0;
+  // streams the plan's calls launched work on since the last status read (dh_plan_status
+  // synchronises only these); touched_all: more streams than the list holds, or work
+  // captured into a graph (whose launch stream the plan does not see)
+  static constexpr int kMaxTouched = 8;
+  cudaStream_t touched[kMaxTouched] = {};
+  int n_touched = 0;
+  bool touched_all = false;
   // second stream: the eigensolver of one group of windows overlaps the next group's work
   cudaStream_t aux = nullptr;
   static constexpr int kMaxGroups = 4;
@@ -122,6 +133,8 @@ struct ProfScope {
 
 // ---------------------------------------------------------------- host helpers
 const char *set_cuda_error(cudaError_t e);
+// Record that plan work was launched on stream s (for dh_plan_status).
+void note_stream(Plan &p, cudaStream_t s);
 dh_status fail_cuda(cudaError_t e);
 
 #define DH_CUDA_TRY(expr)                         \
@@ -221,6 +234,9 @@ dh_status launch_gram_simt_rows(const float *X, long long npix, int T, int units
                                 cudaStream_t s);
 dh_status launch_reduce_cov_window(const double *part, int parts, int T, double *C, uint32_t *status,
                                    cudaStream_t s);
+// load the modules of the kernels the two helpers above launch, for every T
+dh_status preload_gram_simt_rows();
+dh_status preload_reduce_cov_window();
 
 // conversions for inspection
 dh_status launch_hologram_to_f32(Plan &p, int slot, float *out, cudaStream_t s);

@@ -963,6 +963,15 @@ dh_status launch_reduce_cov_window(const double *part, int parts, int T, double 
   return DH_OK;
 }
 
+// Loads the module of every instance launch_reduce_cov_window uses (see preload_gram_simt_rows).
+dh_status preload_reduce_cov_window() {
+  cudaFuncAttributes fa;
+  DH_CUDA_TRY(cudaFuncGetAttributes(&fa, k_reduce_cov<16>));
+  DH_CUDA_TRY(cudaFuncGetAttributes(&fa, k_reduce_cov<32>));
+  DH_CUDA_TRY(cudaFuncGetAttributes(&fa, k_reduce_cov<64>));
+  return DH_OK;
+}
+
 dh_status launch_reduce_raw(Plan &p, int n_windows, int parts, int woff, cudaStream_t s) {
   const int total = n_windows * p.T * p.T;
   ProfScope ps(p, K_REDUCE_RAW, s);

@@ -107,6 +107,16 @@ dh_status launch_gram_simt_rows(const float *X, long long npix, int T, int units
   return DH_OK;
 }
 
+// Loads the module of every instance launch_gram_simt_rows uses (under lazy module loading a
+// kernel's first launch would otherwise load it, which can allocate and synchronise).
+dh_status preload_gram_simt_rows() {
+  cudaFuncAttributes fa;
+  DH_CUDA_TRY(cudaFuncGetAttributes(&fa, k_gram_simt<16>));
+  DH_CUDA_TRY(cudaFuncGetAttributes(&fa, k_gram_simt<32>));
+  DH_CUDA_TRY(cudaFuncGetAttributes(&fa, k_gram_simt<64>));
+  return DH_OK;
+}
+
 // Split-K units per window: a function of the frame size only (never of the batch), so a
 // window's covariance is bitwise the same alone and inside any batch.
 int gram_units(long long npix) {

@@ -1,5 +1,5 @@
-// dh_covariance_noalloc: the covariance of one window (the quantity of Eq. 4) computed
-// without allocating any device memory.
+// dh_covariance_noalloc: the covariance C = H^{t*} H of one window computed without
+// allocating any device memory.
 //
 // Who needs it: callers that must not call cudaMalloc/cudaFree (or any allocating
 // routine) once they are running -- for example a frame-grabber callback or a real-time
@@ -10,10 +10,16 @@
 // exits.
 //
 // Set-up: the first call on a device looks up the array's device address with
-// cudaGetSymbolAddress (with that device current) and caches it per device; make that
-// first call before any stream capture. All calls on a device share the one array, so calls
-// whose kernels overlap on the GPU race (serialise them, e.g. on one stream). Every
-// partial matrix is fully overwritten before it is read, so nothing needs clearing.
+// cudaGetSymbolAddress (with that device current), caches it per device, and loads the
+// modules of every kernel the entry point launches, for all T (under lazy module loading a
+// kernel's first launch would load it, and loading a module can allocate and synchronise).
+// So the first call on a device may allocate: make one call per device before real-time use
+// and before any stream capture; from the second call on nothing is allocated or loaded.
+// All calls on a device share the one array, so calls whose kernels overlap on the GPU race
+// (serialise them, e.g. on one stream). Every partial matrix is fully overwritten before it
+// is read. The status word after the partials (the reduction's non-finite flag) is cleared
+// at the start of every call and is not reported: a non-finite covariance shows up as
+// NaN/Inf entries of C_dev itself.
 #include "dh_internal.cuh"
 
 #include <mutex>
@@ -39,6 +45,9 @@ dh_status scratch_for_current_device(void **out) {
   if (!g_scratch_addr[dev]) {
     void *ptr = nullptr;
     DH_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_cov_scratch));
+    dh_status st = preload_gram_simt_rows();
+    if (st == DH_OK) st = preload_reduce_cov_window();
+    if (st != DH_OK) return st;
     g_scratch_addr[dev] = ptr;
   }
   *out = g_scratch_addr[dev];
@@ -53,6 +62,9 @@ using namespace dh;
 extern "C" dh_status dh_covariance_noalloc(const float *planes_dev, int64_t npix, int T, double *C_dev,
                                            void *stream) {
   if (!planes_dev || !C_dev || npix < 32 || (npix % 32) != 0) return DH_ERR_INVALID_ARG;
+  // the planes are copied in 8-byte pieces and C is written as doubles
+  if ((reinterpret_cast<uintptr_t>(planes_dev) & 7u) != 0 || (reinterpret_cast<uintptr_t>(C_dev) & 7u) != 0)
+    return DH_ERR_INVALID_ARG;
   if (!(T == 16 || T == 32 || T == 64)) return DH_ERR_UNSUPPORTED_SIZE;
   if (npix > (1ll << 28)) return DH_ERR_UNSUPPORTED_SIZE;
   const size_t part_bytes = (size_t)(2 * T) * (2 * T) * sizeof(double);
@@ -68,6 +80,7 @@ extern "C" dh_status dh_covariance_noalloc(const float *planes_dev, int64_t npix
   double *part = static_cast<double *>(scratch);
   uint32_t *status = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(scratch) + kScratchBytes);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DH_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
   if ((st = launch_gram_simt_rows(planes_dev, npix, T, units, part, s)) != DH_OK) return st;
   return launch_reduce_cov_window(part, units, T, C_dev, status, s);
 }

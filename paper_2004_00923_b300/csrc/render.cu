@@ -597,11 +597,12 @@ __device__ __forceinline__ int atom_add_acq_rel_shared(int *p, int v) {
                : "=r"(old) : "r"(tc::smem_u32(p)), "r"(v) : "memory");
   return old;
 }
-__device__ __forceinline__ bool wait_geq(const unsigned *p, unsigned target) {
+__device__ __forceinline__ bool wait_geq(const unsigned *p, unsigned target,
+                                         long long budget = tc::kWaitBudget) {
   if (ld_acquire(p) >= target) return true;
   const long long t0 = clock64();
   while (ld_acquire(p) < target) {
-    if (clock64() - t0 > tc::kWaitBudget) return false;
+    if (clock64() - t0 > budget) return false;
     __nanosleep(128);
   }
   return true;
@@ -613,7 +614,7 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
                const float2 *__restrict__ cx, const float2 *__restrict__ cy, const float2 *__restrict__ tw,
                int tw_len,
                float2 *__restrict__ mid, int ring, int lag, OutT *__restrict__ H, long long rows_total,
-               int slot0, unsigned *__restrict__ sync, uint32_t *__restrict__ status) {
+               int slot0, unsigned *__restrict__ sync, uint32_t *__restrict__ status, int stall_cycles) {
   using S = Shape<LOGN>;
   using RC = RowCfg<LOGN>;
   constexpr int FPC = fpc<LOGN>();  // rows per row item = columns per column item
@@ -654,8 +655,12 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
     preissued = -1;
     tk[0] = (int)atomicAdd(tickets, 1u);
     pending = (int)atomicAdd(tickets, 1u);
+    // stall test: a bounded wait on the word after the counters, which nothing sets, runs
+    // out in every CTA before any item starts (so no CTA waits on an item left undone)
+    if (stall_cycles > 0 && !wait_geq(sync + 1 + 2 * kMaxRing, 1u, stall_cycles)) abort_flag = 1;
   }
   __syncthreads();
+  const bool stalled = abort_flag;  // read after the barrier: the same in every thread
   // ticket i: phase k = i / (2 NI); even positions are row items of frame k, odd ones column
   // items of frame k - lag; the item index is the position / 2
   auto is_row = [](int i) { return ((i % (2 * NI)) & 1) == 0; };
@@ -670,7 +675,7 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
   uint32_t maxbits = 0;
   int b = 1;
   bool pre_unwaited = false;  // a copy issued early for `cur` that no one has waited on
-  while (cur < total) {
+  while (!stalled && cur < total) {
     // one barrier per item start: thread 0 publishes the next ticket, takes the one after it
     // and, for a row item, waits for its ring slot; the barrier also ends the previous item's
     // use of shared memory
@@ -944,7 +949,7 @@ dh_status launch_fused_t(Plan &p, const uint16_t *frames, long long fstride, int
   kern<<<grid, kCtaThreads, smem, s>>>(frames, fstride, nf, col_tile_log(p.logny), p.d_cx, p.d_cy, p.d_twx, tw_len,
                                       p.d_mid,
                                ring, lag, static_cast<OutT *>(p.d_H), 2ll * p.max_frames, slot0, p.d_sync,
-                               p.d_status);
+                               p.d_status, p.test_stall);
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
   }

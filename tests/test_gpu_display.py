@@ -1,6 +1,10 @@
 """Display normalisation (each image divided by its mean) and 8-bit display codes, through
-the C ABI, against the oracle; the display codes are decided in FP32 on both sides from the
-same mean, so they must agree exactly. Also the headless PGM output."""
+the C ABI, against the oracle. The oracle takes the image alone: its own FP64 mean and FP64
+code decisions. The kernel decides each code in FP32 (value * float(gain / mean)), within
+about 2 FP32 roundings (~1.2e-7 relative, < 4e-5 of a code at 255) of the FP64 value, so the
+codes agree exactly except where the FP64 value lies within TIE_DIST of a rounding
+half-integer; there a difference of 1 is allowed, and the number of such pixels is counted
+and bounded. Also the headless PGM output."""
 
 import numpy as np
 import pytest
@@ -11,6 +15,10 @@ from dh_synth import SpeckleParams, SpeckleStream
 from parity_helpers import LAM, PITCH, Z, to_gpu
 
 pytestmark = pytest.mark.gpu
+
+# distance (in code units) from a rounding half-integer within which FP32 and FP64 decisions
+# may differ: 2.5 x the FP32 bound above at the top code
+TIE_DIST = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -35,8 +43,18 @@ def test_normalize_pca_images(dh, tmp_path):
         assert abs(means[w].item() - mean_ref) <= 1e-12 * mean_ref
         n = norm[w].double().cpu().numpy()
         assert np.max(np.abs(n - N_ref) / np.maximum(N_ref, 1e-30)) <= 2e-7
-        codes = oracle.display_u8(img[w].cpu().numpy(), means[w].item(), 100.0)
-        assert np.array_equal(disp[w].cpu().numpy(), codes)
+        codes = oracle.display_u8(M[w], 100.0)
+        v = oracle.display_value(M[w], 100.0)
+        near_tie = (np.abs(v - np.floor(v) - 0.5) < TIE_DIST) & (v < 255.5)
+        got = disp[w].cpu().numpy().astype(np.int32)
+        diff = np.abs(got - codes.astype(np.int32))
+        assert np.all(diff[~near_tie] == 0), int(np.count_nonzero(diff[~near_tie]))
+        assert np.all(diff[near_tie] <= 1)
+        # the tie band is 2e-4 of a code wide: expect about 2e-4 of the pixels in it
+        n_tie = int(np.count_nonzero(near_tie))
+        print(f"window {w}: {n_tie} of {M[w].size} pixels near a tie, "
+              f"{int(np.count_nonzero(diff))} codes differ")
+        assert n_tie <= 1e-3 * M[w].size + 4
     path = tmp_path / "window0.pgm"
     dh.save_pgm(str(path), disp[0])
     data = path.read_bytes()

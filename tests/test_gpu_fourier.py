@@ -77,9 +77,8 @@ def test_fourier_rejects_bad_bins(dh):
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
 def test_svd_fourier_windows_match_oracle(dh, T, prec):
     """Eqs. 2-3 then 8-9: SVD filter keeping components 2..T-1, then DFT bins. The filter is
-    the projector onto the kept eigenvectors, so like the image of Eqs. 6-7 it moves by about
-    ||dC|| / gap at the range boundary (the same gap-aware tolerance)."""
-    from parity_helpers import EPS_C, boundary_gap, lam_tol
+    the projector onto the kept eigenvectors; the stated image tolerance applies."""
+    from parity_helpers import lam_tol
     b0, b1 = BANDS[T]
     frames = SpeckleStream(SpeckleParams(128, 128), seed=70 + T).next(2 * T).numpy()
     with dh.Plan(128, 128, LAM, Z, PITCH, T=T, precision=prec, max_frames=2 * T,
@@ -91,8 +90,8 @@ def test_svd_fourier_windows_match_oracle(dh, T, prec):
     for w in range(2):
         M, lam_ref = oracle.svd_fourier_window(frames[w * T:(w + 1) * T], LAM, Z, PITCH, 2, T - 1,
                                                b0, b1)
-        tol = max(TOL_IMG[prec], EPS_C[prec] / boundary_gap(lam_ref, 2, T - 1))
-        assert rel(img[w], M) <= tol, (w, rel(img[w], M), tol)
+        print(f"T={T} {prec} window {w}: image {rel(img[w], M):.2e}")
+        assert rel(img[w], M) <= TOL_IMG[prec], (w, rel(img[w], M))
         assert np.max(np.abs(lam[w] - lam_ref)) / lam_ref[0] <= lam_tol(prec, 128 * 128)
 
 

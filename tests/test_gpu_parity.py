@@ -15,7 +15,8 @@ import torch
 
 import oracle
 from dh_synth import SpeckleParams, SpeckleStream, known_rank_frames, speckle_window
-from parity_helpers import LAM, PITCH, TOL_IMG, TOL_LAM, Z, check_window, lam_tol, rel, to_gpu
+from parity_helpers import (EXTREME_RANGES, LAM, PITCH, TOL_IMG, TOL_LAM, Z, check_window,
+                            check_window_extreme_range, lam_tol, rel, to_gpu)
 
 pytestmark = pytest.mark.gpu
 
@@ -101,12 +102,25 @@ def test_window_lengths(dh, T, prec):
     check_window(img[0], lam[0], C[0], f, 2, T - 1, prec)
 
 
+# FP16 storage of H alone rounds every value by up to 2^-12 relative; the projected image of
+# a range then carries ~u sqrt(E / (T M_kept)) relative error, E the energy and M_kept the
+# kept power. For the paper's own range (k0 = 12: the 20 weakest components, E / M_kept ~ 500
+# on this generator) that is 1.06-1.13e-3 in exact arithmetic with FP16-rounded H (emulated
+# from the oracle at 64^2 .. 512^2), above the 1e-3 of the fast form whatever the kernels do.
+STORAGE_FLOOR = {("fp16", 12, 31): "FP16 storage alone gives 1.1e-3 at k0 = 12 (E / M_kept ~ 500)"}
+
+
 @pytest.mark.parametrize("k0,k1", [(0, 31), (0, 0), (31, 31), (5, 17), (12, 31)])
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
-def test_retained_ranges(dh, k0, k1, prec):
+def test_retained_ranges(dh, k0, k1, prec, request):
+    if (prec, k0, k1) in STORAGE_FLOOR:
+        request.applymarker(pytest.mark.xfail(strict=True, reason=STORAGE_FLOOR[(prec, k0, k1)]))
     f = speckle_window(64, 64, 32, seed=77).numpy()
     img, lam, C, _ = gpu_windows(dh, f, 32, prec, k0, k1, 1, 32)
-    check_window(img[0], lam[0], C[0], f, k0, k1, prec)
+    if (k0, k1) in EXTREME_RANGES:
+        check_window_extreme_range(img[0], lam[0], C[0], f, k0, k1, prec)
+    else:
+        check_window(img[0], lam[0], C[0], f, k0, k1, prec)
 
 
 def test_full_range_is_parseval(dh):
@@ -225,7 +239,8 @@ def test_invalid_calls_return_errors(dh):
         with pytest.raises(dh.DHError):
             plan.render_frames(f, first_slot=8)  # slots beyond the reservation
         lib = plan._lib
-        for opt, bad in ((0, 2), (1, 1), (1, 65), (2, 64), (3, 3), (4, 2), (5, 2), (5, -1), (6, 0)):
+        for opt, bad in ((0, 2), (1, 1), (1, 65), (2, 64), (3, 3), (4, 2), (5, 2), (5, -1), (6, -1),
+                         (6, 100000001), (7, 0)):
             assert lib.dh_plan_set_option(plan._h, opt, bad) == 1, (opt, bad)  # DH_ERR_INVALID_ARG
         v = ctypes.c_int(-1)
         assert lib.dh_plan_get_option(plan._h, 5, ctypes.byref(v)) == 0 and v.value == 0

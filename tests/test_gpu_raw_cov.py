@@ -9,7 +9,7 @@ import torch
 
 import oracle
 from dh_synth import SpeckleParams, SpeckleStream
-from parity_helpers import LAM, PITCH, TOL_IMG, Z, boundary_gap, rel, to_gpu
+from parity_helpers import LAM, PITCH, TOL_IMG, Z, rel, to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -66,8 +66,8 @@ def test_raw_covariance_windows_match_oracle(dh, T, prec):
         # the projection still reads the 16-bit holograms: the stated image tolerance holds
         # for FP16 storage (BF16 storage is documented not to meet it)
         if prec == "fp16":
-            tol = max(TOL_IMG["fp16"], 1e-5 / boundary_gap(lam_ref, 2, T - 1))
-            assert rel(img[w], M) <= tol, (w, rel(img[w], M))
+            print(f"T={T} window {w}: image {rel(img[w], M):.2e}")
+            assert rel(img[w], M) <= TOL_IMG["fp16"], (w, rel(img[w], M))
 
 
 def test_raw_covariance_through_host_buffers(dh):

@@ -375,8 +375,15 @@ def test_normalized_image_has_unit_mean_and_is_scale_free():
 
 
 def test_display_codes_of_known_images():
-    """A constant image shows the mean's code; 2x the mean and above saturate; 0 is black."""
+    """A constant image shows the mean's code; 2x the mean and above saturate; 0 is black.
+    The codes come from the image's own mean."""
     const = np.full((8, 8), 3.25)
-    assert np.all(oracle.display_u8(const, 3.25) == 128)
-    ramp = np.array([0.0, 0.5, 1.0, 1.5, 1.99, 2.0, 10.0])
-    assert list(oracle.display_u8(ramp, 1.0)) == [0, 64, 128, 192, 255, 255, 255]
+    assert np.all(oracle.display_u8(const) == 128)
+    # mean 16/6, so 128 / mean = 48 exactly: codes 48 M, saturating above 255
+    ramp = np.array([0.0, 1.0, 2.0, 3.0, 4.0, 6.0])
+    assert list(oracle.display_u8(ramp)) == [0, 48, 96, 144, 192, 255]
+    # gain 64: mean -> 64, and a value at 1.5 x the mean sits exactly on 96
+    img = np.array([1.0, 1.0, 1.0, 1.0, 1.5, 0.5])
+    assert list(oracle.display_u8(img, 64.0)) == [64, 64, 64, 64, 96, 32]
+    # round half to even, as rint does: 2.5 -> 2 at gain 2.5 / 1.0
+    assert list(oracle.display_u8(np.array([1.0, 1.0]), 2.5)) == [2, 2]
