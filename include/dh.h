@@ -152,6 +152,12 @@ dh_status dh_plan_reserve(dh_plan_t plan, int max_frames, int max_windows);
  *   dh_plan_status returns DH_ERR_TIMEOUT. The holograms of that call are not written.
  *   0 (default): off. */
 #define DH_OPT_TEST_STALL 6
+/* DH_OPT_RENDER_FFT: the arithmetic of Eq. 1's DFTs. 0 (default): automatic. 1: the
+ *   CUDA-core FFT (FP32 Stockham passes). 2: for 1024 x 1024 frames, each 1024-point DFT as two
+ *   batched 32-point DFTs on the tensor cores (FP16 hi + lo operands, three products, FP32
+ *   accumulation; ~1e-7 relative, like the FP32 FFT) with the twiddles, chirps and stores on
+ *   the CUDA cores; DH_ERR_UNSUPPORTED_SIZE for other sizes. */
+#define DH_OPT_RENDER_FFT 7
 dh_status dh_plan_set_option(dh_plan_t plan, int option, int value);
 dh_status dh_plan_get_option(dh_plan_t plan, int option, int *value);
 

@@ -101,6 +101,12 @@ class Plan:
         for opt, val in ((0, 0 if persistent else 1), (1, int(ring)), (2, int(lag))):
             _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(self._h, opt, val))
 
+    def set_render_fft(self, kind: str = "auto") -> None:
+        """DH_OPT_RENDER_FFT: "auto" (0), "cuda" (1: CUDA-core FFT) or "tensor" (2: 32-point
+        DFT stages on the tensor cores, 1024 x 1024 frames)."""
+        _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(
+            self._h, 7, {"auto": 0, "cuda": 1, "tensor": 2}[kind]))
+
     def set_covariance_source(self, source) -> None:
         """DH_OPT_COVARIANCE: "holograms" (Eq. 4 as written, the default; also False), "raw"
         (exact C = I^T I from the uint16 frames where the call has them; also True) or "band"

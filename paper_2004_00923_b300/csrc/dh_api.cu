@@ -79,8 +79,11 @@ void free_store(Plan &p) {
   }
 }
 
+bool tc_render_sizes(const Plan &p) { return p.nx == 1024 && p.ny == 1024; }
+
 size_t table_bytes(const Plan &p) {
-  return sizeof(float2) * (p.nx + p.ny + twiddle_len(p.lognx) + twiddle_len(p.logny)) + 16;
+  return sizeof(float2) * (p.nx + p.ny + twiddle_len(p.lognx) + twiddle_len(p.logny)) + 16 +
+         (tc_render_sizes(p) ? tc_tables_bytes() : 0);
 }
 
 // Device bytes of every buffer a plan allocates, from its sizes, reservation and precision.
@@ -428,7 +431,13 @@ dh_status dh_plan_create(dh_plan_t *out, int nx, int ny, double lambda_m, double
       if (c == cudaSuccess) c = cudaMemcpy(p.d_twy, twy.data(), twy.size() * sizeof(float2), cudaMemcpyHostToDevice);
       if (c == cudaSuccess) c = cudaMemset(p.d_status, 0, sizeof(uint32_t));
       if (c == cudaSuccess) c = cudaMemset(p.d_sync, 0, sizeof(unsigned) * (2 + 2 * 64));
-      st = c == cudaSuccess ? alloc_store(p) : fail_cuda(c);
+      if (c == cudaSuccess && tc_render_sizes(p)) {
+        std::vector<char> tct(tc_tables_bytes());
+        build_tc_tables(tct.data());
+        st = dalloc(p, &p.d_tc, tct.size());
+        if (st == DH_OK) c = cudaMemcpy(p.d_tc, tct.data(), tct.size(), cudaMemcpyHostToDevice);
+      }
+      if (st == DH_OK) st = c == cudaSuccess ? alloc_store(p) : fail_cuda(c);
     }
   }
   if (st != DH_OK) {
@@ -460,6 +469,7 @@ void release(dh_plan_t h) {
   dfree(q.stage[0]); dfree(q.stage[1]); dfree(q.img); dfree(q.eig);
   dfree(p.d_band); dfree(p.d_band_part);
   dfree(p.d_cx); dfree(p.d_cy); dfree(p.d_twx); dfree(p.d_twy); dfree(p.d_status); dfree(p.d_sync);
+  dfree(p.d_tc);
   dh_plan *base = h->base;
   delete h;
   if (base) {
@@ -555,6 +565,7 @@ dh_status dh_plan_get_option(dh_plan_t h, int option, int *value) {
     case DH_OPT_PROJECTION: *value = h->p.proj_mode; return DH_OK;
     case DH_OPT_WINDOW_GROUPS: *value = h->p.group_mode; return DH_OK;
     case DH_OPT_TEST_STALL: *value = h->p.test_stall; return DH_OK;
+    case DH_OPT_RENDER_FFT: *value = h->p.render_fft; return DH_OK;
   }
   return DH_ERR_INVALID_ARG;
 }
@@ -653,6 +664,11 @@ dh_status dh_plan_set_option(dh_plan_t h, int option, int value) {
     case DH_OPT_TEST_STALL:
       if (value < 0 || value > 100000000) return DH_ERR_INVALID_ARG;
       h->p.test_stall = value;
+      return DH_OK;
+    case DH_OPT_RENDER_FFT:
+      if (value < 0 || value > 2) return DH_ERR_INVALID_ARG;
+      if (value == 2 && !h->p.d_tc) return DH_ERR_UNSUPPORTED_SIZE;
+      h->p.render_fft = value;
       return DH_OK;
   }
   return DH_ERR_INVALID_ARG;

@@ -32,6 +32,9 @@ struct Plan {
   // tables
   float2 *d_cx = nullptr, *d_cy = nullptr;   // chirp * 1/sqrt(n) per axis
   float2 *d_twx = nullptr, *d_twy = nullptr; // Stockham twiddles per axis
+  void *d_tc = nullptr;                      // tensor-core render tables (1024^2 frames)
+  // arithmetic of Eq. 1's DFTs: 0 = automatic, 1 = CUDA cores, 2 = tensor cores (1024^2)
+  int render_fft = 0;
   // render intermediate (row-pass output): a chunk of frames sized to stay in L2
   float2 *d_mid = nullptr;
   int mid_frames = 0;
@@ -115,7 +118,8 @@ struct Plan {
 enum KernelId {
   K_RENDER_ROWS = 0, K_RENDER_COLS, K_GRAM_SIMT, K_GRAM_TC, K_REDUCE_COV, K_JACOBI,
   K_PROJECT_SIMT, K_PROJECT_TC, K_FOURIER_OP, K_SVD_FOURIER_OP, K_RENDER_FUSED, K_GRAM_RAW,
-  K_REDUCE_RAW, K_FOURIER_SLIDING, K_BAND_GRAM, K_BAND_REDUCE, K_BAND_COV, K_PROJECT_SPAN, K_FOURIER_SPAN, K_COUNT
+  K_REDUCE_RAW, K_FOURIER_SLIDING, K_BAND_GRAM, K_BAND_REDUCE, K_BAND_COV, K_PROJECT_SPAN, K_FOURIER_SPAN,
+  K_RENDER_ROWS_TC, K_RENDER_COLS_TC, K_RENDER_FUSED_TC, K_COUNT
 };
 const char *kernel_name(int kid);
 dh_status profile_enable(Plan &p, int on);
@@ -151,6 +155,10 @@ void build_twiddles(int logn, float2 *host_out);  // host, FP64 -> FP32
 // work items per frame and pass of the render (square frames): N / FFTs per CTA
 int render_items_per_frame(const Plan &p);
 int twiddle_len(int logn);
+// tensor-core render of 1024^2 frames: whether the plan uses it, and its tables
+bool tc_render_applies(const Plan &p);
+size_t tc_tables_bytes();
+void build_tc_tables(void *host_out);
 
 // Partial Gram matrices per window (split-K over pixels), fixed per frame size.
 int gram_units(long long npix);

@@ -25,7 +25,8 @@ const char *kNames[K_COUNT] = {"render_rows", "render_cols", "gram_simt", "gram_
                                "reduce_cov", "jacobi", "project_simt", "project_tc",
                                "fourier_operand", "svd_fourier_operand", "render_fused", "gram_raw",
                                "reduce_raw", "fourier_sliding", "band_gram", "band_reduce",
-                               "band_cov", "project_span", "fourier_span"};
+                               "band_cov", "project_span", "fourier_span", "render_rows_tc",
+                               "render_cols_tc", "render_fused_tc"};
 }  // namespace
 
 const char *kernel_name(int kid) { return kid >= 0 && kid < K_COUNT ? kNames[kid] : "?"; }

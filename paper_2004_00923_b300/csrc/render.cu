@@ -501,6 +501,8 @@ __device__ __forceinline__ bool col_work(const float2 *__restrict__ src, float2 
   return true;
 }
 
+#include "render_tc.cuh"
+
 // Row pass over a chunk of frames: one item = FPC consecutive rows of one frame.
 template <int LOGN>
 __global__ void __launch_bounds__(cta_threads<LOGN>(), rows_per_sm<LOGN>())
@@ -1014,8 +1016,90 @@ void build_twiddles(int logn, float2 *out) {
   if (off == 0 && R2 == 1) out[0] = make_float2(1.f, 0.f);
 }
 
+namespace {
+template <typename OutT>
+dh_status launch_tc_chunks_t(Plan &p, const uint16_t *frames, long long fstride, int n_frames, int slot0,
+                             cudaStream_t s) {
+  auto kr = k_render_rows_tc;
+  auto kc = k_render_cols_tc<OutT>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    DH_CUDA_TRY(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, tcr::SMEM_BYTES));
+    DH_CUDA_TRY(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, tcr::SMEM_BYTES));
+    attr_set = true;
+  }
+  const uint8_t *tcg = static_cast<const uint8_t *>(p.d_tc);
+  for (int f0 = 0; f0 < n_frames; f0 += p.mid_frames) {
+    const int nf = (n_frames - f0) < p.mid_frames ? (n_frames - f0) : p.mid_frames;
+    const int items = nf * tcr::ITEMS_PER_FRAME;  // warpgroup items per pass
+    int grid = 2 * p.num_sms;
+    if (grid * tcr::WGS > items) grid = (items + tcr::WGS - 1) / tcr::WGS;
+    {
+      ProfScope ps(p, K_RENDER_ROWS_TC, s);
+      kr<<<grid, tcr::THREADS, tcr::SMEM_BYTES, s>>>(frames + (long long)f0 * fstride, fstride, tcg, p.d_cx,
+                                                     p.d_cy, p.d_mid, items, p.d_status);
+      DH_CUDA_TRY(cudaGetLastError());
+    }
+    {
+      ProfScope ps(p, K_RENDER_COLS_TC, s);
+      kc<<<grid, tcr::THREADS, tcr::SMEM_BYTES, s>>>(p.d_mid, tcg, p.d_cx, static_cast<OutT *>(p.d_H),
+                                                     2ll * p.max_frames, slot0 + f0, items, p.d_status);
+      DH_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  return DH_OK;
+}
+}  // namespace
+
+bool tc_render_applies(const Plan &p) {
+  return p.render_fft == 2 && p.nx == tcr::N && p.ny == tcr::N && p.d_tc != nullptr;
+}
+
+// Tables of the tensor-core render (1024-point axes): the real embedding [[Wr, Wi], [-Wi, Wr]]
+// of the 32-point DFT W[a][b] = exp(+2 pi i a b / 32) as FP16 hi then lo ([n][k] rows of 64),
+// then the twiddles w^(a b) / 4 (w = exp(+2 pi i / 1024)) in pairs of consecutive a per lane b,
+// [a / 2][b] (wx_a, wx_a+1, wy_a, wy_a+1), then (-wy_a, -wy_a+1). Angles are reduced exactly
+// in integers and formed in FP64.
+size_t tc_tables_bytes() { return tcr::GLOB_BYTES; }
+void build_tc_tables(void *out) {
+  const double two_pi = 6.283185307179586476925286766559;
+  char *base = static_cast<char *>(out);
+  __half *w = reinterpret_cast<__half *>(base + tcr::GLOB_W);
+  for (int n = 0; n < 64; ++n)
+    for (int k = 0; k < 64; ++k) {
+      const int a = n & 31, b = k & 31;
+      const double ang = two_pi * (double)((a * b) % 32) / 32.0;
+      const double c = cos(ang), sn = sin(ang);
+      const double v = n < 32 ? (k < 32 ? c : -sn) : (k < 32 ? sn : c);
+      const __half hi = __float2half_rn((float)v);
+      const __half lo = __float2half_rn((float)(v - (double)__half2float(hi)));
+      w[n * 64 + k] = hi;
+      w[64 * 64 + n * 64 + k] = lo;
+    }
+  auto tw = [&](int a, int b, bool sine) {
+    const double ang = two_pi * (double)((a * b) % tcr::N) / (double)tcr::N;
+    return (float)(0.25 * (sine ? sin(ang) : cos(ang)));
+  };
+  float4 *twp = reinterpret_cast<float4 *>(base + tcr::GLOB_TWP);
+  float2 *twn = reinterpret_cast<float2 *>(base + tcr::GLOB_TWN);
+  for (int pr = 0; pr < 16; ++pr)
+    for (int b = 0; b < 32; ++b) {
+      const int a = 2 * pr;
+      twp[pr * 32 + b] = make_float4(tw(a, b, false), tw(a + 1, b, false), tw(a, b, true), tw(a + 1, b, true));
+      twn[pr * 32 + b] = make_float2(-tw(a, b, true), -tw(a + 1, b, true));
+    }
+}
+
 dh_status launch_render(Plan &p, const uint16_t *frames, long long frame_stride, int n_frames,
                         int slot0, cudaStream_t s) {
+  // 1024^2 frames with the tensor-core DFT stages
+  if (tc_render_applies(p)) {
+    switch (p.prec) {
+      case DH_PREC_FP32: return launch_tc_chunks_t<float>(p, frames, frame_stride, n_frames, slot0, s);
+      case DH_PREC_FP16: return launch_tc_chunks_t<__half>(p, frames, frame_stride, n_frames, slot0, s);
+      case DH_PREC_BF16: return launch_tc_chunks_t<__nv_bfloat16>(p, frames, frame_stride, n_frames, slot0, s);
+    }
+  }
   // square frames from 256^2: every frame of the call in one persistent launch
   if (fused_ring(p, 1, 1)) {
     switch (p.prec) {
