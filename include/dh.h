@@ -158,17 +158,49 @@ dh_status dh_plan_reserve(dh_plan_t plan, int max_frames, int max_windows);
  *   accumulation; ~1e-7 relative, like the FP32 FFT) with the twiddles, chirps and stores on
  *   the CUDA cores; DH_ERR_UNSUPPORTED_SIZE for other sizes. */
 #define DH_OPT_RENDER_FFT 7
+/* DH_OPT_FFT_RADIX: the radix of the CUDA-core FFT passes of Eq. 1. 0 (default): each
+ *   length's own (32 at 32, 512, 1024 and 2048; 8 at 64; 16 otherwise); 16 or 32: that radix
+ *   on every axis whose length has it instantiated (16 at 512, 1024, 2048; 32 at 4096; each
+ *   length's default), the other axes keep their default; DH_ERR_UNSUPPORTED_SIZE if no axis
+ *   has it. Results differ from the default only in rounding. Synchronous. Views: DH_ERR_STATE.
+ * DH_OPT_GRAM_UNITS: split-K units per window of the tensor-core covariance of Eq. 4 (16-bit
+ *   storage; DH_ERR_STATE for FP32 plans): 0 (default) = the frame size's own, else a power of
+ *   two dividing n_x n_y / 256 (DH_ERR_UNSUPPORTED_SIZE otherwise). A window's covariance stays
+ *   bitwise the same alone and in any batch for a given setting; settings differ only in the
+ *   order of the FP64 partial sums. Reallocates the per-window buffers (synchronous). */
+#define DH_OPT_FFT_RADIX 8
+#define DH_OPT_GRAM_UNITS 9
 dh_status dh_plan_set_option(dh_plan_t plan, int option, int value);
 dh_status dh_plan_get_option(dh_plan_t plan, int option, int *value);
 
-/* Autotuner: render n_frames (capped at the plan's slots) zero frames with every candidate
- * schedule (chunks; the persistent ring at the automatic lag, half and twice it, and the
- * automatic ring with one frame more lag) and keep
- * the fastest in the plan's options (all candidates give bitwise the same holograms; the
- * render time does not depend on the frame values). Discards rendered holograms; allocates
- * and frees a temporary frame buffer; synchronises `stream`. Call it once after
- * dh_plan_reserve, before any graph capture. */
+/* Autotuner: times every candidate on zero frames (render and covariance time do not depend
+ * on the values; best of three after a warm-up) and keeps the fastest in the plan's options:
+ *   1. the DFT arithmetic of Eq. 1 (DH_OPT_RENDER_FFT 1 at the default and at the alternative
+ *      DH_OPT_FFT_RADIX, and 2 for 1024 x 1024 frames), each with the default schedule;
+ *   2. for the CUDA-core FFT, the schedule (DH_OPT_RENDER_SCHEDULE, _RING, _LAG): chunks; the
+ *      persistent ring at the automatic lag, half and twice it; the automatic ring with one
+ *      frame more lag;
+ *   3. 16-bit storage: the covariance's split-K units (DH_OPT_GRAM_UNITS: the default, half and
+ *      twice it), on up to 32 windows of the store.
+ * Schedules give bitwise the same holograms; radix, DFT arithmetic and split-K units change
+ * only the rounding. Renders n_frames (capped at the plan's slots) frames; discards rendered
+ * holograms; allocates and frees a temporary frame buffer; synchronises `stream` and the
+ * device. Call it after dh_plan_reserve, before any graph capture. */
 dh_status dh_plan_autotune(dh_plan_t plan, int n_frames, void *stream);
+
+/* The autotuner's persistent cache: a JSON file {"version": 1, "entries": {key: {option: value,
+ * ...}}} whose key is the plan's frame size, T, precision, device name and SM count, and whose
+ * values are the options the autotuner sets (render_schedule, render_ring, render_lag,
+ * render_fft, fft_radix, gram_units).
+ * dh_plan_tune_load: applies the plan's entry if the file has one (*found = 1), else changes
+ *   nothing (*found = 0; also when the file does not exist). DH_ERR_INVALID_ARG for a file that
+ *   is not such JSON, or an entry with a value the options reject (nothing applied).
+ * dh_plan_tune_save: writes the plan's current options as its entry, keeping every other
+ *   entry (written to path.tmp, then renamed over path). DH_ERR_INVALID_ARG if an existing
+ *   file cannot be parsed (it is left as it is) or written.
+ * Host-side file I/O only; the options they set behave as dh_plan_set_option. */
+dh_status dh_plan_tune_load(dh_plan_t plan, const char *path, int *found);
+dh_status dh_plan_tune_save(dh_plan_t plan, const char *path);
 
 /* Bytes of device memory the plan holds now (all buffers). */
 size_t dh_plan_device_bytes(dh_plan_t plan);

@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import contextlib
 import ctypes
+import os
 
 import torch
 
@@ -132,19 +133,49 @@ class Plan:
                                                            _stream_ptr(stream)))
 
     def render_schedule(self) -> dict:
-        """The plan's render options: persistent (bool), ring and lag (0 = automatic)."""
+        """The plan's render and covariance options: persistent (bool), ring and lag (0 =
+        automatic), fft ("auto" / "cuda" / "tensor"), radix (0 = each length's default) and
+        gram_units (0 = the frame size's default)."""
         v = ctypes.c_int(0)
         out = {}
-        for opt, key in ((0, "persistent"), (1, "ring"), (2, "lag")):
+        for opt, key in ((0, "persistent"), (1, "ring"), (2, "lag"), (7, "fft"), (8, "radix"),
+                         (9, "gram_units")):
             _lib.check("dh_plan_get_option", self._lib.dh_plan_get_option(self._h, opt, ctypes.byref(v)))
-            out[key] = (v.value == 0) if opt == 0 else v.value
+            if opt == 0:
+                out[key] = v.value == 0
+            elif opt == 7:
+                out[key] = {0: "auto", 1: "cuda", 2: "tensor"}[v.value]
+            else:
+                out[key] = v.value
         return out
 
-    def autotune(self, n_frames: int = 256, stream=None) -> dict:
-        """dh_plan_autotune: time the render schedules on zero frames and keep the fastest."""
-        _lib.check("dh_plan_autotune", self._lib.dh_plan_autotune(self._h, int(n_frames),
-                                                                   _stream_ptr(stream)))
-        return self.render_schedule()
+    def set_fft_radix(self, radix: int = 0) -> None:
+        """DH_OPT_FFT_RADIX: 0 (each length's default), 16 or 32 where instantiated."""
+        _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(self._h, 8, int(radix)))
+
+    def set_gram_units(self, units: int = 0) -> None:
+        """DH_OPT_GRAM_UNITS: split-K units per window of the tensor-core covariance (0 =
+        the frame size's default)."""
+        _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(self._h, 9, int(units)))
+
+    def autotune(self, n_frames: int = 256, stream=None, cache: str | None = None) -> dict:
+        """dh_plan_autotune: time the candidate DFT arithmetic, radix, render schedule and
+        covariance split-K units on zero frames and keep the fastest. With `cache`, the plan's
+        entry in that JSON file is applied instead when present (dh_plan_tune_load), and the
+        picks are saved there after a measurement (dh_plan_tune_save). The returned options
+        carry "from_cache"."""
+        found = ctypes.c_int(0)
+        if cache is not None:
+            _lib.check("dh_plan_tune_load", self._lib.dh_plan_tune_load(
+                self._h, os.fsencode(cache), ctypes.byref(found)))
+        if not found.value:
+            _lib.check("dh_plan_autotune", self._lib.dh_plan_autotune(self._h, int(n_frames),
+                                                                       _stream_ptr(stream)))
+            if cache is not None:
+                _lib.check("dh_plan_tune_save", self._lib.dh_plan_tune_save(self._h, os.fsencode(cache)))
+        out = self.render_schedule()
+        out["from_cache"] = bool(found.value)
+        return out
 
     @property
     def device_bytes(self) -> int:

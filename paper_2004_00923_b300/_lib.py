@@ -48,6 +48,8 @@ SIGNATURES = [
     ("dh_plan_set_option", _i, [_vp, _i, _i]),
     ("dh_plan_get_option", _i, [_vp, _i, ctypes.POINTER(_i)]),
     ("dh_plan_autotune", _i, [_vp, _i, _vp]),
+    ("dh_plan_tune_load", _i, [_vp, ctypes.c_char_p, ctypes.POINTER(_i)]),
+    ("dh_plan_tune_save", _i, [_vp, ctypes.c_char_p]),
     ("dh_plan_device_bytes", ctypes.c_size_t, [_vp]),
     ("dh_plan_footprint", ctypes.c_size_t, [_i, _i, _i, _i, _i, _i]),
     ("dh_render_frames", _i, [_vp, _vp, _i64, _i, _i, _vp]),

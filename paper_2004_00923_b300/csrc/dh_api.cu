@@ -11,6 +11,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 struct dh_plan {
@@ -167,6 +168,46 @@ dh_status alloc_store(Plan &p, const Plan *base = nullptr) {
     p.mid_frames = z.mid_frames;
     if ((st = dalloc(p, &p.d_mid, z.mid)) != DH_OK) return st;
   }
+  return alloc_windows(p);
+}
+
+// The CUDA-core FFT radix of the plan (0 = each length's default, 16 or 32 where that radix is
+// instantiated for an axis length): the inter-pass twiddle tables follow it. Synchronous.
+dh_status set_fft_radix(Plan &p, int radix) {
+  if (radix != 0 && radix != 16 && radix != 32) return DH_ERR_INVALID_ARG;
+  if (p.is_view) return DH_ERR_STATE;
+  if (!fft_radix_available(p.lognx, radix) && !fft_radix_available(p.logny, radix))
+    return DH_ERR_UNSUPPORTED_SIZE;
+  const int old_rx = row_spec(p), old_cy = col_spec(p);
+  const int keep = p.fft_radix;
+  p.fft_radix = radix;
+  const int rx = row_spec(p), cy = col_spec(p);
+  if (rx == old_rx && cy == old_cy) return DH_OK;
+  std::vector<float2> twx(twiddle_len(rx)), twy(twiddle_len(cy));
+  build_twiddles(rx, twx.data());
+  build_twiddles(cy, twy.data());
+  cudaError_t e = cudaDeviceSynchronize();  // no render in flight reads the old tables
+  if (e != cudaSuccess) { p.fft_radix = keep; return fail_cuda(e); }
+  dfree(p.d_twx); dfree(p.d_twy);
+  p.bytes -= sizeof(float2) * (twiddle_len(old_rx) + twiddle_len(old_cy));
+  dh_status st = dalloc(p, &p.d_twx, twx.size() * sizeof(float2));
+  if (st == DH_OK) st = dalloc(p, &p.d_twy, twy.size() * sizeof(float2));
+  if (st != DH_OK) return st;
+  e = cudaMemcpy(p.d_twx, twx.data(), twx.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p.d_twy, twy.data(), twy.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? DH_OK : fail_cuda(e);
+}
+
+// Split-K units per window of the tensor-core covariance (0 = the default for the frame size):
+// a power of two dividing n / 256, so that every window length's pixel chunks tile a unit.
+// The per-window partial buffers are reallocated (synchronous).
+dh_status set_gram_units(Plan &p, int units) {
+  if (units < 0 || units > 1024 || (units & (units - 1)) != 0) return DH_ERR_INVALID_ARG;
+  if (p.prec == DH_PREC_FP32) return DH_ERR_STATE;  // the tensor-core covariance only
+  if (units > 0 && p.npix % (256ll * units) != 0) return DH_ERR_UNSUPPORTED_SIZE;
+  if (units == p.gram_units) return DH_OK;
+  DH_CUDA_TRY(cudaDeviceSynchronize());
+  p.gram_units = units;
   return alloc_windows(p);
 }
 
@@ -344,6 +385,8 @@ Executor &executor(int device) {
 }
 
 }  // namespace
+
+Plan &plan_of(dh_plan *h) { return h->p; }
 
 // Entry points of the serving runtime (server.cu) into one plan, under the plan's guard.
 dh_status plan_pca(dh_plan *h, int first_slot, int slot_stride, int n_windows, int k0, int k1,
@@ -566,14 +609,24 @@ dh_status dh_plan_get_option(dh_plan_t h, int option, int *value) {
     case DH_OPT_WINDOW_GROUPS: *value = h->p.group_mode; return DH_OK;
     case DH_OPT_TEST_STALL: *value = h->p.test_stall; return DH_OK;
     case DH_OPT_RENDER_FFT: *value = h->p.render_fft; return DH_OK;
+    case DH_OPT_FFT_RADIX: *value = h->p.fft_radix; return DH_OK;
+    case DH_OPT_GRAM_UNITS: *value = h->p.gram_units; return DH_OK;
   }
   return DH_ERR_INVALID_ARG;
 }
 
-// Time every candidate render schedule on n_frames zero frames (render time does not depend
-// on the values: no data-dependent control flow) and keep the fastest. Candidates: chunks,
-// and the persistent ring with the automatic lag, half of it and twice it (ring twice the
-// lag), and the automatic ring with one frame more lag.
+// The autotuner. Render time does not depend on the pixel values (no data-dependent control
+// flow), nor does the covariance's, so every candidate is timed on zero frames (best of
+// three after a warm-up) and the fastest kept:
+//   1. the DFT arithmetic of Eq. 1: the CUDA-core FFT at each length's default radix, at the
+//      alternative radix where one is instantiated, and the tensor-core DFT stages (1024^2);
+//   2. for the CUDA-core FFT, the schedule: chunks, and the persistent ring at the automatic
+//      lag, half of it and twice it (ring twice the lag), and the automatic ring with one
+//      frame more lag;
+//   3. for 16-bit storage, the covariance's split-K units: the default for the frame size,
+//      half and twice it (timed on up to 32 windows of the store).
+// Schedules give bitwise the same holograms; the radix, the DFT arithmetic and the split-K
+// units change only the rounding.
 dh_status dh_plan_autotune(dh_plan_t h, int n_frames, void *stream) {
   if (!h || n_frames < 1) return DH_ERR_INVALID_ARG;
   Plan &p = h->p;
@@ -584,9 +637,58 @@ dh_status dh_plan_autotune(dh_plan_t h, int n_frames, void *stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   uint16_t *zeros = nullptr;
   DH_CUDA_TRY(cudaMalloc(&zeros, (size_t)n_frames * p.npix * sizeof(uint16_t)));
+  const int saved[6] = {p.render_mode, p.render_ring, p.render_lag, p.render_fft, p.fft_radix, p.gram_units};
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = cudaMemsetAsync(zeros, 0, (size_t)n_frames * p.npix * sizeof(uint16_t), s);
+  dh_status st = e == cudaSuccess ? DH_OK : fail_cuda(e);
+  // best of three timed runs of f() after a warm-up, in ms (1e30 on failure)
+  auto time_of = [&](auto f) -> float {
+    if (st != DH_OK || (st = f()) != DH_OK) return 1e30f;
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 3 && st == DH_OK; ++rep) {
+      e = cudaEventRecord(a, s);
+      if (e == cudaSuccess) st = f();
+      if (st == DH_OK && e == cudaSuccess) e = cudaEventRecord(b, s);
+      if (st == DH_OK && e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (st == DH_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      if (e != cudaSuccess && st == DH_OK) st = fail_cuda(e);
+      if (st == DH_OK && ms < tmin) tmin = ms;
+    }
+    return st == DH_OK ? tmin : 1e30f;
+  };
+  auto render = [&]() { return launch_render(p, zeros, p.npix, n_frames, 0, s); };
+
+  // 1. DFT arithmetic, each with the default schedule
+  struct Fft { int fft, radix; };
+  std::vector<Fft> ffts = {{1, 0}};
+  for (int rx : {16, 32}) {
+    const bool alt = (fft_spec_for(p.lognx, rx) != p.lognx) || (fft_spec_for(p.logny, rx) != p.logny);
+    if (alt) ffts.push_back({1, rx});
+  }
+  if (p.d_tc) ffts.push_back({2, 0});
+  p.render_mode = 0; p.render_ring = 0; p.render_lag = 0;
+  float best = 1e30f;
+  Fft fpick = {1, 0};
+  for (const Fft &f : ffts) {
+    if (st != DH_OK) break;
+    p.render_fft = f.fft;
+    if ((st = set_fft_radix(p, f.radix)) != DH_OK) break;
+    const float ms = time_of(render);
+    if (ms < best) { best = ms; fpick = f; }
+  }
+  if (st == DH_OK) {
+    p.render_fft = fpick.fft;
+    st = set_fft_radix(p, fpick.radix);
+  }
+
+  // 2. schedules of the CUDA-core FFT
   struct Cand { int mode, ring, lag; };
-  std::vector<Cand> cands = {{1, 0, 0}};
-  {
+  Cand pick = {0, 0, 0};
+  if (st == DH_OK && p.render_fft != 2) {
+    std::vector<Cand> cands = {{1, 0, 0}};
     // automatic lag of this plan (grid of 2 CTAs per SM, the persistent kernel's residency)
     const int items = render_items_per_frame(p);
     const long long grid = 2ll * p.num_sms;
@@ -596,34 +698,35 @@ dh_status dh_plan_autotune(dh_plan_t h, int n_frames, void *stream) {
     // one frame more lag in the same ring (a larger ring spills the intermediate from L2)
     if (lag >= 2 && 2 * lag <= 64 && 2 * lag <= p.mid_frames) cands.push_back({0, 2 * lag, lag + 1});
     if (p.mid_frames >= 3 && lag == 1) cands.push_back({0, 3, 1});
-  }
-  const int saved[3] = {p.render_mode, p.render_ring, p.render_lag};
-  cudaEvent_t a = nullptr, b = nullptr;
-  cudaError_t e = cudaEventCreate(&a);
-  if (e == cudaSuccess) e = cudaEventCreate(&b);
-  if (e == cudaSuccess) e = cudaMemsetAsync(zeros, 0, (size_t)n_frames * p.npix * sizeof(uint16_t), s);
-  float best = 1e30f;
-  Cand pick = {saved[0], saved[1], saved[2]};
-  dh_status st = e == cudaSuccess ? DH_OK : fail_cuda(e);
-  for (const Cand &c : cands) {
-    if (st != DH_OK) break;
-    p.render_mode = c.mode; p.render_ring = c.ring; p.render_lag = c.lag;
-    if ((st = launch_render(p, zeros, p.npix, n_frames, 0, s)) != DH_OK) break;  // warm-up
-    float tmin = 1e30f;
-    for (int rep = 0; rep < 3 && st == DH_OK; ++rep) {
-      e = cudaEventRecord(a, s);
-      if (e == cudaSuccess) st = launch_render(p, zeros, p.npix, n_frames, 0, s);
-      if (st == DH_OK && e == cudaSuccess) e = cudaEventRecord(b, s);
-      if (st == DH_OK && e == cudaSuccess) e = cudaEventSynchronize(b);
-      float ms = 0.f;
-      if (st == DH_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-      if (e != cudaSuccess && st == DH_OK) st = fail_cuda(e);
-      if (ms < tmin) tmin = ms;
+    best = 1e30f;
+    for (const Cand &c : cands) {
+      p.render_mode = c.mode; p.render_ring = c.ring; p.render_lag = c.lag;
+      const float ms = time_of(render);
+      if (ms < best) { best = ms; pick = c; }
     }
-    if (st == DH_OK && tmin < best) { best = tmin; pick = c; }
   }
   p.render_mode = pick.mode; p.render_ring = pick.ring; p.render_lag = pick.lag;
-  if (st != DH_OK) { p.render_mode = saved[0]; p.render_ring = saved[1]; p.render_lag = saved[2]; }
+
+  // 3. split-K units of the tensor-core covariance (16-bit storage)
+  const int n_win = std::min(std::min(p.max_windows, p.max_frames / p.T), 32);
+  if (st == DH_OK && p.prec != DH_PREC_FP32 && n_win >= 1) {
+    const int u0 = gram_tc_default_units(p.npix);
+    int upick = 0;
+    best = 1e30f;
+    for (int u : {u0, u0 / 2, 2 * u0}) {
+      if (u < 1 || p.npix % (256ll * u) != 0) continue;
+      if ((st = set_gram_units(p, u == u0 ? 0 : u)) != DH_OK) break;
+      int parts = 0;
+      const float ms = time_of([&]() { return launch_gram_tc(p, 0, p.T, n_win, &parts, s); });
+      if (ms < best) { best = ms; upick = u == u0 ? 0 : u; }
+    }
+    if (st == DH_OK) st = set_gram_units(p, upick);
+  }
+  if (st != DH_OK) {
+    p.render_mode = saved[0]; p.render_ring = saved[1]; p.render_lag = saved[2]; p.render_fft = saved[3];
+    set_fft_radix(p, saved[4]);
+    set_gram_units(p, saved[5]);
+  }
   cudaStreamSynchronize(s);
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
@@ -670,6 +773,10 @@ dh_status dh_plan_set_option(dh_plan_t h, int option, int value) {
       if (value == 2 && !h->p.d_tc) return DH_ERR_UNSUPPORTED_SIZE;
       h->p.render_fft = value;
       return DH_OK;
+    case DH_OPT_FFT_RADIX:
+      return set_fft_radix(h->p, value);
+    case DH_OPT_GRAM_UNITS:
+      return set_gram_units(h->p, value);
   }
   return DH_ERR_INVALID_ARG;
 }

@@ -35,6 +35,12 @@ struct Plan {
   void *d_tc = nullptr;                      // tensor-core render tables (1024^2 frames)
   // arithmetic of Eq. 1's DFTs: 0 = automatic, 1 = CUDA cores, 2 = tensor cores (1024^2)
   int render_fft = 0;
+  // radix of the CUDA-core FFT passes: 0 = each length's default, else 16 or 32 where that
+  // radix is instantiated for an axis length (the other axes keep their default)
+  int fft_radix = 0;
+  // split-K units per window of the tensor-core covariance: 0 = the default for the frame
+  // size, else a power of two dividing n / 256 (DH_OPT_GRAM_UNITS, the autotuner)
+  int gram_units = 0;
   // render intermediate (row-pass output): a chunk of frames sized to stay in L2
   float2 *d_mid = nullptr;
   int mid_frames = 0;
@@ -151,10 +157,17 @@ dh_status fail_cuda(cudaError_t e);
 // Eq. 1: render n_frames frames into hologram slots [slot0, slot0 + n_frames).
 dh_status launch_render(Plan &p, const uint16_t *frames, long long frame_stride, int n_frames,
                         int slot0, cudaStream_t s);
-void build_twiddles(int logn, float2 *host_out);  // host, FP64 -> FP32
+// FFT specs of the render: log2 length in the low 4 bits, log2 radix above (0 = default);
+// the plan's radix choice (0 = default, or 16 / 32 where that radix is instantiated for the
+// length) per axis, and whether a radix is available for a length
+int fft_spec_for(int logn, int radix);
+int row_spec(const Plan &p);
+int col_spec(const Plan &p);
+bool fft_radix_available(int logn, int radix);
+void build_twiddles(int spec, float2 *host_out);  // host, FP64 -> FP32
 // work items per frame and pass of the render (square frames): N / FFTs per CTA
 int render_items_per_frame(const Plan &p);
-int twiddle_len(int logn);
+int twiddle_len(int spec);
 // tensor-core render of 1024^2 frames: whether the plan uses it, and its tables
 bool tc_render_applies(const Plan &p);
 size_t tc_tables_bytes();
@@ -163,6 +176,7 @@ void build_tc_tables(void *host_out);
 // Partial Gram matrices per window (split-K over pixels), fixed per frame size.
 int gram_units(long long npix);
 int gram_tc_parts(const Plan &p);
+int gram_tc_default_units(long long npix);
 int gram_raw_parts(const Plan &p);
 // partial Gram matrices a window may need (hologram or raw-domain covariance)
 inline int parts_per_window(const Plan &p) {

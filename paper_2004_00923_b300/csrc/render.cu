@@ -78,16 +78,27 @@ __host__ __device__ constexpr int bitrev(int k, int bits) {
   return r;
 }
 
+// An FFT spec, the template argument of every length-dependent piece below: log2 of the
+// length in the low 4 bits, log2 of the radix above them (0: the length's default radix,
+// log_radix). The plan picks the radix per axis (dh_plan_set_option DH_OPT_FFT_RADIX, or the
+// autotuner) among the default and the one alternative instantiated per length: radix 16 at
+// 512, 1024 and 2048, radix 32 at 4096.
+__host__ __device__ constexpr int sp_logn(int sp) { return sp & 15; }
+__host__ __device__ constexpr int sp_logr(int sp) { return (sp >> 4) != 0 ? (sp >> 4) : log_radix(sp & 15); }
+__host__ __device__ constexpr int alt_logr(int logn) {
+  return logn >= 9 && logn <= 11 ? 4 : logn == 12 ? 5 : 0;
+}
+
 // Factorisation of one FFT length: L passes of radix R, then (if R2 > 1) one pass of
 // radix R2 in which each thread runs B = R / R2 butterflies. P threads per transform.
 template <int LOGN>
 struct Shape {
-  static constexpr int N = 1 << LOGN;
-  static constexpr int LOGR = log_radix(LOGN);
+  static constexpr int N = 1 << sp_logn(LOGN);
+  static constexpr int LOGR = sp_logr(LOGN);
   static constexpr int R = 1 << LOGR;
   static constexpr int P = N / R;
-  static constexpr int L = LOGN / LOGR;
-  static constexpr int LOGR2 = LOGN - L * LOGR;
+  static constexpr int L = sp_logn(LOGN) / LOGR;
+  static constexpr int LOGR2 = sp_logn(LOGN) - L * LOGR;
   static constexpr int R2 = 1 << LOGR2;
   static constexpr int B = R / R2;
   static constexpr int NPASS = L + (R2 > 1 ? 1 : 0);
@@ -252,7 +263,7 @@ __host__ __device__ constexpr int rows_per_sm() {
 template <int LOGN>
 __host__ __device__ constexpr int cols_per_sm() {
   return warp_threads<LOGN>() <= 256
-             ? (Shape<LOGN>::R >= 32 ? (LOGN >= 11 ? 512 : 768) : 1024) / warp_threads<LOGN>() : 1;
+             ? (Shape<LOGN>::R >= 32 ? (sp_logn(LOGN) >= 11 ? 512 : 768) : 1024) / warp_threads<LOGN>() : 1;
 }
 
 template <typename T> __device__ __forceinline__ T to_store(float x);
@@ -793,13 +804,18 @@ __global__ void k_hologram_to_f32(const T *__restrict__ H, int nx, int ny, long 
 }
 
 // ----------------------------------------------------------------- host side
+// Every FFT spec with instances: the default radix of each length, and the alternatives.
+#define DH_FFT_SPECS(X)                                                                   \
+  X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(9 | (4 << 4)) X(10 | (4 << 4)) X(11 | (4 << 4)) \
+  X(12 | (5 << 4))
+
 // log2 of the column-tile width of the intermediate (the column pass's FFTs per CTA)
-int col_tile_log(int logny) {
+int col_tile_log(int spec) {
   int f = 0;
-  switch (logny) {
-    case 4: f = fpc<4>(); break; case 5: f = fpc<5>(); break; case 6: f = fpc<6>(); break;
-    case 7: f = fpc<7>(); break; case 8: f = fpc<8>(); break; case 9: f = fpc<9>(); break;
-    case 10: f = fpc<10>(); break; case 11: f = fpc<11>(); break; case 12: f = fpc<12>(); break;
+  switch (spec) {
+#define DH_CASE(S) case S: f = fpc<S>(); break;
+    DH_FFT_SPECS(DH_CASE)
+#undef DH_CASE
   }
   int l = 0;
   while ((1 << l) < f) ++l;
@@ -809,7 +825,7 @@ int col_tile_log(int logny) {
 template <int LOGN>
 dh_status launch_rows_t(const uint16_t *frames, long long fstride, int ny, const Plan &p,
                         float2 *mid, int nf, cudaStream_t s) {
-  const int cw_log = col_tile_log(p.logny);
+  const int cw_log = col_tile_log(col_spec(p));
   using S = Shape<LOGN>;
   constexpr int FPC = fpc<LOGN>();
   const int threads = FPC * S::P;
@@ -863,32 +879,20 @@ dh_status launch_cols_t(const Plan &p, const float2 *mid, int nf, int slot0, cud
 
 dh_status launch_rows(const Plan &p, const uint16_t *frames, long long fstride, float2 *mid,
                       int nf, cudaStream_t s) {
-  switch (p.lognx) {
-    case 4: return launch_rows_t<4>(frames, fstride, p.ny, p, mid, nf, s);
-    case 5: return launch_rows_t<5>(frames, fstride, p.ny, p, mid, nf, s);
-    case 6: return launch_rows_t<6>(frames, fstride, p.ny, p, mid, nf, s);
-    case 7: return launch_rows_t<7>(frames, fstride, p.ny, p, mid, nf, s);
-    case 8: return launch_rows_t<8>(frames, fstride, p.ny, p, mid, nf, s);
-    case 9: return launch_rows_t<9>(frames, fstride, p.ny, p, mid, nf, s);
-    case 10: return launch_rows_t<10>(frames, fstride, p.ny, p, mid, nf, s);
-    case 11: return launch_rows_t<11>(frames, fstride, p.ny, p, mid, nf, s);
-    case 12: return launch_rows_t<12>(frames, fstride, p.ny, p, mid, nf, s);
+  switch (row_spec(p)) {
+#define DH_CASE(S) case S: return launch_rows_t<S>(frames, fstride, p.ny, p, mid, nf, s);
+    DH_FFT_SPECS(DH_CASE)
+#undef DH_CASE
   }
   return DH_ERR_UNSUPPORTED_SIZE;
 }
 
 template <typename OutT>
 dh_status launch_cols_typed(const Plan &p, const float2 *mid, int nf, int slot0, cudaStream_t s) {
-  switch (p.logny) {
-    case 4: return launch_cols_t<4, OutT>(p, mid, nf, slot0, s);
-    case 5: return launch_cols_t<5, OutT>(p, mid, nf, slot0, s);
-    case 6: return launch_cols_t<6, OutT>(p, mid, nf, slot0, s);
-    case 7: return launch_cols_t<7, OutT>(p, mid, nf, slot0, s);
-    case 8: return launch_cols_t<8, OutT>(p, mid, nf, slot0, s);
-    case 9: return launch_cols_t<9, OutT>(p, mid, nf, slot0, s);
-    case 10: return launch_cols_t<10, OutT>(p, mid, nf, slot0, s);
-    case 11: return launch_cols_t<11, OutT>(p, mid, nf, slot0, s);
-    case 12: return launch_cols_t<12, OutT>(p, mid, nf, slot0, s);
+  switch (col_spec(p)) {
+#define DH_CASE(S) case S: return launch_cols_t<S, OutT>(p, mid, nf, slot0, s);
+    DH_FFT_SPECS(DH_CASE)
+#undef DH_CASE
   }
   return DH_ERR_UNSUPPORTED_SIZE;
 }
@@ -902,7 +906,7 @@ int cta_threads_of(int logn);
 // 64 slots of the counters. The plan's choices override both. ring 0: not applicable.
 int fused_ring(const Plan &p, int grid, int items_per_frame) {
   if (p.render_mode != 0 || p.nx != p.ny || p.lognx < 8 || p.lognx > 12) return 0;
-  if (cta_threads_of(p.lognx) != kCtaThreads) return 0;
+  if (cta_threads_of(row_spec(p)) != kCtaThreads) return 0;
   // untuned plans use it where it measured faster than chunks (512^2, 1024^2); an explicit
   // ring or lag (the autotuner's pick) applies it at any square size from 256^2
   if (p.render_ring == 0 && p.render_lag == 0 && (p.lognx < 9 || p.lognx > 10)) return 0;
@@ -948,7 +952,7 @@ dh_status launch_fused_t(Plan &p, const uint16_t *frames, long long fstride, int
   const int lag = fused_lag(p, ring);
   DH_CUDA_TRY(cudaMemsetAsync(p.d_sync, 0, sizeof(unsigned) * (1 + 2 * ring), s));
   ProfScope ps(p, K_RENDER_FUSED, s);
-  kern<<<grid, kCtaThreads, smem, s>>>(frames, fstride, nf, col_tile_log(p.logny), p.d_cx, p.d_cy, p.d_twx, tw_len,
+  kern<<<grid, kCtaThreads, smem, s>>>(frames, fstride, nf, col_tile_log(LOGN), p.d_cx, p.d_cy, p.d_twx, tw_len,
                                       p.d_mid,
                                ring, lag, static_cast<OutT *>(p.d_H), 2ll * p.max_frames, slot0, p.d_sync,
                                p.d_status, p.test_stall);
@@ -957,10 +961,11 @@ dh_status launch_fused_t(Plan &p, const uint16_t *frames, long long fstride, int
   }
 }
 
-int cta_threads_of(int logn) {
-  switch (logn) {
-    case 8: return cta_threads<8>(); case 9: return cta_threads<9>(); case 10: return cta_threads<10>();
-    case 11: return cta_threads<11>(); case 12: return cta_threads<12>();
+int cta_threads_of(int spec) {
+  switch (spec) {
+#define DH_CASE(S) case S: return cta_threads<S>();
+    DH_FFT_SPECS(DH_CASE)
+#undef DH_CASE
   }
   return 0;
 }
@@ -968,22 +973,39 @@ int cta_threads_of(int logn) {
 template <typename OutT>
 dh_status launch_fused_typed(Plan &p, const uint16_t *frames, long long fstride, int nf, int slot0,
                              cudaStream_t s) {
-  switch (p.lognx) {
+  switch (row_spec(p)) {  // square frames: the same spec on both axes
     case 8: return launch_fused_t<8, OutT>(p, frames, fstride, nf, slot0, s);
     case 9: return launch_fused_t<9, OutT>(p, frames, fstride, nf, slot0, s);
     case 10: return launch_fused_t<10, OutT>(p, frames, fstride, nf, slot0, s);
     case 11: return launch_fused_t<11, OutT>(p, frames, fstride, nf, slot0, s);
     case 12: return launch_fused_t<12, OutT>(p, frames, fstride, nf, slot0, s);
+    case 9 | (4 << 4): return launch_fused_t<9 | (4 << 4), OutT>(p, frames, fstride, nf, slot0, s);
+    case 10 | (4 << 4): return launch_fused_t<10 | (4 << 4), OutT>(p, frames, fstride, nf, slot0, s);
+    case 11 | (4 << 4): return launch_fused_t<11 | (4 << 4), OutT>(p, frames, fstride, nf, slot0, s);
+    case 12 | (5 << 4): return launch_fused_t<12 | (5 << 4), OutT>(p, frames, fstride, nf, slot0, s);
   }
   return DH_ERR_UNSUPPORTED_SIZE;
 }
 
 }  // namespace
 
-int render_items_per_frame(const Plan &p) { return p.nx >> col_tile_log(p.lognx); }
+int render_items_per_frame(const Plan &p) { return p.nx >> col_tile_log(row_spec(p)); }
 
-int twiddle_len(int logn) {
-  const int logr = log_radix(logn), R = 1 << logr, L = logn / logr;
+int fft_spec_for(int logn, int radix) {
+  if (radix == 0) return logn;
+  int lr = 0;
+  while ((1 << lr) < radix) ++lr;
+  if (lr == log_radix(logn)) return logn;
+  return lr == alt_logr(logn) ? (logn | (lr << 4)) : logn;
+}
+int row_spec(const Plan &p) { return fft_spec_for(p.lognx, p.fft_radix); }
+int col_spec(const Plan &p) { return fft_spec_for(p.logny, p.fft_radix); }
+bool fft_radix_available(int logn, int radix) {
+  return radix == 0 || fft_spec_for(logn, radix) != logn || (1 << log_radix(logn)) == radix;
+}
+
+int twiddle_len(int spec) {
+  const int logn = sp_logn(spec), logr = sp_logr(spec), R = 1 << logr, L = logn / logr;
   const int logr2 = logn - L * logr, R2 = 1 << logr2;
   int len = 0;
   for (int p = 1; p < L; ++p) len += (R - 1) * (1 << (p * logr));
@@ -993,8 +1015,8 @@ int twiddle_len(int logn) {
 
 // Inter-pass twiddles w_M^e = exp(+2 pi i e / M), the exponent reduced exactly in integers
 // before the angle is formed in FP64.
-void build_twiddles(int logn, float2 *out) {
-  const int logr = log_radix(logn), R = 1 << logr, L = logn / logr;
+void build_twiddles(int spec, float2 *out) {
+  const int logn = sp_logn(spec), logr = sp_logr(spec), R = 1 << logr, L = logn / logr;
   const int logr2 = logn - L * logr, R2 = 1 << logr2, N = 1 << logn;
   const double two_pi = 6.283185307179586476925286766559;
   auto w = [&](long long e, long long M) {

@@ -42,6 +42,8 @@ int gram_tc_units(long long npix) {
   if (u > 64) u = 64;
   return (int)u;
 }
+// The plan's split-K units: its choice (DH_OPT_GRAM_UNITS, the autotuner), else the default.
+int gram_tc_units_of(const Plan &p) { return p.gram_units > 0 ? p.gram_units : gram_tc_units(p.npix); }
 
 // ======================================================================= covariance
 template <int T>
@@ -707,7 +709,7 @@ dh_status gram_t(Plan &p, int first_slot, int slot_stride, int n_windows, cudaSt
                                      cudaSharedmemCarveoutMaxShared));
     attr = true;
   }
-  const int units_pw = gram_tc_units(p.npix);
+  const int units_pw = gram_tc_units_of(p);
   const int stages_per_unit = (int)(p.npix / units_pw / C::PIX);
   const int total = n_windows * units_pw;
   int per_sm = 0;
@@ -821,7 +823,8 @@ dh_status encode_3d(CUtensorMap *map, void *base, bool bf16, const uint64_t dims
   return r == CUDA_SUCCESS ? DH_OK : DH_ERR_CUDA;
 }
 
-int gram_tc_parts(const Plan &p) { return gram_tc_units(p.npix) * (128 / (2 * p.T)); }
+int gram_tc_parts(const Plan &p) { return gram_tc_units_of(p) * (128 / (2 * p.T)); }
+int gram_tc_default_units(long long npix) { return gram_tc_units(npix); }
 
 dh_status make_tensor_maps(Plan &p) {
   p.tmaps_ok = false;

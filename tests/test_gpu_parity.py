@@ -240,7 +240,7 @@ def test_invalid_calls_return_errors(dh):
             plan.render_frames(f, first_slot=8)  # slots beyond the reservation
         lib = plan._lib
         for opt, bad in ((0, 2), (1, 1), (1, 65), (2, 64), (3, 3), (4, 2), (5, 2), (5, -1), (6, -1),
-                         (6, 100000001), (7, 0)):
+                         (6, 100000001), (7, 3), (8, 64), (9, 3), (10, 0)):
             assert lib.dh_plan_set_option(plan._h, opt, bad) == 1, (opt, bad)  # DH_ERR_INVALID_ARG
         v = ctypes.c_int(-1)
         assert lib.dh_plan_get_option(plan._h, 5, ctypes.byref(v)) == 0 and v.value == 0
@@ -320,18 +320,28 @@ def test_persistent_render_equals_chunked(dh, n, F, prec):
             assert torch.equal(a, b)
 
 
-def test_autotune_keeps_results(dh):
-    """The autotuner only changes the render schedule: the same holograms before and after."""
+def test_autotune_picks_are_plan_options(dh):
+    """The autotuner's picks are plan options: a plan given the same options explicitly renders
+    bitwise the same holograms; picks that change the arithmetic (radix, tensor cores) change
+    only the rounding (within 1e-3 of the 16-bit holograms before tuning)."""
     frames = to_gpu(SpeckleStream(SpeckleParams(512, 512), seed=77).next(6).numpy())
     with dh.Plan(512, 512, LAM, Z, PITCH, T=16, precision="fp16", max_frames=16) as plan:
         plan.render_frames(frames)
         before = [plan.debug_hologram(t).cpu() for t in range(6)]
         pick = plan.autotune(16)
-        assert set(pick) == {"persistent", "ring", "lag"}
+        assert {"persistent", "ring", "lag", "fft", "radix", "gram_units"} <= set(pick)
         plan.render_frames(frames)
         after = [plan.debug_hologram(t).cpu() for t in range(6)]
-    for a, b in zip(before, after):
-        assert torch.equal(a, b)
+    with dh.Plan(512, 512, LAM, Z, PITCH, T=16, precision="fp16", max_frames=16) as again:
+        again.set_render_schedule(pick["persistent"], pick["ring"], pick["lag"])
+        again.set_render_fft(pick["fft"])
+        again.set_fft_radix(pick["radix"])
+        again.set_gram_units(pick["gram_units"])
+        again.render_frames(frames)
+        explicit = [again.debug_hologram(t).cpu() for t in range(6)]
+    for a, b, c in zip(before, after, explicit):
+        assert torch.equal(b, c)
+        assert rel(b.numpy(), a.numpy()) <= 1e-3
 
 
 # ------------------------------------------------------- host buffers, overlapped copies
