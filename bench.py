@@ -235,6 +235,8 @@ def run_ours(args, ws, rank, local):
     plan = dh.Plan(NX, NY, LAM, Z, PITCH, T=T, precision=args.precision,
                    max_frames=nframes * (2 if pipeline else 1), max_windows=nwin)
     plan.set_covariance_source(args.covariance)
+    if args.residual:
+        plan.set_residual(True)
     if args.render_schedule == "auto":
         tuned = plan.autotune(256)  # setup, outside the timed region
     else:
@@ -336,7 +338,7 @@ def run_ours(args, ws, rank, local):
     # dh_pca_batch_host: pinned host frames in, host images and eigenvalues out; the library
     # overlaps the frame copies with the computation of earlier groups of windows
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.residual:  # the host-buffer call has no residual mode
         host_frames = torch.empty(frames.shape, dtype=torch.uint16, pin_memory=True)
         host_frames.copy_(frames)
         host_images = torch.empty(images.shape, dtype=torch.float32, pin_memory=True)
@@ -421,7 +423,9 @@ def run_ours(args, ws, rank, local):
                        "windows_per_step": nwin, "frames_per_step": nframes, "k0": K0, "k1": K1,
                        "precision": args.precision,
                        "l2": "no flush: 4 GiB of input frames per step exceed the 126 MB L2",
-                       "render_schedule": tuned, "covariance": args.covariance,
+                       "render_schedule": tuned,
+                       "covariance": "raw (C = I^T I)" if args.residual else args.covariance,
+                       "storage": "mean-residual" if args.residual else "plain",
                        "pipelined_steps": pipeline,
                        "parallelism": f"replicas x{ws}"},
             "frames_per_s": value * T,
@@ -1230,6 +1234,8 @@ def main(argv=None):
     ap.add_argument("--latency-seconds", type=float, default=10.0,
                     help="headline line: stream time of the serving replay that gives the p50/p99 "
                          "window latency (0 = skip)")
+    ap.add_argument("--residual", action="store_true",
+                    help="headline: mean-residual storage of the 16-bit holograms (DH_OPT_RESIDUAL)")
     ap.add_argument("--no-peaks", action="store_true",
                     help="headline line: skip the FP32/FP64 FMA-rate measurement")
     ap.add_argument("--workload", choices=["paper", "sliding", "uneven", "serving", "fourier"],

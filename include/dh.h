@@ -170,6 +170,16 @@ dh_status dh_plan_reserve(dh_plan_t plan, int max_frames, int max_windows);
  *   order of the FP64 partial sums. Reallocates the per-window buffers (synchronous). */
 #define DH_OPT_FFT_RADIX 8
 #define DH_OPT_GRAM_UNITS 9
+/* DH_OPT_RESIDUAL: mean-residual storage (16-bit storage only; DH_ERR_STATE for FP32 plans).
+ *   1: dh_pca_batch with windows exactly T frames apart stores each window's holograms as
+ *   D_t = F(I_t - M) (Eq. 1 of the residual, F linear), M the window's temporal mean frame
+ *   rounded to integers, keeps mu = F(M) in FP32, projects P = D V + mu (1^T V) (equal to H V
+ *   since H = mu 1^T + D), and takes C = I^T I from the frames (exact). The 16-bit rounding
+ *   then scales with |D| rather than |H|, whose static part is removed; the tensor-core DFT
+ *   render is not used. Other calls on the plan return DH_ERR_STATE while it is on.
+ *   Allocates per window 2 n_x n_y bytes of mean frames, 8 n_x n_y of mu (synchronous).
+ *   0 (default): off. */
+#define DH_OPT_RESIDUAL 10
 dh_status dh_plan_set_option(dh_plan_t plan, int option, int value);
 dh_status dh_plan_get_option(dh_plan_t plan, int option, int *value);
 

@@ -153,6 +153,10 @@ class Plan:
         """DH_OPT_FFT_RADIX: 0 (each length's default), 16 or 32 where instantiated."""
         _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(self._h, 8, int(radix)))
 
+    def set_residual(self, on: bool = True) -> None:
+        """DH_OPT_RESIDUAL: mean-residual storage for pca_batch's windows (16-bit storage)."""
+        _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(self._h, 10, 1 if on else 0))
+
     def set_gram_units(self, units: int = 0) -> None:
         """DH_OPT_GRAM_UNITS: split-K units per window of the tensor-core covariance (0 =
         the frame size's default)."""

@@ -65,6 +65,7 @@ void dfree(Ptr *&ptr) {
 // Per-window buffers: covariance partials, C, lambda, V and the projection operand.
 void free_windows(Plan &p) {
   dfree(p.d_part); dfree(p.d_C); dfree(p.d_lam); dfree(p.d_V); dfree(p.d_B); dfree(p.d_W);
+  dfree(p.d_mean); dfree(p.d_mu); dfree(p.d_mucoef);
   p.tmaps_ok = false;
   p.bytes -= p.window_bytes;
   p.window_bytes = 0;
@@ -89,10 +90,10 @@ size_t table_bytes(const Plan &p) {
 
 // Device bytes of every buffer a plan allocates, from its sizes, reservation and precision.
 struct StoreSizes {
-  size_t tables, H, mid, part, C, lam, V, B, W;
+  size_t tables, H, mid, part, C, lam, V, B, W, resid;
   int mid_frames, parts_total;
   size_t B_window;
-  size_t windows() const { return part + C + lam + V + B + W; }
+  size_t windows() const { return part + C + lam + V + B + W + resid; }
   size_t total() const { return tables + H + mid + windows(); }
 };
 
@@ -124,6 +125,8 @@ StoreSizes store_sizes(const Plan &p) {
   // operand of the tensor-core sliding DFT (at most 2 x 240 x 256 16-bit values)
   z.W = z.B_window;
   if (p.prec != DH_PREC_FP32 && z.W < (256u << 10)) z.W = 256u << 10;
+  // mean-residual storage: mean frames (uint16), mu (FP32 complex), mu coefficients
+  z.resid = p.residual ? (size_t)p.max_windows * ((size_t)p.npix * (2 + 8) + 16ull * p.T) : 0;
   return z;
 }
 
@@ -140,6 +143,11 @@ dh_status alloc_windows(Plan &p) {
   if ((st = dalloc(p, &p.d_V, z.V)) != DH_OK) return st;
   if ((st = dalloc(p, &p.d_B, z.B)) != DH_OK) return st;
   if ((st = dalloc(p, &p.d_W, z.W)) != DH_OK) return st;
+  if (p.residual) {
+    if ((st = dalloc(p, &p.d_mean, (size_t)p.max_windows * p.npix * 2)) != DH_OK) return st;
+    if ((st = dalloc(p, &p.d_mu, (size_t)p.max_windows * p.npix * 8)) != DH_OK) return st;
+    if ((st = dalloc(p, &p.d_mucoef, (size_t)p.max_windows * 16 * p.T)) != DH_OK) return st;
+  }
   p.W_bytes = z.W;
   p.window_bytes = z.windows();
   DH_CUDA_TRY(cudaMemset(p.d_B, 0, z.B));
@@ -198,6 +206,17 @@ dh_status set_fft_radix(Plan &p, int radix) {
   return e == cudaSuccess ? DH_OK : fail_cuda(e);
 }
 
+// Mean-residual storage for dh_pca_batch's windows (16-bit storage): the mean frame, mu and
+// coefficient buffers are allocated with the per-window buffers (synchronous).
+dh_status set_residual(Plan &p, int on) {
+  if (on != 0 && on != 1) return DH_ERR_INVALID_ARG;
+  if (on && p.prec == DH_PREC_FP32) return DH_ERR_STATE;
+  if (on == p.residual) return DH_OK;
+  DH_CUDA_TRY(cudaDeviceSynchronize());
+  p.residual = on;
+  return alloc_windows(p);
+}
+
 // Split-K units per window of the tensor-core covariance (0 = the default for the frame size):
 // a power of two dividing n / 256, so that every window length's pixel chunks tile a unit.
 // The per-window partial buffers are reallocated (synchronous).
@@ -239,6 +258,9 @@ dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int 
                    int slot_stride, int n_windows, int k0, int k1, float *images, double *eig_user,
                    cudaStream_t s, int b0 = -1, int b1 = -1, const uint16_t *raw = nullptr,
                    long long raw_stride = 0) {
+  // mean-residual storage: disjoint windows with their frames at hand, Eqs. 4-7 only
+  if (p.residual && (!frames || !raw || slot_stride != p.T || b0 >= 0 || p.cov_mode == 2 || p.prec == DH_PREC_FP32))
+    return DH_ERR_STATE;
   const int nS = b0 >= 0 ? b1 - b0 + 1 : k1 - k0 + 1;  // projected columns
   const int nop = p.prec == DH_PREC_FP32 ? 2 * nS : (2 * nS + 15) / 16 * 16;  // operand rows
   // overlapping windows: grouped projection (one group layout for the whole call)
@@ -262,20 +284,28 @@ dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int 
   }
   int rendered = 0;  // frames (slots relative to first_slot) already rendered
   dh_status st;
+  if (p.residual) {  // the windows' mean frames M, and mu = F(M) in FP32
+    if ((st = launch_window_mean(p, frames, frame_stride, n_windows, slot_stride, s)) != DH_OK) return st;
+    if ((st = launch_render_to(p, p.d_mean, p.npix, n_windows, 0,
+                               RenderTarget{p.d_mu, DH_PREC_FP32, 0, nullptr, 1}, s)) != DH_OK)
+      return st;
+  }
   for (int g = 0; g < G; ++g) {
     const int w0 = w0s[g], nw = nws[g];
     if (frames) {
       const int need = (G > 1 ? n_windows - 1 : w0 + nw - 1) * slot_stride + p.T;
       if (need > rendered) {
-        st = launch_render(p, frames + (long long)rendered * frame_stride, frame_stride, need - rendered,
-                           first_slot + rendered, s);
+        const RenderTarget to{p.d_H, p.prec, 2ll * p.max_frames, p.residual ? p.d_mean : nullptr, p.T,
+                              rendered};
+        st = launch_render_to(p, frames + (long long)rendered * frame_stride, frame_stride, need - rendered,
+                              first_slot + rendered, to, s);
         if (st != DH_OK) return st;
         rendered = need;
       }
     }
     const int fs = first_slot + w0 * slot_stride;
     int parts = 0;
-    if (raw && p.cov_mode == 1) {
+    if (raw && (p.cov_mode == 1 || p.residual)) {
       p.sm_budget = g > 0 ? p.num_sms - nws[g - 1] : 0;  // beside the previous group's eigensolver
       st = launch_gram_raw(p, raw, raw_stride, (n_windows - 1) * slot_stride + p.T, w0 * slot_stride, slot_stride,
                            nw, &parts, s);
@@ -303,6 +333,7 @@ dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int 
     if (st != DH_OK) return st;
     if (b0 >= 0 && (st = launch_svd_fourier_operand(p, nw, k0, k1, b0, b1, nop, w0, p.aux)) != DH_OK)
       return st;
+    if (p.residual && (st = launch_mu_coef(p, nw, k0, k1, nop, w0, p.aux)) != DH_OK) return st;
     DH_CUDA_TRY(cudaEventRecord(p.ev_jac[g], p.aux));
   }
   for (int g = 0; g < G; ++g) {
@@ -611,6 +642,7 @@ dh_status dh_plan_get_option(dh_plan_t h, int option, int *value) {
     case DH_OPT_RENDER_FFT: *value = h->p.render_fft; return DH_OK;
     case DH_OPT_FFT_RADIX: *value = h->p.fft_radix; return DH_OK;
     case DH_OPT_GRAM_UNITS: *value = h->p.gram_units; return DH_OK;
+    case DH_OPT_RESIDUAL: *value = h->p.residual; return DH_OK;
   }
   return DH_ERR_INVALID_ARG;
 }
@@ -777,6 +809,8 @@ dh_status dh_plan_set_option(dh_plan_t h, int option, int value) {
       return set_fft_radix(h->p, value);
     case DH_OPT_GRAM_UNITS:
       return set_gram_units(h->p, value);
+    case DH_OPT_RESIDUAL:
+      return set_residual(h->p, value);
   }
   return DH_ERR_INVALID_ARG;
 }

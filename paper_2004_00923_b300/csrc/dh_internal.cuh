@@ -41,6 +41,12 @@ struct Plan {
   // split-K units per window of the tensor-core covariance: 0 = the default for the frame
   // size, else a power of two dividing n / 256 (DH_OPT_GRAM_UNITS, the autotuner)
   int gram_units = 0;
+  // mean-residual storage (DH_OPT_RESIDUAL, 16-bit storage): windows of dh_pca_batch store
+  // D = F(I - M) with M the window's rounded mean frame, mu = F(M) in FP32
+  int residual = 0;
+  uint16_t *d_mean = nullptr;  // [max_windows][npix] uint16
+  float *d_mu = nullptr;       // [max_windows][re | im][npix] FP32
+  float *d_mucoef = nullptr;   // [max_windows][a (2T) | b (2T)] FP32
   // render intermediate (row-pass output): a chunk of frames sized to stay in L2
   float2 *d_mid = nullptr;
   int mid_frames = 0;
@@ -157,6 +163,20 @@ dh_status fail_cuda(cudaError_t e);
 // Eq. 1: render n_frames frames into hologram slots [slot0, slot0 + n_frames).
 dh_status launch_render(Plan &p, const uint16_t *frames, long long frame_stride, int n_frames,
                         int slot0, cudaStream_t s);
+// Where a render writes: H of storage type `prec` (16-bit: [p / 64][rows_total][64] blocks;
+// FP32: planes [slot][re|im][npix]), and optionally, per frame, the window mean frame it
+// subtracts first: frame f of the call uses mean + ((mean_first + f) / mean_every) * npix
+// (uint16).
+struct RenderTarget {
+  void *H;
+  dh_precision prec;
+  long long rows_total;
+  const uint16_t *mean;
+  int mean_every;
+  int mean_first = 0;
+};
+dh_status launch_render_to(Plan &p, const uint16_t *frames, long long frame_stride, int n_frames,
+                           int slot0, const RenderTarget &to, cudaStream_t s);
 // FFT specs of the render: log2 length in the low 4 bits, log2 radix above (0 = default);
 // the plan's radix choice (0 = default, or 16 / 32 where that radix is instantiated for the
 // length) per axis, and whether a radix is available for a length
@@ -259,6 +279,12 @@ dh_status launch_reduce_cov_window(const double *part, int parts, int T, double 
 // load the modules of the kernels the two helpers above launch, for every T
 dh_status preload_gram_simt_rows();
 dh_status preload_reduce_cov_window();
+
+// mean-residual storage: the windows' rounded mean frames into p.d_mean, and after the
+// eigensolver the projection's mu coefficients into p.d_mucoef
+dh_status launch_window_mean(Plan &p, const uint16_t *frames, long long frame_stride, int n_windows,
+                             int window_stride, cudaStream_t s);
+dh_status launch_mu_coef(Plan &p, int n_windows, int k0, int k1, int Npad, int woff, cudaStream_t s);
 
 // conversions for inspection
 dh_status launch_hologram_to_f32(Plan &p, int slot, float *out, cudaStream_t s);

@@ -349,7 +349,8 @@ template <int LOGN, bool LEAD_SYNC = true, bool PER_WARP = false, typename Parke
 __device__ __forceinline__ void row_work(const uint4 (&pf)[RowCfg<LOGN>::CPT], float2 *smem, int y0, int ny,
                                          int cw_log, const float2 *__restrict__ cx,
                                          const float2 *__restrict__ cy, const float2 *__restrict__ tw,
-                                         float2 *__restrict__ dst, Parked parked, Freed freed = Freed()) {
+                                         float2 *__restrict__ dst, const uint16_t *__restrict__ mean,
+                                         Parked parked, Freed freed = Freed()) {
   using S = Shape<LOGN>;
   using C = RowCfg<LOGN>;
   using E = Engine<LOGN, (S::P > 32)>;
@@ -373,12 +374,24 @@ __device__ __forceinline__ void row_work(const uint4 (&pf)[RowCfg<LOGN>::CPT], f
   }
   const uint16_t *row16 = reinterpret_cast<const uint16_t *>(sm);
   float2 v[S::R];
+  if (mean == nullptr) {
 #pragma unroll
-  for (int r = 0; r < S::R; ++r) {
-    const int x = j + r * S::P;
-    const float a = __uint_as_float(0x4b000000u | row16[x]) - 8388608.f;  // exact: u < 2^23
-    const float2 c = cx[x];
-    v[r] = make_float2(a * c.x, a * c.y);
+    for (int r = 0; r < S::R; ++r) {
+      const int x = j + r * S::P;
+      const float a = __uint_as_float(0x4b000000u | row16[x]) - 8388608.f;  // exact: u < 2^23
+      const float2 c = cx[x];
+      v[r] = make_float2(a * c.x, a * c.y);
+    }
+  } else {  // the residual I - mean of the frame's window (exact: both integers below 2^16)
+    const uint16_t *mrow = mean + (long long)y * S::N;
+#pragma unroll
+    for (int r = 0; r < S::R; ++r) {
+      const int x = j + r * S::P;
+      const float a = (__uint_as_float(0x4b000000u | row16[x]) - 8388608.f) -
+                      (__uint_as_float(0x4b000000u | __ldg(mrow + x)) - 8388608.f);
+      const float2 c = cx[x];
+      v[r] = make_float2(a * c.x, a * c.y);
+    }
   }
   E::run(v, sm, j, tw, freed);  // its first exchange store is ordered after the reads above
   const float2 cyy = cy[y];
@@ -515,11 +528,12 @@ __device__ __forceinline__ bool col_work(const float2 *__restrict__ src, float2 
 #include "render_tc.cuh"
 
 // Row pass over a chunk of frames: one item = FPC consecutive rows of one frame.
-template <int LOGN>
+template <int LOGN, bool MEAN>
 __global__ void __launch_bounds__(cta_threads<LOGN>(), rows_per_sm<LOGN>())
 k_render_rows(const uint16_t *__restrict__ frames, long long frame_stride, int ny, int cw_log,
               const float2 *__restrict__ cx, const float2 *__restrict__ cy,
-              const float2 *__restrict__ tw, float2 *__restrict__ mid, int n_items) {
+              const float2 *__restrict__ tw, float2 *__restrict__ mid, int n_items,
+              const uint16_t *__restrict__ mean, int mean_every, int mean_first) {
   using C = RowCfg<LOGN>;
   extern __shared__ float2 smem[];
   const int groups = ny / C::FPC;
@@ -530,7 +544,8 @@ k_render_rows(const uint16_t *__restrict__ frames, long long frame_stride, int n
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     const int f = item / groups, y0 = (item % groups) * C::FPC;
     const int nxt = item + (int)gridDim.x;
-    row_work<LOGN>(pf, smem, y0, ny, cw_log, cx, cy, tw, mid + (long long)f * npix, [&]() {
+    row_work<LOGN>(pf, smem, y0, ny, cw_log, cx, cy, tw, mid + (long long)f * npix,
+                   MEAN ? mean + (long long)((mean_first + f) / mean_every) * npix : nullptr, [&]() {
       if (nxt < n_items) row_prefetch<LOGN>(pf, frame_of(nxt), (nxt % groups) * C::FPC);
     });
   }
@@ -621,13 +636,14 @@ __device__ __forceinline__ bool wait_geq(const unsigned *p, unsigned target,
   return true;
 }
 
-template <int LOGN, typename OutT>
+template <int LOGN, typename OutT, bool MEAN>
 __global__ void __launch_bounds__(kCtaThreads, rows_per_sm<LOGN>())
 k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int n_frames, int cw_log,
                const float2 *__restrict__ cx, const float2 *__restrict__ cy, const float2 *__restrict__ tw,
                int tw_len,
                float2 *__restrict__ mid, int ring, int lag, OutT *__restrict__ H, long long rows_total,
-               int slot0, unsigned *__restrict__ sync, uint32_t *__restrict__ status, int stall_cycles) {
+               int slot0, unsigned *__restrict__ sync, uint32_t *__restrict__ status, int stall_cycles,
+               const uint16_t *__restrict__ mean, int mean_every, int mean_first) {
   using S = Shape<LOGN>;
   using RC = RowCfg<LOGN>;
   constexpr int FPC = fpc<LOGN>();  // rows per row item = columns per column item
@@ -740,7 +756,10 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
       const int f = frame_of(cur), i = item_of(cur), rs = f % ring;
       float2 *ring_f = mid + (long long)rs * NPIX;
       if (is_row(cur)) {
-        row_work<LOGN, false, PW>(pf, smem, i * FPC, N, cw_log, s_cx, s_cy, s_tw, ring_f, prefetch_next, freed);
+        row_work<LOGN, false, PW>(pf, smem, i * FPC, N, cw_log, s_cx, s_cy, s_tw, ring_f,
+                                  MEAN ? mean + (long long)((mean_first + f) / mean_every) * NPIX : nullptr,
+                                  prefetch_next,
+                                  freed);
         fence_proxy_async_global();  // this thread's ring writes, for later bulk copies
         if constexpr (PW) {
           __syncwarp();
@@ -824,18 +843,20 @@ int col_tile_log(int spec) {
 
 template <int LOGN>
 dh_status launch_rows_t(const uint16_t *frames, long long fstride, int ny, const Plan &p,
-                        float2 *mid, int nf, cudaStream_t s) {
+                        float2 *mid, int nf, const RenderTarget &to, cudaStream_t s) {
   const int cw_log = col_tile_log(col_spec(p));
   using S = Shape<LOGN>;
   constexpr int FPC = fpc<LOGN>();
   const int threads = FPC * S::P;
   // exchange regions (also the uint16 rows and the staging tile)
   const size_t smem = (size_t)FPC * S::RSTRIDE * sizeof(float2);
-  auto kern = k_render_rows<LOGN>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  // the mean-subtracting variant (mean-residual storage) is a separate instance, so that the
+  // plain one keeps its registers
+  auto kern = to.mean ? k_render_rows<LOGN, true> : k_render_rows<LOGN, false>;
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[to.mean ? 1 : 0]) {
     DH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set = true;
+    attr_set[to.mean ? 1 : 0] = true;
   }
   int per_sm = 0;
   DH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -844,13 +865,15 @@ dh_status launch_rows_t(const uint16_t *frames, long long fstride, int ny, const
   if (grid < 1) grid = 1;
   if (grid > items) grid = items;
   ProfScope ps(const_cast<Plan &>(p), K_RENDER_ROWS, s);
-  kern<<<grid, threads, smem, s>>>(frames, fstride, ny, cw_log, p.d_cx, p.d_cy, p.d_twx, mid, items);
+  kern<<<grid, threads, smem, s>>>(frames, fstride, ny, cw_log, p.d_cx, p.d_cy, p.d_twx, mid, items, to.mean,
+                                    to.mean_every, to.mean_first);
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
 }
 
 template <int LOGN, typename OutT>
-dh_status launch_cols_t(const Plan &p, const float2 *mid, int nf, int slot0, cudaStream_t s) {
+dh_status launch_cols_t(const Plan &p, const float2 *mid, int nf, int slot0, const RenderTarget &to,
+                        cudaStream_t s) {
   using S = Shape<LOGN>;
   constexpr int FPC = fpc<LOGN>();
   const int threads = FPC * S::P;
@@ -871,16 +894,16 @@ dh_status launch_cols_t(const Plan &p, const float2 *mid, int nf, int slot0, cud
   if (grid < 1) grid = 1;
   if (grid > items) grid = items;
   ProfScope ps(const_cast<Plan &>(p), K_RENDER_COLS, s);
-  kern<<<grid, threads, smem, s>>>(mid, p.nx, p.d_twy, static_cast<OutT *>(p.d_H), p.npix,
-                                    2ll * p.max_frames, slot0, items, p.d_status);
+  kern<<<grid, threads, smem, s>>>(mid, p.nx, p.d_twy, static_cast<OutT *>(to.H), p.npix, to.rows_total, slot0,
+                                    items, p.d_status);
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
 }
 
 dh_status launch_rows(const Plan &p, const uint16_t *frames, long long fstride, float2 *mid,
-                      int nf, cudaStream_t s) {
+                      int nf, const RenderTarget &to, cudaStream_t s) {
   switch (row_spec(p)) {
-#define DH_CASE(S) case S: return launch_rows_t<S>(frames, fstride, p.ny, p, mid, nf, s);
+#define DH_CASE(S) case S: return launch_rows_t<S>(frames, fstride, p.ny, p, mid, nf, to, s);
     DH_FFT_SPECS(DH_CASE)
 #undef DH_CASE
   }
@@ -888,9 +911,10 @@ dh_status launch_rows(const Plan &p, const uint16_t *frames, long long fstride, 
 }
 
 template <typename OutT>
-dh_status launch_cols_typed(const Plan &p, const float2 *mid, int nf, int slot0, cudaStream_t s) {
+dh_status launch_cols_typed(const Plan &p, const float2 *mid, int nf, int slot0, const RenderTarget &to,
+                            cudaStream_t s) {
   switch (col_spec(p)) {
-#define DH_CASE(S) case S: return launch_cols_t<S, OutT>(p, mid, nf, slot0, s);
+#define DH_CASE(S) case S: return launch_cols_t<S, OutT>(p, mid, nf, slot0, to, s);
     DH_FFT_SPECS(DH_CASE)
 #undef DH_CASE
   }
@@ -925,7 +949,7 @@ int fused_lag(const Plan &p, int ring) {
 
 template <int LOGN, typename OutT>
 dh_status launch_fused_t(Plan &p, const uint16_t *frames, long long fstride, int nf, int slot0,
-                         cudaStream_t s) {
+                         const RenderTarget &to, cudaStream_t s) {
   if constexpr (cta_threads<LOGN>() != kCtaThreads) {
     return DH_ERR_UNSUPPORTED_SIZE;  // an item of this length needs more threads
   } else {
@@ -936,11 +960,17 @@ dh_status launch_fused_t(Plan &p, const uint16_t *frames, long long fstride, int
   const int tw_len = twiddle_len(LOGN);
   // exchange / tile buffer, then the twiddle and the two chirp tables
   const size_t smem = (row_smem > tile ? row_smem : tile) + (size_t)(tw_len + 2 * S::N) * sizeof(float2);
-  auto kern = k_render_fused<LOGN, OutT>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  // (mean-residual storage is 16-bit only: FP32 outputs have no mean-subtracting instance)
+  auto kern = k_render_fused<LOGN, OutT, false>;
+  if constexpr (sizeof(OutT) == 2) {
+    if (to.mean) kern = k_render_fused<LOGN, OutT, true>;
+  } else {
+    if (to.mean) return DH_ERR_STATE;
+  }
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[to.mean ? 1 : 0]) {
     DH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set = true;
+    attr_set[to.mean ? 1 : 0] = true;
   }
   int per_sm = 0;
   DH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCtaThreads, smem));
@@ -954,8 +984,8 @@ dh_status launch_fused_t(Plan &p, const uint16_t *frames, long long fstride, int
   ProfScope ps(p, K_RENDER_FUSED, s);
   kern<<<grid, kCtaThreads, smem, s>>>(frames, fstride, nf, col_tile_log(LOGN), p.d_cx, p.d_cy, p.d_twx, tw_len,
                                       p.d_mid,
-                               ring, lag, static_cast<OutT *>(p.d_H), 2ll * p.max_frames, slot0, p.d_sync,
-                               p.d_status, p.test_stall);
+                               ring, lag, static_cast<OutT *>(to.H), to.rows_total, slot0, p.d_sync,
+                               p.d_status, p.test_stall, to.mean, to.mean_every, to.mean_first);
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
   }
@@ -972,17 +1002,17 @@ int cta_threads_of(int spec) {
 
 template <typename OutT>
 dh_status launch_fused_typed(Plan &p, const uint16_t *frames, long long fstride, int nf, int slot0,
-                             cudaStream_t s) {
+                             const RenderTarget &to, cudaStream_t s) {
   switch (row_spec(p)) {  // square frames: the same spec on both axes
-    case 8: return launch_fused_t<8, OutT>(p, frames, fstride, nf, slot0, s);
-    case 9: return launch_fused_t<9, OutT>(p, frames, fstride, nf, slot0, s);
-    case 10: return launch_fused_t<10, OutT>(p, frames, fstride, nf, slot0, s);
-    case 11: return launch_fused_t<11, OutT>(p, frames, fstride, nf, slot0, s);
-    case 12: return launch_fused_t<12, OutT>(p, frames, fstride, nf, slot0, s);
-    case 9 | (4 << 4): return launch_fused_t<9 | (4 << 4), OutT>(p, frames, fstride, nf, slot0, s);
-    case 10 | (4 << 4): return launch_fused_t<10 | (4 << 4), OutT>(p, frames, fstride, nf, slot0, s);
-    case 11 | (4 << 4): return launch_fused_t<11 | (4 << 4), OutT>(p, frames, fstride, nf, slot0, s);
-    case 12 | (5 << 4): return launch_fused_t<12 | (5 << 4), OutT>(p, frames, fstride, nf, slot0, s);
+    case 8: return launch_fused_t<8, OutT>(p, frames, fstride, nf, slot0, to, s);
+    case 9: return launch_fused_t<9, OutT>(p, frames, fstride, nf, slot0, to, s);
+    case 10: return launch_fused_t<10, OutT>(p, frames, fstride, nf, slot0, to, s);
+    case 11: return launch_fused_t<11, OutT>(p, frames, fstride, nf, slot0, to, s);
+    case 12: return launch_fused_t<12, OutT>(p, frames, fstride, nf, slot0, to, s);
+    case 9 | (4 << 4): return launch_fused_t<9 | (4 << 4), OutT>(p, frames, fstride, nf, slot0, to, s);
+    case 10 | (4 << 4): return launch_fused_t<10 | (4 << 4), OutT>(p, frames, fstride, nf, slot0, to, s);
+    case 11 | (4 << 4): return launch_fused_t<11 | (4 << 4), OutT>(p, frames, fstride, nf, slot0, to, s);
+    case 12 | (5 << 4): return launch_fused_t<12 | (5 << 4), OutT>(p, frames, fstride, nf, slot0, to, s);
   }
   return DH_ERR_UNSUPPORTED_SIZE;
 }
@@ -1114,8 +1144,14 @@ void build_tc_tables(void *out) {
 
 dh_status launch_render(Plan &p, const uint16_t *frames, long long frame_stride, int n_frames,
                         int slot0, cudaStream_t s) {
-  // 1024^2 frames with the tensor-core DFT stages
-  if (tc_render_applies(p)) {
+  return launch_render_to(p, frames, frame_stride, n_frames, slot0,
+                          RenderTarget{p.d_H, p.prec, 2ll * p.max_frames, nullptr, 1}, s);
+}
+
+dh_status launch_render_to(Plan &p, const uint16_t *frames, long long frame_stride, int n_frames,
+                           int slot0, const RenderTarget &to, cudaStream_t s) {
+  // 1024^2 frames with the tensor-core DFT stages (into the plan's own store, no mean)
+  if (tc_render_applies(p) && to.H == p.d_H && to.mean == nullptr) {
     switch (p.prec) {
       case DH_PREC_FP32: return launch_tc_chunks_t<float>(p, frames, frame_stride, n_frames, slot0, s);
       case DH_PREC_FP16: return launch_tc_chunks_t<__half>(p, frames, frame_stride, n_frames, slot0, s);
@@ -1124,10 +1160,10 @@ dh_status launch_render(Plan &p, const uint16_t *frames, long long frame_stride,
   }
   // square frames from 256^2: every frame of the call in one persistent launch
   if (fused_ring(p, 1, 1)) {
-    switch (p.prec) {
-      case DH_PREC_FP32: return launch_fused_typed<float>(p, frames, frame_stride, n_frames, slot0, s);
-      case DH_PREC_FP16: return launch_fused_typed<__half>(p, frames, frame_stride, n_frames, slot0, s);
-      case DH_PREC_BF16: return launch_fused_typed<__nv_bfloat16>(p, frames, frame_stride, n_frames, slot0, s);
+    switch (to.prec) {
+      case DH_PREC_FP32: return launch_fused_typed<float>(p, frames, frame_stride, n_frames, slot0, to, s);
+      case DH_PREC_FP16: return launch_fused_typed<__half>(p, frames, frame_stride, n_frames, slot0, to, s);
+      case DH_PREC_BF16: return launch_fused_typed<__nv_bfloat16>(p, frames, frame_stride, n_frames, slot0, to, s);
     }
   }
   // Chunks of mid_frames frames: the row pass fills the L2-sized intermediate, the column
@@ -1136,12 +1172,14 @@ dh_status launch_render(Plan &p, const uint16_t *frames, long long frame_stride,
   // and the doubled intermediate no longer stays in L2.)
   for (int f0 = 0; f0 < n_frames; f0 += p.mid_frames) {
     const int nf = (n_frames - f0) < p.mid_frames ? (n_frames - f0) : p.mid_frames;
-    dh_status st = launch_rows(p, frames + (long long)f0 * frame_stride, frame_stride, p.d_mid, nf, s);
+    RenderTarget chunk = to;  // the chunk's frames start f0 frames into the call
+    chunk.mean_first = to.mean_first + f0;
+    dh_status st = launch_rows(p, frames + (long long)f0 * frame_stride, frame_stride, p.d_mid, nf, chunk, s);
     if (st != DH_OK) return st;
-    switch (p.prec) {
-      case DH_PREC_FP32: st = launch_cols_typed<float>(p, p.d_mid, nf, slot0 + f0, s); break;
-      case DH_PREC_FP16: st = launch_cols_typed<__half>(p, p.d_mid, nf, slot0 + f0, s); break;
-      case DH_PREC_BF16: st = launch_cols_typed<__nv_bfloat16>(p, p.d_mid, nf, slot0 + f0, s); break;
+    switch (to.prec) {
+      case DH_PREC_FP32: st = launch_cols_typed<float>(p, p.d_mid, nf, slot0 + f0, chunk, s); break;
+      case DH_PREC_FP16: st = launch_cols_typed<__half>(p, p.d_mid, nf, slot0 + f0, chunk, s); break;
+      case DH_PREC_BF16: st = launch_cols_typed<__nv_bfloat16>(p, p.d_mid, nf, slot0 + f0, chunk, s); break;
     }
     if (st != DH_OK) return st;
   }

@@ -456,11 +456,15 @@ struct ProjCfg {
   static constexpr size_t SMEM = STAGES * A_BYTES + B_MAX + 1024 + 256;
 };
 
-template <int T, bool BF16>
+// RESID: the holograms hold D = H - mu 1^T (mean-residual storage): each accumulator column j
+// of pixel p gets mu_r(p) a_j + mu_i(p) b_j added before it is squared (a, b per window from
+// k_mu_coef, 4T floats apart; mu FP32 planes [window][re|im][npix]).
+template <int T, bool BF16, bool RESID>
 __global__ void __launch_bounds__(ProjCfg<T>::THREADS, 1)
 k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmB,
              int first_slot, int slot_stride, int n_windows, int tiles_pw, int Npad, int B_rows_pw,
-             int b_row0, float *__restrict__ images, int nx, int ny, uint32_t *__restrict__ status) {
+             int b_row0, float *__restrict__ images, int nx, int ny, uint32_t *__restrict__ status,
+             const float *__restrict__ mu, const float *__restrict__ coef) {
   using C = ProjCfg<T>;
   const long long npix = (long long)nx * ny;
   // Holograms are stored with column-major pixels p = kx n_y + ky, so a 128-pixel tile is
@@ -608,17 +612,40 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
       float m = 0.f;
       const uint32_t ta = tmem + lane_addr + buf * C::M2;
       int col = 0;
-      for (; col + 64 <= Npad; col += 64) {
-        float v[64];
-        tmem_ld64(ta + col, v);
+      if constexpr (!RESID) {
+        for (; col + 64 <= Npad; col += 64) {
+          float v[64];
+          tmem_ld64(ta + col, v);
 #pragma unroll
-        for (int i = 0; i < 64; ++i) m = fmaf(v[i], v[i], m);
-      }
-      for (; col < Npad; col += 16) {
-        float v[16];
-        tmem_ld16(ta + col, v);
+          for (int i = 0; i < 64; ++i) m = fmaf(v[i], v[i], m);
+        }
+        for (; col < Npad; col += 16) {
+          float v[16];
+          tmem_ld16(ta + col, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) m = fmaf(v[i], v[i], m);
+          for (int i = 0; i < 16; ++i) m = fmaf(v[i], v[i], m);
+        }
+      } else {  // coefficients: the same address on every lane (one broadcast load each)
+        const float *mw = mu + (long long)w * 2 * npix;
+        const float mr = __ldg(mw + p), mi = __ldg(mw + npix + p);
+        const float4 *ca = reinterpret_cast<const float4 *>(coef + (long long)w * 4 * T);
+        const float4 *cb = reinterpret_cast<const float4 *>(coef + (long long)w * 4 * T + 2 * T);
+        for (; col < Npad; col += 16) {
+          float v[16];
+          tmem_ld16(ta + col, v);
+#pragma unroll
+          for (int i = 0; i < 16; i += 4) {
+            const float4 a = __ldg(ca + (col + i) / 4), b = __ldg(cb + (col + i) / 4);
+            const float x0 = fmaf(mr, a.x, fmaf(mi, b.x, v[i]));
+            const float x1 = fmaf(mr, a.y, fmaf(mi, b.y, v[i + 1]));
+            const float x2 = fmaf(mr, a.z, fmaf(mi, b.z, v[i + 2]));
+            const float x3 = fmaf(mr, a.w, fmaf(mi, b.w, v[i + 3]));
+            m = fmaf(x0, x0, m);
+            m = fmaf(x1, x1, m);
+            m = fmaf(x2, x2, m);
+            m = fmaf(x3, x3, m);
+          }
+        }
       }
       fence_before_sync();
       mbar_arrive(&acc_empty[buf]);
@@ -726,11 +753,11 @@ dh_status gram_t(Plan &p, int first_slot, int slot_stride, int n_windows, cudaSt
   return DH_OK;
 }
 
-template <int T, bool BF16>
+template <int T, bool BF16, bool RESID>
 dh_status project_t(Plan &p, int first_slot, int slot_stride, int n_windows, int Npad, float *images,
                     int woff, cudaStream_t s, const void *shared_op) {
   using C = ProjCfg<T>;
-  auto kern = k_project_tc<T, BF16>;
+  auto kern = k_project_tc<T, BF16, RESID>;
   static bool attr = false;
   if (!attr) {
     DH_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -761,7 +788,8 @@ dh_status project_t(Plan &p, int first_slot, int slot_stride, int n_windows, int
   kern<<<grid, C::THREADS, C::SMEM, s>>>(p.tmap_H, tmB, first_slot, slot_stride, n_windows, tiles_pw, Npad,
                                           shared_op ? 0 : (int)B_rows_pw,
                                           shared_op ? 0 : (int)(woff * B_rows_pw), images, p.nx, p.ny,
-                                          p.d_status);
+                                          p.d_status, RESID ? p.d_mu + 2ll * woff * p.npix : nullptr,
+                                          RESID ? p.d_mucoef + 4ll * woff * p.T : nullptr);
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
 }
@@ -876,14 +904,18 @@ dh_status launch_project_tc(Plan &p, int first_slot, int slot_stride, int n_wind
                             float *images, int woff, cudaStream_t s, const void *shared_op) {
   if (!p.tmaps_ok) return DH_ERR_STATE;
   const bool bf16 = p.prec == DH_PREC_BF16;
+  const bool resid = p.residual && !shared_op;
+#define DH_PROJ(TT)                                                                                          \
+  return bf16 ? (resid ? project_t<TT, true, true>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op) \
+                       : project_t<TT, true, false>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op)) \
+              : (resid ? project_t<TT, false, true>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op) \
+                       : project_t<TT, false, false>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op));
   switch (p.T) {
-    case 16: return bf16 ? project_t<16, true>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op)
-                         : project_t<16, false>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op);
-    case 32: return bf16 ? project_t<32, true>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op)
-                         : project_t<32, false>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op);
-    case 64: return bf16 ? project_t<64, true>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op)
-                         : project_t<64, false>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op);
+    case 16: DH_PROJ(16)
+    case 32: DH_PROJ(32)
+    case 64: DH_PROJ(64)
   }
+#undef DH_PROJ
   return DH_ERR_UNSUPPORTED_SIZE;
 }
 
