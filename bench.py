@@ -44,6 +44,10 @@ WORKLOAD = "1024x1024 uint16 frames, 64 non-overlapping 32-frame windows per ste
 
 
 # --------------------------------------------------------------------------- helpers
+def print_line(line: dict) -> None:
+    print(json.dumps(line), flush=True)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -412,6 +416,28 @@ def run_ours(args, ws, rank, local):
         torch.cuda.empty_cache()
         latency = serve_latency(args, ws, rank, local)
 
+    # ---------------------------------------------------------------- the other workloads
+    # short runs (3 timed steps each, their window-0 parity samples against the oracle), so
+    # that the sliding, uneven and Fourier workloads are measured in the same line
+    workloads = None
+    if not args.no_workloads:
+        workloads = {}
+        sub = argparse.Namespace(**vars(args))
+        sub.steps, sub.warmup, sub.frames = 3, 1, 0
+        for name, fn in (("sliding", run_sliding), ("uneven", run_uneven), ("fourier", run_fourier)):
+            got = []
+            fn(sub, ws, rank, local, emit=got.append)
+            torch.cuda.empty_cache()
+            if got:
+                w = got[0]
+                par = w.get("parity") or {}
+                errs = [v.get("image_rel_l2") for v in par.values() if isinstance(v, dict)]
+                workloads[name] = {
+                    "metric": w["metric"], "value": w["value"], "unit": w["unit"],
+                    "ms_per_step": w["ms_per_step"], "steps": w["steps"],
+                    "parity_image_rel_l2_max": max(e for e in errs if e is not None) if errs else None,
+                    "device_flags": w.get("device_flags"), "workload": w["config"].get("workload")}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -437,6 +463,7 @@ def run_ours(args, ws, rank, local):
             "speedup_vs_plain_fp32": (value / plain["value"]) if plain else None,
             "parity": parity,
             "latency_ms": latency,
+            "workloads": workloads,
             "measured_rates": rates,
             "gpu_launches": launches_total,
             "device_flags": flags,
@@ -593,7 +620,7 @@ def span_bytes(F, npix):
     return total
 
 
-def run_sliding(args, ws, rank, local):
+def run_sliding(args, ws, rank, local, emit=None):
     """16-, 32- and 64-frame windows at stride 8 over 2048 frames of 1024^2: each frame is
     rendered once into a FP16 store read by all three window lengths (views), and the whole
     step is one CUDA graph."""
@@ -716,7 +743,7 @@ def run_sliding(args, ws, rank, local):
             "roofline": roofline, "cpu_baseline": cpu, "parity": parity,
             "gpu_launches": launches, "device_flags": flags, "clocks": clock_info,
         }
-        print(json.dumps(line), flush=True)
+        (emit or print_line)(line)
     g.close()
     for p in plans.values():
         p.close()
@@ -728,7 +755,7 @@ FOURIER_FRAMES, FOURIER_BINS = 2048, (7, 23)  # the paper's n_1 = 8, n_2 = 24, f
 PAPER_FFT_GVOXEL_S = 17.0  # Table 1, FFT row: output voxels of 32 x 1024^2 windows per s
 
 
-def run_fourier(args, ws, rank, local):
+def run_fourier(args, ws, rank, local, emit=None):
     """Eqs. 8-9 with a new 32-frame window per frame (stride 1) over 2048 frames of 1024^2:
     each frame rendered once (FP16), then the DFT-bin power image of all 2017 windows."""
     import paper_2004_00923_b300 as dh
@@ -808,7 +835,7 @@ def run_fourier(args, ws, rank, local):
             "roofline": roofline, "cpu_baseline": cpu, "parity": parity,
             "gpu_launches": launches, "device_flags": flags, "clocks": clock_info,
         }
-        print(json.dumps(line), flush=True)
+        (emit or print_line)(line)
     g.close()
     plan.close()
     return 0
@@ -818,7 +845,7 @@ def run_fourier(args, ws, rank, local):
 UNEVEN_SIZES = ((512, 40), (1024, 16), (2048, 4))
 
 
-def run_uneven(args, ws, rank, local):
+def run_uneven(args, ws, rank, local, emit=None):
     """512^2 x 40, 1024^2 x 16 and 2048^2 x 4 windows, alternating 32/64 frames, per-size z,
     per-window Doppler spread: one dh_batch_run (sizes on concurrent branches) per step,
     captured in one CUDA graph."""
@@ -940,7 +967,7 @@ def run_uneven(args, ws, rank, local):
             "roofline": roofline, "cpu_baseline": cpu, "parity": parity,
             "gpu_launches": launches, "device_flags": flags, "clocks": clock_info,
         }
-        print(json.dumps(line), flush=True)
+        (emit or print_line)(line)
     gr.close()
     for p in plans_all:
         p.close()
@@ -1236,6 +1263,8 @@ def main(argv=None):
                          "window latency (0 = skip)")
     ap.add_argument("--residual", action="store_true",
                     help="headline: mean-residual storage of the 16-bit holograms (DH_OPT_RESIDUAL)")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="headline line: skip the short sliding / uneven / Fourier runs")
     ap.add_argument("--no-peaks", action="store_true",
                     help="headline line: skip the FP32/FP64 FMA-rate measurement")
     ap.add_argument("--workload", choices=["paper", "sliding", "uneven", "serving", "fourier"],
