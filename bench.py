@@ -241,6 +241,8 @@ def run_ours(args, ws, rank, local):
     plan.set_covariance_source(args.covariance)
     if args.residual:
         plan.set_residual(True)
+    if args.render_fft != "auto":
+        plan.set_render_fft(args.render_fft)
     if args.render_schedule == "auto":
         tuned = plan.autotune(256)  # setup, outside the timed region
     else:
@@ -1261,6 +1263,9 @@ def main(argv=None):
     ap.add_argument("--latency-seconds", type=float, default=10.0,
                     help="headline line: stream time of the serving replay that gives the p50/p99 "
                          "window latency (0 = skip)")
+    ap.add_argument("--render-fft", choices=["auto", "cuda", "tensor"], default="auto",
+                    help="headline: DH_OPT_RENDER_FFT (tensor: the 32-point DFT stages on the tensor "
+                         "cores); with --render-schedule auto the autotuner may still change it")
     ap.add_argument("--residual", action="store_true",
                     help="headline: mean-residual storage of the 16-bit holograms (DH_OPT_RESIDUAL)")
     ap.add_argument("--no-workloads", action="store_true",
