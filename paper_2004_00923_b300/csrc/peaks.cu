@@ -4,8 +4,9 @@
 // rates rather than by nominal unit counts.
 //
 // Each thread runs kChains independent FMA chains (enough to cover the pipe latency) for
-// `iters` rounds; the chains' final values are stored only if they equal a value they can
-// never reach, which keeps the work live without memory traffic. FLOPs = 2 per FMA lane.
+// `iters` rounds; a chain's final value is stored (to a one-element buffer) only if it equals
+// a value it can never reach, which keeps the work live without memory traffic. FLOPs = 2 per
+// FMA lane.
 #include "dh_internal.cuh"
 
 namespace dh {
@@ -51,26 +52,31 @@ __global__ void __launch_bounds__(kThreads) k_fma_rate(int iters, T *__restrict_
   }
 #pragma unroll
   for (int c = 0; c < kChains; ++c)
-    if (is_sentinel<T>(x[c])) sink[blockIdx.x * kThreads + threadIdx.x] = x[c];
+    if (is_sentinel<T>(x[c])) *sink = x[c];
 }
 
 template <typename T>
 dh_status time_rate(int iters, int blocks, int lanes, float *ms, double *flops, cudaStream_t s) {
   cudaEvent_t a = nullptr, b = nullptr;
-  DH_CUDA_TRY(cudaEventCreate(&a));
-  DH_CUDA_TRY(cudaEventCreate(&b));
-  k_fma_rate<T><<<blocks, kThreads, 0, s>>>(iters, nullptr);  // warm-up
-  cudaError_t e = cudaGetLastError();
+  T *sink = nullptr;
+  cudaError_t e = cudaMalloc(&sink, sizeof(T));
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) {
+    k_fma_rate<T><<<blocks, kThreads, 0, s>>>(iters, sink);  // warm-up
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaEventRecord(a, s);
   if (e == cudaSuccess) {
-    k_fma_rate<T><<<blocks, kThreads, 0, s>>>(iters, nullptr);
+    k_fma_rate<T><<<blocks, kThreads, 0, s>>>(iters, sink);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaEventRecord(b, s);
   if (e == cudaSuccess) e = cudaEventSynchronize(b);
   if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (sink) cudaFree(sink);
   if (e != cudaSuccess) return fail_cuda(e);
   // FMAs per thread: iters x 8 x kChains, each on `lanes` values
   *flops = 2.0 * lanes * (double)iters * 8.0 * kChains * (double)blocks * kThreads;
