@@ -17,8 +17,10 @@
 //     real embedding of the retained eigenvectors split into hi + lo 16-bit parts (two
 //     MMAs into the same accumulator). The epilogue squares and sums the accumulator row
 //     of each pixel straight into the image; P is never stored.
-// Roles: warp 0 issues TMA, warp 1 issues MMAs (one thread), the remaining warps drain
-// TMEM. Every mbarrier wait is bounded (tc::kWaitBudget); on expiry the CTA raises
+// Roles: warp 0 issues TMA, warp 1 issues MMAs (one thread of it; the warp takes no
+// shared-memory step inside its loop, see named_sync), the next warps drain TMEM, and the last
+// warp waits on each stage's mbarriers and releases the MMA warp through the stage's named
+// barrier. Every mbarrier wait is bounded (tc::kWaitBudget); on expiry the CTA raises
 // DH_FLAG_WAIT_TIMEOUT, stops issuing work, waits for its own TMA copies in flight,
 // frees its tensor memory and exits.
 #include <cudaTypedefs.h>
@@ -60,7 +62,8 @@ struct GramCfg {
   // SM, T = 32 / 64 one CTA per SM (8 stages, 4 TMEM accumulators of 128 columns).
   static constexpr int NCOL = T == 64 ? 64 : 32;
   static constexpr int EPI_WARPS = 4 * (M2 / NCOL);
-  static constexpr int THREADS = 64 + 32 * EPI_WARPS;
+  static constexpr int WAITER = 2 + EPI_WARPS;     // the warp that watches the mbarriers
+  static constexpr int THREADS = 64 + 32 * EPI_WARPS + 32;
   static constexpr bool KAHAN = T <= 32;
   static constexpr int CTAS_PER_SM = T == 16 ? 2 : 1;
   static constexpr int STAGES = CTAS_PER_SM == 2 ? 6 : 8;
@@ -81,13 +84,15 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmH, int first_slot, int slot_stri
   uint64_t *empty = full + C::STAGES;
   uint64_t *acc_full = empty + C::STAGES;
   uint64_t *acc_empty = acc_full + C::NB;
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(acc_empty + C::NB);
+  uint64_t *mma_done = acc_empty + C::NB;
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(mma_done + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     for (int b = 0; b < C::NB; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 32 * C::EPI_WARPS); }
+    mbar_init(mma_done, 1);
     *abort_flag = 0;
     fence_barrier_init();
     prefetch_tmap(&tmH);
@@ -126,20 +131,21 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmH, int first_slot, int slot_stri
         }
       }
     }
-  } else if (warp == 1) {
-    if (lane == 0) {  // ---------------- MMA issuer
-      constexpr uint32_t idesc = idesc_f16(BF16, false, false, 128, 128);
-      int slot = 0; uint32_t ph = 0; int grp = 0;
-      for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x) {
-        for (int g0 = 0; g0 < stages_per_unit && !*abort_flag; g0 += C::GROUP, ++grp) {
-          const int n = stages_per_unit - g0 < C::GROUP ? stages_per_unit - g0 : C::GROUP;
-          const int buf = grp % C::NB;
-          if (!mbar_wait(&acc_empty[buf], ((grp / C::NB) & 1) ^ 1)) { fail(); break; }
+  } else if (warp == 1) {  // ---------------- MMA issuer
+    // The whole warp runs the loop (named barriers are per warp) and lane 0 issues. Stage k
+    // waits on named barrier 1 + k % STAGES, which the waiter passes once the stage's data has
+    // landed and, for a group's first stage, its accumulator buffer is free; the loop has no
+    // exit of its own, so its barrier steps pair one to one with the waiter's.
+    constexpr uint32_t idesc = idesc_f16(BF16, false, false, 128, 128);
+    int slot = 0, grp = 0;
+    for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
+      for (int g0 = 0; g0 < stages_per_unit; g0 += C::GROUP, ++grp) {
+        const int n = stages_per_unit - g0 < C::GROUP ? stages_per_unit - g0 : C::GROUP;
+        const uint32_t d = tmem + (grp % C::NB) * 128;
+        for (int i = 0; i < n; ++i) {
+          named_sync(1 + slot, 64);
           fence_after_sync();
-          const uint32_t d = tmem + buf * 128;
-          for (int i = 0; i < n; ++i) {
-            if (!mbar_wait(&full[slot], ph)) { fail(); break; }
-            fence_after_sync();
+          if (lane == 0) {
             const uint32_t base = smem_u32(stages + slot * C::STAGE_BYTES);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -147,9 +153,42 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmH, int first_slot, int slot_stri
               mma_f16(d, desc, desc, idesc, (i > 0 || k > 0) ? 1u : 0u);
             }
             mma_commit(&empty[slot]);
-            if (++slot == C::STAGES) { slot = 0; ph ^= 1; }
           }
-          mma_commit(&acc_full[buf]);
+          __syncwarp();
+          if (++slot == C::STAGES) slot = 0;
+        }
+        if (lane == 0) mma_commit(&acc_full[grp % C::NB]);
+        __syncwarp();
+      }
+    }
+    // every MMA has completed before the tensor memory is freed (also after an abort)
+    if (lane == 0) mma_commit(mma_done);
+    __syncwarp();
+    mbar_wait(mma_done, 0);
+  } else if (warp == C::WAITER) {  // ---------------- waiter
+    // Stage k's release needs its TMA data (full) and, for a group's first stage, the
+    // accumulator buffer back from the epilogue (acc_empty). Normally it runs ahead of the MMA
+    // warp by fewer than STAGES stages (a stage's data needs its slot released by the MMAs of
+    // the stage STAGES before), so each named barrier has at most one pending arrival. After a
+    // failed wait or an abort elsewhere it stops waiting and steps in lock-step (bar.sync), so
+    // the MMA warp still completes its loop.
+    int slot = 0, grp = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
+      for (int g0 = 0; g0 < stages_per_unit; g0 += C::GROUP, ++grp) {
+        const int n = stages_per_unit - g0 < C::GROUP ? stages_per_unit - g0 : C::GROUP;
+        if (ok) ok = !__any_sync(0xffffffffu, *abort_flag != 0) &&
+                     __all_sync(0xffffffffu, mbar_wait(&acc_empty[grp % C::NB], ((grp / C::NB) & 1) ^ 1));
+        for (int i = 0; i < n; ++i) {
+          if (ok) ok = !__any_sync(0xffffffffu, *abort_flag != 0) && __all_sync(0xffffffffu, mbar_wait(&full[slot], ph));
+          if (ok) {
+            named_arrive(1 + slot, 64);
+          } else {
+            if (lane == 0 && !*abort_flag) fail();
+            named_sync(1 + slot, 64);
+          }
+          if (++slot == C::STAGES) { slot = 0; ph ^= 1; }
         }
       }
     }
@@ -232,11 +271,12 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmH, int first_slot, int slot_stri
 // The Fresnel transform of Eq. 1 is unitary per frame, so C = H^{t*} H = I^T I exactly: the
 // covariance can be formed from the uint16 frames themselves, exactly, at half the bytes of
 // the 16-bit holograms. Each value is split I = 256 hi + lo (hi, lo < 256, exact in FP16); a
-// converter warpgroup turns each TMA-loaded uint16 tile (T frames x 64 pixels) into the
-// operand rows [hi_0; lo_0; hi_1; lo_1; ...] (2T rows, K-major, 128-byte swizzle: the layout
-// the hologram Gram reads), and the same stacked 128 x 128 MMA forms the 2T x 2T Gram G of
-// those rows. Products are < 2^16 and a stage sums 64 of them per element, so every
-// accumulator value is an exact integer below 2^23; the epilogue adds each drained value to
+// converter warpgroup turns each TMA-loaded uint16 tile (T frames x 256 pixels: each frame
+// read as one 512-byte run) into the operand rows [hi_0; lo_0; hi_1; lo_1; ...] of 64-pixel
+// chunks (2T rows, K-major, 128-byte swizzle: the layout the hologram Gram reads), and the
+// same stacked 128 x 128 MMA forms the 2T x 2T Gram G of those rows. Products are < 2^16 and
+// a drain sums 128 of them per element (two operand stages), so every drained accumulator
+// value is an exact integer below 2^23; the epilogue adds each drained value to
 // a 32-bit integer sum (through the FP32 mantissa: bits(v + 2^23) = 0x4B000000 + v), which is
 // exact while a unit's sum stays below 2^32 (<= 65536 pixels per unit). The reduction then
 // forms C = 65536 G_hh + 256 (G_hl + G_lh) + G_ll in FP64, exact while sum I^2 < 2^53.
@@ -244,16 +284,27 @@ template <int T>
 struct RawCfg {
   static constexpr int M2 = 2 * T;
   static constexpr int R = 128 / M2;               // 64-pixel chunks stacked per stage
-  static constexpr int PIX = 64 * R;               // pixels per stage
+  static constexpr int PIX = 64 * R;               // pixels per operand stage
   static constexpr int OP_BYTES = 128 * 128;       // operand stage: 128 rows x 64 pixels, FP16
-  static constexpr int RAW_BYTES = R * T * 128;    // uint16 stage: R boxes of T frames x 64 pixels
+  // uint16 stage: one TMA box of T frames x BOXP pixels (rows 512 bytes apart, no swizzle), so
+  // each frame is read in 512-byte runs; it feeds OPS_PER_RAW operand stages
+  static constexpr int BOXP = 256;
+  static constexpr int RAW_BYTES = BOXP * T * 2;
+  static constexpr int OPS_PER_RAW = BOXP / PIX;
+  // operand stages accumulated per TMEM drain: a drained value sums GROUP * 64 byte products
+  // (< 2^16 each), which must stay below 2^23 for the epilogue's exact integer sums
+  static constexpr int GROUP = 2;
+  static_assert(GROUP * 64 * 255 * 255 < (1 << 23), "drained sums must stay exact");
   static constexpr int NCOL = T == 64 ? 64 : 32;
   static constexpr int EPI_WARPS = 4 * (M2 / NCOL);
-  static constexpr int CONV_THREADS = 128;
-  static constexpr int THREADS = 64 + CONV_THREADS + 32 * EPI_WARPS;
+  // converter threads: two warps per SM sub-partition where the registers allow (T = 32; T = 16
+  // runs two CTAs per SM, T = 64 needs more registers a thread)
+  static constexpr int CONV_THREADS = T == 32 ? 256 : 128;
+  static constexpr int WAITER = 2 + CONV_THREADS / 32 + EPI_WARPS;  // watches the mbarriers
+  static constexpr int THREADS = 64 + CONV_THREADS + 32 * EPI_WARPS + 32;
   static constexpr int CTAS_PER_SM = T == 16 ? 2 : 1;
   static constexpr int OP_STAGES = CTAS_PER_SM == 2 ? 3 : 6;
-  static constexpr int RAW_STAGES = CTAS_PER_SM == 2 ? 4 : 8;
+  static constexpr int RAW_STAGES = CTAS_PER_SM == 2 ? 4 : 98304 / RAW_BYTES;  // 6 (T = 32), 3 (T = 64)
   static constexpr int NB = CTAS_PER_SM == 2 ? 2 : 4;
   static constexpr int TMEM_COLS = 128 * NB;
   static constexpr size_t SMEM = OP_STAGES * OP_BYTES + RAW_STAGES * RAW_BYTES + 1024 + 512;
@@ -267,9 +318,12 @@ int gram_raw_units(long long npix) {
   return (int)(u > need ? u : need);
 }
 
-__device__ __forceinline__ uint32_t byte_pair_to_half2(uint32_t w) {
-  // two bytes in the low byte of each 16-bit lane -> FP16 1024 + b (exact), then - 1024
-  const uint32_t h = w | 0x64006400u;
+// Bytes SEL picks of w (one per 16-bit lane; 0x4341: bytes 1 and 3, 0x4240: bytes 0 and 2) as
+// FP16 values: each byte b goes under the exponent byte 0x64 (one byte permute), which is
+// FP16 1024 + b exactly, and 1024 is subtracted.
+template <uint32_t SEL>
+__device__ __forceinline__ uint32_t bytes_to_half2(uint32_t w) {
+  const uint32_t h = __byte_perm(w, 0x64646464u, SEL);
   __half2 x = *reinterpret_cast<const __half2 *>(&h);
   x = __hsub2(x, __half2(__float2half(1024.f), __float2half(1024.f)));
   return *reinterpret_cast<uint32_t *>(&x);
@@ -288,7 +342,8 @@ k_gram_raw_tc(const __grid_constant__ CUtensorMap tmI, int first_frame, int wind
   uint64_t *raw_full = bars, *raw_empty = raw_full + C::RAW_STAGES;
   uint64_t *op_full = raw_empty + C::RAW_STAGES, *op_empty = op_full + C::OP_STAGES;
   uint64_t *acc_full = op_empty + C::OP_STAGES, *acc_empty = acc_full + C::NB;
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(acc_empty + C::NB);
+  uint64_t *mma_done = acc_empty + C::NB;
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(mma_done + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -296,6 +351,7 @@ k_gram_raw_tc(const __grid_constant__ CUtensorMap tmI, int first_frame, int wind
     for (int s = 0; s < C::RAW_STAGES; ++s) { mbar_init(&raw_full[s], 1); mbar_init(&raw_empty[s], C::CONV_THREADS); }
     for (int s = 0; s < C::OP_STAGES; ++s) { mbar_init(&op_full[s], C::CONV_THREADS); mbar_init(&op_empty[s], 1); }
     for (int b = 0; b < C::NB; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 32 * C::EPI_WARPS); }
+    mbar_init(mma_done, 1);
     *abort_flag = 0;
     fence_barrier_init();
     prefetch_tmap(&tmI);
@@ -317,13 +373,10 @@ k_gram_raw_tc(const __grid_constant__ CUtensorMap tmI, int first_frame, int wind
         const int w = u / units_pw, uu = u % units_pw;
         const int f0 = first_frame + w * window_stride;
         const long long p0 = (long long)uu * stages_per_unit * C::PIX;
-        for (int st = 0; st < stages_per_unit; ++st) {
+        for (int st = 0; st < stages_per_unit / C::OPS_PER_RAW; ++st) {
           if (!mbar_wait(&raw_empty[slot], ph ^ 1)) { fail(); break; }
           mbar_arrive_expect_tx(&raw_full[slot], C::RAW_BYTES);
-          uint8_t *dst = raws + slot * C::RAW_BYTES;
-#pragma unroll
-          for (int c = 0; c < C::R; ++c)
-            tma_load_2d(dst + c * T * 128, &tmI, &raw_full[slot], (int)(p0 + st * C::PIX + c * 64), f0);
+          tma_load_2d(raws + slot * C::RAW_BYTES, &tmI, &raw_full[slot], (int)(p0 + st * C::BOXP), f0);
           ++issued;
           if (++slot == C::RAW_STAGES) { slot = 0; ph ^= 1; }
         }
@@ -335,26 +388,55 @@ k_gram_raw_tc(const __grid_constant__ CUtensorMap tmI, int first_frame, int wind
         }
       }
     }
-  } else if (warp == 1) {
-    if (lane == 0) {  // ---------------- MMA issuer
-      constexpr uint32_t idesc = idesc_f16(false, false, false, 128, 128);
-      int slot = 0; uint32_t ph = 0; int grp = 0;
-      for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x) {
-        for (int st = 0; st < stages_per_unit && !*abort_flag; ++st, ++grp) {
-          const int buf = grp % C::NB;
-          if (!mbar_wait(&acc_empty[buf], ((grp / C::NB) & 1) ^ 1)) { fail(); break; }
+  } else if (warp == 1) {  // ---------------- MMA issuer (the whole warp; lane 0 issues)
+    // Operand stage k waits on named barrier 1 + k % OP_STAGES, passed by the waiter once the
+    // converters have filled it and, for a group's first stage, the accumulator is free; no
+    // shared-memory step inside the loop (see named_sync) and no exit of its own.
+    constexpr uint32_t idesc = idesc_f16(false, false, false, 128, 128);
+    int slot = 0, grp = 0;
+    for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
+      for (int g0 = 0; g0 < stages_per_unit; g0 += C::GROUP, ++grp) {
+        const int n = stages_per_unit - g0 < C::GROUP ? stages_per_unit - g0 : C::GROUP;
+        const uint32_t d = tmem + (grp % C::NB) * 128;
+        for (int i = 0; i < n; ++i) {
+          named_sync(1 + slot, 64);
           fence_after_sync();
-          const uint32_t d = tmem + buf * 128;
-          if (!mbar_wait(&op_full[slot], ph)) { fail(); break; }
-          fence_after_sync();
-          const uint32_t base = smem_u32(ops + slot * C::OP_BYTES);
+          if (lane == 0) {
+            const uint32_t base = smem_u32(ops + slot * C::OP_BYTES);
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const uint64_t desc = smem_desc(base + 32 * k, 16, 1024, kSwizzle128);
-            mma_f16(d, desc, desc, idesc, k > 0 ? 1u : 0u);
+            for (int k = 0; k < 4; ++k) {
+              const uint64_t desc = smem_desc(base + 32 * k, 16, 1024, kSwizzle128);
+              mma_f16(d, desc, desc, idesc, (i > 0 || k > 0) ? 1u : 0u);
+            }
+            mma_commit(&op_empty[slot]);
           }
-          mma_commit(&op_empty[slot]);
-          mma_commit(&acc_full[buf]);
+          __syncwarp();
+          if (++slot == C::OP_STAGES) slot = 0;
+        }
+        if (lane == 0) mma_commit(&acc_full[grp % C::NB]);
+        __syncwarp();
+      }
+    }
+    if (lane == 0) mma_commit(mma_done);  // every MMA completes before the tensor memory is freed
+    __syncwarp();
+    mbar_wait(mma_done, 0);
+  } else if (warp == C::WAITER) {  // ---------------- waiter (see k_gram_tc)
+    int slot = 0, grp = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
+      for (int g0 = 0; g0 < stages_per_unit; g0 += C::GROUP, ++grp) {
+        const int n = stages_per_unit - g0 < C::GROUP ? stages_per_unit - g0 : C::GROUP;
+        if (ok) ok = !__any_sync(0xffffffffu, *abort_flag != 0) &&
+                     __all_sync(0xffffffffu, mbar_wait(&acc_empty[grp % C::NB], ((grp / C::NB) & 1) ^ 1));
+        for (int i = 0; i < n; ++i) {
+          if (ok) ok = !__any_sync(0xffffffffu, *abort_flag != 0) && __all_sync(0xffffffffu, mbar_wait(&op_full[slot], ph));
+          if (ok) {
+            named_arrive(1 + slot, 64);
+          } else {
+            if (lane == 0 && !*abort_flag) fail();
+            named_sync(1 + slot, 64);
+          }
           if (++slot == C::OP_STAGES) { slot = 0; ph ^= 1; }
         }
       }
@@ -364,31 +446,35 @@ k_gram_raw_tc(const __grid_constant__ CUtensorMap tmI, int first_frame, int wind
     int rslot = 0, oslot = 0; uint32_t rph = 0, oph = 0;
     for (int u = blockIdx.x; u < total_units && !__any_sync(0xffffffffu, *abort_flag); u += gridDim.x) {
       bool ok = true;
-      for (int st = 0; st < stages_per_unit; ++st) {
+      for (int st = 0; st < stages_per_unit / C::OPS_PER_RAW && ok; ++st) {
         if (!__all_sync(0xffffffffu, mbar_wait(&raw_full[rslot], rph))) { fail(); ok = false; break; }
+        for (int o = 0; o < C::OPS_PER_RAW; ++o) {
         if (!__all_sync(0xffffffffu, mbar_wait(&op_empty[oslot], oph ^ 1))) { fail(); ok = false; break; }
-        const uint8_t *src = raws + rslot * C::RAW_BYTES;
+        // frame t's pixels of this operand stage: 512-byte rows, operand stage o at o * PIX pixels
+        const uint8_t *src = raws + rslot * C::RAW_BYTES + o * C::PIX * 2;
         uint8_t *dst = ops + oslot * C::OP_BYTES;
 #pragma unroll
         for (int it = 0; it < C::R * T * 8 / C::CONV_THREADS; ++it) {
           const int item = ct + it * C::CONV_THREADS;   // (chunk c, frame t, 16-byte column j)
           const int j = item & 7, t = (item >> 3) % T, c = (item >> 3) / T;
-          const uint4 v = *reinterpret_cast<const uint4 *>(src + c * T * 128 + t * 128 + ((j ^ (t & 7)) << 4));
+          const uint4 v = *reinterpret_cast<const uint4 *>(src + t * (C::BOXP * 2) + c * 128 + (j << 4));
           uint4 hi, lo;
-          hi.x = byte_pair_to_half2((v.x >> 8) & 0x00FF00FFu); lo.x = byte_pair_to_half2(v.x & 0x00FF00FFu);
-          hi.y = byte_pair_to_half2((v.y >> 8) & 0x00FF00FFu); lo.y = byte_pair_to_half2(v.y & 0x00FF00FFu);
-          hi.z = byte_pair_to_half2((v.z >> 8) & 0x00FF00FFu); lo.z = byte_pair_to_half2(v.z & 0x00FF00FFu);
-          hi.w = byte_pair_to_half2((v.w >> 8) & 0x00FF00FFu); lo.w = byte_pair_to_half2(v.w & 0x00FF00FFu);
+          hi.x = bytes_to_half2<0x4341u>(v.x); lo.x = bytes_to_half2<0x4240u>(v.x);
+          hi.y = bytes_to_half2<0x4341u>(v.y); lo.y = bytes_to_half2<0x4240u>(v.y);
+          hi.z = bytes_to_half2<0x4341u>(v.z); lo.z = bytes_to_half2<0x4240u>(v.z);
+          hi.w = bytes_to_half2<0x4341u>(v.w); lo.w = bytes_to_half2<0x4240u>(v.w);
           const int rh = c * C::M2 + 2 * t, rl = rh + 1;  // operand rows of hi_t and lo_t
           *reinterpret_cast<uint4 *>(dst + rh * 128 + ((j ^ (rh & 7)) << 4)) = hi;
           *reinterpret_cast<uint4 *>(dst + rl * 128 + ((j ^ (rl & 7)) << 4)) = lo;
         }
         // the tensor cores read the operand through the async proxy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&raw_empty[rslot]);
         mbar_arrive(&op_full[oslot]);
-        if (++rslot == C::RAW_STAGES) { rslot = 0; rph ^= 1; }
         if (++oslot == C::OP_STAGES) { oslot = 0; oph ^= 1; }
+        }
+        if (!ok) break;
+        mbar_arrive(&raw_empty[rslot]);
+        if (++rslot == C::RAW_STAGES) { rslot = 0; rph ^= 1; }
       }
       if (!ok) break;
     }
@@ -406,7 +492,8 @@ k_gram_raw_tc(const __grid_constant__ CUtensorMap tmI, int first_frame, int wind
 #pragma unroll
       for (int j = 0; j < C::NCOL; ++j) acc[j] = 0u;
       bool ok = true;
-      for (int st = 0; st < stages_per_unit; ++st, ++grp) {
+      uint32_t drains = 0;
+      for (int g0 = 0; g0 < stages_per_unit; g0 += C::GROUP, ++grp, ++drains) {
         const int buf = grp % C::NB;
         if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (grp / C::NB) & 1))) {
           fail(); ok = false; break;
@@ -425,7 +512,7 @@ k_gram_raw_tc(const __grid_constant__ CUtensorMap tmI, int first_frame, int wind
       }
       if (!ok) break;
       // remove the 0x4B000000 of every drained value (mod 2^32)
-      const uint32_t bias = (uint32_t)stages_per_unit * 0x4B000000u;
+      const uint32_t bias = drains * 0x4B000000u;
       double *dst = part + ((long long)(w * units_pw + uu) * C::R + c) * C::M2 * C::M2 +
                     (long long)r * C::M2 + ch * C::NCOL;
 #pragma unroll
@@ -805,19 +892,21 @@ dh_status gram_raw_t(Plan &p, const uint16_t *frames, long long frame_stride, in
                                      cudaSharedmemCarveoutMaxShared));
     attr = true;
   }
-  // uint16 frames as a 2-D tensor: npix x n_frames, box 64 pixels x T frames, 128-byte swizzle
+  // uint16 frames as a 2-D tensor: npix x n_frames, box BOXP pixels x T frames, no swizzle
   auto fn = encode_fn();
   if (!fn) return DH_ERR_CUDA;
   CUtensorMap tm;
   const cuuint64_t dims[2] = {(cuuint64_t)p.npix, (cuuint64_t)n_frames};
   const cuuint64_t strides[1] = {(cuuint64_t)frame_stride * 2};
-  const cuuint32_t box[2] = {64, (cuuint32_t)T};
+  const cuuint32_t box[2] = {(cuuint32_t)C::BOXP, (cuuint32_t)T};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<uint16_t *>(frames), dims, strides, box,
-                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return DH_ERR_CUDA;
   const int units_pw = gram_raw_units(p.npix);
+  // a unit's pixels: a whole number of uint16 boxes (npix >= 256, both powers of two)
+  if ((p.npix / units_pw) % C::BOXP != 0) return DH_ERR_UNSUPPORTED_SIZE;
   const int stages_per_unit = (int)(p.npix / units_pw / C::PIX);
   const int total = n_windows * units_pw;
   int per_sm = 0;
