@@ -13,7 +13,9 @@
 // times in all rather than once per window containing it.
 //
 // Pipeline (one CTA per SM): warp 0 issues TMA loads of the 128-row x 64-pixel boxes of a
-// stage (a box past the last slot reads zeros), warp 1 issues the MMAs, eight epilogue warps
+// stage (a box past the last slot reads zeros), warp 1 issues the MMAs (released stage by
+// stage through named barriers by a waiter warp, so that it takes no shared-memory step in its
+// loop: see named_sync), eight epilogue warps
 // (TMEM lane quarter x column half) drain the accumulator every GROUP stages into FP32 unit
 // sums (short TMEM accumulations keep the tensor cores' truncation bias near 5e-7) and write
 // FP64 partials per (block, product, split-K unit); a reduction sums the units in FP64 and an
@@ -38,7 +40,8 @@ struct BandCfg {
   static constexpr int GROUP = 2;                    // stages per TMEM drain
   static constexpr int NB = 4;                       // accumulators of 128 columns
   static constexpr int EPI_WARPS = 8;                // lane quarter x column half (64 columns)
-  static constexpr int THREADS = 64 + 32 * EPI_WARPS;
+  static constexpr int WAITER = 2 + EPI_WARPS;       // watches the mbarriers for the MMA warp
+  static constexpr int THREADS = 64 + 32 * EPI_WARPS + 32;
   static constexpr size_t SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 };
 
@@ -56,13 +59,15 @@ k_band_gram(const __grid_constant__ CUtensorMap tm, int row0, int n_blocks, int 
   uint64_t *empty = full + C::STAGES;
   uint64_t *acc_full = empty + C::STAGES;
   uint64_t *acc_empty = acc_full + C::NB;
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(acc_empty + C::NB);
+  uint64_t *mma_done = acc_empty + C::NB;
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(mma_done + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     for (int b = 0; b < C::NB; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 32 * C::EPI_WARPS); }
+    mbar_init(mma_done, 1);
     *abort_flag = 0;
     fence_barrier_init();
     prefetch_tmap(&tm);
@@ -101,21 +106,19 @@ k_band_gram(const __grid_constant__ CUtensorMap tm, int row0, int n_blocks, int 
         }
       }
     }
-  } else if (warp == 1) {
-    if (lane == 0) {  // ---------------- MMA issuer: D[128 x 128] += X_b x (X_b or X_b+1)^T
-      constexpr uint32_t idesc = idesc_f16(BF16, false, false, 128, 128);
-      int slot = 0; uint32_t ph = 0; int grp = 0;
-      for (int wu = blockIdx.x; wu < total_units && !*abort_flag; wu += gridDim.x) {
-        const int h = (wu / units) & 1;
-        for (int g0 = 0; g0 < stages_per_unit && !*abort_flag; g0 += C::GROUP, ++grp) {
-          const int n = stages_per_unit - g0 < C::GROUP ? stages_per_unit - g0 : C::GROUP;
-          const int buf = grp % C::NB;
-          if (!mbar_wait(&acc_empty[buf], ((grp / C::NB) & 1) ^ 1)) { fail(); break; }
+  } else if (warp == 1) {  // ---------------- MMA issuer: D[128 x 128] += X_b x (X_b or X_b+1)^T
+    // whole warp, lane 0 issues; stage k waits on named barrier 1 + k % STAGES (the waiter)
+    constexpr uint32_t idesc = idesc_f16(BF16, false, false, 128, 128);
+    int slot = 0, grp = 0;
+    for (int wu = blockIdx.x; wu < total_units; wu += gridDim.x) {
+      const int h = (wu / units) & 1;
+      for (int g0 = 0; g0 < stages_per_unit; g0 += C::GROUP, ++grp) {
+        const int n = stages_per_unit - g0 < C::GROUP ? stages_per_unit - g0 : C::GROUP;
+        const uint32_t d = tmem + (grp % C::NB) * 128;
+        for (int i = 0; i < n; ++i) {
+          named_sync(1 + slot, 64);
           fence_after_sync();
-          const uint32_t d = tmem + buf * 128;
-          for (int i = 0; i < n; ++i) {
-            if (!mbar_wait(&full[slot], ph)) { fail(); break; }
-            fence_after_sync();
+          if (lane == 0) {
             const uint32_t base = smem_u32(stages + slot * C::STAGE_BYTES);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -124,9 +127,38 @@ k_band_gram(const __grid_constant__ CUtensorMap tm, int row0, int n_blocks, int 
               mma_f16(d, da, db, idesc, (i > 0 || k > 0) ? 1u : 0u);
             }
             mma_commit(&empty[slot]);
-            if (++slot == C::STAGES) { slot = 0; ph ^= 1; }
           }
-          mma_commit(&acc_full[buf]);
+          __syncwarp();
+          if (++slot == C::STAGES) slot = 0;
+        }
+        if (lane == 0) mma_commit(&acc_full[grp % C::NB]);
+        __syncwarp();
+      }
+    }
+    if (lane == 0) mma_commit(mma_done);  // every MMA completes before the tensor memory is freed
+    __syncwarp();
+    mbar_wait(mma_done, 0);
+  } else if (warp == C::WAITER) {  // ---------------- waiter
+    // Fewer than STAGES stages ahead of the MMA warp (a stage's data needs its slot released by
+    // the MMAs of the stage STAGES before): one pending arrival per named barrier at most. After
+    // a failed wait or an abort it steps in lock-step (bar.sync).
+    int slot = 0, grp = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int wu = blockIdx.x; wu < total_units; wu += gridDim.x) {
+      for (int g0 = 0; g0 < stages_per_unit; g0 += C::GROUP, ++grp) {
+        const int n = stages_per_unit - g0 < C::GROUP ? stages_per_unit - g0 : C::GROUP;
+        if (ok) ok = !__any_sync(0xffffffffu, *abort_flag != 0) &&
+                     __all_sync(0xffffffffu, mbar_wait(&acc_empty[grp % C::NB], ((grp / C::NB) & 1) ^ 1));
+        for (int i = 0; i < n; ++i) {
+          if (ok) ok = !__any_sync(0xffffffffu, *abort_flag != 0) && __all_sync(0xffffffffu, mbar_wait(&full[slot], ph));
+          if (ok) {
+            named_arrive(1 + slot, 64);
+          } else {
+            if (lane == 0 && !*abort_flag) fail();
+            named_sync(1 + slot, 64);
+          }
+          if (++slot == C::STAGES) { slot = 0; ph ^= 1; }
         }
       }
     }

@@ -12,7 +12,9 @@
 // projection there is no subtraction: the power is Eq. 7's sum over the kept columns.
 //
 // Roles: warp 0 issues TMA, warp 1 the MMAs, warps 2-5 (one per TMEM lane quarter) drain
-// TMEM. Waits are bounded (DH_FLAG_WAIT_TIMEOUT).
+// TMEM, warp 6 waits on the mbarriers and releases the MMA warp tile by tile through named
+// barriers (so the MMA warp takes no shared-memory step in its loop: see named_sync). Waits are
+// bounded (DH_FLAG_WAIT_TIMEOUT).
 #include "dh_internal.cuh"
 #include "tc_sm100.cuh"
 
@@ -24,7 +26,8 @@ using namespace tc;
 constexpr int kFsG = 7;                     // windows per group
 constexpr int kFsCpw = 34;                  // real columns per window (17 bins, Re and Im)
 constexpr int kFsNpad = 240;                // kFsG x kFsCpw = 238, rounded up to 16
-constexpr int kFsThreads = 64 + 128;
+constexpr int kFsWaiter = 6;                // warp that watches the mbarriers (after 4 epilogue warps)
+constexpr int kFsThreads = 64 + 128 + 32;
 constexpr int kFsMaxStages = 4;
 constexpr size_t kFsSmemLimit = 232448;
 constexpr double kFsScale = 1024.0;         // W scaled by 2^10 (the lo part stays normal)
@@ -73,7 +76,8 @@ k_fourier_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
   uint64_t *acc_full = empty + kFsMaxStages;
   uint64_t *acc_empty = acc_full + 2;
   uint64_t *bfull = acc_empty + 2;
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bfull + 1);
+  uint64_t *mma_done = bfull + 1;
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(mma_done + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -89,6 +93,7 @@ k_fourier_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
     for (int i = 0; i < stages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 128); }
     mbar_init(bfull, 1);
+    mbar_init(mma_done, 1);
     *abort_flag = 0;
     fence_barrier_init();
     prefetch_tmap(&tmA);
@@ -130,20 +135,20 @@ k_fourier_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
         mbar_wait(bfull, 0);
       }
     }
-  } else if (warp == 1) {
-    if (lane == 0) {  // ---------------- MMA issuer: D[128 px x kFsNpad] = span^T x operand^T
-      const uint32_t idesc = idesc_f16(false, true, false, 128, kFsNpad);
-      const int k_steps = rows / 16;
-      const int half_bytes = img_bytes / 2;
-      int slot = 0, it = 0; uint32_t ph = 0;
-      bool ok = mbar_wait(bfull, 0);
-      if (!ok) fail();
-      for (long long u = u_begin; u < u_end && ok && !*abort_flag; ++u) {
-        for (int i = 0; i < 8; ++i, ++it) {
-          const int buf = it & 1;
-          if (!mbar_wait(&acc_empty[buf], ((it >> 1) & 1) ^ 1)) { fail(); ok = false; break; }
-          if (!mbar_wait(&full[slot], ph)) { fail(); ok = false; break; }
-          fence_after_sync();
+  } else if (warp == 1) {  // ---------------- MMA issuer: D[128 px x kFsNpad] = span^T x operand^T
+    // The whole warp runs the loop and lane 0 issues; tile k waits on named barrier
+    // 1 + k % stages, which the waiter passes once the tile has landed and its accumulator
+    // buffer is free (no shared-memory step inside the loop: see named_sync).
+    const uint32_t idesc = idesc_f16(false, true, false, 128, kFsNpad);
+    const int k_steps = rows / 16;
+    const int half_bytes = img_bytes / 2;
+    int slot = 0, it = 0;
+    for (long long u = u_begin; u < u_end; ++u) {
+      for (int i = 0; i < 8; ++i, ++it) {
+        const int buf = it & 1;
+        named_sync(1 + slot, 64);
+        fence_after_sync();
+        if (lane == 0) {
           const uint32_t d = tmem + buf * 256;
           const uint64_t adesc0 = smem_desc(smem_u32(stage0 + slot * stage_bytes), rows * 128, 1024, kSwizzle128);
           for (int half = 1; half >= 0; --half) {  // small lo products first
@@ -156,8 +161,34 @@ k_fourier_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
           }
           mma_commit(&empty[slot]);
           mma_commit(&acc_full[buf]);
-          if (++slot == stages) { slot = 0; ph ^= 1; }
         }
+        __syncwarp();
+        if (++slot == stages) slot = 0;
+      }
+    }
+    if (lane == 0) mma_commit(mma_done);  // every MMA completes before the tensor memory is freed
+    __syncwarp();
+    mbar_wait(mma_done, 0);
+  } else if (warp == kFsWaiter) {  // ---------------- waiter
+    // Runs ahead of the MMA warp by fewer than `stages` tiles (a tile's data needs its slot
+    // released by the MMAs of the tile `stages` before), so each named barrier has at most one
+    // pending arrival; after a failed wait or an abort it steps in lock-step (bar.sync).
+    int slot = 0, it = 0;
+    uint32_t ph = 0;
+    bool ok = __all_sync(0xffffffffu, mbar_wait(bfull, 0));  // the operand, once
+    for (long long u = u_begin; u < u_end; ++u) {
+      for (int i = 0; i < 8; ++i, ++it) {
+        const int buf = it & 1;
+        if (ok) ok = !__any_sync(0xffffffffu, *abort_flag != 0) &&
+                     __all_sync(0xffffffffu, mbar_wait(&acc_empty[buf], ((it >> 1) & 1) ^ 1)) &&
+                     __all_sync(0xffffffffu, mbar_wait(&full[slot], ph));
+        if (ok) {
+          named_arrive(1 + slot, 64);
+        } else {
+          if (lane == 0 && !*abort_flag) fail();
+          named_sync(1 + slot, 64);
+        }
+        if (++slot == stages) { slot = 0; ph ^= 1; }
       }
     }
   } else {  // ------------------------------ epilogue: lane quarter q, all 7 windows

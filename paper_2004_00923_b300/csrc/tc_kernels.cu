@@ -539,7 +539,8 @@ struct ProjCfg {
   static constexpr int B_ROW = KB * 2;                     // bytes
   static constexpr int B_MAX = 2 * M2 * M2 * 2;            // hi + lo, Npad <= 2T
   static constexpr int TMEM_COLS = M2 <= 32 ? 64 : 2 * M2; // two accumulators
-  static constexpr int THREADS = 64 + 128;
+  static constexpr int WAITER = 6;                         // after the 4 epilogue warps
+  static constexpr int THREADS = 64 + 128 + 32;
   static constexpr size_t SMEM = STAGES * A_BYTES + B_MAX + 1024 + 256;
 };
 
@@ -574,7 +575,8 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
   uint64_t *acc_empty = acc_full + 2;
   uint64_t *bfull = acc_empty + 2;
   uint64_t *bempty = bfull + 1;
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bempty + 1);
+  uint64_t *mma_done = bempty + 1;
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(mma_done + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -592,6 +594,7 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
     for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 128); }
     mbar_init(bfull, 1);
     mbar_init(bempty, 1);
+    mbar_init(mma_done, 1);
     *abort_flag = 0;
     fence_barrier_init();
     prefetch_tmap(&tmH);
@@ -642,22 +645,18 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
         if (b_pending) mbar_wait(bfull, bph ^ 1);
       }
     }
-  } else if (warp == 1) {
-    if (lane == 0) {  // ---------------- MMA issuer
-      const uint32_t idesc = idesc_f16(BF16, true, false, 128, Npad);
-      int slot = 0; uint32_t ph = 0, bph = 0;
-      int cur_w = -1, it = 0;
-      for (long long t = t_begin; t < t_end && !*abort_flag; ++t, ++it) {
-        const int w = (int)(t / tiles_pw);
-        if (w != cur_w) {
-          if (!mbar_wait(bfull, bph)) { fail(); break; }
-          bph ^= 1;
-          cur_w = w;
-        }
-        const int buf = it & 1;
-        if (!mbar_wait(&acc_empty[buf], ((it >> 1) & 1) ^ 1)) { fail(); break; }
-        if (!mbar_wait(&full[slot], ph)) { fail(); break; }
-        fence_after_sync();
+  } else if (warp == 1) {  // ---------------- MMA issuer (whole warp, lane 0 issues)
+    // Tile k waits on named barrier 1 + k % STAGES, passed by the waiter once the tile has
+    // landed, its accumulator buffer is free and (first tile of a window) the window's operand
+    // is in place; no shared-memory step inside the loop (see named_sync).
+    const uint32_t idesc = idesc_f16(BF16, true, false, 128, Npad);
+    int slot = 0, it = 0;
+    for (long long t = t_begin; t < t_end; ++t, ++it) {
+      const int w = (int)(t / tiles_pw);
+      const int buf = it & 1;
+      named_sync(1 + slot, 64);
+      fence_after_sync();
+      if (lane == 0) {
         const uint32_t d = tmem + buf * C::M2;
         const uint32_t a0 = smem_u32(stages + slot * C::A_BYTES);
         const uint32_t b0 = smem_u32(bsm);
@@ -679,10 +678,40 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
         }
         mma_commit(&empty[slot]);
         mma_commit(&acc_full[buf]);
-        if (++slot == C::STAGES) { slot = 0; ph ^= 1; }
         const bool last_of_window = (t + 1 == t_end) || ((int)((t + 1) / tiles_pw) != w);
         if (last_of_window) mma_commit(bempty);
       }
+      __syncwarp();
+      if (++slot == C::STAGES) slot = 0;
+    }
+    if (lane == 0) mma_commit(mma_done);  // every MMA completes before the tensor memory is freed
+    __syncwarp();
+    mbar_wait(mma_done, 0);
+  } else if (warp == C::WAITER) {  // ---------------- waiter
+    // Fewer than STAGES tiles ahead of the MMA warp (a tile's data needs its slot released by
+    // the MMAs of the tile STAGES before): one pending arrival per named barrier at most. After
+    // a failed wait or an abort it steps in lock-step (bar.sync).
+    int slot = 0, it = 0, cur_w = -1;
+    uint32_t ph = 0, bph = 0;
+    bool ok = true;
+    for (long long t = t_begin; t < t_end; ++t, ++it) {
+      const int w = (int)(t / tiles_pw);
+      const int buf = it & 1;
+      if (ok && w != cur_w) {
+        ok = !__any_sync(0xffffffffu, *abort_flag != 0) && __all_sync(0xffffffffu, mbar_wait(bfull, bph));
+        bph ^= 1;
+        cur_w = w;
+      }
+      if (ok) ok = !__any_sync(0xffffffffu, *abort_flag != 0) &&
+                   __all_sync(0xffffffffu, mbar_wait(&acc_empty[buf], ((it >> 1) & 1) ^ 1)) &&
+                   __all_sync(0xffffffffu, mbar_wait(&full[slot], ph));
+      if (ok) {
+        named_arrive(1 + slot, 64);
+      } else {
+        if (lane == 0 && !*abort_flag) fail();
+        named_sync(1 + slot, 64);
+      }
+      if (++slot == C::STAGES) { slot = 0; ph ^= 1; }
     }
   } else {  // ------------------------------ epilogue: 4 warps, one pixel per TMEM lane
     const int q = warp & 3;
