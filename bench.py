@@ -535,13 +535,17 @@ def measure_rates(local) -> dict:
             if best is None or r["tflops"] > best["tflops"]:
                 best = r
         out[kind] = {"tflops": best["tflops"], "ms": best["ms"]}
+    # tensor-core issue rate of the covariance / projection MMA shape, three issue forms
+    out["mma_issue"] = {f: dh.measure_mma_issue(f, stages=4096)
+                        for f in ("back-to-back", "mbarrier-wait", "waiter-warp")}
     clocks.end()
     info = clocks.stop()
     out["fp32_peak_tflops"] = max(out["fp32"]["tflops"], out["fp32x2"]["tflops"])
     out["fp64_peak_tflops"] = out["fp64"]["tflops"]
     out["clocks"] = info
     out["how"] = ("dh_measure_fma_rate: 4 x SMs CTAs x 256 threads x 8 independent FMA chains, "
-                  "best of 3 timed launches (CUDA events) after a warm-up")
+                  "best of 3 timed launches (CUDA events) after a warm-up; dh_measure_mma_issue: "
+                  "one CTA per SM, 4096 stages of four M = N = 128, K = 16 FP16 MMAs")
     return out
 
 

@@ -372,6 +372,18 @@ int dh_profile_read(dh_plan_t plan, int n, const char **names, int *launches, do
 dh_status dh_measure_fma_rate(int kind, int iters, int blocks_per_sm, float *ms, double *flops,
                               void *stream);
 
+/* Tensor-core issue-rate measurement (the paper has no counterpart; it serves the design and
+ * the rooflines of the tensor-core kernels of Eqs. 4 and 6): one CTA per SM issues `stages`
+ * (1..2^24) stages of four tcgen05.mma kind::f16 (M = 128, N = 128, K = 16, FP16 operands in
+ * shared memory, FP32 accumulation in tensor memory) from one thread, with a commit per stage,
+ * once to warm up and once timed with CUDA events on `stream` (synchronised). form 0: back to
+ * back; 1: the issuing warp waits on a (completed) mbarrier before each stage; 2: another warp
+ * does that wait and releases the issuing warp through a named barrier. *ms receives the timed
+ * launch's duration, *cycles_per_mma the slowest CTA's SM cycles per MMA and *flops the
+ * launch's floating-point operations. DH_ERR_TIMEOUT if a wait gave up. */
+dh_status dh_measure_mma_issue(int form, int stages, float *ms, double *cycles_per_mma, double *flops,
+                               void *stream);
+
 /* The covariance of one window, C = H^{t*} H (the FP32 plain path's covariance), without
  * any device allocation, for callers that cannot call cudaMalloc while running (for example
  * a frame-grabber callback in a real-time acquisition loop, where an allocation can

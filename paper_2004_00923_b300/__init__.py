@@ -361,6 +361,21 @@ def measure_fma_rate(kind: str = "fp32", iters: int = 4096, blocks_per_sm: int =
             "tflops": float(fl.value) / (float(ms.value) * 1e-3) / 1e12}
 
 
+def measure_mma_issue(form: str = "back-to-back", stages: int = 4096, stream=None) -> dict:
+    """dh_measure_mma_issue: tcgen05.mma (M = N = 128, K = 16) issue rate, one CTA per SM.
+    form: "back-to-back" (0), "mbarrier-wait" (1: the issuing warp waits on an mbarrier each
+    stage) or "waiter-warp" (2: another warp waits and releases it by a named barrier).
+    Returns {"ms", "cycles_per_mma", "tflops"}."""
+    lib = _lib.load()
+    f = {"back-to-back": 0, "mbarrier-wait": 1, "waiter-warp": 2}[form]
+    ms, cyc, fl = ctypes.c_float(0), ctypes.c_double(0), ctypes.c_double(0)
+    _lib.check("dh_measure_mma_issue", lib.dh_measure_mma_issue(f, int(stages), ctypes.byref(ms),
+                                                                ctypes.byref(cyc), ctypes.byref(fl),
+                                                                _stream_ptr(stream)))
+    return {"ms": float(ms.value), "cycles_per_mma": float(cyc.value),
+            "tflops": float(fl.value) / (float(ms.value) * 1e-3) / 1e12}
+
+
 def normalize_images(images: torch.Tensor, normalized: bool = True, display: bool = False,
                      gain: float = 128.0, in_place: bool = False, stream=None):
     """dh_normalize_images on CUDA FP32 images [n, ny, nx]: returns (normalized or None,

@@ -72,6 +72,8 @@ SIGNATURES = [
     ("dh_covariance_noalloc", _i, [_vp, _i64, _i, _vp, _vp]),
     ("dh_measure_fma_rate", _i, [_i, _i, _i, ctypes.POINTER(ctypes.c_float),
                                  ctypes.POINTER(_d), _vp]),
+    ("dh_measure_mma_issue", _i, [_i, _i, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_d),
+                                  ctypes.POINTER(_d), _vp]),
     ("dh_batch_run", _i, [ctypes.POINTER(BatchItem), _i, _vp]),
     ("dh_server_create", _i, [ctypes.POINTER(_vp), ctypes.c_size_t]),
     ("dh_server_stream_bytes", ctypes.c_size_t, [_i, _i, _i, _i, _i]),
