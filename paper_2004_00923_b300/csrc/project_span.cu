@@ -21,7 +21,9 @@
 // frames leave per window) and subtracts. The result clamps at 0.
 //
 // Roles: warp 0 issues TMA (span tiles, and the group operand as one bulk copy), warp 1
-// issues the MMAs, eight epilogue warps (TMEM lane quarter x half of the group's windows)
+// issues the MMAs (released tile by tile through named barriers by a waiter warp, the last
+// one, so that it takes no shared-memory step in its loop), eight epilogue warps (TMEM lane
+// quarter x half of the group's windows)
 // drain TMEM, sum energies and write the images, 8 adjacent image columns per pass (the
 // store's pixels run down image columns). A stage is released when both the MMAs and the
 // epilogue's energy reads are done. Waits are bounded (DH_FLAG_WAIT_TIMEOUT).
@@ -34,7 +36,11 @@ namespace {
 using namespace tc;
 
 constexpr int kSpanEpiWarps = 8;
-constexpr int kSpanThreads = 64 + 32 * kSpanEpiWarps;
+constexpr int kSpanWaiter = 2 + kSpanEpiWarps;  // the warp that watches the MMA warp's mbarriers
+// named barriers: 1-4 pair the epilogue warps of a lane quarter; the MMA warp's stages use
+// kSpanStageBar + slot (slot < kSpanMaxStages = 4), so 5-8
+constexpr int kSpanStageBar = 5;
+constexpr int kSpanThreads = 64 + 32 * kSpanEpiWarps + 32;
 constexpr int kSpanMaxG = 8;
 constexpr int kSpanMaxStages = 4;
 constexpr int kNacc = 4;  // partial accumulators per buffer (k-step kk goes to kk % 4)
@@ -114,7 +120,8 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
   uint64_t *acc_empty = acc_full + 4;
   uint64_t *bfull = acc_empty + 4;
   uint64_t *bempty = bfull + 1;
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bempty + 1);
+  uint64_t *mma_done = bempty + 1;
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(mma_done + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -131,6 +138,7 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
     for (int b = 0; b < nbuf; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 32 * kSpanEpiWarps); }
     mbar_init(bfull, 1);
     mbar_init(bempty, 1);
+    mbar_init(mma_done, 1);
     *abort_flag = 0;
     fence_barrier_init();
     prefetch_tmap(&tmA);
@@ -181,26 +189,23 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
         if (b_pending) mbar_wait(bfull, bph ^ 1);
       }
     }
-  } else if (warp == 1) {
-    if (lane == 0) {  // ---------------- MMA issuer: D[128 px x n_pad] = span^T x operand^T
-      const uint32_t idesc = idesc_f16(BF16, true, false, 128, n_pad);
-      const int k_steps = rows / 16;
-      const int half_bytes = img_bytes / 2;
-      int slot = 0; uint32_t ph = 0, bph = 0;
-      int cur = -1, it = 0;
-      bool ok = true;
-      for (long long u = u_begin; u < u_end && ok && !*abort_flag; ++u) {
-        const int grp = (int)(u / cpg);
-        if (grp != cur) {
-          if (!mbar_wait(bfull, bph)) { fail(); break; }
-          bph ^= 1;
-          cur = grp;
-        }
-        for (int i = 0; i < 8; ++i, ++it) {
-          const int buf = it % nbuf;
-          if (!mbar_wait(&acc_empty[buf], ((it / nbuf) & 1) ^ 1)) { fail(); ok = false; break; }
-          if (!mbar_wait(&full[slot], ph)) { fail(); ok = false; break; }
-          fence_after_sync();
+  } else if (warp == 1) {  // ---------------- MMA issuer: D[128 px x n_pad] = span^T x operand^T
+    // The whole warp runs the loop and lane 0 issues; tile k waits on named barrier
+    // kSpanStageBar + k % stages, which the waiter passes once the tile has landed, its
+    // accumulator buffer is free and (first tile of a group) the group's operand is in place;
+    // no shared-memory step inside the loop (a shared-memory access waits for the issued MMAs'
+    // operand reads) and no exit of its own.
+    const uint32_t idesc = idesc_f16(BF16, true, false, 128, n_pad);
+    const int k_steps = rows / 16;
+    const int half_bytes = img_bytes / 2;
+    int slot = 0, it = 0;
+    for (long long u = u_begin; u < u_end; ++u) {
+      const int grp = (int)(u / cpg);
+      for (int i = 0; i < 8; ++i, ++it) {
+        const int buf = it % nbuf;
+        named_sync(kSpanStageBar + slot, 64);
+        fence_after_sync();
+        if (lane == 0) {
           const uint32_t d = tmem + buf * acc_stride;
           // descriptors advance by their start-address field (address >> 4; shared memory is
           // below 256 KiB, so the 14-bit field never carries)
@@ -220,10 +225,43 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
           }
           mma_commit(&empty[slot]);
           mma_commit(&acc_full[buf]);
-          if (++slot == stages) { slot = 0; ph ^= 1; }
         }
-        const bool last_of_group = (u + 1 == u_end) || ((int)((u + 1) / cpg) != grp);
-        if (ok && last_of_group) mma_commit(bempty);
+        __syncwarp();
+        if (++slot == stages) slot = 0;
+      }
+      const bool last_of_group = (u + 1 == u_end) || ((int)((u + 1) / cpg) != grp);
+      if (lane == 0 && last_of_group) mma_commit(bempty);
+      __syncwarp();
+    }
+    if (lane == 0) mma_commit(mma_done);  // every MMA completes before the tensor memory is freed
+    __syncwarp();
+    mbar_wait(mma_done, 0);
+  } else if (warp == kSpanWaiter) {  // ---------------- waiter
+    // Fewer than `stages` tiles ahead of the MMA warp (a tile's data needs its slot released
+    // by the MMAs of the tile `stages` before): one pending arrival per named barrier at most.
+    // After a failed wait or an abort it steps in lock-step (bar.sync).
+    int slot = 0, it = 0, cur = -1;
+    uint32_t ph = 0, bph = 0;
+    bool ok = true;
+    for (long long u = u_begin; u < u_end; ++u) {
+      const int grp = (int)(u / cpg);
+      if (ok && grp != cur) {
+        ok = !__any_sync(0xffffffffu, *abort_flag != 0) && __all_sync(0xffffffffu, mbar_wait(bfull, bph));
+        bph ^= 1;
+        cur = grp;
+      }
+      for (int i = 0; i < 8; ++i, ++it) {
+        const int buf = it % nbuf;
+        if (ok) ok = !__any_sync(0xffffffffu, *abort_flag != 0) &&
+                     __all_sync(0xffffffffu, mbar_wait(&acc_empty[buf], ((it / nbuf) & 1) ^ 1)) &&
+                     __all_sync(0xffffffffu, mbar_wait(&full[slot], ph));
+        if (ok) {
+          named_arrive(kSpanStageBar + slot, 64);
+        } else {
+          if (lane == 0 && !*abort_flag) fail();
+          named_sync(kSpanStageBar + slot, 64);
+        }
+        if (++slot == stages) { slot = 0; ph ^= 1; }
       }
     }
   } else {  // ------------------------------ epilogue: lane quarter q, windows 4h..4h+3
