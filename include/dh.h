@@ -149,7 +149,10 @@ dh_status dh_plan_reserve(dh_plan_t plan, int max_frames, int max_windows);
  *   persistent render (DH_OPT_RENDER_SCHEDULE 0) first wait `value` SM cycles (at most 1e8)
  *   on a device word that nothing sets; the bounded wait runs out, the CTA raises
  *   DH_FLAG_WAIT_TIMEOUT and skips its work (no CTA is left waiting on another), and the next
- *   dh_plan_status returns DH_ERR_TIMEOUT. The holograms of that call are not written.
+ *   dh_plan_status returns DH_ERR_TIMEOUT. The holograms of that call are not written. It
+ *   does the same to the waiter warp of the 16-bit tensor-core covariance (DH_OPT_COVARIANCE
+ *   0): its first wait, on a barrier that completes only at the end of the launch, runs out,
+ *   and the launch takes its abort path (the covariances of that call are not formed).
  *   0 (default): off. */
 #define DH_OPT_TEST_STALL 6
 /* DH_OPT_RENDER_FFT: the arithmetic of Eq. 1's DFTs. 0 (default): automatic. 1: the

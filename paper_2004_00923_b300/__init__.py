@@ -342,8 +342,9 @@ class Plan:
 
     def set_test_stall(self, cycles: int) -> None:
         """DH_OPT_TEST_STALL (test only): the persistent render's CTAs first wait `cycles`
-        SM cycles on a device word nothing sets, give up, and skip their work; the next status
-        read reports DH_ERR_TIMEOUT. 0 turns it off."""
+        SM cycles on a device word nothing sets, give up, and skip their work; the 16-bit
+        tensor-core covariance's waiter warp does the same and the launch takes its abort path;
+        the next status read reports DH_ERR_TIMEOUT. 0 turns it off."""
         _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(self._h, 6, int(cycles)))
 
 

@@ -141,8 +141,9 @@ k_band_gram(const __grid_constant__ CUtensorMap tm, int row0, int n_blocks, int 
   } else if (warp == C::WAITER) {  // ---------------- waiter
     // Fewer than STAGES stages ahead of the MMA warp (a stage's data needs its slot released by
     // the MMAs of the stage STAGES before): one pending arrival per named barrier at most. After
-    // a failed wait or an abort it steps in lock-step (bar.sync).
-    int slot = 0, grp = 0;
+    // a failed wait or an abort it stops waiting for data and arrives once the MMAs of the
+    // stage STAGES before have completed, so the MMA warp still completes its loop.
+    int slot = 0, grp = 0, released = 0;
     uint32_t ph = 0;
     bool ok = true;
     for (int wu = blockIdx.x; wu < total_units; wu += gridDim.x) {
@@ -152,12 +153,15 @@ k_band_gram(const __grid_constant__ CUtensorMap tm, int row0, int n_blocks, int 
                      __all_sync(0xffffffffu, mbar_wait(&acc_empty[grp % C::NB], ((grp / C::NB) & 1) ^ 1));
         for (int i = 0; i < n; ++i) {
           if (ok) ok = !__any_sync(0xffffffffu, *abort_flag != 0) && __all_sync(0xffffffffu, mbar_wait(&full[slot], ph));
-          if (ok) {
-            named_arrive(1 + slot, 64);
-          } else {
+          if (!ok) {
             if (lane == 0 && !*abort_flag) fail();
-            named_sync(1 + slot, 64);
+            // without the data wait, keep at most one pending arrival on this named barrier:
+            // wait (bounded) for the MMAs of the stage C::STAGES before, which the MMA warp
+            // issued after passing the barrier for that stage
+            if (released >= C::STAGES) (void)__all_sync(0xffffffffu, mbar_wait(&empty[slot], ph ^ 1));
           }
+          named_arrive(1 + slot, 64);
+          ++released;
           if (++slot == C::STAGES) { slot = 0; ph ^= 1; }
         }
       }

@@ -172,8 +172,9 @@ k_fourier_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
   } else if (warp == kFsWaiter) {  // ---------------- waiter
     // Runs ahead of the MMA warp by fewer than `stages` tiles (a tile's data needs its slot
     // released by the MMAs of the tile `stages` before), so each named barrier has at most one
-    // pending arrival; after a failed wait or an abort it steps in lock-step (bar.sync).
-    int slot = 0, it = 0;
+    // pending arrival; after a failed wait or an abort it stops waiting for data and arrives
+    // once the MMAs of the tile `stages` before have completed.
+    int slot = 0, it = 0, released = 0;
     uint32_t ph = 0;
     bool ok = __all_sync(0xffffffffu, mbar_wait(bfull, 0));  // the operand, once
     for (long long u = u_begin; u < u_end; ++u) {
@@ -182,12 +183,15 @@ k_fourier_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
         if (ok) ok = !__any_sync(0xffffffffu, *abort_flag != 0) &&
                      __all_sync(0xffffffffu, mbar_wait(&acc_empty[buf], ((it >> 1) & 1) ^ 1)) &&
                      __all_sync(0xffffffffu, mbar_wait(&full[slot], ph));
-        if (ok) {
-          named_arrive(1 + slot, 64);
-        } else {
+        if (!ok) {
           if (lane == 0 && !*abort_flag) fail();
-          named_sync(1 + slot, 64);
+          // without the data wait, keep at most one pending arrival on this named barrier:
+          // wait (bounded) for the MMAs of the stage stages before, which the MMA warp
+          // issued after passing the barrier for that stage
+          if (released >= stages) (void)__all_sync(0xffffffffu, mbar_wait(&empty[slot], ph ^ 1));
         }
+        named_arrive(1 + slot, 64);
+        ++released;
         if (++slot == stages) { slot = 0; ph ^= 1; }
       }
     }

@@ -121,7 +121,8 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
   uint64_t *bfull = acc_empty + 4;
   uint64_t *bempty = bfull + 1;
   uint64_t *mma_done = bempty + 1;
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(mma_done + 1);
+  uint64_t *prog = mma_done + 1;  // [kSpanMaxStages]: a slot's MMAs completed (MMA warp only)
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(prog + kSpanMaxStages);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -134,7 +135,11 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
   const int gx = nx >> 3;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < stages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1 + kSpanEpiWarps); }
+    for (int i = 0; i < stages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1 + kSpanEpiWarps);
+      mbar_init(&prog[i], 1);
+    }
     for (int b = 0; b < nbuf; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 32 * kSpanEpiWarps); }
     mbar_init(bfull, 1);
     mbar_init(bempty, 1);
@@ -224,6 +229,7 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
             }
           }
           mma_commit(&empty[slot]);
+          mma_commit(&prog[slot]);
           mma_commit(&acc_full[buf]);
         }
         __syncwarp();
@@ -239,8 +245,10 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
   } else if (warp == kSpanWaiter) {  // ---------------- waiter
     // Fewer than `stages` tiles ahead of the MMA warp (a tile's data needs its slot released
     // by the MMAs of the tile `stages` before): one pending arrival per named barrier at most.
-    // After a failed wait or an abort it steps in lock-step (bar.sync).
-    int slot = 0, it = 0, cur = -1;
+    // After a failed wait or an abort it stops waiting for data and arrives once the MMAs of
+    // the tile `stages` before have completed (prog, committed by the MMA warp alone: the
+    // slot's `empty` also counts the epilogue, which stops on an abort).
+    int slot = 0, it = 0, cur = -1, released = 0;
     uint32_t ph = 0, bph = 0;
     bool ok = true;
     for (long long u = u_begin; u < u_end; ++u) {
@@ -255,12 +263,15 @@ k_project_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
         if (ok) ok = !__any_sync(0xffffffffu, *abort_flag != 0) &&
                      __all_sync(0xffffffffu, mbar_wait(&acc_empty[buf], ((it / nbuf) & 1) ^ 1)) &&
                      __all_sync(0xffffffffu, mbar_wait(&full[slot], ph));
-        if (ok) {
-          named_arrive(kSpanStageBar + slot, 64);
-        } else {
+        if (!ok) {
           if (lane == 0 && !*abort_flag) fail();
-          named_sync(kSpanStageBar + slot, 64);
+          // without the data wait, keep at most one pending arrival on this named barrier:
+          // wait (bounded) for the MMAs of the stage stages before, which the MMA warp
+          // issued after passing the barrier for that stage
+          if (released >= stages) (void)__all_sync(0xffffffffu, mbar_wait(&prog[slot], ph ^ 1));
         }
+        named_arrive(kSpanStageBar + slot, 64);
+        ++released;
         if (++slot == stages) { slot = 0; ph ^= 1; }
       }
     }

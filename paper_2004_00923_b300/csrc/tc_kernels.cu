@@ -75,7 +75,8 @@ struct GramCfg {
 template <int T, bool BF16>
 __global__ void __launch_bounds__(GramCfg<T>::THREADS, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap tmH, int first_slot, int slot_stride, int n_windows,
-          int units_pw, int stages_per_unit, double *__restrict__ part, uint32_t *__restrict__ status) {
+          int units_pw, int stages_per_unit, double *__restrict__ part, uint32_t *__restrict__ status,
+          int stall_cycles) {
   using C = GramCfg<T>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = align1024(smem_raw);
@@ -170,11 +171,17 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmH, int first_slot, int slot_stri
     // accumulator buffer back from the epilogue (acc_empty). Normally it runs ahead of the MMA
     // warp by fewer than STAGES stages (a stage's data needs its slot released by the MMAs of
     // the stage STAGES before), so each named barrier has at most one pending arrival. After a
-    // failed wait or an abort elsewhere it stops waiting and steps in lock-step (bar.sync), so
-    // the MMA warp still completes its loop.
-    int slot = 0, grp = 0;
+    // failed wait or an abort elsewhere it stops waiting for data and arrives for stage k once
+    // the MMAs of stage k - STAGES have completed (empty: the MMA warp passed that stage's
+    // barrier before issuing them), which keeps the one-pending-arrival rule, so the MMA warp
+    // still completes its loop. (A bar.sync there instead could meet the waiter's own earlier
+    // arrival on the same barrier and leave the MMA warp's last bar.sync without a partner.)
+    int slot = 0, grp = 0, released = 0;
     uint32_t ph = 0;
     bool ok = true;
+    // stall test (DH_OPT_TEST_STALL): a bounded wait on the barrier that completes only after
+    // the MMA warp's last stage runs out, and the launch takes its abort path from stage 0
+    if (stall_cycles > 0) ok = __all_sync(0xffffffffu, mbar_wait(mma_done, 0, stall_cycles));
     for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
       for (int g0 = 0; g0 < stages_per_unit; g0 += C::GROUP, ++grp) {
         const int n = stages_per_unit - g0 < C::GROUP ? stages_per_unit - g0 : C::GROUP;
@@ -182,12 +189,15 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmH, int first_slot, int slot_stri
                      __all_sync(0xffffffffu, mbar_wait(&acc_empty[grp % C::NB], ((grp / C::NB) & 1) ^ 1));
         for (int i = 0; i < n; ++i) {
           if (ok) ok = !__any_sync(0xffffffffu, *abort_flag != 0) && __all_sync(0xffffffffu, mbar_wait(&full[slot], ph));
-          if (ok) {
-            named_arrive(1 + slot, 64);
-          } else {
+          if (!ok) {
             if (lane == 0 && !*abort_flag) fail();
-            named_sync(1 + slot, 64);
+            // without the data wait, keep at most one pending arrival on this named barrier:
+            // wait (bounded) for the MMAs of the stage C::STAGES before, which the MMA warp
+            // issued after passing the barrier for that stage
+            if (released >= C::STAGES) (void)__all_sync(0xffffffffu, mbar_wait(&empty[slot], ph ^ 1));
           }
+          named_arrive(1 + slot, 64);
+          ++released;
           if (++slot == C::STAGES) { slot = 0; ph ^= 1; }
         }
       }
@@ -421,7 +431,7 @@ k_gram_raw_tc(const __grid_constant__ CUtensorMap tmI, int first_frame, int wind
     __syncwarp();
     mbar_wait(mma_done, 0);
   } else if (warp == C::WAITER) {  // ---------------- waiter (see k_gram_tc)
-    int slot = 0, grp = 0;
+    int slot = 0, grp = 0, released = 0;
     uint32_t ph = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
@@ -431,12 +441,15 @@ k_gram_raw_tc(const __grid_constant__ CUtensorMap tmI, int first_frame, int wind
                      __all_sync(0xffffffffu, mbar_wait(&acc_empty[grp % C::NB], ((grp / C::NB) & 1) ^ 1));
         for (int i = 0; i < n; ++i) {
           if (ok) ok = !__any_sync(0xffffffffu, *abort_flag != 0) && __all_sync(0xffffffffu, mbar_wait(&op_full[slot], ph));
-          if (ok) {
-            named_arrive(1 + slot, 64);
-          } else {
+          if (!ok) {
             if (lane == 0 && !*abort_flag) fail();
-            named_sync(1 + slot, 64);
+            // without the data wait, keep at most one pending arrival on this named barrier:
+            // wait (bounded) for the MMAs of the stage C::OP_STAGES before, which the MMA warp
+            // issued after passing the barrier for that stage
+            if (released >= C::OP_STAGES) (void)__all_sync(0xffffffffu, mbar_wait(&op_empty[slot], ph ^ 1));
           }
+          named_arrive(1 + slot, 64);
+          ++released;
           if (++slot == C::OP_STAGES) { slot = 0; ph ^= 1; }
         }
       }
@@ -690,8 +703,9 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
   } else if (warp == C::WAITER) {  // ---------------- waiter
     // Fewer than STAGES tiles ahead of the MMA warp (a tile's data needs its slot released by
     // the MMAs of the tile STAGES before): one pending arrival per named barrier at most. After
-    // a failed wait or an abort it steps in lock-step (bar.sync).
-    int slot = 0, it = 0, cur_w = -1;
+    // a failed wait or an abort it stops waiting for data and arrives once the MMAs of the
+    // tile STAGES before have completed (see k_gram_tc).
+    int slot = 0, it = 0, cur_w = -1, released = 0;
     uint32_t ph = 0, bph = 0;
     bool ok = true;
     for (long long t = t_begin; t < t_end; ++t, ++it) {
@@ -705,12 +719,15 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
       if (ok) ok = !__any_sync(0xffffffffu, *abort_flag != 0) &&
                    __all_sync(0xffffffffu, mbar_wait(&acc_empty[buf], ((it >> 1) & 1) ^ 1)) &&
                    __all_sync(0xffffffffu, mbar_wait(&full[slot], ph));
-      if (ok) {
-        named_arrive(1 + slot, 64);
-      } else {
+      if (!ok) {
         if (lane == 0 && !*abort_flag) fail();
-        named_sync(1 + slot, 64);
+        // without the data wait, keep at most one pending arrival on this named barrier:
+        // wait (bounded) for the MMAs of the stage C::STAGES before, which the MMA warp
+        // issued after passing the barrier for that stage
+        if (released >= C::STAGES) (void)__all_sync(0xffffffffu, mbar_wait(&empty[slot], ph ^ 1));
       }
+      named_arrive(1 + slot, 64);
+      ++released;
       if (++slot == C::STAGES) { slot = 0; ph ^= 1; }
     }
   } else {  // ------------------------------ epilogue: 4 warps, one pixel per TMEM lane
@@ -864,7 +881,7 @@ dh_status gram_t(Plan &p, int first_slot, int slot_stride, int n_windows, cudaSt
   if (grid > total) grid = total;
   ProfScope ps(p, K_GRAM_TC, s);
   kern<<<grid, C::THREADS, C::SMEM, s>>>(p.tmap_H, first_slot, slot_stride, n_windows, units_pw,
-                                          stages_per_unit, p.d_part, p.d_status);
+                                          stages_per_unit, p.d_part, p.d_status, p.test_stall);
   DH_CUDA_TRY(cudaGetLastError());
   return DH_OK;
 }

@@ -42,12 +42,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Wait until the phase with the given parity has completed; false after kWaitBudget.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Wait until the phase with the given parity has completed; false after `budget` SM cycles
+// (kWaitBudget by default).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long budget = kWaitBudget) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitBudget) return false;
+    if (clock64() - t0 > budget) return false;
   }
   return true;
 }

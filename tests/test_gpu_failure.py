@@ -93,3 +93,29 @@ def test_status_read_does_not_wait_for_other_streams(dh):
         other.synchronize()
         assert not long_done, "the unrelated kernel ended before the status read returned"
         assert dt < 0.25, dt
+
+
+def test_covariance_abort_path_ends_and_reports_timeout(dh):
+    """The 16-bit tensor-core covariance with its waiter warp timed out from the first stage:
+    the MMA warp still completes its loop (the waiter releases each stage once the MMAs of the
+    stage a ring before have completed), the launch ends by itself, the call reports
+    DH_ERR_TIMEOUT, and the next call on the same plan is correct."""
+    n, T, nw = 256, 32, 4
+    frames = SpeckleStream(SpeckleParams(n, n), seed=33).next(nw * T).numpy()
+    with dh.Plan(n, n, LAM, Z, PITCH, T=T, precision="fp16", max_frames=nw * T, max_windows=nw) as plan:
+        plan.set_render_schedule(False)  # the chunked render: the stall reaches only the covariance
+        assert plan.status() == 0
+        plan.set_test_stall(20000)
+        t0 = time.perf_counter()
+        plan.pca_batch(to_gpu(frames), nw, T, 2, T - 1)
+        rc, flags = _status(plan)
+        dt = time.perf_counter() - t0
+        assert rc == DH_ERR_TIMEOUT, rc
+        assert flags & FLAG_WAIT_TIMEOUT
+        assert dt < 5.0, dt
+        plan.set_test_stall(0)
+        images, _ = plan.pca_batch(to_gpu(frames), nw, T, 2, T - 1)
+        rc, flags = _status(plan)
+        assert (rc, flags) == (DH_OK, 0)
+        M, _, _, _ = oracle.pca_window(frames[:T], LAM, Z, PITCH, 2, T - 1)
+        assert rel(images[0].double().cpu().numpy(), M) < 1e-3
