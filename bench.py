@@ -343,7 +343,7 @@ def run_ours(args, ws, rank, local):
     # ---------------------------------------------------------------- end to end (host buffers)
     # dh_pca_batch_host: pinned host frames in, host images and eigenvalues out; the library
     # overlaps the frame copies with the computation of earlier groups of windows
-    e2e = None
+    e2e, e2e_packed = None, None
     if not args.no_e2e and not args.residual:  # the host-buffer call has no residual mode
         host_frames = torch.empty(frames.shape, dtype=torch.uint16, pin_memory=True)
         host_frames.copy_(frames)
@@ -366,7 +366,41 @@ def run_ours(args, ws, rank, local):
                "h2d_bytes_per_step": int(host_frames.numel() * 2),
                "d2h_bytes_per_step": int(host_images.numel() * 4 + host_eig.numel() * 8),
                "ms_per_step": e_ms, "call": "dh_pca_batch_host (copies overlapped with compute)"}
+        ref_images = host_images.clone()
         del host_frames
+
+        # the same with the frames as a 12-bit camera delivers them packed (Mono12p: two
+        # pixels in three bytes), expanded on the device: 3/4 of the bytes over the host link.
+        # The packing is the synthetic camera's output format, made once before timing.
+        v = (frames.view(torch.int16).to(torch.int32) & 0xFFFF).view(frames.shape[0], -1, 2)
+        if int(v.max()) < 4096:
+            lo, hi = v[..., 0], v[..., 1]
+            packed = torch.stack((lo & 0xFF, (lo >> 8) | ((hi & 0xF) << 4), hi >> 4), dim=-1)
+            host_packed = torch.empty((frames.shape[0], packed.shape[1] * 3), dtype=torch.uint8,
+                                      pin_memory=True)
+            host_packed.copy_(packed.to(torch.uint8).view(frames.shape[0], -1))
+            del lo, hi, packed
+
+            def e2e_packed_step():
+                plan.pca_batch_host_packed12(host_packed, nwin, T, K0, K1, host_images, host_eig, sync=False)
+
+            e2e_packed_step()
+            torch.cuda.synchronize()
+            same = bool(torch.equal(host_images, ref_images))
+            barrier(ws)
+            t0 = time.perf_counter()
+            for _ in range(n_e2e):
+                e2e_packed_step()
+            torch.cuda.synchronize()
+            p_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / n_e2e, ws)
+            e2e_packed = {"value": whole_job_rate(nwin, ws, p_ms), "unit": UNIT,
+                          "h2d_bytes_per_step": int(host_packed.numel()),
+                          "d2h_bytes_per_step": int(host_images.numel() * 4 + host_eig.numel() * 8),
+                          "ms_per_step": p_ms, "format": "Mono12p (12-bit packed, 2 pixels in 3 bytes)",
+                          "call": "dh_pca_batch_host_packed12 (copies overlapped, expanded on the device)",
+                          "images_bitwise_equal_to_uint16_call": same}
+            del host_packed
+        del ref_images, v
 
     # ---------------------------------------------------------------- plain FP32 GPU path
     plain = None
@@ -461,6 +495,7 @@ def run_ours(args, ws, rank, local):
             "roofline": roofline,
             "cpu_baseline": cpu_baseline,
             "e2e": e2e,
+            "e2e_packed12": e2e_packed,
             "plain_fp32": plain,
             "speedup_vs_plain_fp32": (value / plain["value"]) if plain else None,
             "parity": parity,

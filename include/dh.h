@@ -331,6 +331,27 @@ dh_status dh_pca_batch_host(dh_plan_t plan, const uint16_t *frames_host, int64_t
                             int n_windows, int window_stride_frames, int k0, int k1,
                             float *images_host, double *eigvals_host, void *stream);
 
+/* dh_pca_batch_host for 12-bit camera frames in the packed pixel format Mono12p (GenICam
+ * PFNC): pixel i of a frame occupies bits [12 i, 12 i + 12) of the frame's bytes read as one
+ * little-endian bit string (two pixels in three bytes; pixel i = frame row-major index y n_x +
+ * x). Frame i starts at frames_host + i * frame_stride_bytes (at least n_x n_y 3/2 bytes, a
+ * multiple of 4). The packed bytes are copied (3/4 of the uint16 bytes) and expanded to uint16
+ * on the device; everything else, including the results, is as dh_pca_batch_host with those
+ * uint16 frames. The paper's camera delivers 12-bit frames; the format is a deployment choice
+ * with no counterpart in the paper. */
+dh_status dh_pca_batch_host_packed12(dh_plan_t plan, const uint8_t *frames_host, int64_t frame_stride_bytes,
+                                     int n_windows, int window_stride_frames, int k0, int k1,
+                                     float *images_host, double *eigvals_host, void *stream);
+
+/* Expand n_frames (<= 65535) Mono12p frames of npix pixels (a multiple of 8) from device
+ * memory (frame f at src_dev + f * src_stride_bytes: >= npix 3/2, a multiple of 4; src_dev
+ * 4-byte aligned) to uint16 (frame f at dst_dev + f * dst_stride_elems: >= npix, a multiple
+ * of 8; dst_dev 16-byte aligned). Asynchronous on `stream`. The device half of
+ * dh_pca_batch_host_packed12, exported for tests and for callers that stage frames
+ * themselves. */
+dh_status dh_unpack_mono12p(const uint8_t *src_dev, int64_t src_stride_bytes, int64_t npix, int n_frames,
+                            uint16_t *dst_dev, int64_t dst_stride_elems, void *stream);
+
 /* Inspection (tests): copy hologram slot `slot` as interleaved FP32 (re, im) pairs,
  * n_x n_y of them, to out_dev. Asynchronous. */
 dh_status dh_debug_hologram(dh_plan_t plan, int slot, float *out_dev, void *stream);

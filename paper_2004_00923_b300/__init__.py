@@ -298,6 +298,29 @@ class Plan:
             (stream or torch.cuda.current_stream()).synchronize()
         return images_host, eigvals_host
 
+    def pca_batch_host_packed12(self, frames_packed: torch.Tensor, n_windows: int, window_stride: int,
+                                k0: int, k1: int, images_host: torch.Tensor | None = None,
+                                eigvals_host: torch.Tensor | None = None, want_eigvals: bool = True,
+                                stream=None, sync: bool = True):
+        """dh_pca_batch_host_packed12: as pca_batch_host, for Mono12p frames in host memory
+        (a contiguous uint8 tensor [F, n_x n_y 3/2], e.g. from pack_mono12p)."""
+        f = frames_packed
+        nbytes = self.nx * self.ny // 2 * 3
+        if f.dtype != torch.uint8 or f.is_cuda or f.dim() != 2 or f.shape[1] != nbytes or not f.is_contiguous():
+            raise TypeError(f"frames must be a contiguous host uint8 tensor [F, {nbytes}]")
+        pin = f.is_pinned()
+        if images_host is None:
+            images_host = torch.empty((n_windows, self.ny, self.nx), dtype=torch.float32, pin_memory=pin)
+        if eigvals_host is None and want_eigvals:
+            eigvals_host = torch.empty((n_windows, self.T), dtype=torch.float64, pin_memory=pin)
+        _lib.check("dh_pca_batch_host_packed12", self._lib.dh_pca_batch_host_packed12(
+            self._h, _ptr(f), nbytes, int(n_windows), int(window_stride), int(k0), int(k1),
+            _ptr(images_host), _ptr(eigvals_host) if eigvals_host is not None else None,
+            _stream_ptr(stream)))
+        if sync:
+            (stream or torch.cuda.current_stream()).synchronize()
+        return images_host, eigvals_host
+
     # -- inspection -----------------------------------------------------------
     def debug_hologram(self, slot: int, stream=None) -> torch.Tensor:
         out = torch.empty((self.ny, self.nx, 2), dtype=torch.float32, device="cuda")
@@ -346,6 +369,40 @@ class Plan:
         tensor-core covariance's waiter warp does the same and the launch takes its abort path;
         the next status read reports DH_ERR_TIMEOUT. 0 turns it off."""
         _lib.check("dh_plan_set_option", self._lib.dh_plan_set_option(self._h, 6, int(cycles)))
+
+
+def pack_mono12p(frames) -> torch.Tensor:
+    """Host-side packing of 12-bit frames (values < 4096, uint16 [F, ny, nx] as a numpy array or
+    a CPU tensor) into Mono12p: pixel i of a frame occupies bits [12 i, 12 i + 12) of the frame's
+    bytes read as one little-endian bit string, so pixels 2j and 2j + 1 fill bytes 3j .. 3j + 2.
+    Returns a contiguous uint8 tensor [F, ny nx 3/2]. Raises ValueError on values >= 4096."""
+    import numpy as np
+    a = frames.numpy() if isinstance(frames, torch.Tensor) else np.asarray(frames)
+    if a.dtype != np.uint16 or a.ndim != 3 or (a.shape[1] * a.shape[2]) % 2:
+        raise TypeError("frames must be uint16 [F, ny, nx] with an even pixel count")
+    if a.size and int(a.max()) >= 4096:
+        raise ValueError("Mono12p holds 12-bit values (< 4096)")
+    v = a.reshape(a.shape[0], -1, 2).astype(np.uint32)
+    lo, hi = v[..., 0], v[..., 1]
+    out = np.empty((a.shape[0], v.shape[1], 3), dtype=np.uint8)
+    out[..., 0] = lo & 0xFF
+    out[..., 1] = (lo >> 8) | ((hi & 0xF) << 4)
+    out[..., 2] = hi >> 4
+    return torch.from_numpy(out.reshape(a.shape[0], -1))
+
+
+def unpack_mono12p(packed: torch.Tensor, ny: int, nx: int, stream=None) -> torch.Tensor:
+    """dh_unpack_mono12p: Mono12p frames on the device (uint8 [F, ny nx 3/2]) to uint16
+    [F, ny, nx] on the device."""
+    lib = _lib.load()
+    if packed.dtype != torch.uint8 or not packed.is_cuda or packed.dim() != 2 or not packed.is_contiguous():
+        raise TypeError("packed must be a contiguous CUDA uint8 tensor [F, ny nx 3/2]")
+    npix = ny * nx
+    out = torch.empty((packed.shape[0], ny, nx), dtype=torch.uint16, device=packed.device)
+    _lib.check("dh_unpack_mono12p", lib.dh_unpack_mono12p(_ptr(packed), int(packed.shape[1]), npix,
+                                                         int(packed.shape[0]), _ptr(out), npix,
+                                                         _stream_ptr(stream)))
+    return out
 
 
 def measure_fma_rate(kind: str = "fp32", iters: int = 4096, blocks_per_sm: int = 4,

@@ -61,6 +61,8 @@ SIGNATURES = [
     ("dh_pca_window", _i, [_vp, _i, _i, _vp, _vp, _vp]),
     ("dh_pca_batch", _i, [_vp, _vp, _i64, _i, _i, _i, _i, _vp, _vp, _vp]),
     ("dh_pca_batch_host", _i, [_vp, _vp, _i64, _i, _i, _i, _i, _vp, _vp, _vp]),
+    ("dh_pca_batch_host_packed12", _i, [_vp, _vp, _i64, _i, _i, _i, _i, _vp, _vp, _vp]),
+    ("dh_unpack_mono12p", _i, [_vp, _i64, _i64, _i, _vp, _i64, _vp]),
     ("dh_normalize_images", _i, [_vp, _i, _i64, _vp, _vp, ctypes.c_float, _vp, _vp]),
     ("dh_debug_hologram", _i, [_vp, _i, _vp, _vp]),
     ("dh_debug_covariance", _i, [_vp, _i, _vp, _vp]),

@@ -164,8 +164,8 @@ dh_status alloc_store(Plan &p, const Plan *base = nullptr) {
   p.band_frames = 0;  // a new store has no band yet
   const StoreSizes z = store_sizes(p);
   // the host-buffer pipeline's buffers (kept across reservations) stay counted
-  const size_t pipe = 2 * p.pipe.stage_elems * sizeof(uint16_t) + p.pipe.img_elems * sizeof(float) +
-                      p.pipe.eig_elems * sizeof(double);
+  const size_t pipe = 2 * p.pipe.stage_elems * sizeof(uint16_t) + 2 * p.pipe.pstage_bytes +
+                      p.pipe.img_elems * sizeof(float) + p.pipe.eig_elems * sizeof(double);
   p.bytes = (p.is_view ? 0 : z.tables) + pipe;
   p.H_elem_bytes = p.prec == DH_PREC_FP32 ? 4 : 2;
   dh_status st;
@@ -540,7 +540,7 @@ void release(dh_plan_t h) {
   if (q.down) cudaStreamDestroy(q.down);
   for (cudaEvent_t ev : {q.start, q.done, q.finished, q.copied[0], q.copied[1], q.freed[0], q.freed[1]})
     if (ev) cudaEventDestroy(ev);
-  dfree(q.stage[0]); dfree(q.stage[1]); dfree(q.img); dfree(q.eig);
+  dfree(q.stage[0]); dfree(q.stage[1]); dfree(q.pstage[0]); dfree(q.pstage[1]); dfree(q.img); dfree(q.eig);
   dfree(p.d_band); dfree(p.d_band_part);
   dfree(p.d_cx); dfree(p.d_cy); dfree(p.d_twx); dfree(p.d_twy); dfree(p.d_status); dfree(p.d_sync);
   dfree(p.d_tc);
@@ -959,7 +959,10 @@ dh_status dh_pca_batch(dh_plan_t h, const uint16_t *frames_dev, int64_t frame_st
                   frame_stride_elems);
 }
 
-dh_status dh_pca_batch_host(dh_plan_t h, const uint16_t *frames_host, int64_t frame_stride_elems,
+// The host pipeline of dh_pca_batch_host and dh_pca_batch_host_packed12. `frames_host` holds
+// uint16 frames `host_stride` elements apart, or (packed) Mono12p frames `host_stride` bytes
+// apart, which are copied as bytes and expanded on the device into the uint16 staging buffer.
+static dh_status host_batch(dh_plan_t h, const void *frames_host, int64_t host_stride, bool packed,
                             int n_windows, int window_stride_frames, int k0, int k1, float *images_host,
                             double *eigvals_host, void *stream) {
   if (!h || !frames_host || !images_host || n_windows < 1 || window_stride_frames < 1) return DH_ERR_INVALID_ARG;
@@ -968,9 +971,13 @@ dh_status dh_pca_batch_host(dh_plan_t h, const uint16_t *frames_host, int64_t fr
   if (k0 < 0 || k1 < k0 || k1 >= p.T) return DH_ERR_INVALID_ARG;
   const int ws = window_stride_frames, T = p.T;
   const long long nf_all = (long long)(n_windows - 1) * ws + T;
-  if (nf_all > p.max_frames || n_windows > p.max_windows || frame_stride_elems < p.npix ||
-      (frame_stride_elems & 7) != 0)
+  if (nf_all > p.max_frames || n_windows > p.max_windows) return DH_ERR_INVALID_ARG;
+  if (packed ? (host_stride < p.npix / 2 * 3 || (host_stride & 3) != 0)
+             : (host_stride < p.npix || (host_stride & 7) != 0))
     return DH_ERR_INVALID_ARG;
+  // the uint16 frames the render reads: the caller's stride, or dense after expansion
+  const int64_t frame_stride_elems = packed ? p.npix : host_stride;
+  const size_t host_frame_bytes = packed ? (size_t)host_stride : (size_t)host_stride * sizeof(uint16_t);
   Busy g(h->busy);
   if (!g.ok) return DH_ERR_STATE;
   // groups of windows whose new frames fit a 256-frame staging buffer (one window per group
@@ -995,6 +1002,17 @@ dh_status dh_pca_batch_host(dh_plan_t h, const uint16_t *frames_host, int64_t fr
     if ((st = dalloc(p, &q.stage[0], stage_elems * sizeof(uint16_t))) != DH_OK) return st;
     if ((st = dalloc(p, &q.stage[1], stage_elems * sizeof(uint16_t))) != DH_OK) return st;
     q.stage_elems = stage_elems;
+  }
+  const size_t pstage_bytes = packed ? (size_t)cap * host_frame_bytes : 0;
+  if (q.pstage_bytes < pstage_bytes) {  // the packed bytes' own staging buffers
+    DH_CUDA_TRY(cudaDeviceSynchronize());
+    dfree(q.pstage[0]); dfree(q.pstage[1]);
+    p.bytes -= 2 * q.pstage_bytes;
+    q.pstage_bytes = 0;
+    dh_status st;
+    if ((st = dalloc(p, &q.pstage[0], pstage_bytes)) != DH_OK) return st;
+    if ((st = dalloc(p, &q.pstage[1], pstage_bytes)) != DH_OK) return st;
+    q.pstage_bytes = pstage_bytes;
   }
   if (q.img_elems < img_elems || q.eig_elems < eig_elems) {
     DH_CUDA_TRY(cudaDeviceSynchronize());
@@ -1025,12 +1043,16 @@ dh_status dh_pca_batch_host(dh_plan_t h, const uint16_t *frames_host, int64_t fr
     }
     const int b = grp & 1;
     if (grp >= 2) DH_CUDA_TRY(cudaStreamWaitEvent(q.up, q.freed[b], 0));  // group grp-2 rendered
-    DH_CUDA_TRY(cudaMemcpyAsync(q.stage[b], frames_host + f0 * frame_stride_elems,
-                                (size_t)nf * frame_stride_elems * sizeof(uint16_t), cudaMemcpyHostToDevice,
-                                q.up));
+    const char *src = static_cast<const char *>(frames_host) + (size_t)f0 * host_frame_bytes;
+    DH_CUDA_TRY(cudaMemcpyAsync(packed ? static_cast<void *>(q.pstage[b]) : static_cast<void *>(q.stage[b]), src,
+                                (size_t)nf * host_frame_bytes, cudaMemcpyHostToDevice, q.up));
     DH_CUDA_TRY(cudaEventRecord(q.copied[b], q.up));
     DH_CUDA_TRY(cudaStreamWaitEvent(s, q.copied[b], 0));
-    dh_status st = launch_render(p, q.stage[b], frame_stride_elems, (int)nf, (int)f0, s);
+    dh_status st;
+    if (packed && (st = launch_unpack_mono12p(q.pstage[b], host_stride, p.npix, (int)nf, q.stage[b],
+                                              frame_stride_elems, s)) != DH_OK)
+      return st;
+    st = launch_render(p, q.stage[b], frame_stride_elems, (int)nf, (int)f0, s);
     if (st != DH_OK) return st;
     // the raw-domain covariance reads the staged frames: only when the group's windows lie
     // wholly in them (windows T or more frames apart)
@@ -1050,6 +1072,20 @@ dh_status dh_pca_batch_host(dh_plan_t h, const uint16_t *frames_host, int64_t fr
   DH_CUDA_TRY(cudaEventRecord(q.finished, q.down));
   DH_CUDA_TRY(cudaStreamWaitEvent(s, q.finished, 0));  // the caller's stream ends with the results
   return DH_OK;
+}
+
+dh_status dh_pca_batch_host(dh_plan_t h, const uint16_t *frames_host, int64_t frame_stride_elems,
+                            int n_windows, int window_stride_frames, int k0, int k1, float *images_host,
+                            double *eigvals_host, void *stream) {
+  return host_batch(h, frames_host, frame_stride_elems, false, n_windows, window_stride_frames, k0, k1,
+                    images_host, eigvals_host, stream);
+}
+
+dh_status dh_pca_batch_host_packed12(dh_plan_t h, const uint8_t *frames_host, int64_t frame_stride_bytes,
+                                     int n_windows, int window_stride_frames, int k0, int k1, float *images_host,
+                                     double *eigvals_host, void *stream) {
+  return host_batch(h, frames_host, frame_stride_bytes, true, n_windows, window_stride_frames, k0, k1,
+                    images_host, eigvals_host, stream);
 }
 
 dh_status dh_debug_hologram(dh_plan_t h, int slot, float *out_dev, void *stream) {

@@ -116,6 +116,8 @@ struct Plan {
     cudaEvent_t copied[2] = {}, freed[2] = {};
     uint16_t *stage[2] = {};
     size_t stage_elems = 0;
+    uint8_t *pstage[2] = {};  // packed 12-bit frames as copied (dh_pca_batch_host_packed12)
+    size_t pstage_bytes = 0;
     float *img = nullptr;
     double *eig = nullptr;
     size_t img_elems = 0, eig_elems = 0;
@@ -282,6 +284,8 @@ dh_status preload_reduce_cov_window();
 
 // mean-residual storage: the windows' rounded mean frames into p.d_mean, and after the
 // eigensolver the projection's mu coefficients into p.d_mucoef
+dh_status launch_unpack_mono12p(const uint8_t *src, long long src_stride_bytes, long long npix, int n_frames,
+                                uint16_t *dst, long long dst_stride_elems, cudaStream_t s);  // unpack.cu
 dh_status launch_window_mean(Plan &p, const uint16_t *frames, long long frame_stride, int n_windows,
                              int window_stride, cudaStream_t s);
 dh_status launch_mu_coef(Plan &p, int n_windows, int k0, int k1, int Npad, int woff, cudaStream_t s);
