@@ -651,8 +651,10 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
   constexpr int NI = N / FPC;       // row items = column items per frame
   constexpr long long NPIX = (long long)N * N;
   static_assert(RC::NT == kCtaThreads, "fused render needs full-size items on both axes");
-  // one transform a warp (n = 1024): a row item's warps stage and release their rows each on
-  // their own (rows_done counts rows), with no CTA barrier inside the item
+  // one transform a warp (n = 1024): a row item's warps stage their rows each on their own,
+  // with no CTA barrier inside the item; the last warp to finish releases the item's FPC rows
+  // (rows_done counts rows). One gpu-scope release per item instead of one per warp measured
+  // 2.6% faster (9.47 against 9.72 ms for 2048 frames at 1024^2).
   constexpr bool PW = S::P == 32;
   constexpr unsigned ROWS_PER_FRAME = PW ? (unsigned)N : (unsigned)NI;
   extern __shared__ float2 smem[];
@@ -669,6 +671,7 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
   // current item by the last warp to make its final read of the buffer (n_freed counts them),
   // so it lands while the current item finishes; `preissued` is the ticket it was issued for.
   __shared__ int n_freed, preissued;
+  __shared__ int n_rows_fin;  // warps of the current row item that have written their row
   unsigned *tickets = sync, *rows_done = sync + 1, *cols_done = sync + 1 + ring;
   const int total = (n_frames + lag) * 2 * NI;
   // thread 0 takes tickets two items ahead: the one it takes at an item's start is published
@@ -681,6 +684,7 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
     tc::fence_barrier_init();
     abort_flag = 0;
     n_freed = 0;
+    n_rows_fin = 0;
     preissued = -1;
     tk[0] = (int)atomicAdd(tickets, 1u);
     pending = (int)atomicAdd(tickets, 1u);
@@ -763,7 +767,13 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
         fence_proxy_async_global();  // this thread's ring writes, for later bulk copies
         if constexpr (PW) {
           __syncwarp();
-          if ((threadIdx.x & 31) == 0) red_release_add(rows_done + rs, 1u);  // after the warp's writes
+          // the shared counter's acquire-release orders every warp's ring writes (and proxy
+          // fences) before the last warp's gpu-scope release; the next item's increments follow
+          // the next item-start barrier, after the reset
+          if ((threadIdx.x & 31) == 0 && atom_add_acq_rel_shared(&n_rows_fin, 1) == kCtaThreads / 32 - 1) {
+            n_rows_fin = 0;
+            red_release_add(rows_done + rs, (unsigned)FPC);
+          }
         } else {
           __syncthreads();
           if (threadIdx.x == 0) red_release_add(rows_done + rs, 1u);  // after the CTA's writes
