@@ -625,6 +625,14 @@ __device__ __forceinline__ int atom_add_acq_rel_shared(int *p, int v) {
                : "=r"(old) : "r"(tc::smem_u32(p)), "r"(v) : "memory");
   return old;
 }
+__device__ __forceinline__ int ld_acquire_cta_shared(const int *p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(tc::smem_u32(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_cta_shared(int *p, int v) {
+  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(tc::smem_u32(p)), "r"(v) : "memory");
+}
 __device__ __forceinline__ bool wait_geq(const unsigned *p, unsigned target,
                                          long long budget = tc::kWaitBudget) {
   if (ld_acquire(p) >= target) return true;
@@ -652,9 +660,11 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
   constexpr long long NPIX = (long long)N * N;
   static_assert(RC::NT == kCtaThreads, "fused render needs full-size items on both axes");
   // one transform a warp (n = 1024): a row item's warps stage their rows each on their own,
-  // with no CTA barrier inside the item; the last warp to finish releases the item's FPC rows
-  // (rows_done counts rows). One gpu-scope release per item instead of one per warp measured
-  // 2.6% faster (9.47 against 9.72 ms for 2048 frames at 1024^2).
+  // with no CTA barrier inside the item; the last warp to finish records the item's ring slot
+  // in `pend_rs`, and thread 0 releases its FPC rows (rows_done counts rows) right after the
+  // next item-start barrier, so that the release's wait for the ring writes overlaps the other
+  // warps' work. Measured for 2048 frames at 1024^2: one release per warp 9.72 ms, one per
+  // item by its last warp 9.47 ms, deferred to the next item 9.38 ms.
   constexpr bool PW = S::P == 32;
   constexpr unsigned ROWS_PER_FRAME = PW ? (unsigned)N : (unsigned)NI;
   extern __shared__ float2 smem[];
@@ -672,6 +682,7 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
   // so it lands while the current item finishes; `preissued` is the ticket it was issued for.
   __shared__ int n_freed, preissued;
   __shared__ int n_rows_fin;  // warps of the current row item that have written their row
+  __shared__ int pend_rs;     // 1 + the ring slot of a finished row item not yet released, or 0
   unsigned *tickets = sync, *rows_done = sync + 1, *cols_done = sync + 1 + ring;
   const int total = (n_frames + lag) * 2 * NI;
   // thread 0 takes tickets two items ahead: the one it takes at an item's start is published
@@ -685,6 +696,7 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
     abort_flag = 0;
     n_freed = 0;
     n_rows_fin = 0;
+    pend_rs = 0;
     preissued = -1;
     tk[0] = (int)atomicAdd(tickets, 1u);
     pending = (int)atomicAdd(tickets, 1u);
@@ -717,10 +729,32 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
       pending = (int)atomicAdd(tickets, 1u);
       if (valid(cur) && is_row(cur)) {
         const int f = frame_of(cur);
-        if (!wait_geq(cols_done + f % ring, (unsigned)(f / ring) * NI)) abort_flag = 1;
+        // while it waits, thread 0 also releases the previous row item's rows as soon as its
+        // last warp has recorded them: with a ring of few frames the awaited column items may
+        // need exactly those rows
+        const unsigned *slot = cols_done + f % ring;
+        const unsigned target = (unsigned)(f / ring) * NI;
+        if (ld_acquire(slot) < target) {
+          const long long t0 = clock64();
+          while (ld_acquire(slot) < target) {
+            const int pr = ld_acquire_cta_shared(&pend_rs);
+            if (pr) {
+              pend_rs = 0;
+              red_release_add(rows_done + pr - 1, (unsigned)FPC);
+            }
+            if (clock64() - t0 > tc::kWaitBudget) { abort_flag = 1; break; }
+            __nanosleep(128);
+          }
+        }
       }
     }
     __syncthreads();
+    // the previous item's rows, if it was a row item (its last warp recorded the slot before
+    // the barrier, after counting every warp's ring writes)
+    if (threadIdx.x == 0 && pend_rs) {
+      red_release_add(rows_done + pend_rs - 1, (unsigned)FPC);
+      pend_rs = 0;
+    }
     const int nxt = tk[b];
     b ^= 1;
     const bool pre = preissued == cur;  // read before any write of this item (see freed)
@@ -768,11 +802,12 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
         if constexpr (PW) {
           __syncwarp();
           // the shared counter's acquire-release orders every warp's ring writes (and proxy
-          // fences) before the last warp's gpu-scope release; the next item's increments follow
-          // the next item-start barrier, after the reset
+          // fences) before the last warp's record, whose release store thread 0 acquires (in its
+          // ring-slot wait) or reads after the next item-start barrier; the next item's
+          // increments follow that barrier, after the reset
           if ((threadIdx.x & 31) == 0 && atom_add_acq_rel_shared(&n_rows_fin, 1) == kCtaThreads / 32 - 1) {
             n_rows_fin = 0;
-            red_release_add(rows_done + rs, (unsigned)FPC);
+            st_release_cta_shared(&pend_rs, rs + 1);
           }
         } else {
           __syncthreads();
@@ -794,6 +829,8 @@ k_render_fused(const uint16_t *__restrict__ frames, long long frame_stride, int 
     }
     cur = nxt;
   }
+  __syncthreads();  // the last item's rows, if still unreleased
+  if (threadIdx.x == 0 && pend_rs) red_release_add(rows_done + pend_rs - 1, (unsigned)FPC);
   if (abort_flag && threadIdx.x == 0) {
     atomicOr(status, DH_FLAG_WAIT_TIMEOUT);
     // let a late copy land before the CTA exits: the last one waited on, and one issued early
