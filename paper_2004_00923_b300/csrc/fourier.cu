@@ -43,10 +43,11 @@ __global__ void k_fourier_operand(int T, int k0, int k1, int Npad, int prec, voi
     if (prec == DH_PREC_FP32) {
       static_cast<float *>(Bop)[e] = (float)v;
     } else if (prec == DH_PREC_FP16) {
+      // one FP16 rounding of W (the lo half is zero): its 2^-11 relative rounding moves the
+      // image by a few 1e-5, and the overlapping-window span kernel uses the same operand
       __half *hi = static_cast<__half *>(Bop);
-      const __half h = to16<__half>((float)v);
-      hi[e] = h;
-      hi[(long long)Npad * M + e] = to16<__half>((float)(v - (double)from16(h)));
+      hi[e] = to16<__half>((float)v);
+      hi[(long long)Npad * M + e] = to16<__half>(0.f);
     } else {
       __nv_bfloat16 *hi = static_cast<__nv_bfloat16 *>(Bop);
       const __nv_bfloat16 h = to16<__nv_bfloat16>((float)v);

@@ -5,11 +5,15 @@
 // embedding of W's kept columns at span rows 2 (s g + t) + c (zeros elsewhere). Each CTA
 // loads it once. Per 128-pixel tile the span of the group's frames (T + 6 s) is loaded once
 // (TMA) and one MMA chain over the span rows (M = 128 pixels, N = 7 x 2 nS columns, K = span
-// rows; hi + lo 16-bit parts of W) gives every window's kept DFT bins; the epilogue sums
+// rows; W rounded once to FP16) gives every window's kept DFT bins; the epilogue sums
 // their squares per window (Eq. 9) and writes the images, 8 adjacent image columns per pass.
 // Columns are bin-major (n = j G + g: real column j of window g), so the window of every
 // column is a compile-time constant in the unrolled epilogue. Unlike the eigenvector
 // projection there is no subtraction: the power is Eq. 7's sum over the kept columns.
+// W is one FP16 operand, not a hi + lo pair: its rounding (2^-11 relative) moves the image by
+// a few 1e-5 relative, under a tenth of the 16-bit storage's own 3e-4 (measured by emulating
+// both roundings on the oracle's holograms), and one product instead of two halves the tensor
+// work this kernel was bound by.
 //
 // Roles: warp 0 issues TMA, warp 1 the MMAs, warps 2-5 (one per TMEM lane quarter) drain
 // TMEM, warp 6 waits on the mbarriers and releases the MMA warp tile by tile through named
@@ -30,9 +34,9 @@ constexpr int kFsWaiter = 6;                // warp that watches the mbarriers (
 constexpr int kFsThreads = 64 + 128 + 32;
 constexpr int kFsMaxStages = 4;
 constexpr size_t kFsSmemLimit = 232448;
-constexpr double kFsScale = 1024.0;         // W scaled by 2^10 (the lo part stays normal)
+constexpr double kFsScale = 1024.0;         // W scaled by 2^10 (exact: a power of two)
 
-// The group operand: hi + lo images of kFsNpad x k_pad, K-major, 128-byte swizzled
+// The group operand: one FP16 image of kFsNpad x k_pad, K-major, 128-byte swizzled
 // (64-element sub-blocks; the 16-byte chunk index XOR row % 8). Column n = j G + g: window g,
 // real column j = 2 b + c of kept bin k0 + b (c = 0: Re, 1: Im of sum_t H_t w_{t,k}); row
 // r = 2 (s g + t) + cc (cc = 0: Re H_t, 1: Im H_t), w_{t,k} = exp(-2 pi i t k / T) / sqrt(T).
@@ -56,9 +60,7 @@ __global__ void k_fs_operand(int T, int k0, int nS, int s, int k_pad, __half *__
     const int sub = r >> 6, kk = r & 63;
     const long long i =
         ((long long)sub * kFsNpad * 128 + n * 128 + (((kk >> 3) ^ (n & 7)) << 4) + ((kk & 7) << 1)) >> 1;
-    const __half h = __float2half_rn((float)v);
-    hi[i] = h;
-    hi[(long long)per + i] = __float2half_rn((float)(v - (double)__half2float(h)));
+    hi[i] = __float2half_rn((float)v);
   }
 }
 
@@ -141,7 +143,6 @@ k_fourier_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
     // buffer is free (no shared-memory step inside the loop: see named_sync).
     const uint32_t idesc = idesc_f16(false, true, false, 128, kFsNpad);
     const int k_steps = rows / 16;
-    const int half_bytes = img_bytes / 2;
     int slot = 0, it = 0;
     for (long long u = u_begin; u < u_end; ++u) {
       for (int i = 0; i < 8; ++i, ++it) {
@@ -151,13 +152,11 @@ k_fourier_span(const __grid_constant__ CUtensorMap tmA, const uint8_t *__restric
         if (lane == 0) {
           const uint32_t d = tmem + buf * 256;
           const uint64_t adesc0 = smem_desc(smem_u32(stage0 + slot * stage_bytes), rows * 128, 1024, kSwizzle128);
-          for (int half = 1; half >= 0; --half) {  // small lo products first
-            const uint64_t bdesc0 = smem_desc(smem_u32(bsm) + half * half_bytes, 16, 1024, kSwizzle128);
-            for (int kk = 0; kk < k_steps; ++kk) {
-              const uint64_t adesc = adesc0 + (uint64_t)(kk * 128);
-              const uint64_t bdesc = bdesc0 + (uint64_t)(((kk >> 2) * kFsNpad * 128 + (kk & 3) * 32) >> 4);
-              mma_f16(d, adesc, bdesc, idesc, (half == 1 && kk == 0) ? 0u : 1u);
-            }
+          const uint64_t bdesc0 = smem_desc(smem_u32(bsm), 16, 1024, kSwizzle128);
+          for (int kk = 0; kk < k_steps; ++kk) {
+            const uint64_t adesc = adesc0 + (uint64_t)(kk * 128);
+            const uint64_t bdesc = bdesc0 + (uint64_t)(((kk >> 2) * kFsNpad * 128 + (kk & 3) * 32) >> 4);
+            mma_f16(d, adesc, bdesc, idesc, kk == 0 ? 0u : 1u);
           }
           mma_commit(&empty[slot]);
           mma_commit(&acc_full[buf]);
@@ -267,7 +266,7 @@ bool fourier_span_applies(const Plan &p, int slot_stride, int n_windows, int nS)
   const int rows = (2 * (p.T + (kFsG - 1) * slot_stride) + 15) / 16 * 16;
   if (rows > 256) return false;
   const int k_pad = (rows + 63) / 64 * 64;
-  const size_t img = (size_t)2 * kFsNpad * k_pad * 2;
+  const size_t img = (size_t)kFsNpad * k_pad * 2;
   if (img > p.W_bytes) return false;
   return (size_t)2 * rows * 256 + img + 1024 + 256 <= kFsSmemLimit;
 }
@@ -276,7 +275,7 @@ dh_status launch_fourier_span(Plan &p, int first_slot, int slot_stride, int n_wi
                               float *images, cudaStream_t s) {
   const int rows = (2 * (p.T + (kFsG - 1) * slot_stride) + 15) / 16 * 16;
   const int k_pad = (rows + 63) / 64 * 64;
-  const int img = 2 * kFsNpad * k_pad * 2;
+  const int img = kFsNpad * k_pad * 2;
   const size_t fixed = (size_t)img + 1024 + 256;
   int stages = (int)((kFsSmemLimit - fixed) / ((size_t)rows * 256));
   if (stages > kFsMaxStages) stages = kFsMaxStages;

@@ -327,6 +327,25 @@ def test_persistent_render_equals_chunked(dh, n, F, prec):
             assert torch.equal(a, b)
 
 
+def test_persistent_render_smallest_ring(dh):
+    """The smallest ring (2 frame intermediates, lag 1) at 256^2, where the grid's items in
+    flight span many more frames than the ring holds: a CTA's ring-slot wait can then need the
+    rows of the row item it finished last, whose release it has deferred, so the wait itself
+    must publish them. The holograms equal the chunked schedule's bitwise and no wait times
+    out."""
+    n, F = 256, 40
+    frames = to_gpu(SpeckleStream(SpeckleParams(n, n), seed=4242).next(F).numpy())
+    out = []
+    for sched in ((False, 0, 0), (True, 2, 1)):
+        with dh.Plan(n, n, LAM, Z, PITCH, T=16, precision="fp16", max_frames=F) as plan:
+            plan.set_render_schedule(*sched)
+            plan.render_frames(frames)
+            out.append([plan.debug_hologram(t).cpu() for t in range(0, F, 3)])
+            assert plan.status() == 0
+    for a, b in zip(out[0], out[1]):
+        assert torch.equal(a, b)
+
+
 def test_autotune_picks_are_plan_options(dh):
     """The autotuner's picks are plan options: a plan given the same options explicitly renders
     bitwise the same holograms; picks that change the arithmetic (radix, tensor cores) change
