@@ -266,8 +266,9 @@ dh_status dh_band_gram(dh_plan_t plan, int first_slot, int n_frames, void *strea
  * M[p] = sum_{k=k0..k1} |sum_t H_t[p] w_{t,k}|^2 for window w = slots
  * [first_slot + w * slot_stride, + T). No covariance or eigendecomposition is computed;
  * windows of any number and stride (stride 1 = a new window per frame) share the rendered
- * holograms. Runs on the tensor cores for 16-bit storage (the DFT operand split into hi +
- * lo 16-bit parts), on FP32 CUDA cores for FP32 storage. Overlapping windows (stride < T)
+ * holograms. Runs on the tensor cores for 16-bit storage (the DFT operand rounded once to
+ * FP16 with FP16 holograms, which adds a few 1e-5 to the image's relative error; split into
+ * hi + lo BF16 parts with BF16 holograms), on FP32 CUDA cores for FP32 storage. Overlapping windows (stride < T)
  * are computed together where possible: 7 at a time from one load of their frames on the
  * tensor cores (FP16 storage, 17 bins as the paper's 7..23 at T = 32, n_y >= 128), else one
  * frame read twice per window by a sliding DFT recurrence (stride 1). Asynchronous. */
