@@ -262,7 +262,13 @@ dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int 
   if (p.residual && (!frames || !raw || slot_stride != p.T || b0 >= 0 || p.cov_mode == 2 || p.prec == DH_PREC_FP32))
     return DH_ERR_STATE;
   const int nS = b0 >= 0 ? b1 - b0 + 1 : k1 - k0 + 1;  // projected columns
-  const int nop = p.prec == DH_PREC_FP32 ? 2 * nS : (2 * nS + 15) / 16 * 16;  // operand rows
+  int nop = p.prec == DH_PREC_FP32 ? 2 * nS : (2 * nS + 15) / 16 * 16;  // operand rows
+  // residual storage: the u-column form where two more operand columns fit (residual.cu)
+  p.resid_ucol = 0;
+  if (p.residual && b0 < 0 && (2 * nS + 2 + 15) / 16 * 16 <= 2 * p.T) {
+    nop = (2 * nS + 2 + 15) / 16 * 16;
+    p.resid_ucol = 1;
+  }
   // overlapping windows: grouped projection (one group layout for the whole call)
   const SpanLayout span = b0 < 0 ? span_layout(p, slot_stride, n_windows, k0, k1) : SpanLayout{};
   // Two groups where the eigensolver (one CTA per window) can run beside the other group's
@@ -333,7 +339,7 @@ dh_status pca_impl(Plan &p, const uint16_t *frames, long long frame_stride, int 
     if (st != DH_OK) return st;
     if (b0 >= 0 && (st = launch_svd_fourier_operand(p, nw, k0, k1, b0, b1, nop, w0, p.aux)) != DH_OK)
       return st;
-    if (p.residual && (st = launch_mu_coef(p, nw, k0, k1, nop, w0, p.aux)) != DH_OK) return st;
+    if (p.residual && (st = launch_mu_coef(p, nw, k0, k1, nop, w0, p.resid_ucol != 0, p.aux)) != DH_OK) return st;
     DH_CUDA_TRY(cudaEventRecord(p.ev_jac[g], p.aux));
   }
   for (int g = 0; g < G; ++g) {

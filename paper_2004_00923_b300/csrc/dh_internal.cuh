@@ -46,7 +46,10 @@ struct Plan {
   int residual = 0;
   uint16_t *d_mean = nullptr;  // [max_windows][npix] uint16
   float *d_mu = nullptr;       // [max_windows][re | im][npix] FP32
-  float *d_mucoef = nullptr;   // [max_windows][a (2T) | b (2T)] FP32
+  float *d_mucoef = nullptr;   // [max_windows][a (2T) | b (2T)] FP32, or [sigma, ...]
+  // per call: the residual projection takes mu's cross term from two operand columns (the
+  // u-column form, see residual.cu) instead of per-column coefficients
+  int resid_ucol = 0;
   // render intermediate (row-pass output): a chunk of frames sized to stay in L2
   float2 *d_mid = nullptr;
   int mid_frames = 0;
@@ -283,12 +286,13 @@ dh_status preload_gram_simt_rows();
 dh_status preload_reduce_cov_window();
 
 // mean-residual storage: the windows' rounded mean frames into p.d_mean, and after the
-// eigensolver the projection's mu coefficients into p.d_mucoef
+// eigensolver the projection's mu coefficients into p.d_mucoef (ucol: sigma there, and u's
+// two columns into the last two of the Npad operand columns)
 dh_status launch_unpack_mono12p(const uint8_t *src, long long src_stride_bytes, long long npix, int n_frames,
                                 uint16_t *dst, long long dst_stride_elems, cudaStream_t s);  // unpack.cu
 dh_status launch_window_mean(Plan &p, const uint16_t *frames, long long frame_stride, int n_windows,
                              int window_stride, cudaStream_t s);
-dh_status launch_mu_coef(Plan &p, int n_windows, int k0, int k1, int Npad, int woff, cudaStream_t s);
+dh_status launch_mu_coef(Plan &p, int n_windows, int k0, int k1, int Npad, int woff, bool ucol, cudaStream_t s);
 
 // conversions for inspection
 dh_status launch_hologram_to_f32(Plan &p, int slot, float *out, cudaStream_t s);

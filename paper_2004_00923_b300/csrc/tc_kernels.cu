@@ -557,10 +557,14 @@ struct ProjCfg {
   static constexpr size_t SMEM = STAGES * A_BYTES + B_MAX + 1024 + 256;
 };
 
-// RESID: the holograms hold D = H - mu 1^T (mean-residual storage): each accumulator column j
-// of pixel p gets mu_r(p) a_j + mu_i(p) b_j added before it is squared (a, b per window from
-// k_mu_coef, 4T floats apart; mu FP32 planes [window][re|im][npix]).
-template <int T, bool BF16, bool RESID>
+// RESID (mean-residual storage: the holograms hold D = H - mu 1^T; mu FP32 planes
+// [window][re|im][npix]):
+//   1  each accumulator column j of pixel p gets mu_r(p) a_j + mu_i(p) b_j added before it is
+//      squared (a, b per window from k_mu_coef, 4T floats apart);
+//   2  the u-column form (residual.cu): columns Npad - 2 and Npad - 1 hold D u, and the power
+//      is the plain sum over the other columns + 2 Re(conj(mu) D u) + |mu|^2 sigma (sigma the
+//      window's first coefficient).
+template <int T, bool BF16, int RESID>
 __global__ void __launch_bounds__(ProjCfg<T>::THREADS, 1)
 k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmB,
              int first_slot, int slot_stride, int n_windows, int tiles_pw, int Npad, int B_rows_pw,
@@ -740,12 +744,21 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
       const int p = tile_p((int)(t % tiles_pw)) + 32 * q + lane;
       const int kx = p / ny, ky = p % ny;
       const int buf = it & 1;
+      // u-column form: mu and sigma are loaded before the accumulator wait, which hides their
+      // latency
+      float mr = 0.f, mi = 0.f, sig = 0.f;
+      if constexpr (RESID == 2) {
+        const float *mw = mu + (long long)w * 2 * npix;
+        mr = __ldg(mw + p);
+        mi = __ldg(mw + npix + p);
+        sig = __ldg(coef + (long long)w * 4 * T);  // the same on every lane
+      }
       if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (it >> 1) & 1))) { fail(); break; }
       fence_after_sync();
       float m = 0.f;
       const uint32_t ta = tmem + lane_addr + buf * C::M2;
       int col = 0;
-      if constexpr (!RESID) {
+      if constexpr (RESID == 0) {
         for (; col + 64 <= Npad; col += 64) {
           float v[64];
           tmem_ld64(ta + col, v);
@@ -758,6 +771,35 @@ k_project_tc(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CU
 #pragma unroll
           for (int i = 0; i < 16; ++i) m = fmaf(v[i], v[i], m);
         }
+      } else if constexpr (RESID == 2) {
+        // up to 64 columns a pass, their loads issued together and waited on once; the 16-column
+        // chunk that ends at Npad holds Re and Im of D u in its last two columns (Npad is a
+        // multiple of 16, and every condition below is the same on every lane)
+        float du_r = 0.f, du_i = 0.f;
+        for (int base = 0; base < Npad; base += 64) {
+          float v[64];
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (base + 16 * c < Npad) tmem_ld16_nowait(ta + base + 16 * c, *reinterpret_cast<float(*)[16]>(&v[16 * c]));
+          tmem_wait_ld(v);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            if (base + 16 * c < Npad) {
+#pragma unroll
+              for (int i = 0; i < 14; ++i) m = fmaf(v[16 * c + i], v[16 * c + i], m);
+              if (base + 16 * c + 16 == Npad) {
+                du_r = v[16 * c + 14];
+                du_i = v[16 * c + 15];
+              } else {
+                m = fmaf(v[16 * c + 14], v[16 * c + 14], m);
+                m = fmaf(v[16 * c + 15], v[16 * c + 15], m);
+              }
+            }
+          }
+        }
+        m = fmaf(2.f, fmaf(mr, du_r, mi * du_i), m);
+        m = fmaf(sig, fmaf(mr, mr, mi * mi), m);
+        m = fmaxf(m, 0.f);
       } else {  // coefficients: the same address on every lane (one broadcast load each)
         const float *mw = mu + (long long)w * 2 * npix;
         const float mr = __ldg(mw + p), mi = __ldg(mw + npix + p);
@@ -886,7 +928,7 @@ dh_status gram_t(Plan &p, int first_slot, int slot_stride, int n_windows, cudaSt
   return DH_OK;
 }
 
-template <int T, bool BF16, bool RESID>
+template <int T, bool BF16, int RESID>
 dh_status project_t(Plan &p, int first_slot, int slot_stride, int n_windows, int Npad, float *images,
                     int woff, cudaStream_t s, const void *shared_op) {
   using C = ProjCfg<T>;
@@ -1039,18 +1081,20 @@ dh_status launch_project_tc(Plan &p, int first_slot, int slot_stride, int n_wind
                             float *images, int woff, cudaStream_t s, const void *shared_op) {
   if (!p.tmaps_ok) return DH_ERR_STATE;
   const bool bf16 = p.prec == DH_PREC_BF16;
-  const bool resid = p.residual && !shared_op;
+  const int resid = p.residual && !shared_op ? (p.resid_ucol ? 2 : 1) : 0;
+#define DH_PROJ_R(TT, BB)                                                                                    \
+  return resid == 2 ? project_t<TT, BB, 2>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op) \
+       : resid == 1 ? project_t<TT, BB, 1>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op) \
+                    : project_t<TT, BB, 0>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op);
 #define DH_PROJ(TT)                                                                                          \
-  return bf16 ? (resid ? project_t<TT, true, true>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op) \
-                       : project_t<TT, true, false>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op)) \
-              : (resid ? project_t<TT, false, true>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op) \
-                       : project_t<TT, false, false>(p, first_slot, slot_stride, n_windows, Npad, images, woff, s, shared_op));
+  if (bf16) { DH_PROJ_R(TT, true) } else { DH_PROJ_R(TT, false) }
   switch (p.T) {
     case 16: DH_PROJ(16)
     case 32: DH_PROJ(32)
     case 64: DH_PROJ(64)
   }
 #undef DH_PROJ
+#undef DH_PROJ_R
   return DH_ERR_UNSUPPORTED_SIZE;
 }
 

@@ -60,6 +60,20 @@ def test_residual_window_lengths_and_ranges(dh, T):
             assert e <= TOL_IMG["fp16"], (k0, k1, w, e)
 
 
+@pytest.mark.parametrize("T", [16, 32])
+def test_residual_full_range_coefficient_form(dh, T):
+    """Every component kept: the operand has no two columns to spare for D u, so the mean's
+    term is added to each accumulator column (the per-column form); the image still matches
+    the oracle. The other ranges above take the u-column form."""
+    frames = speckle_window(128, 64, 2 * T, seed=T + 700).numpy()
+    img, _ = _run(dh, frames, T, 2, 0, T - 1, "fp16", True, 128, 64)
+    for w in range(2):
+        M, _, _, _ = oracle.pca_window(frames[w * T:(w + 1) * T], LAM, Z, PITCH, 0, T - 1)
+        e = rel(img[w], M)
+        print(f"residual T={T} [0,{T - 1}] window {w}: image {e:.2e}")
+        assert e <= TOL_IMG["fp16"], (w, e)
+
+
 def test_residual_improves_on_plain_16bit_storage(dh):
     """Same windows, same retained range: the residual image error is below the plain one."""
     T, n = 32, 2
