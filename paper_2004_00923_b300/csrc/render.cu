@@ -387,8 +387,10 @@ __device__ __forceinline__ void row_work(const uint4 (&pf)[RowCfg<LOGN>::CPT], f
 #pragma unroll
     for (int r = 0; r < S::R; ++r) {
       const int x = j + r * S::P;
-      const float a = (__uint_as_float(0x4b000000u | row16[x]) - 8388608.f) -
-                      (__uint_as_float(0x4b000000u | __ldg(mrow + x)) - 8388608.f);
+      // the difference d (|d| < 2^16) taken in integers, then made a float by placing it in
+      // the mantissa of 2^23 + 2^22 (one 3-input add, one float subtraction, exact)
+      const int d = (int)row16[x] - (int)__ldg(mrow + x);
+      const float a = __int_as_float(0x4b400000 + d) - 12582912.f;
       const float2 c = cx[x];
       v[r] = make_float2(a * c.x, a * c.y);
     }
