@@ -96,3 +96,23 @@ def test_sliding_configuration(dh, frames):
         for L in (32, 64):
             plans[L].close()
         base.close()
+
+
+def test_largest_frames(dh):
+    """The largest frame size the library takes, 4096^2 (16 MiB pixels a frame): two 16-frame
+    windows, FP16 storage, with the plan's default schedule; window 0 element by element
+    against the oracle, both through the energy trace."""
+    n, T, nwin = 4096, 16, 2
+    f = SpeckleStream(SpeckleParams(n, n), seed=4096, device=torch.device("cuda")).next(T * nwin)
+    energy = (f.to(torch.int64) ** 2).sum(dim=(1, 2)).cpu().numpy()
+    with dh.Plan(n, n, LAM, Z, PITCH, T=T, precision="fp16", max_frames=T * nwin, max_windows=nwin) as plan:
+        img, lam = plan.pca_batch(f, nwin, T, 2, T - 1)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        lam = lam.cpu().numpy()
+        for w in range(nwin):
+            e = window_energy(energy, w * T, T)
+            assert abs(lam[w].sum() - e) <= 5e-6 * e, w
+        C = plan.debug_covariance(0).cpu().numpy()
+        check_window(img[0].cpu().numpy().astype(np.float64), lam[0], C, f[:T].cpu().numpy(), 2, T - 1,
+                     "fp16", label="4096^2")
