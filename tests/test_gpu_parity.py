@@ -106,6 +106,18 @@ def test_window_lengths(dh, T, prec):
     check_window(img[0], lam[0], C[0], f, 2, T - 1, prec)
 
 
+@pytest.mark.parametrize("nx,ny,T", [(16, 16, 16), (32, 16, 16), (16, 32, 32), (64, 16, 32)])
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_smallest_frames(dh, nx, ny, T, prec):
+    """The smallest frames the library takes (16 pixels a side) through the whole path,
+    against the oracle at the stated tolerances (eigenvalues at the storage bound below
+    256^2 pixels)."""
+    f = speckle_window(nx, ny, T, seed=nx * 7 + ny + T).numpy()
+    img, lam, C, flags = gpu_windows(dh, f, T, prec, 2, T - 1, 1, T)
+    assert flags == 0
+    check_window(img[0], lam[0], C[0], f, 2, T - 1, prec, label=f"{nx}x{ny}")
+
+
 # FP16 storage of H alone rounds every value by up to 2^-12 relative; the projected image of
 # a range then carries ~u sqrt(E / (T M_kept)) relative error, E the energy and M_kept the
 # kept power. For the paper's own range (k0 = 12: the 20 weakest components, E / M_kept ~ 500
