@@ -1,7 +1,12 @@
 // Tracing: optional per-kernel device timing. When enabled on a plan, every kernel the
 // plan launches is bracketed by a pair of CUDA events recorded on the launch stream;
 // dh_profile_read() synchronises and returns launches and total milliseconds per kernel.
+// Every launch is also inside an NVTX range named for its stage (always on: without a tool
+// attached an NVTX call returns at once), so that profilers can attribute kernels to stages
+// (e.g. ncu --nvtx --nvtx-include "render_fused/").
 #include "dh_internal.cuh"
+
+#include <nvtx3/nvToolsExt.h>
 
 #include <vector>
 
@@ -32,6 +37,7 @@ const char *kNames[K_COUNT] = {"render_rows", "render_cols", "gram_simt", "gram_
 const char *kernel_name(int kid) { return kid >= 0 && kid < K_COUNT ? kNames[kid] : "?"; }
 
 ProfScope::ProfScope(Plan &plan, int k, cudaStream_t st) : p(plan), kid(k), s(st), slot(-1) {
+  nvtxRangePushA(kernel_name(k));
   if (!p.prof) return;
   // launches being captured into a CUDA graph are not timed (the events would become graph
   // nodes, not timestamps of a run)
@@ -45,9 +51,11 @@ ProfScope::ProfScope(Plan &plan, int k, cudaStream_t st) : p(plan), kid(k), s(st
 }
 
 ProfScope::~ProfScope() {
-  if (!p.prof || slot < 0) return;
-  ProfState *ps = static_cast<ProfState *>(p.prof);
-  cudaEventRecord(ps->recs[slot].b, s);
+  if (p.prof && slot >= 0) {
+    ProfState *ps = static_cast<ProfState *>(p.prof);
+    cudaEventRecord(ps->recs[slot].b, s);
+  }
+  nvtxRangePop();
 }
 
 void profile_free(Plan &p) {

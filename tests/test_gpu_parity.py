@@ -168,6 +168,25 @@ def test_covariance_is_integer_gram(dh):
     assert np.max(np.abs(C[0].imag)) < 5e-6 * np.max(G)
 
 
+# ------------------------------------------------------------ determinism
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_repeated_calls_are_bitwise_equal(dh, prec):
+    """The same batch twice on one plan: bitwise the same images and eigenvalues, whatever
+    the run-time order of the persistent render's tickets, the split-K covariance units and
+    the two window groups sharing SMs (40 windows); the Fourier span path likewise."""
+    T, n = 32, 40
+    frames = to_gpu(np.concatenate([speckle_window(128, 128, T, seed=900 + w).numpy() for w in range(n)]))
+    with dh.Plan(128, 128, LAM, Z, PITCH, T=T, precision=prec, max_frames=n * T, max_windows=n) as plan:
+        runs = []
+        for _ in range(2):
+            img, lam = plan.pca_batch(frames, n, T, 2, T - 1)
+            runs.append((img.cpu(), lam.cpu()))
+        assert plan.status() == 0
+        assert torch.equal(runs[0][0], runs[1][0]) and torch.equal(runs[0][1], runs[1][1])
+        fourier = [plan.fourier_windows(0, 1, 64, 7, 23).cpu() for _ in range(2)]
+        assert torch.equal(fourier[0], fourier[1])
+
+
 # ------------------------------------------------------------ batching semantics
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
 def test_window_alone_equals_in_batch(dh, prec):
