@@ -500,6 +500,19 @@ dh_status dh_server_add_stream(dh_server_t server, int nx, int ny, double lambda
  * the budget. */
 dh_status dh_server_remove_stream(dh_server_t server, int stream_id);
 
+/* Restart from the autotuner's cache (see dh_plan_tune_load): every stream admitted after
+ * this call gets its plan's options from the JSON file at `path` when the file has an entry
+ * for the stream's frame size, T, storage type and device. With autotune = 1 a stream
+ * without an entry is autotuned once at admission (dh_plan_autotune on its 2T slots:
+ * synchronous, some milliseconds of device time) and its picks are saved to the file, so
+ * that a restarted server rebuilds the same plans without measuring. path = NULL turns it
+ * off. The path is copied. An unreadable file makes later admissions fail with
+ * DH_ERR_INVALID_ARG (nothing allocated). The paper's pipeline has no counterpart. */
+dh_status dh_server_set_tune_cache(dh_server_t server, const char *path, int autotune);
+
+/* One option (DH_OPT_*) of an admitted stream's plan, as dh_plan_get_option. */
+dh_status dh_server_stream_option(dh_server_t server, int stream_id, int option, int *value);
+
 /* Device bytes charged to admitted streams. */
 size_t dh_server_used_bytes(dh_server_t server);
 

@@ -559,6 +559,20 @@ class Server:
         _lib.check("dh_server_remove_stream", self._lib.dh_server_remove_stream(self._h, sid))
         self.streams.pop(sid, None)
 
+    def set_tune_cache(self, path: str | None, autotune: bool = False) -> None:
+        """dh_server_set_tune_cache: streams admitted from now on take their plan options from
+        the autotune cache at `path` (and, with autotune, are tuned once and saved when it has
+        no entry for them); None turns it off."""
+        _lib.check("dh_server_set_tune_cache", self._lib.dh_server_set_tune_cache(
+            self._h, os.fsencode(path) if path is not None else None, 1 if autotune else 0))
+
+    def stream_option(self, sid: int, option: int) -> int:
+        """dh_server_stream_option: one DH_OPT_* option of a stream's plan."""
+        v = ctypes.c_int(0)
+        _lib.check("dh_server_stream_option", self._lib.dh_server_stream_option(
+            self._h, int(sid), int(option), ctypes.byref(v)))
+        return v.value
+
     @property
     def used_bytes(self) -> int:
         return int(self._lib.dh_server_used_bytes(self._h))

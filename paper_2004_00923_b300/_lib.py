@@ -82,6 +82,8 @@ SIGNATURES = [
     ("dh_server_add_stream", _i, [_vp, _i, _i, _d, _d, _d, _i, _i, _i, _i, _i,
                                   ctypes.POINTER(_i)]),
     ("dh_server_remove_stream", _i, [_vp, _i]),
+    ("dh_server_set_tune_cache", _i, [_vp, ctypes.c_char_p, _i]),
+    ("dh_server_stream_option", _i, [_vp, _i, _i, ctypes.POINTER(_i)]),
     ("dh_server_used_bytes", ctypes.c_size_t, [_vp]),
     ("dh_server_push", _i, [_vp, _i, _vp, _i64, _i]),
     ("dh_server_poll", _i, [_vp, ctypes.POINTER(WindowResult), _i]),

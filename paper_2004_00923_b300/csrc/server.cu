@@ -11,6 +11,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <string>
 #include <new>
 #include <vector>
 
@@ -65,6 +66,8 @@ struct CamStream {
 struct dh_server {
   size_t budget = 0, used = 0;
   int device = 0;
+  std::string tune_path;  // autotune cache applied to admitted streams' plans (empty: none)
+  bool tune_autotune = false;
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
   std::mutex mu;        // streams, budget
   std::mutex done_mu;   // completion queue (also taken by the driver's callback thread)
@@ -151,8 +154,17 @@ dh_status dh_server_add_stream(dh_server_t s, int nx, int ny, double lambda_m, d
   if (st == DH_OK && prec != DH_PREC_FP32) st = dh_plan_set_precision(c->plan, prec);
   if (st == DH_OK) st = dh_plan_reserve(c->plan, 2 * T, 1);
   cudaError_t e = cudaSuccess;
+  if (st == DH_OK) e = cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) st = fail_cuda(e);
+  if (st == DH_OK && !s->tune_path.empty()) {  // the autotune cache: apply, or tune and save
+    int found = 0;
+    st = dh_plan_tune_load(c->plan, s->tune_path.c_str(), &found);
+    if (st == DH_OK && !found && s->tune_autotune) {
+      st = dh_plan_autotune(c->plan, 2 * T, c->cs);
+      if (st == DH_OK) st = dh_plan_tune_save(c->plan, s->tune_path.c_str());
+    }
+  }
   if (st == DH_OK) {
-    e = cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_frames, (size_t)2 * T * c->npix * sizeof(uint16_t));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_images, (size_t)ring_windows * c->npix * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_eig, (size_t)ring_windows * T * sizeof(double));
@@ -172,6 +184,22 @@ dh_status dh_server_add_stream(dh_server_t s, int nx, int ny, double lambda_m, d
   s->streams[c->id] = c;
   *stream_id = c->id;
   return DH_OK;
+}
+
+dh_status dh_server_set_tune_cache(dh_server_t s, const char *path, int autotune) {
+  if (!s || (autotune != 0 && autotune != 1)) return DH_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->tune_path = path ? path : "";
+  s->tune_autotune = path && autotune == 1;
+  return DH_OK;
+}
+
+dh_status dh_server_stream_option(dh_server_t s, int stream_id, int option, int *value) {
+  if (!s || !value) return DH_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->streams.find(stream_id);
+  if (it == s->streams.end()) return DH_ERR_INVALID_ARG;
+  return dh_plan_get_option(it->second->plan, option, value);
 }
 
 dh_status dh_server_remove_stream(dh_server_t s, int stream_id) {

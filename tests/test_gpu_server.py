@@ -129,3 +129,55 @@ def test_frame_gap_and_backpressure(dh):
     srv.drain()
     assert [r["window"] for r in srv.poll()] == [2]
     srv.close()
+
+
+OPTS = {"schedule": 0, "ring": 1, "lag": 2, "fft": 7, "radix": 8, "gram_units": 9}
+
+
+def test_restart_from_tune_cache(dh, tmp_path):
+    """A server autotunes a stream once and saves the picks; a restarted server (a new one
+    on the same cache file) admits the same stream with the same plan options without
+    measuring, and its windows equal a stand-alone plan given those options, bitwise."""
+    cache = str(tmp_path / "tune.json")
+    nx, ny, T = 256, 256, 32
+    srv = dh.Server(4 * GiB)
+    srv.set_tune_cache(cache, autotune=True)
+    sid = srv.add_stream(nx, ny, LAM, Z, PITCH, T, "fp16", 2, T - 1, ring_windows=2)
+    first = {k: srv.stream_option(sid, o) for k, o in OPTS.items()}
+    srv.close()
+    with open(cache) as fh:
+        text = fh.read()
+    assert '"entries"' in text and str(nx) in text
+    # restart: load only, never measure (the file is left as it is)
+    srv = dh.Server(4 * GiB)
+    srv.set_tune_cache(cache, autotune=False)
+    sid = srv.add_stream(nx, ny, LAM, Z, PITCH, T, "fp16", 2, T - 1, ring_windows=2)
+    assert {k: srv.stream_option(sid, o) for k, o in OPTS.items()} == first
+    with open(cache) as fh:
+        assert fh.read() == text
+    f = SpeckleStream(SpeckleParams(nx, ny), seed=77).next(T).pin_memory()
+    srv.push(sid, f, 0)
+    srv.drain()
+    res = srv.poll(4)
+    assert len(res) == 1
+    with dh.Plan(nx, ny, LAM, Z, PITCH, T=T, precision="fp16", max_frames=2 * T) as plan:
+        for k, o in OPTS.items():
+            assert plan._lib.dh_plan_set_option(plan._h, o, first[k]) == 0, k
+        img, lam = plan.pca_batch(f.cuda(), 1, T, 2, T - 1)
+        torch.cuda.synchronize()
+    assert torch.equal(res[0]["image"], img[0].cpu())
+    assert torch.equal(res[0]["eigvals"], lam[0].cpu())
+    srv.close()
+
+
+def test_tune_cache_unreadable_file_refuses_admission(dh, tmp_path):
+    bad = tmp_path / "bad.json"
+    bad.write_text("not json")
+    srv = dh.Server(4 * GiB)
+    srv.set_tune_cache(str(bad))
+    with pytest.raises(dh.DHError) as e:
+        srv.add_stream(128, 128, LAM, Z, PITCH, 16, "fp16", 2, 15, ring_windows=1)
+    assert e.value.code == 1
+    assert srv.used_bytes == 0
+    assert bad.read_text() == "not json"
+    srv.close()
