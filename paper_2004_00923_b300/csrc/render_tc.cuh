@@ -80,7 +80,7 @@ struct Ctx {
   const float2 *twn;
   const float4 *cxm;
   uint64_t *mma_bar;        // this warpgroup's MMA barrier
-  volatile int *stage_ok;   // its leader's verdict on the last MMA wait
+  volatile int *stage_ok;   // its leader's outcome of the last MMA wait
   uint32_t mma_phase;
   uint32_t tmem;            // this warpgroup's 64 accumulator columns (lane 0)
   int wg;                   // warpgroup index in the CTA
@@ -154,7 +154,7 @@ __device__ __forceinline__ void write_kmajor_row(const Ctx &c, int r, const floa
 
 // One stage of this warpgroup: its operand writes (and tensor-memory reads) are ordered
 // before the MMAs, its leader issues 4 K-steps x 3 products, commits and waits for their
-// completion (bounded), and a warpgroup barrier hands the result and the verdict on.
+// completion (bounded), and a warpgroup barrier hands the result and the outcome on.
 __device__ __forceinline__ void run_stage(Ctx &c, bool mn_major) {
   tc::fence_before_sync();
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -320,7 +320,7 @@ __device__ __forceinline__ bool col_item(Ctx &c, const float2 *__restrict__ src,
   float2 v[32];
 #pragma unroll
   for (int l1 = 0; l1 < 32; ++l1) v[l1] = tile[(32 * l1 + l2) * ITEM + xc];
-  // the copy's verdict, and every read of the tile before the operand overwrites it
+  // the copy's outcome, and every read of the tile before the operand overwrites it
   if (!wg_all(c, got)) {
     c.ok = false;
     return false;
