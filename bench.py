@@ -328,6 +328,8 @@ def run_ours(args, ws, rank, local):
 
     # ---------------------------------------------------------------- measured FMA rates
     rates = None if args.no_peaks else measure_rates(local)
+    if rates is not None:
+        rates["library_fft2"] = library_fft2(NX)
 
     # ---------------------------------------------------------------- roofline
     hbm, bf16_peak, peak_kind = measured_peaks()
@@ -339,6 +341,10 @@ def run_ours(args, ws, rank, local):
     roofline = roofline_of(per_kernel, alg, hbm, peak_kind, ms / 1e3,
                            {k: fl for k in RENDER_KERNELS}, alg_steps=steps,
                            fp32_peak=rates["fp32_peak_tflops"] if rates else None)
+    if rates is not None:
+        rk = per_kernel.get("render_fused")
+        if rk and rk["launches"]:
+            rates["library_fft2"]["render_us_per_frame"] = rk["ms_total"] * 1e3 / (rk["launches"] * nframes)
 
     # ---------------------------------------------------------------- end to end (host buffers)
     # dh_pca_batch_host: pinned host frames in, host images and eigenvalues out; the library
@@ -582,6 +588,30 @@ def measure_rates(local) -> dict:
                   "best of 3 timed launches (CUDA events) after a warm-up; dh_measure_mma_issue: "
                   "one CTA per SM, 4096 stages of four M = N = 128, K = 16 FP16 MMAs")
     return out
+
+
+def library_fft2(n: int, batch: int = 256) -> dict:
+    """Context for the render: cuFFT's batched 2D FFT of complex64 n x n frames (through
+    torch.fft.fft2, the library's own code path), the transform of Eq. 1 alone (no uint16
+    conversion, chirps or 16-bit output). Best of 3 timings of 5 calls each (CUDA events)."""
+    x = torch.randn(batch, n, n, dtype=torch.complex64, device="cuda")
+    for _ in range(3):
+        y = torch.fft.fft2(x)
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            y = torch.fft.fft2(x)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        best = ms if best is None else min(best, ms)
+    del x, y
+    torch.cuda.empty_cache()
+    return {"us_per_frame": best * 1e3 / batch, "frames": batch,
+            "what": f"cuFFT batched 2D FFT of complex64 {n}x{n} frames (torch.fft.fft2), the "
+                    "transform of Eq. 1 alone: context for the render, not part of the step"}
 
 
 def roofline_of(per_kernel: dict, alg: dict, hbm: float, peak_kind: str, step_s: float,
