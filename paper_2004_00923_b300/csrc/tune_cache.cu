@@ -8,6 +8,7 @@
 // keeps every other entry of the file.
 #include "dh_internal.cuh"
 
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -165,11 +166,22 @@ bool read_file(const char *path, JVal &root, bool &exists) {
   return r.p == r.end;
 }
 
+// A JSON string: quotes and backslashes escaped, control characters (which the reader decodes
+// from escapes in other entries' keys) written back as escapes, so the file stays readable.
 void put_string(std::string &o, const std::string &s) {
   o += '"';
   for (char ch : s) {
-    if (ch == '"' || ch == '\\') o += '\\';
-    o += ch;
+    const unsigned char u = (unsigned char)ch;
+    if (ch == '"' || ch == '\\') {
+      o += '\\';
+      o += ch;
+    } else if (u < 0x20) {
+      char esc[8];
+      snprintf(esc, sizeof esc, "\\u%04x", (unsigned)u);
+      o += esc;
+    } else {
+      o += ch;
+    }
   }
   o += '"';
 }
@@ -254,12 +266,14 @@ extern "C" dh_status dh_plan_tune_save(dh_plan_t h, const char *path) {
       bool f2 = true;
       for (const auto &fv : kv.second.obj) {
         if (fv.second.kind != JVal::NUM) continue;
+        char num[64];
+        const double x = fv.second.num;
+        if (!std::isfinite(x)) continue;  // not representable in JSON: the field is dropped
+        if (std::fabs(x) < 9.0e15 && x == (double)(long long)x) snprintf(num, sizeof num, ": %lld", (long long)x);
+        else snprintf(num, sizeof num, ": %.17g", x);
         out += f2 ? "" : ", ";
         f2 = false;
         put_string(out, fv.first);
-        char num[64];
-        if (fv.second.num == (double)(long long)fv.second.num) snprintf(num, sizeof num, ": %lld", (long long)fv.second.num);
-        else snprintf(num, sizeof num, ": %.17g", fv.second.num);
         out += num;
       }
       out += "}";

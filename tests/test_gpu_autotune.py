@@ -160,3 +160,21 @@ def test_autotune_cache_refuses_bad_files(dh, tmp_path):
             plan.autotune(16, cache=str(good))
         assert e.value.code == 1
         assert plan.render_schedule() == before
+
+
+def test_autotune_cache_keeps_other_entries_readable(dh, tmp_path):
+    """Saving rewrites every other entry of the file: a key holding an escaped control
+    character is escaped again, a huge number stays a number and a non-finite one (which JSON
+    cannot hold) is dropped, so the file stays strict JSON and keeps the other entries."""
+    path = tmp_path / "shared.json"
+    path.write_text('{"version": 1, "entries": {"other\\nkey": {"render_ring": 8, '
+                    '"big": 1e300, "bad": NaN}}}')
+    with dh.Plan(256, 256, LAM, Z, PITCH, T=16, precision="fp16") as plan:
+        assert plan._lib.dh_plan_tune_save(plan._h, os.fsencode(str(path))) == 0
+
+    def no_constants(name):
+        raise ValueError(f"non-JSON constant {name}")
+
+    doc = json.loads(path.read_text(), parse_constant=no_constants)
+    assert doc["entries"]["other\nkey"] == {"render_ring": 8, "big": 1e300}
+    assert len(doc["entries"]) == 2
