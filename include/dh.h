@@ -193,8 +193,8 @@ dh_status dh_plan_get_option(dh_plan_t plan, int option, int *value);
  *   2. for the CUDA-core FFT, the schedule (DH_OPT_RENDER_SCHEDULE, _RING, _LAG): chunks; the
  *      persistent ring at the automatic lag, half and twice it; the automatic ring with one
  *      frame more lag;
- *   3. 16-bit storage: the covariance's split-K units (DH_OPT_GRAM_UNITS: the default, half and
- *      twice it), on up to 32 windows of the store.
+ *   3. 16-bit storage: the covariance's split-K units (DH_OPT_GRAM_UNITS: the default, half,
+ *      twice and a quarter of it), on up to 32 windows of the store.
  * Schedules give bitwise the same holograms; radix, DFT arithmetic and split-K units change
  * only the rounding. Renders n_frames (capped at the plan's slots) frames; discards rendered
  * holograms; allocates and frees a temporary frame buffer; synchronises `stream` and the

@@ -751,7 +751,7 @@ dh_status dh_plan_autotune(dh_plan_t h, int n_frames, void *stream) {
     const int u0 = gram_tc_default_units(p.npix);
     int upick = 0;
     best = 1e30f;
-    for (int u : {u0, u0 / 2, 2 * u0}) {
+    for (int u : {u0, u0 / 2, 2 * u0, u0 / 4}) {
       if (u < 1 || p.npix % (256ll * u) != 0) continue;
       if ((st = set_gram_units(p, u == u0 ? 0 : u)) != DH_OK) break;
       int parts = 0;

@@ -76,9 +76,9 @@ def test_radix_option_rejects_what_is_not_instantiated(dh):
         assert plan.render_schedule()["radix"] == 16
 
 
-@pytest.mark.parametrize("units", [0, 2, 8])
+@pytest.mark.parametrize("units", [0, 1, 2, 8])
 def test_covariance_split_k_units_match_oracle(dh, units):
-    """The default split-K units of a 256^2 frame (4) and half and twice it: every window
+    """The default split-K units of a 256^2 frame (4) and a quarter, half and twice it: every window
     at the stated tolerances, and the covariance the same up to the order of its sums."""
     T, n = 32, 3
     frames = np.concatenate([speckle_window(256, 256, T, seed=50 + w).numpy() for w in range(n)])
