@@ -319,7 +319,8 @@ dh_status dh_normalize_images(const float *images_dev, int n_images, int64_t npi
 
 /* dh_pca_batch from HOST memory, overlapping the transfers with the computation: frames
  * (uint16, frame i at frames_host + i * frame_stride_elems) are copied to the device in
- * groups of windows (up to 256 frames a group) on a copy stream, into two alternating
+ * groups of windows (up to 256 frames a group; the last groups halve down to one window, so
+ * little work follows the last copy) on a copy stream, into two alternating
  * staging buffers, while the caller's stream renders and demodulates the previous group; the
  * images (n_windows x n_x n_y FP32) and, if eigvals_host is not NULL, the eigenvalues
  * (n_windows x T FP64) of each group are copied back on a second copy stream as soon as the

@@ -1036,8 +1036,12 @@ static dh_status host_batch(dh_plan_t h, const void *frames_host, int64_t host_s
   DH_CUDA_TRY(cudaStreamWaitEvent(q.up, q.start, 0));
   DH_CUDA_TRY(cudaStreamWaitEvent(q.down, q.start, 0));
   long long rendered = 0;  // frames 0 .. rendered-1 are in their slots (ws <= T)
-  for (int w0 = 0, grp = 0; w0 < n_windows; w0 += G, ++grp) {
-    const int nw = n_windows - w0 < G ? n_windows - w0 : G;
+  for (int w0 = 0, grp = 0; w0 < n_windows; ++grp) {
+    // full groups, then the last ones halve (G/2, G/4, ..., 1, 1): less work follows the last
+    // copy, whose end the call cannot finish before (each window's result does not depend on
+    // the grouping)
+    const int left = n_windows - w0;
+    const int nw = left > G ? G : left > 1 ? (left + 1) / 2 : left;
     long long f0, nf;
     if (ws > T) {
       f0 = (long long)w0 * ws;
@@ -1074,6 +1078,7 @@ static dh_status host_batch(dh_plan_t h, const void *frames_host, int64_t host_s
     if (eigvals_host)
       DH_CUDA_TRY(cudaMemcpyAsync(eigvals_host + (size_t)w0 * T, q.eig + (size_t)w0 * T,
                                   (size_t)nw * T * sizeof(double), cudaMemcpyDeviceToHost, q.down));
+    w0 += nw;
   }
   DH_CUDA_TRY(cudaEventRecord(q.finished, q.down));
   DH_CUDA_TRY(cudaStreamWaitEvent(s, q.finished, 0));  // the caller's stream ends with the results
