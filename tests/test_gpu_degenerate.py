@@ -116,3 +116,21 @@ def test_more_windows_than_sms(dh):
         M, lam_ref, _, _ = oracle.pca_window(frames[w * T:(w + 1) * T], LAM, Z, PITCH, 2, T - 1)
         assert rel(img[w], M) <= TOL_IMG["fp16"], w
         assert np.max(np.abs(lam[w] - lam_ref)) <= 1e-5 * lam_ref[0], w
+
+
+@pytest.mark.parametrize("persistent", [True, False])
+def test_store_overflow_flag(dh, persistent):
+    """16-bit storage beyond its range: a uniform frame at the largest 16-bit value has
+    hologram components near 2.3e5 at 256^2 (the oracle's FP64 render), beyond FP16's 65504,
+    so the render (persistent or chunked) raises DH_FLAG_STORE_OVERFLOW (0x1); the same frames
+    stored in BF16 or FP32 do not, and speckle frames (components near 1.1e4) do not. Only the
+    render runs: no window stage reads the non-finite planes."""
+    T = 16
+    hot = to_gpu(np.full((T, 256, 256), 65535, dtype=np.uint16))
+    cool = to_gpu(speckle_window(256, 256, T, seed=0).numpy())
+    for prec, frames, want in (("fp16", hot, 1), ("bf16", hot, 0), ("fp32", hot, 0), ("fp16", cool, 0)):
+        with dh.Plan(256, 256, LAM, Z, PITCH, T=T, precision=prec) as plan:
+            plan.set_render_schedule(persistent)
+            plan.render_frames(frames)
+            assert plan.status() == want, (prec, want)
+            assert plan.status() == 0  # the bits are cleared by the read
