@@ -826,13 +826,19 @@ k_jacobi(const double *__restrict__ C, double *__restrict__ lam, double *__restr
 
 #endif
 
-  // decreasing order, ties by original index
+  // decreasing order, ties by original index. A NaN (from a non-finite C, which the covariance
+  // reduction flags) orders after every number, so that the ranks are a permutation whatever
+  // the values and every index taken from perm below stays in [0, T).
   if (tid < T) dsort[tid] = xr[tid * LD + tid];
   __syncthreads();
   if (tid < T) {
-    const double d = dsort[tid];
+    auto key = [](double x) { return isnan(x) ? -INFINITY : x; };
+    const double d = key(dsort[tid]);
     int rank = 0;
-    for (int j = 0; j < T; ++j) rank += (dsort[j] > d) || (dsort[j] == d && j < tid);
+    for (int j = 0; j < T; ++j) {
+      const double x = key(dsort[j]);
+      rank += (x > d) || (x == d && j < tid);
+    }
     perm[rank] = tid;
   }
   __syncthreads();

@@ -134,3 +134,25 @@ def test_store_overflow_flag(dh, persistent):
             plan.render_frames(frames)
             assert plan.status() == want, (prec, want)
             assert plan.status() == 0  # the bits are cleared by the read
+
+
+def test_nonfinite_covariance_is_flagged(dh):
+    """Holograms beyond FP16's range (as in test_store_overflow_flag) make C non-finite. The
+    window's call raises DH_FLAG_NONFINITE_C (0x2) and DH_FLAG_EIG_NOT_CONVERGED (0x4) beside
+    the overflow bit: every stage runs to its bounded end (the eigensolver's sweeps stop at
+    their limit, and its ordering puts NaN eigenvalues last, so the ranks stay a
+    permutation). The plan then gives a correct window again."""
+    T = 16
+    hot = np.full((T, 256, 256), 65535, dtype=np.uint16)
+    cool = speckle_window(256, 256, T, seed=3).numpy()
+    with dh.Plan(256, 256, LAM, Z, PITCH, T=T, precision="fp16") as plan:
+        plan.render_stack(to_gpu(hot))
+        plan.pca_window(2, T - 1)
+        flags = plan.status()
+        assert flags & 0x7 == 0x7, flags
+        plan.render_stack(to_gpu(cool))
+        img, lam = plan.pca_window(2, T - 1)
+        assert plan.status() == 0
+    M, lam_ref, _, _ = oracle.pca_window(cool, LAM, Z, PITCH, 2, T - 1)
+    assert rel(img.double().cpu().numpy(), M) <= TOL_IMG["fp16"]
+    assert np.max(np.abs(lam.numpy() - lam_ref)) <= 1e-5 * lam_ref[0]
