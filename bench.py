@@ -434,16 +434,18 @@ def run_ours(args, ws, rank, local):
         import oracle
         f0 = frames[:T].cpu().numpy()
         t0 = time.perf_counter()
-        M, lam_ref, _, _ = oracle.pca_window(f0, LAM, Z, PITCH, K0, K1)
+        M, lam_ref, C_ref, _ = oracle.pca_window(f0, LAM, Z, PITCH, K0, K1)
         sec = time.perf_counter() - t0
         cpu_baseline = {"value": 1.0 / sec, "unit": UNIT, "cores": oracle.num_threads(),
                         "kind": "oracle",
                         "sample": "window 0 of the step (1024x1024x32), FP64 C oracle, OpenMP"}
         img0 = images[0].double().cpu().numpy()
         lam0 = eig[0].cpu().numpy()
+        C0 = plan.debug_covariance(0).cpu().numpy()  # the last step's window 0
         parity = {"window": 0,
                   "image_rel_l2": float(np.linalg.norm(img0 - M) / np.linalg.norm(M)),
                   "eig_normwise": float(np.max(np.abs(lam0 - lam_ref)) / lam_ref[0]),
+                  "C_rel_fro": float(np.linalg.norm(C0 - C_ref) / np.linalg.norm(C_ref)),
                   "tolerance_image": 1e-3 if args.precision != "fp32" else 1e-4,
                   "tolerance_eig": 1e-5}
 
