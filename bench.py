@@ -480,7 +480,8 @@ def run_ours(args, ws, rank, local):
                     "metric": w["metric"], "value": w["value"], "unit": w["unit"],
                     "ms_per_step": w["ms_per_step"], "steps": w["steps"],
                     "parity_image_rel_l2_max": max(e for e in errs if e is not None) if errs else None,
-                    "device_flags": w.get("device_flags"), "workload": w["config"].get("workload")}
+                    "device_flags": w.get("device_flags"), "workload": w["config"].get("workload"),
+                    "render_schedule": w["config"].get("render_schedule")}
 
     if rank == 0:
         line = {
@@ -693,6 +694,16 @@ def span_bytes(F, npix):
     return total
 
 
+def tune_plan(plan, args, n_frames: int = 256) -> dict:
+    """The render and covariance options of a workload's rendering plan, set up outside the
+    timed region: the library's autotuner (dh_plan_autotune: DFT arithmetic, FFT radix, render
+    schedule, split-K units) unless the command line fixes the render schedule."""
+    if args.render_schedule == "auto":
+        return plan.autotune(n_frames)
+    plan.set_render_schedule(args.render_schedule == "persistent", args.render_ring, args.render_lag)
+    return plan.render_schedule()
+
+
 def run_sliding(args, ws, rank, local, emit=None):
     """16-, 32- and 64-frame windows at stride 8 over 2048 frames of 1024^2: each frame is
     rendered once into a FP16 store read by all three window lengths (views), and the whole
@@ -706,6 +717,7 @@ def run_sliding(args, ws, rank, local, emit=None):
     n = {L: (F - L) // SLIDE_STRIDE + 1 for L in SLIDE_LENGTHS}
     frames = SpeckleStream(SpeckleParams(NX, NY), seed=2000 + rank, device=dev).next(F)
     base = dh.Plan(NX, NY, LAM, Z, PITCH, T=16, precision="fp16", max_frames=F, max_windows=n[16])
+    tuned = tune_plan(base, args)  # before the views: the base plan renders for all of them
     plans = {16: base, 32: base.view(32, n[32]), 64: base.view(64, n[64])}
     images = {L: torch.empty((n[L], NY, NX), dtype=torch.float32, device=dev) for L in SLIDE_LENGTHS}
     eig = {L: torch.empty((n[L], L), dtype=torch.float64, device=dev) for L in SLIDE_LENGTHS}
@@ -809,6 +821,7 @@ def run_sliding(args, ws, rank, local, emit=None):
                                      "components" if args.projection == "grouped"
                        else "per window (Eq. 7 over the kept components)",
                        "windows_per_step": n, "k0": 2, "k1": "T-1",
+                       "render_schedule": tuned,
                        "l2": "no flush: 4 GiB of frames and 8 GiB of holograms per step",
                        "parallelism": f"replicas x{ws}"},
             "frames_per_s": F * ws / (ms_max / 1e3),
@@ -841,6 +854,7 @@ def run_fourier(args, ws, rank, local, emit=None):
     k0, k1 = FOURIER_BINS
     frames = SpeckleStream(SpeckleParams(NX, NY), seed=5000 + rank, device=dev).next(F)
     plan = dh.Plan(NX, NY, LAM, Z, PITCH, T=T, precision=args.precision, max_frames=F)
+    tuned = tune_plan(plan, args)
     images = torch.empty((nwin, NY, NX), dtype=torch.float32, device=dev)
 
     def step():
@@ -899,6 +913,7 @@ def run_fourier(args, ws, rank, local, emit=None):
             "config": {"workload": f"fourier: {F} frames of 1024x1024 uint16, a 32-frame window "
                                    f"per frame ({nwin} windows), DFT bins 7..23, one CUDA graph "
                                    "per step", "precision": args.precision,
+                       "render_schedule": tuned,
                        "l2": "no flush: 4 GiB of frames and 8 GiB of holograms per step",
                        "parallelism": f"replicas x{ws}"},
             "output_gvoxel_per_s": gvox,
@@ -929,11 +944,12 @@ def run_uneven(args, ws, rank, local, emit=None):
     dev = torch.device("cuda", local)
     groups = uneven_batch(UNEVEN_SIZES, seed=3000 + rank, device=dev)
     stride = 96
-    sizes, items, plans_all = [], [], []
+    sizes, items, plans_all, tuned = [], [], [], {}
     for g in groups:
         n = {L: len(g.starts(L)) for L in (32, 64)}
         base = dh.Plan(g.n, g.n, LAM, g.z, PITCH, T=32, precision=args.precision,
                        max_frames=g.frames.shape[0], max_windows=n[32])
+        tuned[f"{g.n}x{g.n}"] = tune_plan(base, args, min(256, g.frames.shape[0]))
         plans = {32: base, 64: base.view(64, n[64])}
         out = {L: (torch.empty((n[L], g.n, g.n), dtype=torch.float32, device=dev),
                    torch.empty((n[L], L), dtype=torch.float64, device=dev)) for L in plans}
@@ -1033,6 +1049,7 @@ def run_uneven(args, ws, rank, local, emit=None):
                        "precision": args.precision,
                        "sizes": [{"n": g.n, "z": g.z, "windows": n, "frames": g.frames.shape[0]}
                                  for g, n, _, _ in sizes],
+                       "render_schedule": tuned,
                        "l2": "no flush: 4 GiB of frames per step",
                        "parallelism": f"replicas x{ws}"},
             "frames_per_s": nframes * ws / (ms_max / 1e3),
