@@ -208,10 +208,12 @@ __device__ int jacobi_sweeps(Real *ar, Real *ai, Real *vr, Real *vi, double tol,
           // items (k, i) share its row i and belong to distinct pairs, so they touch disjoint
           // elements; all their operands are loaded before any result is stored, which lets the
           // loads overlap (the arithmetic is unchanged). Measured: the sliding step's
-          // eigensolver 5.65 -> 5.37 ms, the uneven step's 8.76 -> 8.26 ms. Below T = 64 the loop is kept as it is (its CTA runs
-          // beside the other window group's covariance and projection in the headline step,
-          // where a batched form measured slower for the whole step).
+          // eigensolver 5.65 -> 5.37 ms, the uneven step's 8.76 -> 8.26 ms. Below T = 64 the
+          // loop is kept as it is (its CTA runs beside the other window group's covariance and
+          // projection in the headline step, where a batched form measured slower for the whole
+          // step). The kernel runs exactly kJacThreads<T>() threads.
           constexpr int NT = kJacThreads<T>(), IPT = NP * T / NT;
+          static_assert(NP * T % NT == 0, "whole items per thread");
           Real xa[IPT][4], xv[IPT][4];
 #pragma unroll
           for (int m = 0; m < IPT; ++m) {
@@ -257,8 +259,8 @@ __device__ int jacobi_sweeps(Real *ar, Real *ai, Real *vr, Real *vi, double tol,
         __syncthreads();
         // rows of A: A_pj' = c A_pj - w A_qj ;  A_qj' = conj(w) A_pj + c A_qj. The pair's own
         // entries come out exact: A_pq = A_qp = 0 and real diagonal entries (also for a
-        // skipped rotation, whose A_pq is below the skip level). At T = 64 a thread's items (k, j)
-        // share its column j in distinct pairs: loads first, as in the column pass.
+        // skipped rotation, whose A_pq is below the skip level). At T = 64 a thread's items
+        // (k, j) share its column j in distinct pairs: loads first, as in the column pass.
         if constexpr (T == 64) {
           constexpr int NT = kJacThreads<T>(), IPT = NP * T / NT;
           Real x4[IPT][4];
